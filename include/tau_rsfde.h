@@ -1,0 +1,189 @@
+/*
+ * tau_rsfde.h — C ABI of the GB300 (sm_103a) τ-preconditioned GMRES solver for the
+ * quasi-compact Crank–Nicolson discretisation of the d-dimensional
+ * variable-coefficient Riesz space-fractional diffusion equation
+ * (She, Zhang, Gu, Serra-Capizzano, arXiv:2404.10221).
+ *
+ * Problem (§1, Eq. (RSFDE)):  e(x,t) u_t = sum_i kappa_i d^{alpha_i}_{x_i} u + f  on
+ * Omega = prod (L_i, R_i), u = 0 on the boundary, u(x,0) = psi(x).
+ * Each Crank–Nicolson step (§2, Eq. (tls)) solves
+ *     A^{(m)} u^{(m+1)} = b^{(m)},   A^{(m)} = B_alpha E^{(m+1/2)} + S_alpha,
+ *     b^{(m)} = (B_alpha E^{(m+1/2)} - S_alpha) u^{(m)} + dt F^{(m+1/2)},
+ * with B_alpha = B_{alpha_d} ⊗ ... ⊗ B_{alpha_1} (Eq. (Ha)), S_alpha the Kronecker sum of
+ * Eq. (Salpha) built from the fractional-weight Toeplitz matrices of Eq. (eq0), by GMRES
+ * left-preconditioned with the τ preconditioner of Eq. (Pa) (one-sided form, Eq. (one-sided)).
+ * The library runs the algebraically identical form  M^{-1} A u = M^{-1} b  with
+ * M = B_alpha P_alpha = ebar B_alpha + tau(S_alpha); the τ matrices commute (§3), so
+ * P^{-1} Ã = M^{-1} A and P^{-1} b̃ = M^{-1} b and the Krylov iterates are the same.
+ * M^{-1} is applied as a d-dimensional DST-I, a pointwise divide by the eigenvalues
+ * mu_k = ebar prod beta + sum_i eta_i q^{(i)} prod_{l!=i} beta (Eqs. (diag), (q), Lemma Heig,
+ * Lemma le:eig), and a second DST-I.
+ *
+ * Conventions shared by every call:
+ *   - Grid vectors hold the interior nodes x_J, J in prod {1..n_i}, in lexicographic order
+ *     with x_1 fastest (§2); length n_tot = prod n_i; FP64.
+ *   - Calls return tau_status: 0 = TAU_OK, negative = error.  tau_last_error() returns a
+ *     thread-local message for the last failing call of the calling thread.
+ *   - No call aborts, traps or spins without bound.  Device-side waits are bounded and end
+ *     with TAU_ETIMEOUT.
+ *   - The library owns every tau_problem and every device buffer it allocates.  Callers own
+ *     the host arrays and device pointers they pass; the library never frees them and never
+ *     keeps them past the call, except where a call says otherwise.
+ *   - All device work of a problem is issued on the CUDA stream given to tau_create
+ *     (NULL = legacy default stream).  Device pointers passed to a call must be usable on
+ *     that stream; calls that take device pointers are asynchronous with respect to the host
+ *     unless stated otherwise.
+ */
+#ifndef TAU_RSFDE_H
+#define TAU_RSFDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tau_status;
+#define TAU_OK 0
+#define TAU_EINVAL (-1)       /* invalid argument (size, order alpha, NULL pointer, ...) */
+#define TAU_ECUDA (-2)        /* a CUDA runtime call failed; the message names it */
+#define TAU_ENOMEM (-3)       /* device allocation failed */
+#define TAU_ETIMEOUT (-4)     /* a bounded device wait ran out */
+#define TAU_ESTATE (-5)       /* call out of order (e.g. tau_solve before tau_setup) */
+#define TAU_EUNSUPPORTED (-6) /* valid request the build does not support (message says why) */
+#define TAU_ENOTCONV (-7)     /* GMRES hit max_iter without meeting tol (result still written) */
+
+#define TAU_X0_ZERO 0         /* GMRES initial guess 0 for every step */
+#define TAU_X0_PREV 1         /* GMRES initial guess u^{(m)} */
+
+#define TAU_FP64 0            /* plain FP64 arithmetic everywhere */
+
+#define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
+#define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
+#define TAU_ROUTE_DENSE 2     /* explicit n_i x n_i mode products (any n_i <= 8192) */
+
+typedef struct tau_problem tau_problem;
+
+/* Problem and solver parameters (§1 Eq. (RSFDE); §4 for the GMRES settings). */
+typedef struct {
+  int d;                /* spatial dimension, 1..3 */
+  int64_t n[3];         /* interior points per dimension, n_i >= 1; h_i = (R_i - L_i)/(n_i + 1) */
+  double L[3], R[3];    /* interval ends, L_i < R_i */
+  double alpha[3];      /* fractional orders, 1 < alpha_i < 2 */
+  double kappa[3];      /* kappa_i >= 0, sum kappa_i > 0 */
+  double T;             /* final time > 0 */
+  int64_t M;            /* number of Crank–Nicolson steps, dt = T / M */
+  double tol;           /* GMRES stop: ||r_k|| <= tol ||r_0|| on the preconditioned residual */
+  int max_iter;         /* GMRES iteration cap per step, 1..1000 (no restart) */
+  int x0_mode;          /* TAU_X0_ZERO or TAU_X0_PREV */
+  int precision;        /* TAU_FP64 */
+  int route[3];         /* TAU_ROUTE_* per dimension */
+  double e_min, e_max;  /* bounds of e over the grid and all t_{m+1/2} for ebar (Eqs. (bard),
+                           (dhat)); pass NaN for both to let tau_setup scan them */
+} tau_problem_desc;
+
+/* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
+ * copied by tau_set_fields; the caller keeps ownership):
+ *   time_coef[k*rank + r] = c_r(t_k)   for the n_times time levels the field needs
+ *                                       (e and f: t_{m+1/2}, m = 0..M-1, so n_times = M;
+ *                                        psi: n_times = 1),
+ *   space[i][r*(n_i+2) + j] = phi_{r,i}(x_{i,j}),  j = 0..n_i+1 (boundary nodes included). */
+typedef struct {
+  int rank;
+  int64_t n_times;
+  const double* time_coef;
+  const double* space[3];
+} tau_field;
+
+/* Per-problem statistics (host copy). */
+typedef struct {
+  int64_t steps_done;       /* m: number of completed steps */
+  int64_t total_iters;      /* sum of GMRES iterations over completed steps */
+  int last_iters;           /* iterations of the last step */
+  int max_iters_step;       /* largest per-step count so far */
+  double last_relres;       /* |g_k| / ||r_0|| of the last step (preconditioned, Givens estimate) */
+  double ebar, e_hat, e_check; /* Eqs. (bard), (dhat) */
+  int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT or TAU_ROUTE_DENSE) */
+  int graph;                /* 1 if steps run as CUDA-graph launches with device-side loop control */
+  int64_t device_bytes;     /* device memory held by the problem */
+} tau_stats;
+
+/* Create a problem: validates desc, allocates device state (Krylov basis of
+ * (max_iter+1) * n_tot doubles plus O(n_tot) work vectors).  `stream` is a cudaStream_t or NULL.
+ * Errors: TAU_EINVAL (bad desc), TAU_EUNSUPPORTED (route/size not supported), TAU_ENOMEM, TAU_ECUDA. */
+tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** out);
+
+/* Copy the field tables of e (Eq. (tls): E^{(m+1/2)} = diag e(G, t_{m+1/2})), f (source, evaluated
+ * at t_{m+1/2} on the padded grid) and psi (u^{(0)} = psi(G)) to the device.
+ * Requires e->n_times == f->n_times == M and psi->n_times == 1.  Synchronous. */
+tau_status tau_set_fields(tau_problem* p, const tau_field* e, const tau_field* f, const tau_field* psi);
+
+/* One-time setup (Remark after Theorem GMRES: the preconditioner does not depend on the step):
+ * FCD weights (§2), Toeplitz spectra, tau eigenvalues q (Eq. (q)), beta (Lemma Heig), 1/mu,
+ * ebar (scan of e over G x {t_{m+1/2}} unless desc bounds are given), u^{(0)} = psi(G), m = 0.
+ * Synchronous. */
+tau_status tau_setup(tau_problem* p);
+
+/* Advance `count` Crank–Nicolson steps (count <= M - m).  Asynchronous: the host only enqueues
+ * work; per-step statistics are read by tau_get_stats (which synchronises).  Returns TAU_ENOTCONV
+ * from tau_get_stats/tau_sync if any step hit max_iter. */
+tau_status tau_step(tau_problem* p, int64_t count);
+
+/* All remaining steps, then synchronise; returns TAU_ENOTCONV if some step hit max_iter. */
+tau_status tau_solve(tau_problem* p);
+
+/* Wait for enqueued work; return TAU_ENOTCONV if some completed step hit max_iter. */
+tau_status tau_sync(tau_problem* p);
+
+/* Copy u^{(m)} (n_tot doubles) to `out` (host memory if is_device == 0, else a device pointer);
+ * *m_out (optional) receives m.  Host copies are synchronous; device copies are enqueued. */
+tau_status tau_get_solution(tau_problem* p, double* out, int is_device, int64_t* m_out);
+
+/* Replace u^{(m)} and m (resume from a checkpoint; 0 <= m <= M).  Same memory rules. */
+tau_status tau_set_solution(tau_problem* p, const double* u, int is_device, int64_t m);
+
+/* Statistics (synchronises the stream). */
+tau_status tau_get_stats(tau_problem* p, tau_stats* out);
+
+/* GMRES iterations of steps 0..min(cap, m)-1 into iters[] (host; synchronises). */
+tau_status tau_get_iters(tau_problem* p, int* iters, int64_t cap);
+
+/* Free everything the problem owns (synchronises its stream first).  NULL is accepted. */
+tau_status tau_destroy(tau_problem* p);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* tau_last_error(void);
+
+/* ---- operator-level entry points (device pointers, n_tot doubles each, enqueued on the
+ *      problem's stream; require tau_setup).  They expose each step of the solver on its own. */
+
+/* y = A^{(m)} x = B_alpha (e(.,t_{m+1/2}) ∘ x) + S_alpha x, Eq. (tls), 0 <= m < M. */
+tau_status tau_apply_A(tau_problem* p, int64_t m, const double* x, double* y);
+
+/* z = M^{-1} r with M = ebar B_alpha + tau(S_alpha) (Eqs. (Pa), (tauSalpha), (diag)). */
+tau_status tau_apply_Minv(tau_problem* p, const double* r, double* z);
+
+/* z = M^{-1} A^{(m)} x: one preconditioned matvec of the GMRES loop (fused kernels). */
+tau_status tau_apply_MinvA(tau_problem* p, int64_t m, const double* x, double* z);
+
+/* b = (B_alpha E^{(m+1/2)} - S_alpha) u + dt F^{(m+1/2)}, Eq. (tls) with F from Eq. (2.2)/Appendix A. */
+tau_status tau_rhs(tau_problem* p, int64_t m, const double* u, double* b);
+
+/* y = S_d x: orthonormal d-dimensional DST-I, S = sqrt(2/(n+1)) [sin(pi j k/(n+1))] (§3). */
+tau_status tau_dst(tau_problem* p, const double* x, double* y);
+
+/* y = (I ⊗ .. ⊗ S_{alpha_dim} ⊗ .. ⊗ I) x: the fractional-weight Toeplitz matrix of Eq. (eq0)
+ * along dimension dim (0-based; unscaled, no eta). */
+tau_status tau_toeplitz_mode(tau_problem* p, int dim, const double* x, double* y);
+
+/* ebar, e_hat, e_check (Eqs. (bard), (dhat)); requires tau_setup. */
+tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_check);
+
+/* Measured FP64 FMA throughput of the current device in FLOP/s (diagnostic used for the
+ * roofline of the FP64-bound kernels; runs a bounded kernel for a few milliseconds). */
+tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAU_RSFDE_H */

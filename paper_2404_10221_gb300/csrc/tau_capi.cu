@@ -1,0 +1,817 @@
+// C ABI of the τ-preconditioned GMRES solver: problem lifetime, one-time setup, the
+// Crank–Nicolson step as a CUDA graph with device-side GMRES loop control, and the
+// operator-level entry points.  See include/tau_rsfde.h for the contract of every call.
+#include "tau_rsfde.h"
+#include "tau_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace tau;
+
+namespace {
+
+thread_local std::string g_err;
+
+tau_status fail(tau_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t _e = (call);                                                                 \
+    if (_e != cudaSuccess) return fail(TAU_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));  \
+  } while (0)
+
+#define TRY(call)                       \
+  do {                                  \
+    tau_status _s = (call);             \
+    if (_s != TAU_OK) return _s;        \
+  } while (0)
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct tau_problem {
+  tau_problem_desc desc{};
+  cudaStream_t st = nullptr;    // caller's stream: every operation is enqueued here
+  cudaStream_t cap = nullptr;   // library stream used only to record the step graph
+  int d = 0;
+  int n[3] = {1, 1, 1};
+  int64_t n_tot = 0;
+  double dt = 0, h[3] = {0, 0, 0}, eta[3] = {0, 0, 0};
+  int route[3] = {0, 0, 0};
+  // device buffers
+  double *V = nullptr, *u = nullptr, *b = nullptr, *A = nullptr, *C = nullptr, *E = nullptr, *Fdt = nullptr,
+         *invmu = nullptr, *tmp = nullptr;
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *gv = nullptr, *h1 = nullptr, *h2 = nullptr, *y = nullptr;
+  double *pdots = nullptr, *pnorm = nullptr, *escan = nullptr;
+  GmresDev* g = nullptr;
+  int* iters = nullptr;
+  double2* tw = nullptr;
+  double2* spec[3] = {nullptr, nullptr, nullptr};
+  double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
+  double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
+  double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
+  double *e_sp[3] = {nullptr, nullptr, nullptr}, *f_hsp[3] = {nullptr, nullptr, nullptr},
+         *psi_sp[3] = {nullptr, nullptr, nullptr};
+  int re = 0, rf = 0, rp = 0;
+  bool fields_set = false, setup_done = false;
+  double ebar = 0, ehat = 0, echeck = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ok = false;
+  int* h_done = nullptr;  // pinned flag for the host-loop fallback
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t m_host = 0;
+};
+
+namespace {
+
+tau_status dalloc(tau_problem* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TAU_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*ptr);
+  p->bytes += (int64_t)bytes;
+  return TAU_OK;
+}
+
+template <typename T>
+tau_status dalloc_n(tau_problem* p, T** ptr, size_t count) {
+  return dalloc(p, reinterpret_cast<void**>(ptr), count * sizeof(T));
+}
+
+template <typename T>
+tau_status upload(tau_problem* p, T** dst, const T* src, size_t count) {
+  TRY(dalloc_n(p, dst, count));
+  CK(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+  return TAU_OK;
+}
+
+FieldDev field_dev(const tau_problem* p) {
+  FieldDev f{};
+  f.d = p->d;
+  for (int i = 0; i < 3; ++i) {
+    f.n[i] = i < p->d ? p->n[i] : 1;
+    f.e_sp[i] = p->e_sp[i];
+    f.f_hsp[i] = p->f_hsp[i];
+  }
+  f.n_tot = p->n_tot;
+  f.re = p->re;
+  f.rf = p->rf;
+  f.e_tc = p->e_tc;
+  f.f_tc = p->f_tc;
+  f.dt = p->dt;
+  return f;
+}
+
+Pass base_pass(const tau_problem* p, int ax) {
+  Pass P{};
+  P.ax = ax;
+  P.len = p->n[ax];
+  int64_t inner = 1;
+  for (int i = 0; i < ax; ++i) inner *= p->n[i];
+  P.inner = inner;
+  P.nlines = p->n_tot / P.len;
+  DimData& D = P.dim;
+  D.n = p->n[ax];
+  D.K = p->n[ax] + 1;
+  D.route = p->route[ax];
+  D.bdiag = 1.0 - p->desc.alpha[ax] / 12.0;
+  D.boff = p->desc.alpha[ax] / 24.0;
+  D.eta = p->eta[ax];
+  D.spec = p->spec[ax];
+  D.s = p->s[ax];
+  D.sintab = p->sintab[ax];
+  const size_t per_line = 16 * (size_t)P.len + (D.route == ROUTE_FFT ? 16 * (size_t)D.K : 0);
+  int64_t lpb = (int64_t)(32768 / per_line);
+  if (lpb < 1) lpb = 1;
+  if (lpb > 16) lpb = 16;
+  const int64_t cap = ax == 0 ? P.nlines : inner;
+  if (lpb > cap) lpb = cap;
+  P.lpb = (int)lpb;
+  const int64_t outer = P.nlines / inner;
+  P.ntiles = ax == 0 ? (P.nlines + lpb - 1) / lpb : outer * ((inner + lpb - 1) / lpb);
+  P.tw = p->tw;
+  P.vbase = p->V;
+  P.vstride = p->n_tot;
+  return P;
+}
+
+// I/O of a pass chain: plain pointers, or V_j / V_{j+1} selected on the device.
+struct ChainIO {
+  const double* x = nullptr;
+  double* out = nullptr;
+  int in_sel = 0, out_sel = 0;
+  const GmresDev* g = nullptr;
+};
+
+tau_status enq(const Pass& P, cudaStream_t st) {
+  CK(launch_pass(P, st));
+  return TAU_OK;
+}
+
+// DST along dims top..1 (descending), DST·(1/mu)·DST along dim 0, DST along dims 1..d-1,
+// reading `x` in the first pass and working in place on `out` afterwards.
+tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainIO& io, int top, bool first_reads_x) {
+  bool rd = first_reads_x;
+  auto dst_pass = [&](int ax, int post) -> tau_status {
+    Pass P = base_pass(p, ax);
+    P.post = post;
+    P.invmu = p->invmu;
+    P.g = io.g;
+    P.in_a = rd ? io.x : io.out;
+    P.in_sel = rd ? io.in_sel : io.out_sel;
+    P.out_a = io.out;
+    P.out_sel = io.out_sel;
+    rd = false;
+    return enq(P, st);
+  };
+  for (int ax = top; ax >= 1; --ax) TRY(dst_pass(ax, POST_DST));
+  TRY(dst_pass(0, POST_DST_MU_DST));
+  for (int ax = 1; ax < p->d; ++ax) TRY(dst_pass(ax, POST_DST));
+  return TAU_OK;
+}
+
+// out = finish( B(e∘x) + sgn*sum_i eta_i (..S_i..) x ), optionally followed by M^{-1}.
+tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainIO& io, double sgn, int finish, const double* src,
+                  bool precond) {
+  const int d = p->d;
+  for (int ax = 0; ax < d; ++ax) {
+    Pass P = base_pass(p, ax);
+    P.mv = 1;
+    P.first = ax == 0;
+    P.last = ax == d - 1;
+    P.seta = sgn * p->eta[ax];
+    P.g = io.g;
+    if (ax == 0) {
+      P.in_a = io.x;
+      P.in_sel = io.in_sel;
+      P.in_c = p->E;
+    } else {
+      P.in_a = p->A;
+      P.in_c = p->C;
+    }
+    if (!P.last) {
+      P.out_a = p->A;
+      P.out_c = p->C;
+    } else {
+      P.out_a = io.out;
+      P.out_sel = io.out_sel;
+      P.finish = finish;
+      P.src = src;
+      P.invmu = p->invmu;
+      if (precond) P.post = d == 1 ? POST_DST_MU_DST : POST_DST;
+    }
+    TRY(enq(P, st));
+  }
+  if (precond && d > 1) {
+    ChainIO t = io;
+    TRY(enq_minv_tail(p, st, t, d - 2, false));
+  }
+  return TAU_OK;
+}
+
+tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainIO& io) {
+  return enq_minv_tail(p, st, io, p->d - 1, true);
+}
+
+tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
+  CK(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
+  ChainIO rhs;
+  rhs.x = p->u;
+  rhs.out = p->b;
+  TRY(enq_mv(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
+  ChainIO r0;
+  r0.out = p->V;
+  if (p->desc.x0_mode == TAU_X0_PREV) {
+    r0.x = p->u;
+    TRY(enq_mv(p, st, r0, 1.0, FIN_RESID, p->b, true));
+  } else {
+    r0.x = p->b;
+    TRY(enq_minv(p, st, r0));
+  }
+  CK(launch_norm_partial(p->V, p->n_tot, p->g, p->pnorm, st));
+  CK(launch_init_beta(p->g, p->pnorm, p->gv, p->V, p->n_tot, st));
+  return TAU_OK;
+}
+
+tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+  ChainIO it;
+  it.in_sel = 1;
+  it.out_sel = 2;
+  it.g = p->g;
+  TRY(enq_mv(p, st, it, 1.0, FIN_NONE, nullptr, true));
+  const int ld = RED_BLOCKS;
+  CK(launch_dots(p->V, p->n_tot, p->g, p->pdots, ld, st));
+  CK(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
+  CK(launch_update_dots(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
+  CK(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
+  CK(launch_update_dots(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
+  CK(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
+  CK(launch_scale_next(p->V, p->n_tot, p->g, st));
+  return TAU_OK;
+}
+
+tau_status enq_epilogue(tau_problem* p, cudaStream_t st) {
+  CK(launch_backsolve_update(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, p->V, p->n_tot, p->u,
+                             p->desc.x0_mode == TAU_X0_PREV, p->iters, st));
+  return TAU_OK;
+}
+
+// Step graph: prologue -> WHILE(body; the Givens kernel sets the condition) -> epilogue.
+tau_status build_graph(tau_problem* p) {
+  cudaGraph_t G = nullptr;
+  CK(cudaGraphCreate(&G, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    cudaGetLastError();
+    return fail(TAU_EUNSUPPORTED, "conditional graph nodes unavailable: %s", cudaGetErrorString(e));
+  }
+  tau_status st = TAU_OK;
+  std::vector<cudaGraphNode_t> leaves;
+  do {
+    e = cudaStreamBeginCaptureToGraph(p->cap, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    st = enq_prologue(p, p->cap);
+    {
+      cudaStreamCaptureStatus cst;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      e = cudaStreamGetCaptureInfo(p->cap, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+      if (e == cudaSuccess) leaves.assign(deps, deps + nd);
+    }
+    cudaGraph_t Gout = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &Gout);
+    if (st != TAU_OK) break;
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) break;
+    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+    memset(cp_raw, 0, sizeof(cp_raw));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    e = cudaGraphAddNode(&cnode, G, leaves.data(), nullptr, leaves.size(), &cp);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(p->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    st = enq_body(p, p->cap, h, 1);
+    e2 = cudaStreamEndCapture(p->cap, &Gout);
+    if (st != TAU_OK) break;
+    if (e2 != cudaSuccess) {
+      e = e2;
+      break;
+    }
+    e = cudaStreamBeginCaptureToGraph(p->cap, G, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    st = enq_epilogue(p, p->cap);
+    e2 = cudaStreamEndCapture(p->cap, &Gout);
+    if (st != TAU_OK) break;
+    if (e2 != cudaSuccess) {
+      e = e2;
+      break;
+    }
+    e = cudaGraphInstantiate(&p->exec, G, 0);
+  } while (0);
+  cudaGraphDestroy(G);
+  if (st != TAU_OK) return st;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TAU_EUNSUPPORTED, "step graph: %s", cudaGetErrorString(e));
+  }
+  return TAU_OK;
+}
+
+// Host-loop fallback: one synchronisation per GMRES iteration.
+tau_status run_step_hostloop(tau_problem* p) {
+  TRY(enq_prologue(p, p->st));
+  cudaGraphConditionalHandle dummy = 0;
+  for (int it = 0; it < p->desc.max_iter; ++it) {
+    CK(cudaMemcpyAsync(p->h_done, &p->g->done, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    if (*p->h_done) break;
+    TRY(enq_body(p, p->st, dummy, 0));
+  }
+  TRY(enq_epilogue(p, p->st));
+  return TAU_OK;
+}
+
+tau_status check_ready(tau_problem* p) {
+  if (!p) return fail(TAU_EINVAL, "problem is NULL");
+  if (!p->setup_done) return fail(TAU_ESTATE, "tau_setup has not run");
+  return TAU_OK;
+}
+
+tau_status sync_status(tau_problem* p) {
+  CK(cudaStreamSynchronize(p->st));
+  GmresDev g;
+  CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
+  if (g.notconv) return fail(TAU_ENOTCONV, "a step reached max_iter=%d without meeting tol", p->desc.max_iter);
+  return TAU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tau_last_error(void) { return g_err.c_str(); }
+
+tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** out) {
+  if (!desc || !out) return fail(TAU_EINVAL, "desc/out is NULL");
+  *out = nullptr;
+  const tau_problem_desc& D = *desc;
+  if (D.d < 1 || D.d > 3) return fail(TAU_EINVAL, "d=%d outside 1..3", D.d);
+  double ksum = 0;
+  int64_t n_tot = 1;
+  for (int i = 0; i < D.d; ++i) {
+    if (D.n[i] < 1 || D.n[i] > (1 << 20)) return fail(TAU_EINVAL, "n[%d]=%lld outside 1..2^20", i, (long long)D.n[i]);
+    if (!(D.alpha[i] > 1.0 && D.alpha[i] < 2.0)) return fail(TAU_EINVAL, "alpha[%d]=%g not in (1,2)", i, D.alpha[i]);
+    if (!(D.kappa[i] >= 0.0)) return fail(TAU_EINVAL, "kappa[%d]=%g < 0", i, D.kappa[i]);
+    if (!(D.R[i] > D.L[i])) return fail(TAU_EINVAL, "R[%d] <= L[%d]", i, i);
+    ksum += D.kappa[i];
+    n_tot *= D.n[i];
+  }
+  if (!(ksum > 0)) return fail(TAU_EINVAL, "sum of kappa must be > 0");
+  if (!(D.T > 0) || D.M < 1) return fail(TAU_EINVAL, "T must be > 0 and M >= 1");
+  if (!(D.tol > 0) || D.max_iter < 1 || D.max_iter > MAX_ITER_CAP)
+    return fail(TAU_EINVAL, "tol must be > 0 and 1 <= max_iter <= %d", MAX_ITER_CAP);
+  if (D.x0_mode != TAU_X0_ZERO && D.x0_mode != TAU_X0_PREV) return fail(TAU_EINVAL, "x0_mode %d", D.x0_mode);
+  if (D.precision != TAU_FP64) return fail(TAU_EUNSUPPORTED, "precision %d", D.precision);
+  if (n_tot > (int64_t)1 << 31) return fail(TAU_EINVAL, "n_tot=%lld too large", (long long)n_tot);
+
+  tau_problem* p = new (std::nothrow) tau_problem();
+  if (!p) return fail(TAU_ENOMEM, "host allocation");
+  p->desc = D;
+  p->st = (cudaStream_t)stream;
+  p->d = D.d;
+  p->n_tot = n_tot;
+  p->dt = D.T / (double)D.M;
+  for (int i = 0; i < D.d; ++i) {
+    p->n[i] = (int)D.n[i];
+    p->h[i] = (D.R[i] - D.L[i]) / (double)(D.n[i] + 1);
+    p->eta[i] = D.kappa[i] * p->dt / (2.0 * std::pow(p->h[i], D.alpha[i]));
+    const int64_t K = D.n[i] + 1;
+    int r = D.route[i];
+    const bool fft_ok = is_pow2(K) && K >= 2 && K <= KMAX;
+    if (r == TAU_ROUTE_AUTO) r = fft_ok ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE;
+    if (r == TAU_ROUTE_FFT && !fft_ok) {
+      delete p;
+      return fail(TAU_EUNSUPPORTED, "FFT route needs n+1 a power of two in [2, %d] (dim %d, n=%lld)", KMAX, i,
+                  (long long)D.n[i]);
+    }
+    if (r == TAU_ROUTE_DENSE && D.n[i] > 8192) {
+      delete p;
+      return fail(TAU_EUNSUPPORTED, "dense route limited to n <= 8192 (dim %d, n=%lld)", i, (long long)D.n[i]);
+    }
+    if (r != TAU_ROUTE_FFT && r != TAU_ROUTE_DENSE) {
+      delete p;
+      return fail(TAU_EINVAL, "route[%d]=%d", i, D.route[i]);
+    }
+    p->route[i] = r == TAU_ROUTE_FFT ? ROUTE_FFT : ROUTE_DENSE;
+  }
+  auto cleanup = [&](tau_status s) {
+    tau_destroy(p);
+    return s;
+  };
+  if (cudaError_t e = init_kernel_attributes(); e != cudaSuccess)
+    return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
+  if (cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking); e != cudaSuccess)
+    return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+  const int mi = D.max_iter;
+  tau_status s = TAU_OK;
+  const size_t n = (size_t)n_tot;
+  if ((s = dalloc_n(p, &p->V, (size_t)(mi + 1) * n)) || (s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
+      (s = dalloc_n(p, &p->A, n)) || (s = dalloc_n(p, &p->C, n)) || (s = dalloc_n(p, &p->E, n)) ||
+      (s = dalloc_n(p, &p->Fdt, n)) || (s = dalloc_n(p, &p->invmu, n)) || (s = dalloc_n(p, &p->tmp, n)) ||
+      (s = dalloc_n(p, &p->H, (size_t)(mi + 1) * mi)) || (s = dalloc_n(p, &p->cs, mi)) ||
+      (s = dalloc_n(p, &p->sn, mi)) || (s = dalloc_n(p, &p->gv, mi + 1)) || (s = dalloc_n(p, &p->h1, mi + 1)) ||
+      (s = dalloc_n(p, &p->h2, mi + 1)) || (s = dalloc_n(p, &p->y, mi + 1)) ||
+      (s = dalloc_n(p, &p->pdots, (size_t)(mi + 1) * RED_BLOCKS)) || (s = dalloc_n(p, &p->pnorm, RED_BLOCKS)) ||
+      (s = dalloc_n(p, &p->escan, 2 * RED_BLOCKS)) || (s = dalloc_n(p, &p->g, 1)) ||
+      (s = dalloc_n(p, &p->iters, (size_t)D.M)) || (s = dalloc_n(p, &p->tw, TWN)))
+    return cleanup(s);
+  if (cudaMallocHost(&p->h_done, sizeof(int)) != cudaSuccess) {
+    p->h_done = nullptr;
+    return cleanup(fail(TAU_ENOMEM, "cudaMallocHost"));
+  }
+  // twiddles tw[t] = exp(-2 pi i t / TWN)
+  std::vector<double2> tw(TWN);
+  for (int t = 0; t < TWN; ++t) {
+    const double a = -2.0 * M_PI * (double)t / (double)TWN;
+    tw[t] = make_double2(std::cos(a), std::sin(a));
+  }
+  if (cudaMemcpy(p->tw, tw.data(), TWN * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cleanup(fail(TAU_ECUDA, "twiddle upload"));
+  if (cudaMemset(p->iters, 0, sizeof(int) * (size_t)D.M) != cudaSuccess) return cleanup(fail(TAU_ECUDA, "memset"));
+  *out = p;
+  return TAU_OK;
+}
+
+tau_status tau_set_fields(tau_problem* p, const tau_field* e, const tau_field* f, const tau_field* psi) {
+  if (!p || !e || !f || !psi) return fail(TAU_EINVAL, "NULL argument");
+  if (p->fields_set) return fail(TAU_ESTATE, "fields already set");
+  const int64_t M = p->desc.M;
+  if (e->n_times != M || f->n_times != M || psi->n_times != 1)
+    return fail(TAU_EINVAL, "n_times must be M=%lld for e and f, 1 for psi", (long long)M);
+  if (e->rank < 1 || f->rank < 0 || psi->rank < 0) return fail(TAU_EINVAL, "bad rank");
+  const tau_field* fs[3] = {e, f, psi};
+  for (auto* fl : fs) {
+    if (fl->rank > 0 && !fl->time_coef) return fail(TAU_EINVAL, "time_coef NULL");
+    for (int i = 0; i < p->d; ++i)
+      if (fl->rank > 0 && !fl->space[i]) return fail(TAU_EINVAL, "space[%d] NULL", i);
+  }
+  p->re = e->rank;
+  p->rf = f->rank;
+  p->rp = psi->rank;
+  TRY(upload(p, &p->e_tc, e->time_coef, (size_t)M * e->rank));
+  TRY(upload(p, &p->f_tc, f->time_coef, (size_t)M * f->rank));
+  TRY(upload(p, &p->psi_tc, psi->time_coef, (size_t)psi->rank));
+  for (int i = 0; i < p->d; ++i) {
+    const int ni = p->n[i];
+    TRY(upload(p, &p->e_sp[i], e->space[i], (size_t)e->rank * (ni + 2)));
+    TRY(upload(p, &p->psi_sp[i], psi->space[i], (size_t)psi->rank * (ni + 2)));
+    // F = (⊗ 𝓗_{alpha_l}) f restricted to the interior (Eq. (2.2) applied to the source; the
+    // 1-D and 2-D forms of Appendix A): for separable f each factor takes the 3-point stencil.
+    const double a = p->desc.alpha[i];
+    std::vector<double> hs((size_t)f->rank * ni);
+    for (int r = 0; r < f->rank; ++r) {
+      const double* sp = f->space[i] + (size_t)r * (ni + 2);
+      for (int j = 0; j < ni; ++j)
+        hs[(size_t)r * ni + j] = (a / 24.0) * sp[j] + (1.0 - a / 12.0) * sp[j + 1] + (a / 24.0) * sp[j + 2];
+    }
+    TRY(upload(p, &p->f_hsp[i], hs.data(), hs.size()));
+  }
+  p->fields_set = true;
+  return TAU_OK;
+}
+
+tau_status tau_setup(tau_problem* p) {
+  if (!p) return fail(TAU_EINVAL, "problem is NULL");
+  if (!p->fields_set) return fail(TAU_ESTATE, "tau_set_fields has not run");
+  if (p->setup_done) return fail(TAU_ESTATE, "tau_setup already ran");
+  const int d = p->d;
+  for (int i = 0; i < d; ++i) {
+    const int N = p->n[i], K = N + 1;
+    const double a = p->desc.alpha[i];
+    // FCD weights by the recurrence of §2: s_0 = Gamma(a+1)/Gamma(a/2+1)^2,
+    // s_k = (1 - (a+1)/(a/2+k)) s_{k-1}.
+    std::vector<double> s(N);
+    s[0] = std::tgamma(a + 1.0) / (std::tgamma(a / 2.0 + 1.0) * std::tgamma(a / 2.0 + 1.0));
+    for (int k = 1; k < N; ++k) s[k] = (1.0 - (a + 1.0) / (a / 2.0 + k)) * s[k - 1];
+    TRY(upload(p, &p->s[i], s.data(), s.size()));
+    // eigenvalues of B_{alpha_i} on sine mode k = 1..N (Lemma Heig)
+    std::vector<double> beta(N);
+    for (int k = 1; k <= N; ++k) {
+      const double sn = std::sin(k * M_PI / (2.0 * N + 2.0));
+      beta[k - 1] = 1.0 - (a / 6.0) * sn * sn;
+    }
+    TRY(upload(p, &p->beta[i], beta.data(), beta.size()));
+    std::vector<double> q(N);
+    if (p->route[i] == ROUTE_FFT) {
+      // circulant embedding c of length 2K: c_0 = s_0, c_k = c_{2K-k} = s_k (1 <= k < N), zeros
+      // elsewhere.  Its real spectrum lambda_k gives the Toeplitz product and, at k = 1..N, the
+      // eigenvalues q_k of tau(S) (Eq. (q)).
+      std::vector<double> c(2 * (size_t)K, 0.0);
+      c[0] = s[0];
+      for (int k = 1; k < N; ++k) c[k] = c[2 * K - k] = s[k];
+      double *dc = nullptr, *dl = nullptr;
+      TRY(upload(p, &dc, c.data(), c.size()));
+      TRY(dalloc_n(p, &dl, (size_t)K + 1));
+      CK(launch_spectrum(K, dc, dl, p->tw, p->st));
+      std::vector<double> lam(K + 1);
+      CK(cudaMemcpyAsync(lam.data(), dl, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+      CK(cudaStreamSynchronize(p->st));
+      std::vector<double2> spec(K / 2 + 1);
+      for (int k = 0; k <= K / 2; ++k) {
+        const double lk = lam[k], lkk = lam[K - k];
+        spec[k] = make_double2((lk + lkk) / (4.0 * K), (lk - lkk) / (4.0 * K));
+      }
+      TRY(upload(p, &p->spec[i], spec.data(), spec.size()));
+      for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
+    } else {
+      // q_k = s_0 + 2 sum_j s_j cos(pi j k / K) (Eq. (q)) with a cosine table
+      std::vector<double> ct(2 * (size_t)K), st(2 * (size_t)K);
+      for (int t = 0; t < 2 * K; ++t) {
+        ct[t] = std::cos(M_PI * t / K);
+        st[t] = std::sin(M_PI * t / K);
+      }
+      for (int k = 1; k <= N; ++k) {
+        double acc = s[0];
+        int64_t ph = 0;
+        for (int j = 1; j < N; ++j) {
+          ph += k;
+          if (ph >= 2 * K) ph -= 2 * K;
+          acc += 2.0 * s[j] * ct[ph];
+        }
+        q[k - 1] = acc;
+      }
+      TRY(upload(p, &p->sintab[i], st.data(), st.size()));
+    }
+    TRY(upload(p, &p->q[i], q.data(), q.size()));
+  }
+  // ebar (Eqs. (bard), (dhat))
+  if (std::isnan(p->desc.e_min) || std::isnan(p->desc.e_max)) {
+    CK(launch_escan(field_dev(p), p->desc.M, p->escan, p->st));
+    std::vector<double> part(2 * RED_BLOCKS);
+    CK(cudaMemcpyAsync(part.data(), p->escan, part.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    double hi = -INFINITY, lo = INFINITY;
+    for (int b = 0; b < RED_BLOCKS; ++b) {
+      hi = std::fmax(hi, part[2 * b]);
+      lo = std::fmin(lo, part[2 * b + 1]);
+    }
+    p->ehat = hi;
+    p->echeck = lo;
+  } else {
+    p->ehat = p->desc.e_max;
+    p->echeck = p->desc.e_min;
+  }
+  if (!(p->echeck > 0.0) || !(p->ehat >= p->echeck))
+    return fail(TAU_EINVAL, "e must be positive: min %g max %g", p->echeck, p->ehat);
+  p->ebar = 0.5 * (p->ehat + p->echeck);
+  CK(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
+  CK(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->u, p->st));
+  GmresDev g{};
+  g.max_iter = p->desc.max_iter;
+  g.tol = p->desc.tol;
+  g.M = p->desc.M;
+  g.m = 0;
+  g.done = 1;
+  CK(cudaMemcpyAsync(p->g, &g, sizeof(g), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  p->m_host = 0;
+  p->setup_done = true;
+  const char* nog = std::getenv("TAU_NO_GRAPH");
+  if (!(nog && nog[0] == '1')) {
+    tau_status gs = build_graph(p);
+    p->graph_ok = gs == TAU_OK;
+    if (!p->graph_ok) g_err.clear();
+  }
+  return TAU_OK;
+}
+
+tau_status tau_step(tau_problem* p, int64_t count) {
+  TRY(check_ready(p));
+  if (count < 0 || p->m_host + count > p->desc.M)
+    return fail(TAU_EINVAL, "count=%lld with m=%lld of M=%lld", (long long)count, (long long)p->m_host,
+                (long long)p->desc.M);
+  for (int64_t c = 0; c < count; ++c) {
+    if (p->graph_ok) {
+      CK(cudaGraphLaunch(p->exec, p->st));
+    } else {
+      TRY(run_step_hostloop(p));
+    }
+    ++p->m_host;
+  }
+  return TAU_OK;
+}
+
+tau_status tau_sync(tau_problem* p) {
+  TRY(check_ready(p));
+  return sync_status(p);
+}
+
+tau_status tau_solve(tau_problem* p) {
+  TRY(check_ready(p));
+  TRY(tau_step(p, p->desc.M - p->m_host));
+  return sync_status(p);
+}
+
+tau_status tau_get_solution(tau_problem* p, double* out, int is_device, int64_t* m_out) {
+  TRY(check_ready(p));
+  if (!out) return fail(TAU_EINVAL, "out is NULL");
+  CK(cudaMemcpyAsync(out, p->u, p->n_tot * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     p->st));
+  if (!is_device) CK(cudaStreamSynchronize(p->st));
+  if (m_out) *m_out = p->m_host;
+  return TAU_OK;
+}
+
+tau_status tau_set_solution(tau_problem* p, const double* u, int is_device, int64_t m) {
+  TRY(check_ready(p));
+  if (!u) return fail(TAU_EINVAL, "u is NULL");
+  if (m < 0 || m > p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M", (long long)m);
+  CK(cudaMemcpyAsync(p->u, u, p->n_tot * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     p->st));
+  // m lives in the device state read by the step graph
+  CK(cudaMemcpyAsync(&p->g->m, &m, sizeof(int64_t), cudaMemcpyHostToDevice, p->st));
+  CK(cudaStreamSynchronize(p->st));
+  p->m_host = m;
+  return TAU_OK;
+}
+
+tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
+  TRY(check_ready(p));
+  if (!out) return fail(TAU_EINVAL, "out is NULL");
+  CK(cudaStreamSynchronize(p->st));
+  GmresDev g;
+  CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
+  std::vector<int> it((size_t)p->desc.M);
+  CK(cudaMemcpy(it.data(), p->iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  memset(out, 0, sizeof(*out));
+  out->steps_done = g.m;
+  int64_t tot = 0;
+  int mx = 0;
+  for (int64_t m = 0; m < g.m && m < p->desc.M; ++m) {
+    tot += it[m];
+    if (it[m] > mx) mx = it[m];
+  }
+  out->total_iters = tot;
+  out->last_iters = g.m > 0 ? it[g.m - 1] : 0;
+  out->max_iters_step = mx;
+  out->last_relres = g.relres;
+  out->ebar = p->ebar;
+  out->e_hat = p->ehat;
+  out->e_check = p->echeck;
+  for (int i = 0; i < 3; ++i) out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE) : 0;
+  out->graph = p->graph_ok ? 1 : 0;
+  out->device_bytes = p->bytes;
+  if (g.notconv) return fail(TAU_ENOTCONV, "a step reached max_iter without meeting tol");
+  return TAU_OK;
+}
+
+tau_status tau_get_iters(tau_problem* p, int* iters, int64_t cap) {
+  TRY(check_ready(p));
+  if (!iters || cap < 0) return fail(TAU_EINVAL, "bad iters/cap");
+  CK(cudaStreamSynchronize(p->st));
+  GmresDev g;
+  CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
+  const int64_t nget = cap < g.m ? cap : g.m;
+  if (nget > 0) CK(cudaMemcpy(iters, p->iters, nget * sizeof(int), cudaMemcpyDeviceToHost));
+  return TAU_OK;
+}
+
+tau_status tau_destroy(tau_problem* p) {
+  if (!p) return TAU_OK;
+  cudaStreamSynchronize(p->st);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  for (void* a : p->allocs) cudaFree(a);
+  if (p->h_done) cudaFreeHost(p->h_done);
+  if (p->cap) cudaStreamDestroy(p->cap);
+  delete p;
+  return TAU_OK;
+}
+
+tau_status tau_apply_A(tau_problem* p, int64_t m, const double* x, double* y) {
+  TRY(check_ready(p));
+  if (!x || !y) return fail(TAU_EINVAL, "NULL vector");
+  if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
+  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  ChainIO io;
+  io.x = x;
+  io.out = y;
+  return enq_mv(p, p->st, io, 1.0, FIN_NONE, nullptr, false);
+}
+
+tau_status tau_apply_MinvA(tau_problem* p, int64_t m, const double* x, double* z) {
+  TRY(check_ready(p));
+  if (!x || !z) return fail(TAU_EINVAL, "NULL vector");
+  if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
+  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  ChainIO io;
+  io.x = x;
+  io.out = z;
+  return enq_mv(p, p->st, io, 1.0, FIN_NONE, nullptr, true);
+}
+
+tau_status tau_apply_Minv(tau_problem* p, const double* r, double* z) {
+  TRY(check_ready(p));
+  if (!r || !z) return fail(TAU_EINVAL, "NULL vector");
+  ChainIO io;
+  io.x = r;
+  io.out = z;
+  return enq_minv(p, p->st, io);
+}
+
+tau_status tau_rhs(tau_problem* p, int64_t m, const double* u, double* b) {
+  TRY(check_ready(p));
+  if (!u || !b) return fail(TAU_EINVAL, "NULL vector");
+  if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
+  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  ChainIO io;
+  io.x = u;
+  io.out = b;
+  return enq_mv(p, p->st, io, -1.0, FIN_ADD_F, p->Fdt, false);
+}
+
+tau_status tau_dst(tau_problem* p, const double* x, double* y) {
+  TRY(check_ready(p));
+  if (!x || !y) return fail(TAU_EINVAL, "NULL vector");
+  for (int ax = 0; ax < p->d; ++ax) {
+    Pass P = base_pass(p, ax);
+    P.post = POST_DST;
+    P.in_a = ax == 0 ? x : y;
+    P.out_a = y;
+    TRY(enq(P, p->st));
+  }
+  return TAU_OK;
+}
+
+tau_status tau_toeplitz_mode(tau_problem* p, int dim, const double* x, double* y) {
+  TRY(check_ready(p));
+  if (!x || !y) return fail(TAU_EINVAL, "NULL vector");
+  if (dim < 0 || dim >= p->d) return fail(TAU_EINVAL, "dim=%d outside 0..d-1", dim);
+  Pass P = base_pass(p, dim);
+  P.toep_only = 1;
+  P.in_a = x;
+  P.out_a = y;
+  return enq(P, p->st);
+}
+
+tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_check) {
+  TRY(check_ready(p));
+  if (ebar) *ebar = p->ebar;
+  if (e_hat) *e_hat = p->ehat;
+  if (e_check) *e_check = p->echeck;
+  return TAU_OK;
+}
+
+tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s) {
+  if (!flops_per_s) return fail(TAU_EINVAL, "NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 4, iters = 4000;
+  double* out = nullptr;
+  CK(cudaMalloc(&out, sizeof(double) * blocks * 256));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(launch_fp64_peak(out, blocks, iters, st));
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < 5; ++r) CK(launch_fp64_peak(out, blocks, iters, st));
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops_per_s = 5.0 * 2.0 * 8.0 * iters * (double)blocks * 256 / (ms * 1e-3);
+  return TAU_OK;
+}
+
+}  // extern "C"

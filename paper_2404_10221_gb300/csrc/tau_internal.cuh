@@ -1,0 +1,145 @@
+// Internal declarations of the τ-GMRES CUDA library (device helpers, pass
+// descriptors, host launchers).  Not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tau {
+
+// Largest half-length complex FFT size K = n + 1 of the FFT route.
+constexpr int KMAX = 4096;
+// Twiddle table tw[t] = exp(-2 pi i t / TWN), t = 0..TWN-1.
+constexpr int TWN = 2 * KMAX;
+// Largest GMRES basis handled by the device-side Givens kernel.
+constexpr int MAX_ITER_CAP = 1000;
+// Blocks used by the reduction kernels (partials per reduction).
+constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
+
+enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2 };
+
+// What the value computed by a matvec pass becomes at the last dimension.
+enum Finish : int {
+  FIN_NONE = 0,    // out = value
+  FIN_ADD_F = 1,   // out = value + Fdt            (right-hand side b)
+  FIN_RESID = 2,   // out = src - value            (residual b - A x)
+};
+
+// What happens to the finished line before it is stored.
+enum Post : int {
+  POST_NONE = 0,
+  POST_DST = 1,        // orthonormal DST-I along this dimension
+  POST_DST_MU_DST = 2, // DST-I, multiply by 1/mu, DST-I  (only on dimension 0)
+};
+
+struct GmresDev;
+
+// Per-dimension data resident on the device.
+struct DimData {
+  int n;              // interior points N_i
+  int K;              // n + 1 (FFT route: power of two)
+  int route;          // Route
+  double bdiag, boff; // B_{alpha_i}: 1 - alpha/12, alpha/24
+  double eta;         // kappa_i dt / (2 h_i^alpha_i)
+  const double2* spec;  // FFT route: (sigma_k, delta_k), k = 0..K/2, Toeplitz spectrum folded
+                        // for the packed real FFT, scaled by 1/K (no eta)
+  const double* s;      // FCD weights s_0..s_{n-1}
+  const double* sintab; // dense route: sin(pi t / K), t = 0..2K-1
+};
+
+// One line pass over an array of shape (n_{d-1}, ..., n_0) along dimension ax.
+struct Pass {
+  int ax;            // dimension (0 = x_1, contiguous)
+  int len;           // n_ax
+  int64_t inner;     // prod_{i<ax} n_i (element stride along the line)
+  int64_t nlines;    // n_tot / len
+  int lpb;           // lines per CTA
+  int64_t ntiles;
+  DimData dim;
+  // matvec channels
+  int mv;            // 1: this pass is a matvec pass
+  int first;         // 1: inputs are (x, e): a = B(e∘x) + s eta T x, c = B x
+  int last;          // 1: no c output; apply Finish
+  double seta;       // +eta (A) or -eta (right-hand side)
+  int toep_only;     // 1: out = T x (no B, no eta) -- Toeplitz parity entry
+  int finish;        // Finish
+  int post;          // Post
+  const double* in_a;  // first pass: x; else channel a
+  const double* in_c;  // first pass: e (may be null when toep_only); else channel c
+  const double* src;   // FIN_RESID minuend or FIN_ADD_F addend (Fdt)
+  const double* invmu; // POST_DST_MU_DST
+  double* out_a;
+  double* out_c;
+  const double2* tw;   // twiddles
+  // GMRES wiring: pointers that depend on the device-side Arnoldi index j
+  const GmresDev* g;         // non-null: skip the pass when g->done
+  double* vbase;             // Krylov basis V (vectors of vstride doubles)
+  int64_t vstride;
+  int in_sel, out_sel;       // 0: in_a/out_a as given, 1: V_j, 2: V_{j+1}
+};
+
+// GMRES state kept in device memory (one per problem).
+struct GmresDev {
+  int j;             // current Arnoldi index: V_j is the newest basis vector
+  int done;          // 1 once converged / capped / broken down
+  int k;             // iterations of the finished step
+  int notconv;       // sticky: some step hit max_iter
+  int max_iter;
+  int pad;
+  double tol;
+  double beta;       // ||r_0||
+  double relres;
+  double hnorm;      // ||w|| of the current column
+  int64_t m;         // current step index
+  int64_t M;
+};
+
+// ---------------------------------------------------------------------------
+// host launchers (tau_kernels.cu)
+// ---------------------------------------------------------------------------
+cudaError_t init_kernel_attributes();
+size_t pass_smem_bytes(const Pass& p);
+cudaError_t launch_pass(const Pass& p, cudaStream_t st);
+cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* tw, cudaStream_t st);
+
+// fields: e_m, Fdt_m for step m (read from g->m unless m_override >= 0)
+struct FieldDev {
+  int d;
+  int n[3];
+  int64_t n_tot;
+  int re, rf;                 // ranks of e and f
+  const double* e_tc;         // [M x re]
+  const double* e_sp[3];      // [re x (n_i+2)]
+  const double* f_tc;         // [M x rf]
+  const double* f_hsp[3];     // [rf x n_i]: 𝓗-stencilled f space tables (interior)
+  double dt;
+};
+cudaError_t launch_fields(const FieldDev& f, const GmresDev* g, int64_t m_override, double* e_out,
+                          double* fdt_out, cudaStream_t st);
+cudaError_t launch_psi(int d, const int* n, int64_t n_tot, int rank, const double* tc, const double* const* sp,
+                       double* out, cudaStream_t st);
+cudaError_t launch_escan(const FieldDev& f, int64_t M, double* partial /*2*RED_BLOCKS*/, cudaStream_t st);
+cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
+                         const double* const* q, const double* eta, double* invmu, cudaStream_t st);
+
+// GMRES building blocks
+// w = V_{j+1} (the slot of the next basis vector) in the CGS2 kernels below.
+cudaError_t launch_dots(const double* V, int64_t n, const GmresDev* g, double* partial, int ld_partial,
+                        cudaStream_t st);
+cudaError_t launch_reduce_dots(const double* partial, int ld_partial, const GmresDev* g, double* h,
+                               cudaStream_t st);
+cudaError_t launch_update_dots(double* V, int64_t n, const GmresDev* g, const double* h, double* partial,
+                               int ld_partial, int want_norm, cudaStream_t st);
+cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* h1,
+                          const double* h2, const double* partial_norm, int ldH,
+                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+cudaError_t launch_scale_next(double* V, int64_t n, const GmresDev* g, cudaStream_t st);
+cudaError_t launch_norm_partial(const double* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st);
+cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, double* V, int64_t n,
+                             cudaStream_t st);
+cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y,
+                                    const double* V, int64_t n, double* u, int x0_prev, int* iters_log,
+                                    cudaStream_t st);
+cudaError_t launch_fp64_peak(double* out, int blocks, int iters, cudaStream_t st);
+
+}  // namespace tau

@@ -1,0 +1,996 @@
+// CUDA kernels of the τ-preconditioned GMRES solver (sm_103a, FP64).
+//
+// Line passes: the matvec A x = B_alpha (e∘x) + sum_i eta_i (⊗_{l!=i} B_l ⊗ S_i) x of Eq. (tls),
+// the right-hand side of Eq. (tls) and the DST-I based τ solve of Eqs. (Pa), (diag) are applied
+// one dimension at a time.  A pass loads a tile of grid lines along one dimension into shared
+// memory, works on them there and writes them back.  Two channels carry the Kronecker terms
+// between passes: after the pass over dimension i,
+//     a = (B_i ... B_1)(e∘x) + sum_{l<=i} eta_l (B_i..S_l..B_1) x,      c = (B_i ... B_1) x,
+// so the pass over dimension i+1 computes a' = B_{i+1} a + eta_{i+1} S_{i+1} c, c' = B_{i+1} c.
+//
+// FFT route (n_i + 1 = K = 2^p): the Toeplitz product S_i x uses the circulant embedding of
+// length 2K and the DST-I of length n_i the odd extension of length 2K; both real transforms of
+// length 2K run as one complex FFT of length K (in-place radix-4 decimation in frequency, whose
+// digit-reversed output is read through dif_pos(); the inverse is the mirrored decimation in
+// time, so no reordering pass is needed).  Dense route (any n_i): explicit O(n_i) sums per output.
+#include "tau_internal.cuh"
+
+#include <math.h>
+
+namespace tau {
+
+constexpr int PASS_THREADS = 128;
+
+// ---------------------------------------------------------------------------
+// complex helpers (FP64)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }  // -i a
+__device__ __forceinline__ double2 mul_pi(double2 a) { return make_double2(-a.y, a.x); }  // +i a
+
+// Position of DFT output k after the in-place radix-4 (final radix-2 when log2 K is odd) DIF.
+__device__ __forceinline__ int dif_pos(int k, int K) {
+  int pos = 0, size = K;
+  while (size > 2) {
+    pos += (k & 3) * (size >> 2);
+    k >>= 2;
+    size >>= 2;
+  }
+  if (size == 2) pos += k;
+  return pos;
+}
+
+// Forward complex DFT of length K (natural order in, digit-reversed out) on nl lines stored at
+// cb + l*cs.  Caller synchronises before; this synchronises after.
+__device__ void fft_dif(double2* cb, int cs, int nl, int K, const double2* __restrict__ tw) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  int size = K;
+  for (; size >= 4; size >>= 2) {
+    const int q = size >> 2;
+    const int tstep = TWN / size;
+    const int nb = K >> 2;
+    for (int b = tid; b < nl * nb; b += T) {
+      const int l = b / nb, loc = b - l * nb;
+      const int g = loc / q, i = loc - g * q;
+      double2* x = cb + l * cs + g * size + i;
+      const double2 a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
+      const double2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), b3 = mul_mi(csub(a1, a3));
+      x[0] = cadd(b0, b2);
+      if (i == 0) {
+        x[q] = cadd(b1, b3);
+        x[2 * q] = csub(b0, b2);
+        x[3 * q] = csub(b1, b3);
+      } else {
+        x[q] = cmul(cadd(b1, b3), __ldg(&tw[i * tstep]));
+        x[2 * q] = cmul(csub(b0, b2), __ldg(&tw[2 * i * tstep]));
+        x[3 * q] = cmul(csub(b1, b3), __ldg(&tw[3 * i * tstep]));
+      }
+    }
+    __syncthreads();
+  }
+  if (size == 2) {
+    const int nb = K >> 1;
+    for (int b = tid; b < nl * nb; b += T) {
+      const int l = b / nb, loc = b - l * nb;
+      double2* x = cb + l * cs + 2 * loc;
+      const double2 a0 = x[0], a1 = x[1];
+      x[0] = cadd(a0, a1);
+      x[1] = csub(a0, a1);
+    }
+    __syncthreads();
+  }
+}
+
+// Unnormalised inverse DFT (times K): digit-reversed in, natural order out.
+__device__ void fft_dit_inv(double2* cb, int cs, int nl, int K, const double2* __restrict__ tw) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int lg = 31 - __clz(K);
+  int size = 4;
+  if (lg & 1) {
+    const int nb = K >> 1;
+    for (int b = tid; b < nl * nb; b += T) {
+      const int l = b / nb, loc = b - l * nb;
+      double2* x = cb + l * cs + 2 * loc;
+      const double2 a0 = x[0], a1 = x[1];
+      x[0] = cadd(a0, a1);
+      x[1] = csub(a0, a1);
+    }
+    __syncthreads();
+    size = 8;
+  }
+  for (; size <= K; size <<= 2) {
+    const int q = size >> 2;
+    const int tstep = TWN / size;
+    const int nb = K >> 2;
+    for (int b = tid; b < nl * nb; b += T) {
+      const int l = b / nb, loc = b - l * nb;
+      const int g = loc / q, i = loc - g * q;
+      double2* x = cb + l * cs + g * size + i;
+      double2 y0 = x[0], y1 = x[q], y2 = x[2 * q], y3 = x[3 * q];
+      if (i != 0) {
+        y1 = cmulc(y1, __ldg(&tw[i * tstep]));
+        y2 = cmulc(y2, __ldg(&tw[2 * i * tstep]));
+        y3 = cmulc(y3, __ldg(&tw[3 * i * tstep]));
+      }
+      const double2 c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
+      x[0] = cadd(c0, c2);
+      x[q] = cadd(c1, c3);
+      x[2 * q] = csub(c0, c2);
+      x[3 * q] = csub(c1, c3);
+    }
+    __syncthreads();
+  }
+}
+
+// Multiply the length-2K real DFT Y of the packed sequence by the real symmetric circulant
+// spectrum lambda, working on the packed half-length DFT Z in place:
+//   E2 = Z_k + conj Z_{K-k},  O2 = -i (Z_k - conj Z_{K-k}),  Y_k = (E2 + W_k O2)/2,
+//   W_k = exp(-i pi k / K).  spec[k] = ((lam_k + lam_{K-k})/(4K), (lam_k - lam_{K-k})/(4K)).
+__device__ void toep_spectral(double2* cb, int cs, int nl, int K, const double2* __restrict__ spec,
+                              const double2* __restrict__ tw) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int np = K / 2 + 1;
+  const int wstep = TWN / (2 * K);
+  for (int b = tid; b < nl * np; b += T) {
+    const int l = b / np, k = b - l * np;
+    const int kk = (K - k) & (K - 1);
+    double2* x = cb + l * cs;
+    const int pk = dif_pos(k, K), pkk = dif_pos(kk, K);
+    const double2 A = x[pk], B = x[pkk];
+    const double2 E2 = make_double2(A.x + B.x, A.y - B.y);
+    const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
+    const double2 W = __ldg(&tw[k * wstep]);
+    const double2 P = cmul(W, O2);
+    const double2 sd = __ldg(&spec[k]);
+    const double2 Ep = make_double2(fma(sd.x, E2.x, sd.y * P.x), fma(sd.x, E2.y, sd.y * P.y));
+    const double2 WcE = cmulc(E2, W);
+    const double2 Op = make_double2(fma(sd.y, WcE.x, sd.x * O2.x), fma(sd.y, WcE.y, sd.x * O2.y));
+    x[pk] = make_double2(Ep.x - Op.y, Ep.y + Op.x);
+    if (kk != k) x[pkk] = make_double2(Ep.x + Op.y, Op.x - Ep.y);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// tile geometry
+// ---------------------------------------------------------------------------
+struct TileGeo {
+  int64_t base;   // address of element (l=0, j=0)
+  int64_t lstep;  // address step between lines of the tile
+  int64_t jstep;  // address step along a line
+  int nvalid;     // number of valid lines in the tile
+};
+
+__device__ __forceinline__ TileGeo tile_geo(const Pass& P, int64_t tile) {
+  TileGeo t;
+  const int64_t N = P.len;
+  if (P.ax == 0) {
+    const int64_t l0 = tile * P.lpb;
+    t.base = l0 * N;
+    t.lstep = N;
+    t.jstep = 1;
+    const int64_t rem = P.nlines - l0;
+    t.nvalid = (int)(rem < P.lpb ? rem : P.lpb);
+  } else {
+    const int64_t tpo = (P.inner + P.lpb - 1) / P.lpb;
+    const int64_t o = tile / tpo;
+    const int64_t c0 = (tile - o * tpo) * P.lpb;
+    t.base = o * N * P.inner + c0;
+    t.lstep = 1;
+    t.jstep = P.inner;
+    const int64_t rem = P.inner - c0;
+    t.nvalid = (int)(rem < P.lpb ? rem : P.lpb);
+  }
+  return t;
+}
+
+// sm[l*N + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
+__device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const double* __restrict__ g,
+                                          double* sm) {
+  const int tot = lpb * N;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int l, j;
+    if (t.jstep == 1) {
+      l = idx / N;
+      j = idx - l * N;
+    } else {
+      j = idx / lpb;
+      l = idx - j * lpb;
+    }
+    sm[l * N + j] = (l < t.nvalid) ? g[t.base + l * t.lstep + (int64_t)j * t.jstep] : 0.0;
+  }
+}
+
+__device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const double* sm, double* g) {
+  const int tot = lpb * N;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int l, j;
+    if (t.jstep == 1) {
+      l = idx / N;
+      j = idx - l * N;
+    } else {
+      j = idx / lpb;
+      l = idx - j * lpb;
+    }
+    if (l < t.nvalid) g[t.base + l * t.lstep + (int64_t)j * t.jstep] = sm[l * N + j];
+  }
+}
+
+__device__ __forceinline__ int tile_index(const TileGeo& t, int N, int lpb, int idx, int& l, int& j) {
+  if (t.jstep == 1) {
+    l = idx / N;
+    j = idx - l * N;
+  } else {
+    j = idx / lpb;
+    l = idx - j * lpb;
+  }
+  return l;
+}
+
+// B_{alpha} along the line (3-point stencil of 𝓗_alpha, zero beyond the interior).
+__device__ __forceinline__ double stencil_B(const double* row, int j, int N, double bd, double bo) {
+  const double lft = j > 0 ? row[j - 1] : 0.0;
+  const double rgt = j + 1 < N ? row[j + 1] : 0.0;
+  return fma(bd, row[j], bo * (lft + rgt));
+}
+
+// ---------------------------------------------------------------------------
+// per-line transforms on shared memory
+// ---------------------------------------------------------------------------
+// Toeplitz product T x for every line: x in xs[l*N + j], result written to ts[l*N + j].
+// ts may alias xs.  FFT route uses cb (lpb lines of K complex).
+__device__ void toeplitz_lines(const Pass& P, const double* xs, double* ts, double2* cb) {
+  const int N = P.len, lpb = P.lpb;
+  const int T = blockDim.x, tid = threadIdx.x;
+  if (P.dim.route == ROUTE_FFT) {
+    const int K = P.dim.K;
+    // pack y_t = x_t (t < N), 0 otherwise, as z_j = (y_2j, y_2j+1)
+    for (int b = tid; b < lpb * K; b += T) {
+      const int l = b / K, jj = b - l * K;
+      const int t0 = 2 * jj, t1 = 2 * jj + 1;
+      const double* row = xs + l * N;
+      cb[l * K + jj] = make_double2(t0 < N ? row[t0] : 0.0, t1 < N ? row[t1] : 0.0);
+    }
+    __syncthreads();
+    fft_dif(cb, K, lpb, K, P.tw);
+    toep_spectral(cb, K, lpb, K, P.dim.spec, P.tw);
+    fft_dit_inv(cb, K, lpb, K, P.tw);
+    for (int b = tid; b < lpb * N; b += T) {
+      const int l = b / N, t = b - l * N;
+      const double2 z = cb[l * K + (t >> 1)];
+      ts[l * N + t] = (t & 1) ? z.y : z.x;
+    }
+    __syncthreads();
+  } else {
+    const double* __restrict__ s = P.dim.s;
+    double acc[8];
+    // dense: (T x)_a = sum_b s_|a-b| x_b; each thread accumulates its outputs in registers first
+    // so ts may alias xs.
+    const int tot = lpb * N;
+    for (int base = 0; base < tot; base += 8 * T) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * T + tid;
+        acc[r] = 0.0;
+        if (idx < tot) {
+          const int l = idx / N, a = idx - l * N;
+          const double* row = xs + l * N;
+          double sacc = 0.0;
+          for (int bb = 0; bb < N; ++bb) sacc = fma(__ldg(&s[abs(a - bb)]), row[bb], sacc);
+          acc[r] = sacc;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * T + tid;
+        if (idx < tot) ts[idx] = acc[r];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Orthonormal DST-I of every line in place: xs[l*N + j] holds x_{j+1}; result y_{k} at xs[l*N + k-1].
+__device__ void dst_lines(const Pass& P, double* xs, double2* cb) {
+  const int N = P.len, lpb = P.lpb;
+  const int T = blockDim.x, tid = threadIdx.x;
+  if (P.dim.route == ROUTE_FFT) {
+    const int K = P.dim.K;
+    // odd extension y_0 = 0, y_t = x_t (1 <= t <= N), y_K = 0, y_t = -x_{2K-t}; packed in pairs
+    for (int b = tid; b < lpb * K; b += T) {
+      const int l = b / K, jj = b - l * K;
+      const double* row = xs + l * N;
+      double v[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int t = 2 * jj + r;
+        v[r] = (t == 0 || t == K) ? 0.0 : (t < K ? row[t - 1] : -row[2 * K - t - 1]);
+      }
+      cb[l * K + jj] = make_double2(v[0], v[1]);
+    }
+    __syncthreads();
+    fft_dif(cb, K, lpb, K, P.tw);
+    // y_k = -Im(Y_k) / sqrt(2K), Y_k = (E2 + W_k O2)/2, and Y_{K-k} = conj(E2 - W_k O2)/2
+    const double sc = 0.5 * rsqrt(2.0 * (double)K);
+    const int np = K / 2;  // k = 1..K/2
+    const int wstep = TWN / (2 * K);
+    for (int b = tid; b < lpb * np; b += T) {
+      const int l = b / np, k = b - l * np + 1;
+      const int kk = K - k;
+      const double2* x = cb + l * K;
+      const double2 A = x[dif_pos(k, K)], B = x[dif_pos(kk & (K - 1), K)];
+      const double imE2 = A.y - B.y;
+      const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
+      const double2 W = __ldg(&P.tw[k * wstep]);
+      const double imP = fma(W.x, O2.y, W.y * O2.x);
+      double* row = xs + l * N;
+      row[k - 1] = -sc * (imE2 + imP);
+      if (kk != k) row[kk - 1] = sc * (imE2 - imP);
+    }
+    __syncthreads();
+  } else {
+    const int K = P.dim.K;
+    const double* __restrict__ st = P.dim.sintab;
+    const double sc = sqrt(2.0 / (double)K);
+    double acc[8];
+    const int tot = lpb * N;
+    for (int base = 0; base < tot; base += 8 * T) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * T + tid;
+        acc[r] = 0.0;
+        if (idx < tot) {
+          const int l = idx / N, k = idx - l * N + 1;
+          const double* row = xs + l * N;
+          double sacc = 0.0;
+          int ph = k;  // (j * k) mod 2K for j = 1
+          for (int j = 1; j <= N; ++j) {
+            sacc = fma(__ldg(&st[ph]), row[j - 1], sacc);
+            ph += k;
+            if (ph >= 2 * K) ph -= 2 * K;
+          }
+          acc[r] = sc * sacc;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = base + r * T + tid;
+        if (idx < tot) xs[idx] = acc[r];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the line-pass kernel
+// ---------------------------------------------------------------------------
+// Shared memory: ra, rc (lpb*N doubles each) then cb (lpb*K complex, FFT route).
+__global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = P.len, lpb = P.lpb;
+  double* ra = reinterpret_cast<double*>(smraw);
+  double* rc = ra + lpb * N;
+  double2* cb = reinterpret_cast<double2*>(rc + lpb * N + ((lpb * N) & 1));
+  if (P.g && P.g->done) return;
+  const TileGeo tg = tile_geo(P, blockIdx.x);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int tot = lpb * N;
+  const double* in_a = P.in_a;
+  double* out_a = P.out_a;
+  if (P.in_sel) in_a = P.vbase + (int64_t)(P.g->j + P.in_sel - 1) * P.vstride;
+  if (P.out_sel) out_a = P.vbase + (int64_t)(P.g->j + P.out_sel - 1) * P.vstride;
+
+  if (P.toep_only) {
+    tile_load(tg, N, lpb, in_a, ra);
+    __syncthreads();
+    toeplitz_lines(P, ra, ra, cb);
+    tile_store(tg, N, lpb, ra, out_a);
+    return;
+  }
+
+  if (P.mv) {
+    tile_load(tg, N, lpb, in_a, ra);
+    tile_load(tg, N, lpb, P.in_c, rc);
+    __syncthreads();
+    const double bd = P.dim.bdiag, bo = P.dim.boff;
+    if (P.first) {
+      // ra = x, rc = e  ->  ra = e∘x (kept), rc = x (Toeplitz input), c_out = B x
+      for (int idx = tid; idx < tot; idx += T) {
+        const double x = ra[idx];
+        const double e = rc[idx];
+        rc[idx] = x;
+        ra[idx] = e * x;
+      }
+      __syncthreads();
+    }
+    // Toeplitz of channel c into cb-backed scratch: result t_j kept in registers below.
+    // First compute c_out = B c (needs c before it is overwritten), stream it to global.
+    if (!P.last) {
+      for (int idx = tid; idx < tot; idx += T) {
+        int l, j;
+        tile_index(tg, N, lpb, idx, l, j);
+        const double v = stencil_B(rc + l * N, j, N, bd, bo);
+        if (l < tg.nvalid) P.out_c[tg.base + l * tg.lstep + (int64_t)j * tg.jstep] = v;
+      }
+    }
+    // value = B a + seta * T c; computed in register batches, then written into rc.
+    __syncthreads();
+    // T c in place (rc <- T c); B a needs ra intact.
+    toeplitz_lines(P, rc, rc, cb);
+    for (int idx = tid; idx < tot; idx += T) {
+      const int l = idx / N, j = idx - l * N;
+      const double ba = stencil_B(ra + l * N, j, N, bd, bo);
+      rc[idx] = fma(P.seta, rc[idx], ba);
+    }
+    __syncthreads();
+    if (!P.last) {
+      tile_store(tg, N, lpb, rc, out_a);
+      return;
+    }
+    if (P.finish == FIN_ADD_F || P.finish == FIN_RESID) {
+      tile_load(tg, N, lpb, P.src, ra);
+      __syncthreads();
+      for (int idx = tid; idx < tot; idx += T)
+        rc[idx] = (P.finish == FIN_ADD_F) ? rc[idx] + ra[idx] : ra[idx] - rc[idx];
+      __syncthreads();
+    }
+    // fall through to post-processing of rc
+  } else {
+    tile_load(tg, N, lpb, in_a, rc);
+    __syncthreads();
+  }
+
+  if (P.post == POST_DST || P.post == POST_DST_MU_DST) {
+    dst_lines(P, rc, cb);
+    if (P.post == POST_DST_MU_DST) {
+      tile_load(tg, N, lpb, P.invmu, ra);
+      __syncthreads();
+      for (int idx = tid; idx < tot; idx += T) rc[idx] *= ra[idx];
+      __syncthreads();
+      dst_lines(P, rc, cb);
+    }
+  }
+  tile_store(tg, N, lpb, rc, out_a);
+}
+
+size_t pass_smem_bytes(const Pass& p) {
+  const size_t real = (size_t)p.lpb * p.len;
+  size_t bytes = 2 * real * sizeof(double) + ((real & 1) ? sizeof(double) : 0);
+  if (p.dim.route == ROUTE_FFT) bytes += (size_t)p.lpb * p.dim.K * sizeof(double2);
+  return bytes;
+}
+
+__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ tw);
+
+cudaError_t init_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+cudaError_t launch_pass(const Pass& p, cudaStream_t st) {
+  if (p.ntiles <= 0) return cudaSuccess;
+  const size_t smem = pass_smem_bytes(p);
+  k_pass<<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// setup: circulant spectrum lambda_k = DFT_{2K}(c)_k, k = 0..K (c real symmetric)
+// ---------------------------------------------------------------------------
+__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* cb = reinterpret_cast<double2*>(smraw);
+  for (int j = threadIdx.x; j < K; j += blockDim.x) cb[j] = make_double2(c[2 * j], c[2 * j + 1]);
+  __syncthreads();
+  fft_dif(cb, K, 1, K, tw);
+  const int wstep = TWN / (2 * K);
+  for (int k = threadIdx.x; k <= K / 2; k += blockDim.x) {
+    const int kk = (K - k) & (K - 1);
+    const double2 A = cb[dif_pos(k, K)], B = cb[dif_pos(kk, K)];
+    const double2 E2 = make_double2(A.x + B.x, A.y - B.y);
+    const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
+    const double2 W = tw[k * wstep];
+    const double2 P = cmul(W, O2);
+    lam[k] = 0.5 * (E2.x + P.x);          // Re Y_k
+    if (k == 0) lam[K] = 0.5 * (E2.x - P.x);  // Y_K = conj(E2 - W O2)/2 at k = 0
+    else if (kk != k) lam[K - k] = 0.5 * (E2.x - P.x);
+  }
+}
+
+cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* tw, cudaStream_t st) {
+  const size_t smem = (size_t)K * sizeof(double2);
+  k_spectrum<<<1, PASS_THREADS, smem, st>>>(K, c, lam, tw);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// fields of step m: e_m = e(G, t_{m+1/2}), Fdt = dt * F^{(m+1/2)}
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void unflatten(int64_t idx, int d, const int* n, int* j) {
+  for (int i = 0; i < d; ++i) {
+    const int64_t q = idx / n[i];
+    j[i] = (int)(idx - q * n[i]);
+    idx = q;
+  }
+}
+
+__global__ void k_fields(const FieldDev F, const GmresDev* __restrict__ g, int64_t m_override, double* e_out,
+                         double* fdt_out) {
+  const int64_t m = m_override >= 0 ? m_override : g->m;
+  const double* etc = F.e_tc + m * F.re;
+  const double* ftc = F.f_tc + m * F.rf;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    unflatten(idx, F.d, F.n, j);
+    double ev = 0.0;
+    for (int r = 0; r < F.re; ++r) {
+      double p = etc[r];
+      for (int i = 0; i < F.d; ++i) p *= F.e_sp[i][r * (F.n[i] + 2) + j[i] + 1];
+      ev += p;
+    }
+    double fv = 0.0;
+    for (int r = 0; r < F.rf; ++r) {
+      double p = ftc[r];
+      for (int i = 0; i < F.d; ++i) p *= F.f_hsp[i][r * F.n[i] + j[i]];
+      fv += p;
+    }
+    if (e_out) e_out[idx] = ev;
+    if (fdt_out) fdt_out[idx] = F.dt * fv;
+  }
+}
+
+cudaError_t launch_fields(const FieldDev& f, const GmresDev* g, int64_t m_override, double* e_out, double* fdt_out,
+                          cudaStream_t st) {
+  int64_t blocks = (f.n_tot + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  k_fields<<<(unsigned)blocks, 256, 0, st>>>(f, g, m_override, e_out, fdt_out);
+  return cudaGetLastError();
+}
+
+struct PsiArgs {
+  int d;
+  int n[3];
+  int64_t n_tot;
+  int rank;
+  const double* tc;
+  const double* sp[3];
+};
+
+__global__ void k_psi(const PsiArgs a, double* out) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.n_tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    unflatten(idx, a.d, a.n, j);
+    double v = 0.0;
+    for (int r = 0; r < a.rank; ++r) {
+      double p = a.tc[r];
+      for (int i = 0; i < a.d; ++i) p *= a.sp[i][r * (a.n[i] + 2) + j[i] + 1];
+      v += p;
+    }
+    out[idx] = v;
+  }
+}
+
+cudaError_t launch_psi(int d, const int* n, int64_t n_tot, int rank, const double* tc, const double* const* sp,
+                       double* out, cudaStream_t st) {
+  PsiArgs a;
+  a.d = d;
+  a.n_tot = n_tot;
+  a.rank = rank;
+  a.tc = tc;
+  for (int i = 0; i < 3; ++i) {
+    a.n[i] = i < d ? n[i] : 1;
+    a.sp[i] = i < d ? sp[i] : nullptr;
+  }
+  int64_t blocks = (n_tot + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  k_psi<<<(unsigned)blocks, 256, 0, st>>>(a, out);
+  return cudaGetLastError();
+}
+
+// min / max of e over the interior grid and all half steps (Eq. (dhat)); block partials.
+__global__ void k_escan(const FieldDev F, int64_t M, double* partial) {
+  __shared__ double smax[256], smin[256];
+  double hi = -INFINITY, lo = INFINITY;
+  const int64_t total = F.n_tot * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = t / F.n_tot;
+    const int64_t idx = t - m * F.n_tot;
+    int j[3] = {0, 0, 0};
+    unflatten(idx, F.d, F.n, j);
+    const double* etc = F.e_tc + m * F.re;
+    double ev = 0.0;
+    for (int r = 0; r < F.re; ++r) {
+      double p = etc[r];
+      for (int i = 0; i < F.d; ++i) p *= F.e_sp[i][r * (F.n[i] + 2) + j[i] + 1];
+      ev += p;
+    }
+    hi = fmax(hi, ev);
+    lo = fmin(lo, ev);
+  }
+  smax[threadIdx.x] = hi;
+  smin[threadIdx.x] = lo;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = smax[0];
+    partial[2 * blockIdx.x + 1] = smin[0];
+  }
+}
+
+cudaError_t launch_escan(const FieldDev& f, int64_t M, double* partial, cudaStream_t st) {
+  k_escan<<<RED_BLOCKS, 256, 0, st>>>(f, M, partial);
+  return cudaGetLastError();
+}
+
+struct MuArgs {
+  int d;
+  int n[3];
+  int64_t n_tot;
+  double ebar;
+  const double* beta[3];
+  const double* q[3];
+  double eta[3];
+};
+
+// 1/mu with mu_J = ebar prod_i beta_i + sum_i eta_i q_i prod_{l!=i} beta_l (Lemma le:eig).
+__global__ void k_invmu(const MuArgs a, double* invmu) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.n_tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    unflatten(idx, a.d, a.n, j);
+    double bprod = 1.0;
+    for (int i = 0; i < a.d; ++i) bprod *= a.beta[i][j[i]];
+    double mu = a.ebar * bprod;
+    for (int i = 0; i < a.d; ++i) {
+      double p = a.eta[i] * a.q[i][j[i]];
+      for (int l = 0; l < a.d; ++l)
+        if (l != i) p *= a.beta[l][j[l]];
+      mu += p;
+    }
+    invmu[idx] = 1.0 / mu;
+  }
+}
+
+cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
+                         const double* const* q, const double* eta, double* invmu, cudaStream_t st) {
+  MuArgs a;
+  a.d = d;
+  a.n_tot = n_tot;
+  a.ebar = ebar;
+  for (int i = 0; i < 3; ++i) {
+    a.n[i] = i < d ? n[i] : 1;
+    a.beta[i] = i < d ? beta[i] : nullptr;
+    a.q[i] = i < d ? q[i] : nullptr;
+    a.eta[i] = i < d ? eta[i] : 0.0;
+  }
+  int64_t blocks = (n_tot + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  k_invmu<<<(unsigned)blocks, 256, 0, st>>>(a, invmu);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// GMRES: classical Gram-Schmidt with one re-orthogonalisation (CGS2), Givens rotations
+// ---------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+constexpr int DOT_CHUNK = 4;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;  // valid in thread 0
+}
+
+// partial[i * ld + blockIdx.x] = sum_{this block's elements} w * V_i, i = 0..j
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const double* __restrict__ V, int64_t n,
+                                                      const GmresDev* __restrict__ g, double* partial, int ld) {
+  __shared__ double sh[32];
+  if (g->done) return;
+  const int jj = g->j;
+  const double* __restrict__ w = V + (int64_t)(jj + 1) * n;
+  for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
+    double acc[DOT_CHUNK] = {0.0, 0.0, 0.0, 0.0};
+    const int ni = min(DOT_CHUNK, jj + 1 - i0);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+      const double wv = w[idx];
+#pragma unroll
+      for (int r = 0; r < DOT_CHUNK; ++r)
+        if (r < ni) acc[r] = fma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < DOT_CHUNK; ++r) {
+      if (r < ni) {
+        const double s = block_sum(acc[r], sh);
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
+      }
+    }
+  }
+}
+
+cudaError_t launch_dots(const double* V, int64_t n, const GmresDev* g, double* partial, int ld, cudaStream_t st) {
+  k_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, partial, ld);
+  return cudaGetLastError();
+}
+
+// h[i] = sum_b partial[i * ld + b], i = 0..j (one warp per i)
+__global__ void k_reduce_dots(const double* __restrict__ partial, int ld, const GmresDev* __restrict__ g, double* h) {
+  if (g->done) return;
+  const int jj = g->j;
+  const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  const int nw = blockDim.x >> 5;
+  for (int i = warp; i <= jj; i += nw) {
+    double s = 0.0;
+    for (int b = ln; b < RED_BLOCKS; b += 32) s += partial[(int64_t)i * ld + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (ln == 0) h[i] = s;
+  }
+}
+
+cudaError_t launch_reduce_dots(const double* partial, int ld, const GmresDev* g, double* h, cudaStream_t st) {
+  k_reduce_dots<<<1, 1024, 0, st>>>(partial, ld, g, h);
+  return cudaGetLastError();
+}
+
+// w -= sum_i h_i V_i; then either partial dots with V_i (CGS2 second pass) or partial ||w||^2.
+__global__ void __launch_bounds__(RED_THREADS) k_update_dots(double* V, int64_t n, const GmresDev* __restrict__ g,
+                                                             const double* __restrict__ h, double* partial, int ld,
+                                                             int want_norm) {
+  __shared__ double sh[32];
+  __shared__ double hs[MAX_ITER_CAP + 1];
+  if (g->done) return;
+  const int jj = g->j;
+  double* w = V + (int64_t)(jj + 1) * n;
+  for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = h[i];
+  __syncthreads();
+  double nacc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double wv = w[idx];
+    for (int i = 0; i <= jj; ++i) wv = fma(-hs[i], V[(int64_t)i * n + idx], wv);
+    w[idx] = wv;
+    nacc = fma(wv, wv, nacc);
+  }
+  if (want_norm) {
+    const double s = block_sum(nacc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    return;
+  }
+  __syncthreads();
+  // second Gram-Schmidt pass: dots of the updated w (this block's elements) with V_i
+  for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
+    double acc[DOT_CHUNK] = {0.0, 0.0, 0.0, 0.0};
+    const int ni = min(DOT_CHUNK, jj + 1 - i0);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+      const double wv = w[idx];
+#pragma unroll
+      for (int r = 0; r < DOT_CHUNK; ++r)
+        if (r < ni) acc[r] = fma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < DOT_CHUNK; ++r) {
+      if (r < ni) {
+        const double s = block_sum(acc[r], sh);
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
+      }
+    }
+  }
+}
+
+cudaError_t launch_update_dots(double* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld,
+                               int want_norm, cudaStream_t st) {
+  k_update_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, want_norm);
+  return cudaGetLastError();
+}
+
+// Column j of the Hessenberg matrix: h1 + h2 (CGS2), ||w||; previous rotations, new rotation,
+// residual estimate |g_{j+1}|, stopping test ||r_j|| <= tol ||r_0|| (§4), cap and breakdown.
+__global__ void k_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* __restrict__ h1,
+                         const double* __restrict__ h2, const double* __restrict__ pnorm, int ldH,
+                         cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double sh[32];
+  if (g->done) {
+    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const int j = g->j;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += pnorm[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x != 0) return;
+  const double hn = sqrt(s);
+  double* col = H + (int64_t)j * ldH;
+  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rr = hypot(col[j], col[j + 1]);
+  double c = 1.0, sgv = 0.0;
+  if (rr > 0.0) {
+    c = col[j] / rr;
+    sgv = col[j + 1] / rr;
+  }
+  cs[j] = c;
+  sn[j] = sgv;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  gv[j + 1] = -sgv * gv[j];
+  gv[j] = c * gv[j];
+  const double res = fabs(gv[j + 1]);
+  g->hnorm = hn;
+  g->relres = res / g->beta;
+  const bool conv = res <= g->tol * g->beta;
+  const bool cap = (j + 1) >= g->max_iter;
+  const bool brk = !(hn > 0.0);
+  if (conv || cap || brk) {
+    g->done = 1;
+    g->k = j + 1;
+    if (!conv && !brk) g->notconv = 1;
+    if (use_cond) cudaGraphSetConditional(cond, 0);
+  } else {
+    g->j = j + 1;
+    if (use_cond) cudaGraphSetConditional(cond, 1);
+  }
+}
+
+cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* h1,
+                          const double* h2, const double* pnorm, int ldH, cudaGraphConditionalHandle cond,
+                          int use_cond, cudaStream_t st) {
+  k_givens<<<1, 256, 0, st>>>(g, H, cs, sn, gv, h1, h2, pnorm, ldH, cond, use_cond);
+  return cudaGetLastError();
+}
+
+// V_{j} <- w / ||w|| where w sits in the slot of V_j (after k_givens advanced j). When the
+// column closed the iteration (done), nothing is scaled.
+__global__ void k_scale_next(double* V, int64_t n, const GmresDev* __restrict__ g) {
+  if (g->done) return;
+  const int j = g->j;
+  const double inv = 1.0 / g->hnorm;
+  double* v = V + (int64_t)j * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    v[idx] *= inv;
+}
+
+cudaError_t launch_scale_next(double* V, int64_t n, const GmresDev* g, cudaStream_t st) {
+  k_scale_next<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const double* __restrict__ w, int64_t n, double* partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(w[idx], w[idx], acc);
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+cudaError_t launch_norm_partial(const double* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st) {
+  (void)g;
+  k_norm_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(w, n, partial);
+  return cudaGetLastError();
+}
+
+// beta = ||r_0||, g_0 = beta, j = 0; done if beta == 0.
+__global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, double* gv) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += partial[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    const double beta = sqrt(s);
+    g->beta = beta;
+    g->j = 0;
+    g->k = 0;
+    g->relres = 0.0;
+    g->hnorm = beta;
+    gv[0] = beta;
+    g->done = beta > 0.0 ? 0 : 1;
+  }
+}
+
+__global__ void k_scale_first(double* V, int64_t n, const GmresDev* __restrict__ g) {
+  if (g->done) return;
+  const double inv = 1.0 / g->beta;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+    V[idx] *= inv;
+}
+
+cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, double* V, int64_t n, cudaStream_t st) {
+  k_init_beta<<<1, 256, 0, st>>>(g, partial, gv);
+  k_scale_first<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+  return cudaGetLastError();
+}
+
+// y = R^{-1} g (upper triangular k x k in H after the rotations), then u = x0 + V_k y.
+__global__ void k_backsolve(GmresDev* g, const double* __restrict__ H, const double* __restrict__ gv, int ldH,
+                            double* y, int* iters_log) {
+  if (threadIdx.x != 0) return;
+  const int k = g->k;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = gv[i];
+    for (int c = i + 1; c < k; ++c) acc -= H[(int64_t)c * ldH + i] * y[c];
+    y[i] = acc / H[(int64_t)i * ldH + i];
+  }
+  if (iters_log) iters_log[g->m] = k;
+}
+
+__global__ void k_update_solution(const GmresDev* __restrict__ g, const double* __restrict__ y,
+                                  const double* __restrict__ V, int64_t n, double* u, int x0_prev) {
+  __shared__ double ys[MAX_ITER_CAP];
+  const int k = g->k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double v = x0_prev ? u[idx] : 0.0;
+    for (int i = 0; i < k; ++i) v = fma(ys[i], V[(int64_t)i * n + idx], v);
+    u[idx] = v;
+  }
+}
+
+__global__ void k_advance(GmresDev* g) {
+  if (threadIdx.x == 0) g->m += 1;
+}
+
+cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y,
+                                    const double* V, int64_t n, double* u, int x0_prev, int* iters_log,
+                                    cudaStream_t st) {
+  k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, iters_log);
+  k_update_solution<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
+  k_advance<<<1, 32, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe (bounded loop; 8 independent chains per thread)
+// ---------------------------------------------------------------------------
+__global__ void k_fp64_peak(double* out, int iters) {
+  double x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = (double)(threadIdx.x + c);
+  const double a = 0.999999, b = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fp64_peak(double* out, int blocks, int iters, cudaStream_t st) {
+  k_fp64_peak<<<blocks, 256, 0, st>>>(out, iters);
+  return cudaGetLastError();
+}
+
+}  // namespace tau

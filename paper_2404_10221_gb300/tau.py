@@ -1,0 +1,330 @@
+"""Thin ctypes binding of libtau_rsfde.so (include/tau_rsfde.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Device vectors are torch CUDA tensors (FP64, contiguous); the stream is torch's
+current stream unless given.  There is no CPU fallback: loading fails loudly if
+the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtau_rsfde.so")
+
+TAU_OK = 0
+TAU_EINVAL = -1
+TAU_ECUDA = -2
+TAU_ENOMEM = -3
+TAU_ETIMEOUT = -4
+TAU_ESTATE = -5
+TAU_EUNSUPPORTED = -6
+TAU_ENOTCONV = -7
+TAU_X0_ZERO = 0
+TAU_X0_PREV = 1
+TAU_FP64 = 0
+TAU_ROUTE_AUTO = 0
+TAU_ROUTE_FFT = 1
+TAU_ROUTE_DENSE = 2
+
+
+class tau_problem_desc(C.Structure):
+    _fields_ = [
+        ("d", C.c_int),
+        ("n", C.c_int64 * 3),
+        ("L", C.c_double * 3),
+        ("R", C.c_double * 3),
+        ("alpha", C.c_double * 3),
+        ("kappa", C.c_double * 3),
+        ("T", C.c_double),
+        ("M", C.c_int64),
+        ("tol", C.c_double),
+        ("max_iter", C.c_int),
+        ("x0_mode", C.c_int),
+        ("precision", C.c_int),
+        ("route", C.c_int * 3),
+        ("e_min", C.c_double),
+        ("e_max", C.c_double),
+    ]
+
+
+class tau_field(C.Structure):
+    _fields_ = [
+        ("rank", C.c_int),
+        ("n_times", C.c_int64),
+        ("time_coef", C.POINTER(C.c_double)),
+        ("space", C.POINTER(C.c_double) * 3),
+    ]
+
+
+class tau_stats(C.Structure):
+    _fields_ = [
+        ("steps_done", C.c_int64),
+        ("total_iters", C.c_int64),
+        ("last_iters", C.c_int),
+        ("max_iters_step", C.c_int),
+        ("last_relres", C.c_double),
+        ("ebar", C.c_double),
+        ("e_hat", C.c_double),
+        ("e_check", C.c_double),
+        ("route", C.c_int * 3),
+        ("graph", C.c_int),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class TauError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tau status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        D = C.POINTER(C.c_double)
+        sigs = {
+            "tau_create": [C.POINTER(tau_problem_desc), P, C.POINTER(P)],
+            "tau_set_fields": [P, C.POINTER(tau_field), C.POINTER(tau_field), C.POINTER(tau_field)],
+            "tau_setup": [P],
+            "tau_step": [P, C.c_int64],
+            "tau_solve": [P],
+            "tau_sync": [P],
+            "tau_get_solution": [P, P, C.c_int, C.POINTER(C.c_int64)],
+            "tau_set_solution": [P, P, C.c_int, C.c_int64],
+            "tau_get_stats": [P, C.POINTER(tau_stats)],
+            "tau_get_iters": [P, C.POINTER(C.c_int), C.c_int64],
+            "tau_destroy": [P],
+            "tau_apply_A": [P, C.c_int64, P, P],
+            "tau_apply_Minv": [P, P, P],
+            "tau_apply_MinvA": [P, C.c_int64, P, P],
+            "tau_rhs": [P, C.c_int64, P, P],
+            "tau_dst": [P, P, P],
+            "tau_toeplitz_mode": [P, C.c_int, P, P],
+            "tau_get_ebar": [P, D, D, D],
+            "tau_measure_fp64_peak": [P, D],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.tau_last_error.argtypes = []
+        L.tau_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, allow=()):
+    if status != TAU_OK and status not in allow:
+        msg = lib().tau_last_error().decode(errors="replace")
+        raise TauError(status, msg)
+    return status
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous FP64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    if stream is not None:
+        return int(stream)
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
+              e_bounds: Optional[tuple] = None) -> tau_problem_desc:
+    """tau_problem_desc from a workloads.Problem."""
+    d = tau_problem_desc()
+    d.d = prob.d
+    for i in range(3):
+        d.n[i] = int(prob.n[i]) if i < prob.d else 1
+        d.L[i] = float(prob.L[i]) if i < len(prob.L) else 0.0
+        d.R[i] = float(prob.R[i]) if i < len(prob.R) else 1.0
+        d.alpha[i] = float(prob.alpha[i]) if i < prob.d else 1.5
+        d.kappa[i] = float(prob.kappa[i]) if i < prob.d else 0.0
+        d.route[i] = int(route[i])
+    d.T = float(prob.T)
+    d.M = int(prob.M)
+    d.tol = float(prob.tol)
+    d.max_iter = int(prob.max_iter)
+    d.x0_mode = int(prob.x0_mode)
+    d.precision = precision
+    if e_bounds is None:
+        d.e_min = d.e_max = math.nan
+    else:
+        d.e_min, d.e_max = float(e_bounds[0]), float(e_bounds[1])
+    return d
+
+
+class _FieldHolder:
+    """Keeps the numpy tables alive while tau_set_fields copies them."""
+
+    def __init__(self, tc: np.ndarray, sp: Sequence[np.ndarray]):
+        self.tc = np.ascontiguousarray(tc, dtype=np.float64)
+        self.sp = [np.ascontiguousarray(s, dtype=np.float64) for s in sp]
+        self.f = tau_field()
+        self.f.rank = self.tc.shape[1]
+        self.f.n_times = self.tc.shape[0]
+        self.f.time_coef = self.tc.ctypes.data_as(C.POINTER(C.c_double))
+        for i, s in enumerate(self.sp):
+            self.f.space[i] = s.ctypes.data_as(C.POINTER(C.c_double))
+
+
+# ---------------------------------------------------------------------------
+# functions with the C ABI's names
+# ---------------------------------------------------------------------------
+def tau_create(desc: tau_problem_desc, stream=None) -> int:
+    h = C.c_void_p()
+    _check(lib().tau_create(C.byref(desc), C.c_void_p(_stream(stream)), C.byref(h)))
+    return h.value
+
+
+def tau_set_fields(h: int, tables: dict):
+    e = _FieldHolder(tables["e_tc"], tables["e_sp"])
+    f = _FieldHolder(tables["f_tc"], tables["f_sp"])
+    p = _FieldHolder(tables["psi_tc"], tables["psi_sp"])
+    _check(lib().tau_set_fields(C.c_void_p(h), C.byref(e.f), C.byref(f.f), C.byref(p.f)))
+
+
+def tau_setup(h: int):
+    _check(lib().tau_setup(C.c_void_p(h)))
+
+
+def tau_step(h: int, count: int = 1):
+    _check(lib().tau_step(C.c_void_p(h), C.c_int64(count)))
+
+
+def tau_solve(h: int, allow_notconv: bool = False):
+    return _check(lib().tau_solve(C.c_void_p(h)), (TAU_ENOTCONV,) if allow_notconv else ())
+
+
+def tau_sync(h: int, allow_notconv: bool = False):
+    return _check(lib().tau_sync(C.c_void_p(h)), (TAU_ENOTCONV,) if allow_notconv else ())
+
+
+def tau_get_solution(h: int, out, is_device: bool):
+    m = C.c_int64()
+    ptr = _ptr(out) if is_device else out.ctypes.data
+    _check(lib().tau_get_solution(C.c_void_p(h), C.c_void_p(ptr), 1 if is_device else 0, C.byref(m)))
+    return m.value
+
+
+def tau_set_solution(h: int, u, is_device: bool, m: int):
+    ptr = _ptr(u) if is_device else np.ascontiguousarray(u, dtype=np.float64).ctypes.data
+    _check(lib().tau_set_solution(C.c_void_p(h), C.c_void_p(ptr), 1 if is_device else 0, C.c_int64(m)))
+
+
+def tau_get_stats(h: int, allow_notconv: bool = True) -> tau_stats:
+    s = tau_stats()
+    _check(lib().tau_get_stats(C.c_void_p(h), C.byref(s)), (TAU_ENOTCONV,) if allow_notconv else ())
+    return s
+
+
+def tau_get_iters(h: int, cap: int) -> np.ndarray:
+    arr = np.zeros(cap, dtype=np.int32)
+    _check(lib().tau_get_iters(C.c_void_p(h), arr.ctypes.data_as(C.POINTER(C.c_int)), C.c_int64(cap)))
+    return arr
+
+
+def tau_destroy(h: int):
+    _check(lib().tau_destroy(C.c_void_p(h)))
+
+
+def tau_apply_A(h: int, m: int, x, y):
+    _check(lib().tau_apply_A(C.c_void_p(h), C.c_int64(m), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
+
+
+def tau_apply_Minv(h: int, r, z):
+    _check(lib().tau_apply_Minv(C.c_void_p(h), C.c_void_p(_ptr(r)), C.c_void_p(_ptr(z))))
+
+
+def tau_apply_MinvA(h: int, m: int, x, z):
+    _check(lib().tau_apply_MinvA(C.c_void_p(h), C.c_int64(m), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(z))))
+
+
+def tau_rhs(h: int, m: int, u, b):
+    _check(lib().tau_rhs(C.c_void_p(h), C.c_int64(m), C.c_void_p(_ptr(u)), C.c_void_p(_ptr(b))))
+
+
+def tau_dst(h: int, x, y):
+    _check(lib().tau_dst(C.c_void_p(h), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
+
+
+def tau_toeplitz_mode(h: int, dim: int, x, y):
+    _check(lib().tau_toeplitz_mode(C.c_void_p(h), C.c_int(dim), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
+
+
+def tau_get_ebar(h: int):
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().tau_get_ebar(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def tau_measure_fp64_peak(stream=None) -> float:
+    v = C.c_double()
+    _check(lib().tau_measure_fp64_peak(C.c_void_p(_stream(stream)), C.byref(v)))
+    return v.value
+
+
+class Problem:
+    """Owner of one tau_problem: create, set fields, set up; destroyed with the object."""
+
+    def __init__(self, workload, precision: int = TAU_FP64, route=(0, 0, 0), stream=None, e_bounds=None):
+        self.workload = workload
+        self.prob = workload.prob
+        self.handle = tau_create(make_desc(self.prob, precision, route, e_bounds), stream)
+        try:
+            tau_set_fields(self.handle, workload.field_tables())
+            tau_setup(self.handle)
+        except Exception:
+            tau_destroy(self.handle)
+            self.handle = None
+            raise
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tau_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, count: int = 1):
+        tau_step(self.handle, count)
+
+    def solve(self, allow_notconv: bool = False):
+        return tau_solve(self.handle, allow_notconv)
+
+    def solution(self):
+        import torch
+        out = torch.empty(self.prob.n_tot, dtype=torch.float64, device="cuda")
+        tau_get_solution(self.handle, out, True)
+        return out
+
+    def stats(self) -> tau_stats:
+        return tau_get_stats(self.handle)
+
+    def iters(self) -> np.ndarray:
+        return tau_get_iters(self.handle, self.prob.M)

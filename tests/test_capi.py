@@ -1,0 +1,122 @@
+"""CPU-side checks of the boundary: the library builds, loads and exports every
+function include/tau_rsfde.h declares; the binding marshals structs and reports
+argument errors; the product path has no CPU fallback."""
+
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tau_rsfde.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_10221_gb300 import build, tau
+    build.build()
+    return tau.lib()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tau_[A-Za-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_expected_calls():
+    names = declared_functions()
+    for must in ["tau_create", "tau_set_fields", "tau_setup", "tau_step", "tau_solve", "tau_get_solution",
+                 "tau_destroy", "tau_apply_A", "tau_apply_Minv", "tau_dst", "tau_toeplitz_mode", "tau_rhs"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layout_matches_c_compiler(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets a C compiler gives the header."""
+    import shutil
+    import subprocess
+    from paper_2404_10221_gb300 import tau
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    checks = {
+        "tau_problem_desc": ["d", "n", "L", "R", "alpha", "kappa", "T", "M", "tol", "max_iter", "x0_mode",
+                             "precision", "route", "e_min", "e_max"],
+        "tau_field": ["rank", "n_times", "time_coef", "space"],
+        "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
+                      "e_hat", "e_check", "route", "graph", "device_bytes"],
+    }
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "tau_rsfde.h"', "int main(void){"]
+    for st, fields in checks.items():
+        src.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fields:
+            src.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = dict(line.split() for line in out if line.strip())
+    for st, fields in checks.items():
+        cls = getattr(tau, st)
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for f in fields:
+            assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_invalid_desc_rejected_before_any_device_call(lib):
+    from paper_2404_10221_gb300 import tau, workloads
+    wl = workloads.c2_2d(n=7, M=2)
+    bad = [("alpha", 0, 1.0), ("alpha", 1, 2.0), ("kappa", 0, -1.0)]
+    for field, i, v in bad:
+        d = tau.make_desc(wl.prob)
+        getattr(d, field)[i] = v
+        with pytest.raises(tau.TauError) as ei:
+            tau.tau_create(d, 0)
+        assert ei.value.status == tau.TAU_EINVAL
+    d = tau.make_desc(wl.prob)
+    d.d = 4
+    with pytest.raises(tau.TauError):
+        tau.tau_create(d, 0)
+    d = tau.make_desc(wl.prob)
+    d.max_iter = 0
+    with pytest.raises(tau.TauError):
+        tau.tau_create(d, 0)
+    d = tau.make_desc(wl.prob, route=(1, 0, 0))
+    d.n[0] = 6                       # FFT route needs n+1 = 2^p
+    with pytest.raises(tau.TauError) as ei:
+        tau.tau_create(d, 0)
+    assert ei.value.status in (tau.TAU_EUNSUPPORTED, tau.TAU_ECUDA)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2404_10221_gb300 import tau
+    assert lib.tau_setup(None) == tau.TAU_EINVAL
+    assert lib.tau_step(None, 1) == tau.TAU_EINVAL
+    assert lib.tau_destroy(None) == tau.TAU_OK
+    assert b"NULL" in lib.tau_last_error() or lib.tau_last_error() != b""
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    from paper_2404_10221_gb300 import tau
+    monkeypatch.setattr(tau, "_lib", None)
+    monkeypatch.setattr(tau, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        tau.lib()
+
+
+def test_make_desc_marshals_problem():
+    from paper_2404_10221_gb300 import tau, workloads
+    wl = workloads.c3_3d(n=15, M=7)
+    d = tau.make_desc(wl.prob)
+    assert d.d == 3 and list(d.n) == [15, 15, 15] and d.M == 7
+    assert list(d.alpha) == [1.2, 1.5, 1.9]
+    assert math.isnan(d.e_min) and math.isnan(d.e_max)

@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs.
+
+Operators: FP64, relative 2-norm <= 1e-12 and max |diff| <= 1e-11 max |ref|
+(FFT rounding is O(eps log n) ~ 1e-14).  Whole solves: relative 2-norm <= 1e-10
+at GMRES tol 1e-12 with per-step iteration counts within +-1 of the oracle.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2404_10221_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OP_RTOL = 1e-12
+SOLVE_RTOL = 1e-10
+
+
+def _tau():
+    from paper_2404_10221_gb300 import tau
+    return tau
+
+
+def _wl(d, n, M=3, seed=0, max_iter=100, x0_mode=0, tol=1e-12):
+    """Workload with the C2/C3 coefficient shapes and per-dimension sizes n."""
+    if d == 1:
+        wl = W.c1_1d(n=n[0], M=M, tol=tol)
+    elif d == 2:
+        base = W.c2_2d(n=n[0], M=M, tol=tol)
+        base.prob.n = list(n)
+        wl = W.manufactured(f"2d_{n}", base.prob, base.e.terms, 2, 2, 1.0)
+    else:
+        base = W.c3_3d(n=n[0], M=M, tol=tol)
+        base.prob.n = list(n)
+        wl = W.manufactured(f"3d_{n}", base.prob, base.e.terms, 2, 2, 1.0)
+    wl.prob.max_iter = max_iter
+    wl.prob.x0_mode = x0_mode
+    return wl
+
+
+def _cuda(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def _cmp(got, ref, rtol=OP_RTOL):
+    got = got.detach().cpu().numpy() if hasattr(got, "detach") else got
+    nr = np.linalg.norm(ref)
+    rel = np.linalg.norm(got - ref) / nr
+    assert rel <= rtol, f"rel 2-norm {rel:.3e}"
+    assert np.abs(got - ref).max() <= 10 * rtol * np.abs(ref).max()
+
+
+SHAPES = [
+    (1, (1,)), (1, (3,)), (1, (7,)), (1, (127,)), (1, (1023,)), (1, (4095,)),
+    (1, (5,)), (1, (100,)),                    # dense route (n+1 not a power of two)
+    (2, (15, 7)), (2, (31, 63)), (2, (20, 9)), (2, (63, 5)),
+    (3, (7, 15, 3)), (3, (5, 6, 7)), (3, (15, 15, 15)),
+]
+
+
+@pytest.fixture(scope="module")
+def problems():
+    cache = {}
+
+    def get(d, n):
+        key = (d, tuple(n))
+        if key not in cache:
+            wl = _wl(d, n, max_iter=4)
+            cache[key] = (wl, _tau().Problem(wl))
+        return cache[key]
+
+    yield get
+    for _, p in cache.values():
+        p.close()
+
+
+@pytest.mark.parametrize("d,n", SHAPES)
+def test_dst_parity(problems, d, n):
+    wl, p = problems(d, n)
+    x = W.random_vector(wl.prob.n_tot, 11)
+    y = torch.empty(wl.prob.n_tot, dtype=torch.float64, device="cuda")
+    _tau().tau_dst(p.handle, _cuda(x), y)
+    torch.cuda.synchronize()
+    X = x.reshape(O.tau_oracle._shape(wl.prob))
+    for i in range(d):
+        X = O.mode_product(X, O.sine_matrix(n[i]), d - 1 - i)
+    _cmp(y, X.reshape(-1))
+
+
+@pytest.mark.parametrize("d,n", SHAPES)
+def test_toeplitz_mode_parity(problems, d, n):
+    wl, p = problems(d, n)
+    x = W.random_vector(wl.prob.n_tot, 12)
+    for dim in range(d):
+        y = torch.empty(wl.prob.n_tot, dtype=torch.float64, device="cuda")
+        _tau().tau_toeplitz_mode(p.handle, dim, _cuda(x), y)
+        torch.cuda.synchronize()
+        X = x.reshape(O.tau_oracle._shape(wl.prob))
+        ref = O.mode_product(X, O.toeplitz_S(wl.prob.alpha[dim], n[dim]), d - 1 - dim).reshape(-1)
+        _cmp(y, ref)
+
+
+@pytest.mark.parametrize("d,n", SHAPES)
+def test_apply_A_rhs_Minv_parity(problems, d, n):
+    tau = _tau()
+    wl, p = problems(d, n)
+    pr = wl.prob
+    t = wl.field_tables()
+    ebar, ehat, echeck = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])
+    g = tau.tau_get_ebar(p.handle)
+    assert abs(g[0] - ebar) <= 1e-14 * ebar and abs(g[1] - ehat) <= 1e-14 * ehat
+    x = W.random_vector(pr.n_tot, 13)
+    xd = _cuda(x)
+    y = torch.empty_like(xd)
+    for m in (0, pr.M - 1):
+        e = O.eval_field_interior(pr, t["e_tc"][m], t["e_sp"])
+        tau.tau_apply_A(p.handle, m, xd, y)
+        torch.cuda.synchronize()
+        _cmp(y, O.apply_A(pr, e, x))
+        tau.tau_rhs(p.handle, m, xd, y)
+        torch.cuda.synchronize()
+        F = O.rhs_F(pr, O.eval_field(pr, t["f_tc"][m], t["f_sp"]))
+        _cmp(y, O.rhs_b(pr, e, x, F))
+        tau.tau_apply_MinvA(p.handle, m, xd, y)
+        torch.cuda.synchronize()
+        _cmp(y, O.apply_Minv(pr, ebar, O.apply_A(pr, e, x)))
+    tau.tau_apply_Minv(p.handle, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_Minv(pr, ebar, x))
+
+
+def _solve_both(wl):
+    tau = _tau()
+    p = tau.Problem(wl)
+    p.solve()
+    u = p.solution().cpu().numpy()
+    its = p.iters()
+    st = p.stats()
+    p.close()
+    ref = O.OracleSolver(wl.prob, wl.field_tables())
+    ref.run()
+    return u, its, ref, st
+
+
+@pytest.mark.parametrize("case", [
+    (1, (127,), 32, 0),      # the 1-D workload in full
+    (1, (31,), 6, 1),        # previous-step initial guess
+    (1, (40,), 4, 0),        # dense route
+    (2, (31, 31), 4, 0),
+    (2, (15, 63), 3, 1),
+    (2, (12, 31), 3, 0),     # mixed routes
+    (3, (7, 7, 7), 3, 0),
+    (3, (15, 7, 3), 2, 1),
+])
+def test_solve_parity(case):
+    d, n, M, x0 = case
+    wl = _wl(d, n, M=M, x0_mode=x0)
+    u, its, ref, st = _solve_both(wl)
+    rel = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    assert rel <= SOLVE_RTOL, f"rel {rel:.3e}"
+    assert np.all(np.abs(its - np.array(ref.iters)) <= 1), (its, ref.iters)
+    assert st.steps_done == M
+
+
+def test_solve_parity_paper_example1_iterations():
+    # Example 1 (Table 2, alpha = 1.5, N+1 = 32, tol 1e-9): GPU and oracle iterate alike.
+    wl = W.paper_example(1, [1.5], 31, 4096)
+    wl.prob.M = 4096
+    tau = _tau()
+    p = tau.Problem(wl)
+    p.step(40)
+    its = p.iters()[:40]
+    p.close()
+    ref = O.OracleSolver(wl.prob, wl.field_tables())
+    ref.run(steps=40)
+    assert np.all(np.abs(its - np.array(ref.iters)) <= 1)
+
+
+def test_full_size_2d_operators_and_two_steps():
+    """The 2-D workload at its full size (1023^2 unknowns, M = 100): operators in full and the
+    first two time steps against the oracle."""
+    tau = _tau()
+    wl = W.c2_2d()
+    pr = wl.prob
+    p = tau.Problem(wl)
+    t = wl.field_tables()
+    ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
+    x = W.random_vector(pr.n_tot, 21)
+    xd = _cuda(x)
+    y = torch.empty_like(xd)
+    e0 = O.eval_field_interior(pr, t["e_tc"][0], t["e_sp"])
+    tau.tau_apply_A(p.handle, 0, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_A(pr, e0, x))
+    tau.tau_apply_Minv(p.handle, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_Minv(pr, ebar, x))
+    p.step(2)
+    u = p.solution().cpu().numpy()
+    its = p.iters()[:2]
+    p.close()
+    ref = O.OracleSolver(pr, t)
+    ref.run(steps=2)
+    rel = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    assert rel <= SOLVE_RTOL, rel
+    assert np.all(np.abs(its - np.array(ref.iters)) <= 1), (its, ref.iters)
+
+
+def test_full_size_3d_operators():
+    """3-D at 255^3 (16.6M unknowns): A and M^{-1} in full against the oracle."""
+    tau = _tau()
+    wl = W.c3_3d()
+    wl.prob.max_iter = 2
+    pr = wl.prob
+    p = tau.Problem(wl)
+    t = wl.field_tables()
+    ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
+    x = W.random_vector(pr.n_tot, 22)
+    xd = _cuda(x)
+    y = torch.empty_like(xd)
+    e0 = O.eval_field_interior(pr, t["e_tc"][0], t["e_sp"])
+    tau.tau_apply_A(p.handle, 0, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_A(pr, e0, x))
+    tau.tau_apply_Minv(p.handle, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_Minv(pr, ebar, x))
+    p.close()
+
+
+def test_properties_dst_involution_and_minv_inverse():
+    """S_d S_d = I and M (M^{-1} r) = r through the library at 1023^2."""
+    tau = _tau()
+    wl = W.c2_2d(M=2)
+    wl.prob.max_iter = 2
+    p = tau.Problem(wl)
+    x = _cuda(W.random_vector(wl.prob.n_tot, 23))
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    tau.tau_dst(p.handle, x, y)
+    tau.tau_dst(p.handle, y, z)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(z - x) / torch.linalg.norm(x)).item() <= 1e-13
+    p.close()
+
+
+def test_checkpoint_resume_matches_straight_run():
+    tau = _tau()
+    wl = _wl(2, (31, 15), M=6)
+    a = tau.Problem(wl)
+    a.solve()
+    ua = a.solution().cpu().numpy()
+    a.close()
+    b = tau.Problem(wl)
+    b.step(3)
+    mid = b.solution().cpu().numpy()
+    b.close()
+    c = tau.Problem(wl)
+    tau.tau_set_solution(c.handle, mid, False, 3)
+    c.step(3)
+    uc = c.solution().cpu().numpy()
+    c.close()
+    assert np.linalg.norm(uc - ua) <= 1e-13 * np.linalg.norm(ua)
+
+
+def test_notconv_reported():
+    tau = _tau()
+    wl = _wl(2, (31, 31), M=2, max_iter=2, tol=1e-14)
+    p = tau.Problem(wl)
+    st = p.solve(allow_notconv=True)
+    assert st == tau.TAU_ENOTCONV
+    assert np.all(p.iters() == 2)
+    p.close()
