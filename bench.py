@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: τ-preconditioned GMRES time stepping, unknowns·steps/s.
+
+Workload: the 2-D RSFDE on (0,1)^2 with n = 1023 per dimension (1,046,529
+unknowns), alpha = (1.4, 1.8), kappa = (1, 0.5), e = 2 + sin(pi x) cos(pi y)(1+t),
+T = 1, M = 100 Crank–Nicolson steps, manufactured u = e^{-t} x^2(1-x)^2 y^2(1-y)^2,
+plain FP64, GMRES tol 1e-12 (synthetic inputs).
+
+One bench step = one Crank–Nicolson step (right-hand side + a complete
+τ-preconditioned GMRES solve + solution update) on the full grid.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank solves its own replica (the solver does not
+shard: weak scaling, no data-path collective); rank 0 prints one JSON line.
+--impl reference times the CPU oracle (test infrastructure) on the same
+workload; it runs on rank 0 only.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "τ-GMRES unknowns·steps/s vs plain FP64 at ≤1e-8 rel err; p50/p99 latency"
+UNIT = "unknowns*steps/s"
+WORKLOAD = "2-D RSFDE n=1023x1023 (1,046,529 unknowns), alpha=(1.4,1.8), kappa=(1,0.5), M=100, plain FP64, GMRES tol 1e-12"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config(n_gpus, extra=None):
+    c = {
+        "workload": WORKLOAD,
+        "n": [1023, 1023],
+        "unknowns": 1023 * 1023,
+        "M": 100,
+        "gmres_tol": 1e-12,
+        "x0": "zero",
+        "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single",
+        "l2": "flushed between timed steps (256 MiB write, outside the timed events); "
+              "per-step working set (Krylov basis + work vectors) exceeds L2",
+    }
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): test infrastructure, timed as it stands
+# ---------------------------------------------------------------------------
+def oracle_steps(steps: int, warmup: int = 0):
+    import numpy as np
+
+    import oracle
+    from paper_2404_10221_gb300 import workloads as W
+
+    wl = W.c2_2d()
+    s = oracle.OracleSolver(wl.prob, wl.field_tables())
+    for _ in range(warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    return wl.prob.n_tot * steps / dt, dt, s
+
+
+def cores_used() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    K, W = args.steps, args.warmup
+    # bounded sample: each oracle step is one full Crank-Nicolson step of the workload; keep the
+    # whole run within a few minutes by capping the step count
+    K = max(1, min(K, 4))
+    W = max(0, min(W, 1))
+    val, dt, s = oracle_steps(K, W)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * dt / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config(args.gpus),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                         "sample": f"{K} full Crank-Nicolson steps of the 1023^2 workload after {W} warm-up "
+                                   f"(NumPy FP64, explicit per-dimension matrices)"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "reasons": reasons, "samples": len(rows)}
+
+
+def pass_flops_2d(n: int) -> float:
+    """Algorithmic FP64 flops of the four line passes of one preconditioned matvec z = M^{-1} A v
+    on an n x n grid (conventional FFT count 2.5 L log2 L per real transform of length L)."""
+    L = 2 * (n + 1)
+    rfft = 2.5 * L * math.log2(L)
+    lines = n
+    toep = 2 * rfft + L                # forward + inverse real FFT, real spectrum multiply
+    dst = rfft
+    per_line = {
+        "mv_first": toep + n * (1 + 5 + 5 + 2),   # e∘x, B(e∘x), B x, fma
+        "mv_last_dst": toep + n * (5 + 2) + dst,
+        "dst_mu_dst": 2 * dst + n,
+        "dst": dst,
+    }
+    return lines * sum(per_line.values())
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    wl = W.c2_2d()
+    pr = wl.prob
+    n_tot = pr.n_tot
+    K, Wm = args.steps, args.warmup
+    if K + Wm > pr.M:
+        K = pr.M - Wm
+    prob = tau.Problem(wl, stream=stream.cuda_stream)
+    h = prob.handle
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up steps (untimed)
+    tau.tau_step(h, Wm)
+    tau.tau_sync(h)
+    barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()                       # L2 flush, outside the timed events
+            starts[i].record(stream)
+            tau.tau_step(h, 1)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    ms = sum(starts[i].elapsed_time(ends[i]) for i in range(K))
+    t_dev = ms * 1e-3
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_dev = tt.item()
+    st = tau.tau_get_stats(h)
+    its = tau.tau_get_iters(h, pr.M)[Wm:Wm + K]
+    kernels = int(K * (st.kernels_prologue + st.kernels_epilogue) + its.sum() * st.kernels_per_iter)
+    value = world * n_tot * K / t_dev
+
+    # ---- live roofline of the dominant kernel: the line-pass kernel (4 launches per matvec)
+    x = torch.randn(n_tot, dtype=torch.float64, device=dev)
+    z = torch.empty_like(x)
+    tau.tau_apply_MinvA(h, 0, x, z)          # computes the step fields once
+    R = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(R):
+        tau.tau_apply_MinvA(h, 0, x, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_chain = e0.elapsed_time(e1) * 1e-3 / R
+    flops = pass_flops_2d(1023)
+    fp64_peak = tau.tau_measure_fp64_peak(stream.cuda_stream)
+    achieved = flops / t_chain / 1e12
+    roof = {"bound": "alu", "kernel": "tau::k_pass (4 launches per preconditioned matvec)",
+            "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / (fp64_peak / 1e12), "traffic": None,
+            "peak_kind": "measured FP64 FMA throughput (in-process probe); nominal 1.25 TFLOP/s",
+            "matvec_ms": t_chain * 1e3, "algorithmic_flops_per_matvec": flops}
+
+    # ---- end to end through the C ABI with host buffers: per step, u^{(m)} in from pinned
+    # host memory, one step, u^{(m+1)} back to pinned host memory
+    e2e = None
+    if K >= 1:
+        prob2 = tau.Problem(wl, stream=stream.cuda_stream)
+        h2 = prob2.handle
+        host_in = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+        host_out = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+        tau.tau_get_solution(h2, host_in.numpy(), False)
+        Ke = min(K, 5)
+        for i in range(min(Wm, 1)):
+            tau.tau_set_solution(h2, host_in.numpy(), False, i)
+            tau.tau_step(h2, 1)
+            tau.tau_get_solution(h2, host_out.numpy(), False)
+            host_in.copy_(host_out)
+        barrier()
+        t0 = time.perf_counter()
+        m0 = min(Wm, 1)
+        for i in range(Ke):
+            tau.tau_set_solution(h2, host_in.numpy(), False, m0 + i)
+            tau.tau_step(h2, 1)
+            tau.tau_get_solution(h2, host_out.numpy(), False)
+            host_in.copy_(host_out)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = tt.item()
+        e2e = {"value": world * n_tot * Ke / te, "unit": UNIT, "h2d_bytes_per_step": n_tot * 8 + 8,
+               "d2h_bytes_per_step": n_tot * 8, "steps": Ke,
+               "api": "tau_set_solution(host) + tau_step(1) + tau_get_solution(host), pinned buffers"}
+        prob2.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (manufactured solution, closed-form Riesz source)",
+        "config": config(world, {"gmres_iters_per_step": float(np.mean(its)) if len(its) else None,
+                                 "graph": bool(st.graph), "wall_s_timed": t_wall}),
+        "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": kernels,
+    }
+    prob.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        val, dt, _ = oracle_steps(args.cpu_steps, 0)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                                "sample": f"{args.cpu_steps} full Crank-Nicolson steps of the same 1023^2 "
+                                          f"workload ({dt:.1f} s, NumPy FP64 with explicit per-dimension "
+                                          f"matrices)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

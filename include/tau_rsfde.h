@@ -106,6 +106,9 @@ typedef struct {
   int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT or TAU_ROUTE_DENSE) */
   int graph;                /* 1 if steps run as CUDA-graph launches with device-side loop control */
   int64_t device_bytes;     /* device memory held by the problem */
+  int64_t kernels_prologue; /* kernels of one step: prologue + iters * per_iter + epilogue */
+  int64_t kernels_per_iter;
+  int64_t kernels_epilogue;
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of

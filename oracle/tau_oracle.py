@@ -109,9 +109,12 @@ def tau_of(t: np.ndarray) -> np.ndarray:
 
 
 def sine_matrix(n: int) -> np.ndarray:
-    """S = sqrt(2/(N+1)) [sin(pi j k/(N+1))]_{j,k=1..N}, §3 (below Eq. (q))."""
-    j = np.arange(1, n + 1)
-    return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * np.outer(j, j) / (n + 1))
+    """S = sqrt(2/(N+1)) [sin(pi j k/(N+1))]_{j,k=1..N}, §3 (below Eq. (q)).
+    The integer j*k is reduced modulo 2(N+1) before forming the angle (sin has period 2 pi),
+    so no entry is evaluated at a large, rounded argument."""
+    j = np.arange(1, n + 1, dtype=np.int64)
+    jk = np.outer(j, j) % (2 * (n + 1))
+    return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * jk / (n + 1))
 
 
 def tau_eigs_q(t: np.ndarray) -> np.ndarray:
@@ -121,7 +124,8 @@ def tau_eigs_q(t: np.ndarray) -> np.ndarray:
     for i in range(n):
         acc = t[0]
         for j in range(1, n):
-            acc += 2.0 * t[j] * math.cos(math.pi * j * (i + 1) / (n + 1))
+            # angle pi j (i+1)/(N+1) with j (i+1) reduced modulo 2(N+1) (cos has period 2 pi)
+            acc += 2.0 * t[j] * math.cos(math.pi * ((j * (i + 1)) % (2 * (n + 1))) / (n + 1))
         q[i] = acc
     return q
 

@@ -17,6 +17,8 @@ using namespace tau;
 namespace {
 
 thread_local std::string g_err;
+// kernels enqueued by this thread (used to count the kernels of the step graph)
+thread_local int64_t tl_launches = 0;
 
 tau_status fail(tau_status st, const char* fmt, ...) {
   char buf[512];
@@ -32,6 +34,12 @@ tau_status fail(tau_status st, const char* fmt, ...) {
   do {                                                                                       \
     cudaError_t _e = (call);                                                                 \
     if (_e != cudaSuccess) return fail(TAU_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));  \
+  } while (0)
+
+#define KL(call)          \
+  do {                    \
+    ++tl_launches;        \
+    CK(call);             \
   } while (0)
 
 #define TRY(call)                       \
@@ -72,6 +80,8 @@ struct tau_problem {
   double ebar = 0, ehat = 0, echeck = 0;
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
+  int64_t k_pro = 0, k_body = 0, k_epi = 0;  // kernels per prologue / GMRES iteration / epilogue
+  int64_t fields_m = -1;                      // step whose e and dt*F sit in E / Fdt
   int* h_done = nullptr;  // pinned flag for the host-loop fallback
   std::vector<void*> allocs;
   int64_t bytes = 0;
@@ -163,7 +173,7 @@ struct ChainIO {
 };
 
 tau_status enq(const Pass& P, cudaStream_t st) {
-  CK(launch_pass(P, st));
+  KL(launch_pass(P, st));
   return TAU_OK;
 }
 
@@ -233,7 +243,7 @@ tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainIO& io) {
 }
 
 tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
-  CK(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
+  KL(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
   ChainIO rhs;
   rhs.x = p->u;
   rhs.out = p->b;
@@ -247,8 +257,9 @@ tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
     r0.x = p->b;
     TRY(enq_minv(p, st, r0));
   }
-  CK(launch_norm_partial(p->V, p->n_tot, p->g, p->pnorm, st));
-  CK(launch_init_beta(p->g, p->pnorm, p->gv, p->V, p->n_tot, st));
+  KL(launch_norm_partial(p->V, p->n_tot, p->g, p->pnorm, st));
+  tl_launches += 1;
+  KL(launch_init_beta(p->g, p->pnorm, p->gv, p->V, p->n_tot, st));
   return TAU_OK;
 }
 
@@ -259,18 +270,19 @@ tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle 
   it.g = p->g;
   TRY(enq_mv(p, st, it, 1.0, FIN_NONE, nullptr, true));
   const int ld = RED_BLOCKS;
-  CK(launch_dots(p->V, p->n_tot, p->g, p->pdots, ld, st));
-  CK(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
-  CK(launch_update_dots(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
-  CK(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
-  CK(launch_update_dots(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
-  CK(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
-  CK(launch_scale_next(p->V, p->n_tot, p->g, st));
+  KL(launch_dots(p->V, p->n_tot, p->g, p->pdots, ld, st));
+  KL(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
+  KL(launch_update_dots(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
+  KL(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
+  KL(launch_update_dots(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
+  KL(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
+  KL(launch_scale_next(p->V, p->n_tot, p->g, st));
   return TAU_OK;
 }
 
 tau_status enq_epilogue(tau_problem* p, cudaStream_t st) {
-  CK(launch_backsolve_update(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, p->V, p->n_tot, p->u,
+  tl_launches += 2;
+  KL(launch_backsolve_update(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, p->V, p->n_tot, p->u,
                              p->desc.x0_mode == TAU_X0_PREV, p->iters, st));
   return TAU_OK;
 }
@@ -291,7 +303,9 @@ tau_status build_graph(tau_problem* p) {
   do {
     e = cudaStreamBeginCaptureToGraph(p->cap, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
+    tl_launches = 0;
     st = enq_prologue(p, p->cap);
+    p->k_pro = tl_launches;
     {
       cudaStreamCaptureStatus cst;
       const cudaGraphNode_t* deps = nullptr;
@@ -317,7 +331,9 @@ tau_status build_graph(tau_problem* p) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(p->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
+    tl_launches = 0;
     st = enq_body(p, p->cap, h, 1);
+    p->k_body = tl_launches;
     e2 = cudaStreamEndCapture(p->cap, &Gout);
     if (st != TAU_OK) break;
     if (e2 != cudaSuccess) {
@@ -326,7 +342,9 @@ tau_status build_graph(tau_problem* p) {
     }
     e = cudaStreamBeginCaptureToGraph(p->cap, G, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
+    tl_launches = 0;
     st = enq_epilogue(p, p->cap);
+    p->k_epi = tl_launches;
     e2 = cudaStreamEndCapture(p->cap, &Gout);
     if (st != TAU_OK) break;
     if (e2 != cudaSuccess) {
@@ -355,6 +373,14 @@ tau_status run_step_hostloop(tau_problem* p) {
     TRY(enq_body(p, p->st, dummy, 0));
   }
   TRY(enq_epilogue(p, p->st));
+  return TAU_OK;
+}
+
+// e and dt*F of step m into E / Fdt for the operator entry points (skipped when already there).
+tau_status fields_for(tau_problem* p, int64_t m) {
+  if (p->fields_m == m) return TAU_OK;
+  KL(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  p->fields_m = m;
   return TAU_OK;
 }
 
@@ -539,7 +565,7 @@ tau_status tau_setup(tau_problem* p) {
       double *dc = nullptr, *dl = nullptr;
       TRY(upload(p, &dc, c.data(), c.size()));
       TRY(dalloc_n(p, &dl, (size_t)K + 1));
-      CK(launch_spectrum(K, dc, dl, p->tw, p->st));
+      KL(launch_spectrum(K, dc, dl, p->tw, p->st));
       std::vector<double> lam(K + 1);
       CK(cudaMemcpyAsync(lam.data(), dl, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
@@ -573,7 +599,7 @@ tau_status tau_setup(tau_problem* p) {
   }
   // ebar (Eqs. (bard), (dhat))
   if (std::isnan(p->desc.e_min) || std::isnan(p->desc.e_max)) {
-    CK(launch_escan(field_dev(p), p->desc.M, p->escan, p->st));
+    KL(launch_escan(field_dev(p), p->desc.M, p->escan, p->st));
     std::vector<double> part(2 * RED_BLOCKS);
     CK(cudaMemcpyAsync(part.data(), p->escan, part.size() * sizeof(double), cudaMemcpyDeviceToHost, p->st));
     CK(cudaStreamSynchronize(p->st));
@@ -591,8 +617,8 @@ tau_status tau_setup(tau_problem* p) {
   if (!(p->echeck > 0.0) || !(p->ehat >= p->echeck))
     return fail(TAU_EINVAL, "e must be positive: min %g max %g", p->echeck, p->ehat);
   p->ebar = 0.5 * (p->ehat + p->echeck);
-  CK(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
-  CK(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->u, p->st));
+  KL(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
+  KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->u, p->st));
   GmresDev g{};
   g.max_iter = p->desc.max_iter;
   g.tol = p->desc.tol;
@@ -617,6 +643,7 @@ tau_status tau_step(tau_problem* p, int64_t count) {
   if (count < 0 || p->m_host + count > p->desc.M)
     return fail(TAU_EINVAL, "count=%lld with m=%lld of M=%lld", (long long)count, (long long)p->m_host,
                 (long long)p->desc.M);
+  if (count > 0) p->fields_m = -1;
   for (int64_t c = 0; c < count; ++c) {
     if (p->graph_ok) {
       CK(cudaGraphLaunch(p->exec, p->st));
@@ -687,6 +714,9 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->e_check = p->echeck;
   for (int i = 0; i < 3; ++i) out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE) : 0;
   out->graph = p->graph_ok ? 1 : 0;
+  out->kernels_prologue = p->k_pro;
+  out->kernels_per_iter = p->k_body;
+  out->kernels_epilogue = p->k_epi;
   out->device_bytes = p->bytes;
   if (g.notconv) return fail(TAU_ENOTCONV, "a step reached max_iter without meeting tol");
   return TAU_OK;
@@ -718,7 +748,7 @@ tau_status tau_apply_A(tau_problem* p, int64_t m, const double* x, double* y) {
   TRY(check_ready(p));
   if (!x || !y) return fail(TAU_EINVAL, "NULL vector");
   if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
-  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  KL(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
   ChainIO io;
   io.x = x;
   io.out = y;
@@ -729,7 +759,7 @@ tau_status tau_apply_MinvA(tau_problem* p, int64_t m, const double* x, double* z
   TRY(check_ready(p));
   if (!x || !z) return fail(TAU_EINVAL, "NULL vector");
   if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
-  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  KL(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
   ChainIO io;
   io.x = x;
   io.out = z;
@@ -749,7 +779,7 @@ tau_status tau_rhs(tau_problem* p, int64_t m, const double* u, double* b) {
   TRY(check_ready(p));
   if (!u || !b) return fail(TAU_EINVAL, "NULL vector");
   if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
-  CK(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  KL(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
   ChainIO io;
   io.x = u;
   io.out = b;

@@ -375,13 +375,14 @@ __device__ void dst_lines(const Pass& P, double* xs, double2* cb) {
 // ---------------------------------------------------------------------------
 // the line-pass kernel
 // ---------------------------------------------------------------------------
-// Shared memory: ra, rc (lpb*N doubles each) then cb (lpb*K complex, FFT route).
+// Shared memory: ra, rc (lpb*N doubles each) then cb (lpb*K complex, FFT route, 16-byte aligned).
 __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = P.len, lpb = P.lpb;
   double* ra = reinterpret_cast<double*>(smraw);
   double* rc = ra + lpb * N;
-  double2* cb = reinterpret_cast<double2*>(rc + lpb * N + ((lpb * N) & 1));
+  // ra and rc together hold an even number of doubles, so cb starts 16-byte aligned
+  double2* cb = reinterpret_cast<double2*>(rc + lpb * N);
   if (P.g && P.g->done) return;
   const TileGeo tg = tile_geo(P, blockIdx.x);
   const int T = blockDim.x, tid = threadIdx.x;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
 
 size_t pass_smem_bytes(const Pass& p) {
   const size_t real = (size_t)p.lpb * p.len;
-  size_t bytes = 2 * real * sizeof(double) + ((real & 1) ? sizeof(double) : 0);
+  size_t bytes = 2 * real * sizeof(double);
   if (p.dim.route == ROUTE_FFT) bytes += (size_t)p.lpb * p.dim.K * sizeof(double2);
   return bytes;
 }

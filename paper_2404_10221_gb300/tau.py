@@ -76,6 +76,9 @@ class tau_stats(C.Structure):
         ("route", C.c_int * 3),
         ("graph", C.c_int),
         ("device_bytes", C.c_int64),
+        ("kernels_prologue", C.c_int64),
+        ("kernels_per_iter", C.c_int64),
+        ("kernels_epilogue", C.c_int64),
     ]
 
 

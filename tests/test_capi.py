@@ -51,7 +51,8 @@ def test_struct_layout_matches_c_compiler(tmp_path):
                              "precision", "route", "e_min", "e_max"],
         "tau_field": ["rank", "n_times", "time_coef", "space"],
         "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
-                      "e_hat", "e_check", "route", "graph", "device_bytes"],
+                      "e_hat", "e_check", "route", "graph", "device_bytes", "kernels_prologue",
+                      "kernels_per_iter", "kernels_epilogue"],
     }
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "tau_rsfde.h"', "int main(void){"]
     for st, fields in checks.items():
