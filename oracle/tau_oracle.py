@@ -120,13 +120,11 @@ def sine_matrix(n: int) -> np.ndarray:
 def tau_eigs_q(t: np.ndarray) -> np.ndarray:
     """q_i = t_0 + 2 sum_{j=1}^{N-1} t_j cos(pi j (i+1)/(N+1)), i = 0..N-1, Eq. (q)."""
     n = len(t)
-    q = np.zeros(n)
-    for i in range(n):
-        acc = t[0]
-        for j in range(1, n):
-            # angle pi j (i+1)/(N+1) with j (i+1) reduced modulo 2(N+1) (cos has period 2 pi)
-            acc += 2.0 * t[j] * math.cos(math.pi * ((j * (i + 1)) % (2 * (n + 1))) / (n + 1))
-        q[i] = acc
+    i1 = np.arange(1, n + 1, dtype=np.int64)          # i + 1 for i = 0..N-1
+    q = np.full(n, t[0], dtype=np.float64)
+    for j in range(1, n):
+        # angle pi j (i+1)/(N+1) with j (i+1) reduced modulo 2(N+1) (cos has period 2 pi)
+        q += 2.0 * t[j] * np.cos(np.pi * ((j * i1) % (2 * (n + 1))) / (n + 1))
     return q
 
 
