@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--matvec-only", type=int, default=0,
+                    help="profiling driver: set up the workload (2 Krylov slots) and run this many "
+                         "preconditioned matvecs (4 line-pass launches each), then exit")
     return ap.parse_args()
 
 
@@ -325,10 +328,31 @@ def run_native(args):
     return 0
 
 
+def run_matvec_only(args):
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    wl = W.c2_2d()
+    wl.prob.max_iter = 2
+    p = tau.Problem(wl)
+    x = torch.randn(wl.prob.n_tot, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(x)
+    for _ in range(args.matvec_only):
+        tau.tau_apply_MinvA(p.handle, 0, x, z)
+    torch.cuda.synchronize()
+    p.close()
+    print(json.dumps({"matvec_only": args.matvec_only, "z_norm": float(torch.linalg.norm(z))}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.matvec_only:
+        return run_matvec_only(args)
     return run_native(args)
 
 
