@@ -186,6 +186,25 @@ tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_c
  * roofline of the FP64-bound kernels; runs a bounded kernel for a few milliseconds). */
 tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s);
 
+/* ---- allocation-free entry point (the paper has no counterpart).
+ *
+ * y = A x = B_alpha (e ∘ x) + S_alpha x for the grid and coefficients of `desc` (d, n, L, R, alpha,
+ * kappa, T, M give h_i, dt and eta_i; the other fields are ignored), without a tau_problem and
+ * without allocating device memory.  For callers that cannot call cudaMalloc: code living inside
+ * a host application whose memory pool owns the device, plugins that must not change the
+ * device's memory footprint, and latency-critical loops where an allocation (which may
+ * synchronise the device) is not acceptable.
+ *   e, x: device pointers to n_tot doubles (e = e(x_J, t) at the interior nodes); y: device
+ *   output of n_tot doubles (must not alias x or e).  Enqueued on `stream` (cudaStream_t or NULL).
+ * Scratch (FCD weights, circulant spectra, twiddles, the two Kronecker channels) lives in one
+ * static device array of about 4.8 MB that every GPU loading the library holds until process
+ * exit; it is rebuilt on each call.  Limits: n_i <= 4095 per dimension and n_tot <= 262,144;
+ * larger problems return TAU_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call shares the array: calls that overlap on the GPU race. */
+tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const double* e, const double* x, double* y,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

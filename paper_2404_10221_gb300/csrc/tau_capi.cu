@@ -52,6 +52,8 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 }  // namespace
 
+void tau::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct tau_problem {
   tau_problem_desc desc{};
   cudaStream_t st = nullptr;    // caller's stream: every operation is enqueued here

@@ -98,6 +98,8 @@ struct GmresDev {
 // host launchers (tau_kernels.cu)
 // ---------------------------------------------------------------------------
 cudaError_t init_kernel_attributes();
+// Message returned by tau_last_error() for the calling thread.
+void set_last_error(const char* msg);
 size_t pass_smem_bytes(const Pass& p);
 cudaError_t launch_pass(const Pass& p, cudaStream_t st);
 cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* tw, cudaStream_t st);

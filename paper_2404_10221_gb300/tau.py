@@ -120,6 +120,7 @@ def lib():
             "tau_toeplitz_mode": [P, C.c_int, P, P],
             "tau_get_ebar": [P, D, D, D],
             "tau_measure_fp64_peak": [P, D],
+            "tau_apply_A_noalloc": [C.POINTER(tau_problem_desc), P, P, P, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -286,6 +287,12 @@ def tau_measure_fp64_peak(stream=None) -> float:
     v = C.c_double()
     _check(lib().tau_measure_fp64_peak(C.c_void_p(_stream(stream)), C.byref(v)))
     return v.value
+
+
+def tau_apply_A_noalloc(desc: tau_problem_desc, e, x, y, stream=None):
+    """y = A x without a problem handle and without device allocation (static scratch)."""
+    _check(lib().tau_apply_A_noalloc(C.byref(desc), C.c_void_p(_ptr(e)), C.c_void_p(_ptr(x)),
+                                     C.c_void_p(_ptr(y)), C.c_void_p(_stream(stream))))
 
 
 class Problem:
