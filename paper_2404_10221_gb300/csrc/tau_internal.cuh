@@ -34,28 +34,45 @@ enum Post : int {
 
 struct GmresDev;
 
-// Per-dimension data resident on the device.
-struct DimData {
+template <typename T> struct Vec2Of;
+template <> struct Vec2Of<double> { using type = double2; };
+template <> struct Vec2Of<float> { using type = float2; };
+template <typename T> using vec2 = typename Vec2Of<T>::type;
+
+// Per-dimension data resident on the device, in the element type T of the pass (FP64 for the
+// plain path, FP32 for the inner solve of the mixed-precision form).
+template <typename T>
+struct DimDataT {
   int n;              // interior points N_i
   int K;              // n + 1 (FFT route: power of two)
   int route;          // Route
-  double bdiag, boff; // B_{alpha_i}: 1 - alpha/12, alpha/24
+  T bdiag, boff;      // B_{alpha_i}: 1 - alpha/12, alpha/24
   double eta;         // kappa_i dt / (2 h_i^alpha_i)
-  const double2* spec;  // FFT route: (sigma_k, delta_k), k = 0..K/2, Toeplitz spectrum folded
+  const vec2<T>* spec;  // FFT route: (sigma_k, delta_k), k = 0..K/2, Toeplitz spectrum folded
                         // for the packed real FFT, scaled by 1/K (no eta)
-  const double* s;      // FCD weights s_0..s_{n-1}
-  const double* sintab; // dense route: sin(pi t / K), t = 0..2K-1
+  const T* s;           // FCD weights s_0..s_{n-1}
+  const T* sintab;      // sin(pi t / K), t = 0..2K-1
+  const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
+  const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I
 };
+using DimData = DimDataT<double>;
+
+// Stage-packed twiddle table of an in-place radix-4 FFT of length S (twp_size(S) entries):
+//   stage of size s (s = S, S/4, ..., >= 4) at offset S - s: [w_s^i | w_s^{2i} | w_s^{3i}], i < s/4,
+//   with w_s = exp(-2 pi i / s); then at offset S: exp(-2 pi i k / (2S)), k = 0..S.
+// Consecutive butterflies of a stage read consecutive entries.
+__host__ __device__ inline int twp_size(int S) { return 2 * S + 1; }
 
 // One line pass over an array of shape (n_{d-1}, ..., n_0) along dimension ax.
-struct Pass {
+template <typename T>
+struct PassT {
   int ax;            // dimension (0 = x_1, contiguous)
   int len;           // n_ax
   int64_t inner;     // prod_{i<ax} n_i (element stride along the line)
   int64_t nlines;    // n_tot / len
   int lpb;           // lines per CTA
   int64_t ntiles;
-  DimData dim;
+  DimDataT<T> dim;
   // matvec channels
   int mv;            // 1: this pass is a matvec pass
   int first;         // 1: inputs are (x, e): a = B(e∘x) + s eta T x, c = B x
@@ -64,19 +81,21 @@ struct Pass {
   int toep_only;     // 1: out = T x (no B, no eta) -- Toeplitz parity entry
   int finish;        // Finish
   int post;          // Post
-  const double* in_a;  // first pass: x; else channel a
-  const double* in_c;  // first pass: e (may be null when toep_only); else channel c
-  const double* src;   // FIN_RESID minuend or FIN_ADD_F addend (Fdt)
-  const double* invmu; // POST_DST_MU_DST
-  double* out_a;
-  double* out_c;
-  const double2* tw;   // twiddles
-  // GMRES wiring: pointers that depend on the device-side Arnoldi index j
-  const GmresDev* g;         // non-null: skip the pass when g->done
-  double* vbase;             // Krylov basis V (vectors of vstride doubles)
+  const T* in_a;        // first pass: x; else channel a
+  const T* in_c;        // channel c (not read by the first pass)
+  const double* e;      // first pass: e at the interior nodes (FP64 storage)
+  const T* src;         // FIN_RESID minuend or FIN_ADD_F addend (Fdt)
+  const T* invmu;       // POST_DST_MU_DST
+  T* out_a;
+  T* out_c;
+  // Krylov wiring: pointers that depend on the device-side Arnoldi index j
+  const GmresDev* g;    // non-null: skip the pass when g->done
+  T* in_base;           // in_sel: 1 -> in_base + j*vstride, 2 -> in_base + (j+1)*vstride
+  T* out_base;          // out_sel: the same for the output
   int64_t vstride;
-  int in_sel, out_sel;       // 0: in_a/out_a as given, 1: V_j, 2: V_{j+1}
+  int in_sel, out_sel;  // 0: in_a/out_a as given
 };
+using Pass = PassT<double>;
 
 // GMRES state kept in device memory (one per problem).
 struct GmresDev {
@@ -100,9 +119,11 @@ struct GmresDev {
 cudaError_t init_kernel_attributes();
 // Message returned by tau_last_error() for the calling thread.
 void set_last_error(const char* msg);
-size_t pass_smem_bytes(const Pass& p);
-cudaError_t launch_pass(const Pass& p, cudaStream_t st);
-cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* tw, cudaStream_t st);
+template <typename T> size_t pass_smem_bytes(const PassT<T>& p);
+template <typename T> cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st);
+cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* twK, cudaStream_t st);
+// Fill a stage-packed twiddle table (twp_size(S) entries) on the device.
+cudaError_t launch_twp(int S, double2* twp, cudaStream_t st);
 
 // fields: e_m, Fdt_m for step m (read from g->m unless m_override >= 0)
 struct FieldDev {

@@ -24,17 +24,20 @@ constexpr int PASS_THREADS = 128;
 // ---------------------------------------------------------------------------
 // complex helpers (FP64)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+__device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) x, decltype(V::x) y) { return V{x, y}; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(tfma(a.x, b.x, -a.y * b.y), tfma(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return mk<V>(tfma(a.x, b.x, a.y * b.y), tfma(a.y, b.x, -a.x * b.y));
 }
-__device__ __forceinline__ double2 mul_mi(double2 a) { return make_double2(a.y, -a.x); }  // -i a
-__device__ __forceinline__ double2 mul_pi(double2 a) { return make_double2(-a.y, a.x); }  // +i a
+template <typename V> __device__ __forceinline__ V mul_mi(V a) { return mk<V>(a.y, -a.x); }  // -i a
+template <typename V> __device__ __forceinline__ V mul_pi(V a) { return mk<V>(-a.y, a.x); }  // +i a
 
 // Position of DFT output k after the in-place radix-4 (final radix-2 when log2 K is odd) DIF.
 __device__ __forceinline__ int dif_pos(int k, int K) {
@@ -49,29 +52,31 @@ __device__ __forceinline__ int dif_pos(int k, int K) {
 }
 
 // Forward complex DFT of length K (natural order in, digit-reversed out) on nl lines stored at
-// cb + l*cs.  Caller synchronises before; this synchronises after.
-__device__ void fft_dif(double2* cb, int cs, int nl, int K, const double2* __restrict__ tw) {
+// cb + l*cs, twiddles from the stage-packed table twp (twp_size(K) entries).  Caller
+// synchronises before; this synchronises after.
+template <typename V>
+__device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp) {
   const int T = blockDim.x, tid = threadIdx.x;
   int size = K;
   for (; size >= 4; size >>= 2) {
     const int q = size >> 2;
-    const int tstep = TWN / size;
+    const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b / nb, loc = b - l * nb;
       const int g = loc / q, i = loc - g * q;
-      double2* x = cb + l * cs + g * size + i;
-      const double2 a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
-      const double2 b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), b3 = mul_mi(csub(a1, a3));
+      V* x = cb + l * cs + g * size + i;
+      const V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
+      const V b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), b3 = mul_mi(csub(a1, a3));
       x[0] = cadd(b0, b2);
       if (i == 0) {
         x[q] = cadd(b1, b3);
         x[2 * q] = csub(b0, b2);
         x[3 * q] = csub(b1, b3);
       } else {
-        x[q] = cmul(cadd(b1, b3), __ldg(&tw[i * tstep]));
-        x[2 * q] = cmul(csub(b0, b2), __ldg(&tw[2 * i * tstep]));
-        x[3 * q] = cmul(csub(b1, b3), __ldg(&tw[3 * i * tstep]));
+        x[q] = cmul(cadd(b1, b3), __ldg(&tws[i]));
+        x[2 * q] = cmul(csub(b0, b2), __ldg(&tws[q + i]));
+        x[3 * q] = cmul(csub(b1, b3), __ldg(&tws[2 * q + i]));
       }
     }
     __syncthreads();
@@ -80,8 +85,8 @@ __device__ void fft_dif(double2* cb, int cs, int nl, int K, const double2* __res
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b / nb, loc = b - l * nb;
-      double2* x = cb + l * cs + 2 * loc;
-      const double2 a0 = x[0], a1 = x[1];
+      V* x = cb + l * cs + 2 * loc;
+      const V a0 = x[0], a1 = x[1];
       x[0] = cadd(a0, a1);
       x[1] = csub(a0, a1);
     }
@@ -89,8 +94,9 @@ __device__ void fft_dif(double2* cb, int cs, int nl, int K, const double2* __res
   }
 }
 
-// Unnormalised inverse DFT (times K): digit-reversed in, natural order out.
-__device__ void fft_dit_inv(double2* cb, int cs, int nl, int K, const double2* __restrict__ tw) {
+// Unnormalised inverse DFT (times K): digit-reversed in, natural order out (same table as fft_dif).
+template <typename V>
+__device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ twp) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int lg = 31 - __clz(K);
   int size = 4;
@@ -98,8 +104,8 @@ __device__ void fft_dit_inv(double2* cb, int cs, int nl, int K, const double2* _
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b / nb, loc = b - l * nb;
-      double2* x = cb + l * cs + 2 * loc;
-      const double2 a0 = x[0], a1 = x[1];
+      V* x = cb + l * cs + 2 * loc;
+      const V a0 = x[0], a1 = x[1];
       x[0] = cadd(a0, a1);
       x[1] = csub(a0, a1);
     }
@@ -108,19 +114,19 @@ __device__ void fft_dit_inv(double2* cb, int cs, int nl, int K, const double2* _
   }
   for (; size <= K; size <<= 2) {
     const int q = size >> 2;
-    const int tstep = TWN / size;
+    const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b / nb, loc = b - l * nb;
       const int g = loc / q, i = loc - g * q;
-      double2* x = cb + l * cs + g * size + i;
-      double2 y0 = x[0], y1 = x[q], y2 = x[2 * q], y3 = x[3 * q];
+      V* x = cb + l * cs + g * size + i;
+      V y0 = x[0], y1 = x[q], y2 = x[2 * q], y3 = x[3 * q];
       if (i != 0) {
-        y1 = cmulc(y1, __ldg(&tw[i * tstep]));
-        y2 = cmulc(y2, __ldg(&tw[2 * i * tstep]));
-        y3 = cmulc(y3, __ldg(&tw[3 * i * tstep]));
+        y1 = cmulc(y1, __ldg(&tws[i]));
+        y2 = cmulc(y2, __ldg(&tws[q + i]));
+        y3 = cmulc(y3, __ldg(&tws[2 * q + i]));
       }
-      const double2 c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
+      const V c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
       x[0] = cadd(c0, c2);
       x[q] = cadd(c1, c3);
       x[2 * q] = csub(c0, c2);
@@ -134,27 +140,26 @@ __device__ void fft_dit_inv(double2* cb, int cs, int nl, int K, const double2* _
 // spectrum lambda, working on the packed half-length DFT Z in place:
 //   E2 = Z_k + conj Z_{K-k},  O2 = -i (Z_k - conj Z_{K-k}),  Y_k = (E2 + W_k O2)/2,
 //   W_k = exp(-i pi k / K).  spec[k] = ((lam_k + lam_{K-k})/(4K), (lam_k - lam_{K-k})/(4K)).
-__device__ void toep_spectral(double2* cb, int cs, int nl, int K, const double2* __restrict__ spec,
-                              const double2* __restrict__ tw) {
+template <typename V>
+__device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict__ spec, const V* __restrict__ twp) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int np = K / 2 + 1;
-  const int wstep = TWN / (2 * K);
   for (int b = tid; b < nl * np; b += T) {
     const int l = b / np, k = b - l * np;
     const int kk = (K - k) & (K - 1);
-    double2* x = cb + l * cs;
+    V* x = cb + l * cs;
     const int pk = dif_pos(k, K), pkk = dif_pos(kk, K);
-    const double2 A = x[pk], B = x[pkk];
-    const double2 E2 = make_double2(A.x + B.x, A.y - B.y);
-    const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
-    const double2 W = __ldg(&tw[k * wstep]);
-    const double2 P = cmul(W, O2);
-    const double2 sd = __ldg(&spec[k]);
-    const double2 Ep = make_double2(fma(sd.x, E2.x, sd.y * P.x), fma(sd.x, E2.y, sd.y * P.y));
-    const double2 WcE = cmulc(E2, W);
-    const double2 Op = make_double2(fma(sd.y, WcE.x, sd.x * O2.x), fma(sd.y, WcE.y, sd.x * O2.y));
-    x[pk] = make_double2(Ep.x - Op.y, Ep.y + Op.x);
-    if (kk != k) x[pkk] = make_double2(Ep.x + Op.y, Op.x - Ep.y);
+    const V A = x[pk], B = x[pkk];
+    const V E2 = mk<V>(A.x + B.x, A.y - B.y);
+    const V O2 = mk<V>(A.y + B.y, B.x - A.x);
+    const V W = __ldg(&twp[K + k]);
+    const V P = cmul(W, O2);
+    const V sd = __ldg(&spec[k]);
+    const V Ep = mk<V>(fma(sd.x, E2.x, sd.y * P.x), fma(sd.x, E2.y, sd.y * P.y));
+    const V WcE = cmulc(E2, W);
+    const V Op = mk<V>(fma(sd.y, WcE.x, sd.x * O2.x), fma(sd.y, WcE.y, sd.x * O2.y));
+    x[pk] = mk<V>(Ep.x - Op.y, Ep.y + Op.x);
+    if (kk != k) x[pkk] = mk<V>(Ep.x + Op.y, Op.x - Ep.y);
   }
   __syncthreads();
 }
@@ -169,7 +174,8 @@ struct TileGeo {
   int nvalid;     // number of valid lines in the tile
 };
 
-__device__ __forceinline__ TileGeo tile_geo(const Pass& P, int64_t tile) {
+template <typename PT>
+__device__ __forceinline__ TileGeo tile_geo(const PT& P, int64_t tile) {
   TileGeo t;
   const int64_t N = P.len;
   if (P.ax == 0) {
@@ -193,8 +199,8 @@ __device__ __forceinline__ TileGeo tile_geo(const Pass& P, int64_t tile) {
 }
 
 // sm[l*N + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
-__device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const double* __restrict__ g,
-                                          double* sm) {
+template <typename S, typename T>
+__device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const S* __restrict__ g, T* sm) {
   const int tot = lpb * N;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
@@ -205,11 +211,12 @@ __device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, cons
       j = idx / lpb;
       l = idx - j * lpb;
     }
-    sm[l * N + j] = (l < t.nvalid) ? g[t.base + l * t.lstep + (int64_t)j * t.jstep] : 0.0;
+    sm[l * N + j] = (l < t.nvalid) ? (T)g[t.base + l * t.lstep + (int64_t)j * t.jstep] : (T)0;
   }
 }
 
-__device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const double* sm, double* g) {
+template <typename T>
+__device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const T* sm, T* g) {
   const int tot = lpb * N;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
@@ -236,10 +243,11 @@ __device__ __forceinline__ int tile_index(const TileGeo& t, int N, int lpb, int 
 }
 
 // B_{alpha} along the line (3-point stencil of 𝓗_alpha, zero beyond the interior).
-__device__ __forceinline__ double stencil_B(const double* row, int j, int N, double bd, double bo) {
-  const double lft = j > 0 ? row[j - 1] : 0.0;
-  const double rgt = j + 1 < N ? row[j + 1] : 0.0;
-  return fma(bd, row[j], bo * (lft + rgt));
+template <typename T>
+__device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
+  const T lft = j > 0 ? row[j - 1] : (T)0;
+  const T rgt = j + 1 < N ? row[j + 1] : (T)0;
+  return tfma(bd, row[j], bo * (lft + rgt));
 }
 
 // ---------------------------------------------------------------------------
@@ -247,51 +255,53 @@ __device__ __forceinline__ double stencil_B(const double* row, int j, int N, dou
 // ---------------------------------------------------------------------------
 // Toeplitz product T x for every line: x in xs[l*N + j], result written to ts[l*N + j].
 // ts may alias xs.  FFT route uses cb (lpb lines of K complex).
-__device__ void toeplitz_lines(const Pass& P, const double* xs, double* ts, double2* cb) {
+template <typename T>
+__device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* cb) {
+  using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
-  const int T = blockDim.x, tid = threadIdx.x;
+  const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_FFT) {
     const int K = P.dim.K;
     // pack y_t = x_t (t < N), 0 otherwise, as z_j = (y_2j, y_2j+1)
-    for (int b = tid; b < lpb * K; b += T) {
+    for (int b = tid; b < lpb * K; b += TH) {
       const int l = b / K, jj = b - l * K;
       const int t0 = 2 * jj, t1 = 2 * jj + 1;
-      const double* row = xs + l * N;
-      cb[l * K + jj] = make_double2(t0 < N ? row[t0] : 0.0, t1 < N ? row[t1] : 0.0);
+      const T* row = xs + l * N;
+      cb[l * K + jj] = mk<V>(t0 < N ? row[t0] : 0.0, t1 < N ? row[t1] : 0.0);
     }
     __syncthreads();
-    fft_dif(cb, K, lpb, K, P.tw);
-    toep_spectral(cb, K, lpb, K, P.dim.spec, P.tw);
-    fft_dit_inv(cb, K, lpb, K, P.tw);
-    for (int b = tid; b < lpb * N; b += T) {
+    fft_dif(cb, K, lpb, K, P.dim.twK);
+    toep_spectral(cb, K, lpb, K, P.dim.spec, P.dim.twK);
+    fft_dit_inv(cb, K, lpb, K, P.dim.twK);
+    for (int b = tid; b < lpb * N; b += TH) {
       const int l = b / N, t = b - l * N;
-      const double2 z = cb[l * K + (t >> 1)];
+      const V z = cb[l * K + (t >> 1)];
       ts[l * N + t] = (t & 1) ? z.y : z.x;
     }
     __syncthreads();
   } else {
-    const double* __restrict__ s = P.dim.s;
-    double acc[8];
+    const T* __restrict__ s = P.dim.s;
+    T acc[8];
     // dense: (T x)_a = sum_b s_|a-b| x_b; each thread accumulates its outputs in registers first
     // so ts may alias xs.
     const int tot = lpb * N;
-    for (int base = 0; base < tot; base += 8 * T) {
+    for (int base = 0; base < tot; base += 8 * TH) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * T + tid;
-        acc[r] = 0.0;
+        const int idx = base + r * TH + tid;
+        acc[r] = (T)0;
         if (idx < tot) {
           const int l = idx / N, a = idx - l * N;
-          const double* row = xs + l * N;
-          double sacc = 0.0;
-          for (int bb = 0; bb < N; ++bb) sacc = fma(__ldg(&s[abs(a - bb)]), row[bb], sacc);
+          const T* row = xs + l * N;
+          T sacc = 0;
+          for (int bb = 0; bb < N; ++bb) sacc = tfma(__ldg(&s[abs(a - bb)]), row[bb], sacc);
           acc[r] = sacc;
         }
       }
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * T + tid;
+        const int idx = base + r * TH + tid;
         if (idx < tot) ts[idx] = acc[r];
       }
       __syncthreads();
@@ -300,61 +310,115 @@ __device__ void toeplitz_lines(const Pass& P, const double* xs, double* ts, doub
 }
 
 // Orthonormal DST-I of every line in place: xs[l*N + j] holds x_{j+1}; result y_{k} at xs[l*N + k-1].
-__device__ void dst_lines(const Pass& P, double* xs, double2* cb) {
+template <typename T>
+__device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
+  using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
-  const int T = blockDim.x, tid = threadIdx.x;
+  const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_FFT) {
-    const int K = P.dim.K;
-    // odd extension y_0 = 0, y_t = x_t (1 <= t <= N), y_K = 0, y_t = -x_{2K-t}; packed in pairs
-    for (int b = tid; b < lpb * K; b += T) {
-      const int l = b / K, jj = b - l * K;
-      const double* row = xs + l * N;
-      double v[2];
+    // DST-I through a real FFT of length K = N+1 (complex FFT of length K2 = K/2):
+    //   w_j = sin(pi j/K)(x_j + x_{K-j}) + (x_j - x_{K-j})/2  (x_0 = x_K = 0),  W = DFT_K(w):
+    //   y_{2k} = -Im W_k,   y_{2k+1} - y_{2k-1} = Re W_k,  y_1 = Re W_0 / 2.
+    const int K = P.dim.K, K2 = K >> 1;
+    const T* __restrict__ sn = P.dim.sintab;
+    const V* __restrict__ tw2 = P.dim.twK2;
+    for (int b = tid; b < lpb * K2; b += TH) {
+      const int l = b / K2, m = b - l * K2;
+      const T* row = xs + l * N;
+      T w[2];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
-        const int t = 2 * jj + r;
-        v[r] = (t == 0 || t == K) ? 0.0 : (t < K ? row[t - 1] : -row[2 * K - t - 1]);
+        const int j = 2 * m + r;
+        T v = 0;
+        if (j > 0) {
+          const T xj = row[j - 1], xk = row[K - j - 1];
+          v = tfma(__ldg(&sn[j]), xj + xk, (T)0.5 * (xj - xk));
+        }
+        w[r] = v;
       }
-      cb[l * K + jj] = make_double2(v[0], v[1]);
+      cb[l * K2 + m] = mk<V>(w[0], w[1]);
     }
     __syncthreads();
-    fft_dif(cb, K, lpb, K, P.tw);
-    // y_k = -Im(Y_k) / sqrt(2K), Y_k = (E2 + W_k O2)/2, and Y_{K-k} = conj(E2 - W_k O2)/2
-    const double sc = 0.5 * rsqrt(2.0 * (double)K);
-    const int np = K / 2;  // k = 1..K/2
-    const int wstep = TWN / (2 * K);
-    for (int b = tid; b < lpb * np; b += T) {
-      const int l = b / np, k = b - l * np + 1;
-      const int kk = K - k;
-      const double2* x = cb + l * K;
-      const double2 A = x[dif_pos(k, K)], B = x[dif_pos(kk & (K - 1), K)];
-      const double imE2 = A.y - B.y;
-      const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
-      const double2 W = __ldg(&P.tw[k * wstep]);
-      const double imP = fma(W.x, O2.y, W.y * O2.x);
-      double* row = xs + l * N;
-      row[k - 1] = -sc * (imE2 + imP);
-      if (kk != k) row[kk - 1] = sc * (imE2 - imP);
+    fft_dif(cb, K2, lpb, K2, tw2);
+    // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
+    // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
+    const T sc = (T)sqrt(2.0 / (double)K);
+    const int np = K2 / 2 + 1;
+    for (int b = tid; b < lpb * np; b += TH) {
+      const int l = b / np, k = b - l * np;
+      const int kk = (K2 - k) & (K2 - 1);
+      const V* z = cb + l * K2;
+      const V A = z[dif_pos(k, K2)], B = z[dif_pos(kk, K2)];
+      const V E2 = mk<V>(A.x + B.x, A.y - B.y);
+      const V O2 = mk<V>(A.y + B.y, B.x - A.x);
+      const V Pw = cmul(__ldg(&tw2[K2 + k]), O2);
+      T* row = xs + l * N;
+      const T h = (T)0.5 * sc;
+      row[2 * k] = h * (E2.x + Pw.x);                       // sc Re W_k
+      if (k > 0) row[2 * k - 1] = -h * (E2.y + Pw.y);       // y_{2k} = -Im W_k
+      if (kk != k) {
+        row[2 * kk] = h * (E2.x - Pw.x);                    // sc Re W_{K2-k}
+        row[2 * kk - 1] = h * (E2.y - Pw.y);                // y_{2(K2-k)} = -Im W_{K2-k}
+      }
+    }
+    __syncthreads();
+    // prefix sums over the even slots of each line: y_{2k+1} = sum_{i<=k} sc Re W_i - sc Re W_0 / 2.
+    // spl threads per line scan contiguous segments; segment offsets by a block-wide shuffle scan.
+    __shared__ T scan_incl[PASS_THREADS];
+    __shared__ T warp_tot[PASS_THREADS / 32];
+    __shared__ T line_half0[PASS_THREADS];
+    int spl = TH / lpb;
+    if (spl < 1) spl = 1;
+    spl = 1 << (31 - __clz(spl));
+    if (spl > K2) spl = K2;
+    const int seg = K2 / spl;
+    const int l = tid / spl, sg = tid - l * spl;
+    const bool act = l < lpb;
+    T* row = xs + (act ? l : 0) * N;
+    T acc = 0;
+    if (act) {
+      if (sg == 0) line_half0[l] = (T)0.5 * row[0];
+      for (int k = sg * seg; k < (sg + 1) * seg; ++k) {
+        acc += row[2 * k];
+        row[2 * k] = acc;
+      }
+    }
+    const int lane = tid & 31, wp = tid >> 5;
+    T v = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T t = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += t;
+    }
+    if (lane == 31) warp_tot[wp] = v;
+    __syncthreads();
+    for (int w2 = 0; w2 < wp; ++w2) v += warp_tot[w2];
+    scan_incl[tid] = v;
+    __syncthreads();
+    if (act) {
+      const T base = l * spl > 0 ? scan_incl[l * spl - 1] : (T)0;
+      const T off = v - acc - base - line_half0[l];
+      for (int k = sg * seg; k < (sg + 1) * seg; ++k) row[2 * k] += off;
     }
     __syncthreads();
   } else {
     const int K = P.dim.K;
-    const double* __restrict__ st = P.dim.sintab;
-    const double sc = sqrt(2.0 / (double)K);
-    double acc[8];
+    const T* __restrict__ st = P.dim.sintab;
+    const T sc = (T)sqrt(2.0 / (double)K);
+    T acc[8];
     const int tot = lpb * N;
-    for (int base = 0; base < tot; base += 8 * T) {
+    for (int base = 0; base < tot; base += 8 * TH) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * T + tid;
-        acc[r] = 0.0;
+        const int idx = base + r * TH + tid;
+        acc[r] = (T)0;
         if (idx < tot) {
           const int l = idx / N, k = idx - l * N + 1;
-          const double* row = xs + l * N;
-          double sacc = 0.0;
+          const T* row = xs + l * N;
+          T sacc = 0;
           int ph = k;  // (j * k) mod 2K for j = 1
           for (int j = 1; j <= N; ++j) {
-            sacc = fma(__ldg(&st[ph]), row[j - 1], sacc);
+            sacc = tfma(__ldg(&st[ph]), row[j - 1], sacc);
             ph += k;
             if (ph >= 2 * K) ph -= 2 * K;
           }
@@ -364,7 +428,7 @@ __device__ void dst_lines(const Pass& P, double* xs, double2* cb) {
       __syncthreads();
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * T + tid;
+        const int idx = base + r * TH + tid;
         if (idx < tot) xs[idx] = acc[r];
       }
       __syncthreads();
@@ -376,21 +440,23 @@ __device__ void dst_lines(const Pass& P, double* xs, double2* cb) {
 // the line-pass kernel
 // ---------------------------------------------------------------------------
 // Shared memory: ra, rc (lpb*N doubles each) then cb (lpb*K complex, FFT route, 16-byte aligned).
-__global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
+template <typename T>
+__global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
+  using V = vec2<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = P.len, lpb = P.lpb;
-  double* ra = reinterpret_cast<double*>(smraw);
-  double* rc = ra + lpb * N;
-  // ra and rc together hold an even number of doubles, so cb starts 16-byte aligned
-  double2* cb = reinterpret_cast<double2*>(rc + lpb * N);
+  T* ra = reinterpret_cast<T*>(smraw);
+  T* rc = ra + lpb * N;
+  // ra and rc together hold an even number of elements, so cb starts aligned to sizeof(V)
+  V* cb = reinterpret_cast<V*>(rc + lpb * N);
   if (P.g && P.g->done) return;
   const TileGeo tg = tile_geo(P, blockIdx.x);
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int tot = lpb * N;
-  const double* in_a = P.in_a;
-  double* out_a = P.out_a;
-  if (P.in_sel) in_a = P.vbase + (int64_t)(P.g->j + P.in_sel - 1) * P.vstride;
-  if (P.out_sel) out_a = P.vbase + (int64_t)(P.g->j + P.out_sel - 1) * P.vstride;
+  const int TH = blockDim.x, tid = threadIdx.x;
+  const int NT = lpb * N;
+  const T* in_a = P.in_a;
+  T* out_a = P.out_a;
+  if (P.in_sel) in_a = P.in_base + (int64_t)(P.g->j + P.in_sel - 1) * P.vstride;
+  if (P.out_sel) out_a = P.out_base + (int64_t)(P.g->j + P.out_sel - 1) * P.vstride;
 
   if (P.toep_only) {
     tile_load(tg, N, lpb, in_a, ra);
@@ -402,14 +468,15 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
 
   if (P.mv) {
     tile_load(tg, N, lpb, in_a, ra);
-    tile_load(tg, N, lpb, P.in_c, rc);
+    if (P.first) tile_load(tg, N, lpb, P.e, rc);
+    else tile_load(tg, N, lpb, P.in_c, rc);
     __syncthreads();
-    const double bd = P.dim.bdiag, bo = P.dim.boff;
+    const T bd = P.dim.bdiag, bo = P.dim.boff;
     if (P.first) {
       // ra = x, rc = e  ->  ra = e∘x (kept), rc = x (Toeplitz input), c_out = B x
-      for (int idx = tid; idx < tot; idx += T) {
-        const double x = ra[idx];
-        const double e = rc[idx];
+      for (int idx = tid; idx < NT; idx += TH) {
+        const T x = ra[idx];
+        const T e = rc[idx];
         rc[idx] = x;
         ra[idx] = e * x;
       }
@@ -418,10 +485,10 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
     // Toeplitz of channel c into cb-backed scratch: result t_j kept in registers below.
     // First compute c_out = B c (needs c before it is overwritten), stream it to global.
     if (!P.last) {
-      for (int idx = tid; idx < tot; idx += T) {
+      for (int idx = tid; idx < NT; idx += TH) {
         int l, j;
         tile_index(tg, N, lpb, idx, l, j);
-        const double v = stencil_B(rc + l * N, j, N, bd, bo);
+        const T v = stencil_B(rc + l * N, j, N, bd, bo);
         if (l < tg.nvalid) P.out_c[tg.base + l * tg.lstep + (int64_t)j * tg.jstep] = v;
       }
     }
@@ -429,10 +496,10 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
     __syncthreads();
     // T c in place (rc <- T c); B a needs ra intact.
     toeplitz_lines(P, rc, rc, cb);
-    for (int idx = tid; idx < tot; idx += T) {
+    for (int idx = tid; idx < NT; idx += TH) {
       const int l = idx / N, j = idx - l * N;
-      const double ba = stencil_B(ra + l * N, j, N, bd, bo);
-      rc[idx] = fma(P.seta, rc[idx], ba);
+      const T ba = stencil_B(ra + l * N, j, N, bd, bo);
+      rc[idx] = tfma((T)P.seta, rc[idx], ba);
     }
     __syncthreads();
     if (!P.last) {
@@ -442,7 +509,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
     if (P.finish == FIN_ADD_F || P.finish == FIN_RESID) {
       tile_load(tg, N, lpb, P.src, ra);
       __syncthreads();
-      for (int idx = tid; idx < tot; idx += T)
+      for (int idx = tid; idx < NT; idx += TH)
         rc[idx] = (P.finish == FIN_ADD_F) ? rc[idx] + ra[idx] : ra[idx] - rc[idx];
       __syncthreads();
     }
@@ -457,7 +524,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
     if (P.post == POST_DST_MU_DST) {
       tile_load(tg, N, lpb, P.invmu, ra);
       __syncthreads();
-      for (int idx = tid; idx < tot; idx += T) rc[idx] *= ra[idx];
+      for (int idx = tid; idx < NT; idx += TH) rc[idx] *= ra[idx];
       __syncthreads();
       dst_lines(P, rc, cb);
     }
@@ -465,44 +532,52 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const Pass P) {
   tile_store(tg, N, lpb, rc, out_a);
 }
 
-size_t pass_smem_bytes(const Pass& p) {
+template <typename T>
+size_t pass_smem_bytes(const PassT<T>& p) {
   const size_t real = (size_t)p.lpb * p.len;
-  size_t bytes = 2 * real * sizeof(double);
-  if (p.dim.route == ROUTE_FFT) bytes += (size_t)p.lpb * p.dim.K * sizeof(double2);
+  size_t bytes = 2 * real * sizeof(T);
+  if (p.dim.route == ROUTE_FFT) bytes += (size_t)p.lpb * p.dim.K * sizeof(vec2<T>);
   return bytes;
 }
 
-__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ tw);
+__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ twK);
 
 cudaError_t init_kernel_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-cudaError_t launch_pass(const Pass& p, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
   if (p.ntiles <= 0) return cudaSuccess;
   const size_t smem = pass_smem_bytes(p);
-  k_pass<<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
+  k_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }
+
+template size_t pass_smem_bytes<double>(const PassT<double>&);
+template size_t pass_smem_bytes<float>(const PassT<float>&);
+template cudaError_t launch_pass<double>(const PassT<double>&, cudaStream_t);
+template cudaError_t launch_pass<float>(const PassT<float>&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // setup: circulant spectrum lambda_k = DFT_{2K}(c)_k, k = 0..K (c real symmetric)
 // ---------------------------------------------------------------------------
-__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ tw) {
+__global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ twK) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double2* cb = reinterpret_cast<double2*>(smraw);
   for (int j = threadIdx.x; j < K; j += blockDim.x) cb[j] = make_double2(c[2 * j], c[2 * j + 1]);
   __syncthreads();
-  fft_dif(cb, K, 1, K, tw);
-  const int wstep = TWN / (2 * K);
+  fft_dif(cb, K, 1, K, twK);
   for (int k = threadIdx.x; k <= K / 2; k += blockDim.x) {
     const int kk = (K - k) & (K - 1);
     const double2 A = cb[dif_pos(k, K)], B = cb[dif_pos(kk, K)];
     const double2 E2 = make_double2(A.x + B.x, A.y - B.y);
     const double2 O2 = make_double2(A.y + B.y, B.x - A.x);
-    const double2 W = tw[k * wstep];
+    const double2 W = twK[K + k];
     const double2 P = cmul(W, O2);
     lam[k] = 0.5 * (E2.x + P.x);          // Re Y_k
     if (k == 0) lam[K] = 0.5 * (E2.x - P.x);  // Y_K = conj(E2 - W O2)/2 at k = 0
@@ -510,9 +585,40 @@ __global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, con
   }
 }
 
-cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* tw, cudaStream_t st) {
+cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* twK, cudaStream_t st) {
   const size_t smem = (size_t)K * sizeof(double2);
-  k_spectrum<<<1, PASS_THREADS, smem, st>>>(K, c, lam, tw);
+  k_spectrum<<<1, PASS_THREADS, smem, st>>>(K, c, lam, twK);
+  return cudaGetLastError();
+}
+
+// Stage-packed twiddles on the device (angles reduced exactly in integers first).
+__global__ void k_twp(int S, double2* twp) {
+  const int n = twp_size(S);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    double num = 0.0, den = 1.0;   // angle = -2 pi num / den
+    if (t < S) {
+      // find the stage holding t: stage of size s starts at S - s and spans 3 s / 4 entries;
+      // entries past the last stage are unused (angle 0)
+      int size = S;
+      while (size >= 4 && t >= S - size + 3 * (size >> 2)) size >>= 2;
+      if (size >= 4) {
+        const int q = size >> 2, off = t - (S - size);
+        const int r = off / q + 1, i = off - (r - 1) * q;
+        num = (double)((r * i) % size);
+        den = (double)size;
+      }
+    } else {
+      num = (double)(t - S);
+      den = 2.0 * S;
+    }
+    double sv, cv;
+    sincospi(-2.0 * num / den, &sv, &cv);
+    twp[t] = make_double2(cv, sv);
+  }
+}
+
+cudaError_t launch_twp(int S, double2* twp, cudaStream_t st) {
+  k_twp<<<(twp_size(S) + 255) / 256, 256, 0, st>>>(S, twp);
   return cudaGetLastError();
 }
 

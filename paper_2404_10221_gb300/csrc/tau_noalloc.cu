@@ -29,30 +29,21 @@ constexpr int NA_MAX_N = KMAX - 1;            // points per dimension (4095)
 constexpr int NA_MAX_DEVICES = 64;
 
 // Layout of the scratch, in doubles.
-constexpr size_t NA_TW = 0;                                   // TWN complex twiddles
-constexpr size_t NA_CHAN_A = NA_TW + 2 * (size_t)TWN;         // channel a
+constexpr size_t NA_CHAN_A = 0;                               // channel a
 constexpr size_t NA_CHAN_C = NA_CHAN_A + NA_MAX_UNKNOWNS;     // channel c
 constexpr size_t NA_DIM0 = NA_CHAN_C + NA_MAX_UNKNOWNS;       // per-dimension tables
 constexpr size_t NA_DIM_S = 0;                                // weights s_0..s_{n-1}
 constexpr size_t NA_DIM_C = NA_DIM_S + KMAX;                  // circulant first column, 2K
 constexpr size_t NA_DIM_LAM = NA_DIM_C + 2 * (size_t)KMAX;    // spectrum lambda_0..lambda_K
 constexpr size_t NA_DIM_SPEC = NA_DIM_LAM + KMAX + 2;         // (sigma, delta) pairs, K/2+1
-constexpr size_t NA_DIM_STRIDE = NA_DIM_SPEC + KMAX + 2;
+constexpr size_t NA_DIM_TWK = NA_DIM_SPEC + KMAX + 2;         // stage-packed twiddles, 2K+1 pairs
+constexpr size_t NA_DIM_STRIDE = NA_DIM_TWK + 4 * (size_t)KMAX + 2;
 constexpr size_t NA_TOTAL = NA_DIM0 + 3 * NA_DIM_STRIDE;      // ~4.8 MB
 
 static __device__ __align__(256) double g_tau_noalloc_scratch[NA_TOTAL];
 
 std::mutex g_na_mutex;
 double* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
-
-// tw[t] = exp(-2 pi i t / TWN)
-__global__ void k_na_twiddles(double2* tw) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < TWN; t += gridDim.x * blockDim.x) {
-    double s, c;
-    sincospi(-2.0 * (double)t / (double)TWN, &s, &c);
-    tw[t] = make_double2(c, s);
-  }
-}
 
 // FCD weights by the recurrence of §2 and the circulant embedding of length 2K of S_alpha
 // (c_0 = s_0, c_k = c_{2K-k} = s_k for 1 <= k < n, zero elsewhere).
@@ -136,10 +127,6 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     base = g_na_ptr[dev];
   }
 
-  double2* tw = reinterpret_cast<double2*>(base + NA_TW);
-  k_na_twiddles<<<(TWN + 255) / 256, 256, 0, st>>>(tw);
-  if ((ce = cudaGetLastError()) != cudaSuccess) return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
-
   const double dt = D.T / (double)D.M;
   DimData dims[3];
   for (int i = 0; i < D.d; ++i) {
@@ -157,9 +144,13 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     Dd.s = dimb + NA_DIM_S;
     Dd.sintab = nullptr;
     Dd.spec = reinterpret_cast<const double2*>(dimb + NA_DIM_SPEC);
+    double2* twk = reinterpret_cast<double2*>(dimb + NA_DIM_TWK);
+    Dd.twK = twk;
+    Dd.twK2 = nullptr;
     k_na_weights<<<1, 256, 0, st>>>(D.alpha[i], n, dimb + NA_DIM_S, dimb + NA_DIM_C);
     if (fft) {
-      if ((ce = launch_spectrum(K, dimb + NA_DIM_C, dimb + NA_DIM_LAM, tw, st)) != cudaSuccess)
+      if ((ce = launch_twp(K, twk, st)) != cudaSuccess) return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
+      if ((ce = launch_spectrum(K, dimb + NA_DIM_C, dimb + NA_DIM_LAM, twk, st)) != cudaSuccess)
         return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
       k_na_spec<<<1, 256, 0, st>>>(K, dimb + NA_DIM_LAM, reinterpret_cast<double2*>(dimb + NA_DIM_SPEC));
     }
@@ -186,7 +177,6 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     if (lpb > cap) lpb = cap;
     P.lpb = (int)lpb;
     P.ntiles = ax == 0 ? (P.nlines + lpb - 1) / lpb : (P.nlines / inner) * ((inner + lpb - 1) / lpb);
-    P.tw = tw;
     P.mv = 1;
     P.first = ax == 0;
     P.last = ax == D.d - 1;
@@ -194,7 +184,8 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     P.finish = FIN_NONE;
     P.post = POST_NONE;
     P.in_a = ax == 0 ? x : chA;
-    P.in_c = ax == 0 ? e : chC;
+    P.in_c = ax == 0 ? nullptr : chC;
+    P.e = ax == 0 ? e : nullptr;
     P.out_a = P.last ? y : chA;
     P.out_c = P.last ? nullptr : chC;
     if ((ce = launch_pass(P, st)) != cudaSuccess) return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
