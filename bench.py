@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision form measurements")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: set up the workload (2 Krylov slots) and run this many "
@@ -191,6 +192,58 @@ def pass_flops_2d(n: int) -> float:
     return lines * sum(per_line.values())
 
 
+def measure_steps(wl, precision, warm, timed, stream, dev):
+    """Time `timed` steps (CUDA events per step, L2 flushed between steps) after `warm` steps."""
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+
+    prob = tau.Problem(wl, precision=precision, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tau.tau_step(prob.handle, warm)
+    tau.tau_sync(prob.handle, allow_notconv=True)
+    ms = 0.0
+    for _ in range(timed):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tau.tau_step(prob.handle, 1)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    u = prob.solution()
+    st = tau.tau_get_stats(prob.handle)
+    its = tau.tau_get_iters(prob.handle, wl.prob.M)[warm:warm + timed]
+    prob.close()
+    return wl.prob.n_tot * timed / (ms * 1e-3), ms / timed, u, st, its
+
+
+def run_forms(stream, dev):
+    """Mixed-precision form against the plain FP64 path: the 3-D 255^3 workload (its own config)
+    and the 2-D benchmark workload."""
+    import numpy as np
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    out = {}
+    for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
+        v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
+        vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)
+        rel = (torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)).item()
+        out[name] = {
+            "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_compared": warm + timed,
+            "mixed_value": vmx, "mixed_ms_per_step": msmx, "plain_fp64_value": v64, "plain_fp64_ms_per_step": ms64,
+            "speedup_vs_plain_fp64": vmx / v64, "rel_err_vs_plain_fp64": rel,
+            "mixed_inner_iters_per_step": float(np.mean(itmx)) if len(itmx) else None,
+            "mixed_sweeps_total": int(stmx.total_sweeps), "plain_iters_per_step": float(np.mean(it64)),
+            "unit": UNIT, "dtype": "f32 inner (FFT tau solve, matvec, Arnoldi) + f64 residual/refinement",
+        }
+    return out
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -247,6 +300,7 @@ def run_native(args):
     st = tau.tau_get_stats(h)
     its = tau.tau_get_iters(h, pr.M)[Wm:Wm + K]
     kernels = int(K * (st.kernels_prologue + st.kernels_epilogue) + its.sum() * st.kernels_per_iter)
+    # (the steps' kernel count from the library's own log, timed steps only)
     value = world * n_tot * K / t_dev
 
     # ---- live roofline of the dominant kernel: the line-pass kernel (4 launches per matvec)
@@ -306,6 +360,7 @@ def run_native(args):
                "api": "tau_set_solution(host) + tau_step(1) + tau_get_solution(host), pinned buffers"}
         prob2.close()
 
+    forms = None if args.no_forms else run_forms(stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -313,6 +368,7 @@ def run_native(args):
         "config": config(world, {"gmres_iters_per_step": float(np.mean(its)) if len(its) else None,
                                  "graph": bool(st.graph), "wall_s_timed": t_wall}),
         "roofline": roof, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": kernels,
+        "forms": forms,
     }
     prob.close()
     if rank == 0 and not args.no_cpu_baseline:

@@ -57,6 +57,9 @@ typedef int tau_status;
 #define TAU_X0_PREV 1         /* GMRES initial guess u^{(m)} */
 
 #define TAU_FP64 0            /* plain FP64 arithmetic everywhere */
+#define TAU_MIXED 1           /* FP64 iterative refinement (residual b - A x, correction, stopping)
+                                 around an inner flexible GMRES whose matvec, tau solve and Arnoldi
+                                 vectors are FP32 (SURVEY spec form 1) */
 
 #define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
@@ -76,10 +79,15 @@ typedef struct {
   double tol;           /* GMRES stop: ||r_k|| <= tol ||r_0|| on the preconditioned residual */
   int max_iter;         /* GMRES iteration cap per step, 1..1000 (no restart) */
   int x0_mode;          /* TAU_X0_ZERO or TAU_X0_PREV */
-  int precision;        /* TAU_FP64 */
+  int precision;        /* TAU_FP64 or TAU_MIXED */
   int route[3];         /* TAU_ROUTE_* per dimension */
   double e_min, e_max;  /* bounds of e over the grid and all t_{m+1/2} for ebar (Eqs. (bard),
                            (dhat)); pass NaN for both to let tau_setup scan them */
+  /* TAU_MIXED only (0 selects the default): */
+  double refine_tol;    /* stop refining at ||b - A x||_2 <= refine_tol ||b - A x_0||_2 (FP64); 1e-10 */
+  int inner_max_iter;   /* inner FGMRES iterations per refinement sweep, 1..1000; 30 */
+  int max_sweeps;       /* refinement sweeps per step; 10 */
+  double inner_tol;     /* inner FGMRES relative residual target; 1e-5 */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
@@ -109,6 +117,9 @@ typedef struct {
   int64_t kernels_prologue; /* kernels of one step: prologue + iters * per_iter + epilogue */
   int64_t kernels_per_iter;
   int64_t kernels_epilogue;
+  int64_t kernels_total;    /* kernels launched by the completed steps */
+  int64_t total_sweeps;     /* TAU_MIXED: refinement sweeps over the completed steps (iters count the
+                               inner FGMRES iterations) */
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of
@@ -179,12 +190,36 @@ tau_status tau_dst(tau_problem* p, const double* x, double* y);
  * along dimension dim (0-based; unscaled, no eta). */
 tau_status tau_toeplitz_mode(tau_problem* p, int dim, const double* x, double* y);
 
+/* FP32 operators of the inner solve of a TAU_MIXED problem (device float vectors of n_tot):
+ * y = A^{(m)} x and z = M^{-1} r with every step in FP32 (tables rounded from their FP64 values). */
+tau_status tau_apply_A_f32(tau_problem* p, int64_t m, const float* x, float* y);
+tau_status tau_apply_Minv_f32(tau_problem* p, const float* r, float* z);
+
 /* ebar, e_hat, e_check (Eqs. (bard), (dhat)); requires tau_setup. */
 tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_check);
 
 /* Measured FP64 FMA throughput of the current device in FLOP/s (diagnostic used for the
  * roofline of the FP64-bound kernels; runs a bounded kernel for a few milliseconds). */
 tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s);
+
+/* ---- batching: many independent problems advanced by one graph launch per step.
+ *
+ * tau_batch_create groups `count` problems that have completed tau_setup, share the CUDA device,
+ * and stand at the same step m with the same M, into one CUDA graph: one branch per problem, each
+ * holding that problem's whole step (right-hand side, its own device-controlled GMRES or
+ * refinement loop, update).  Branches have no dependencies on one another, so the GPU overlaps
+ * the problems' kernels; a problem's arithmetic is the same as when it is stepped alone.
+ * The batch does not own the problems (destroy the batch first).  Problems may mix precisions,
+ * sizes and dimensions.  While a batch exists, do not step its problems individually.
+ * Errors: TAU_EINVAL (NULL, count < 1, problems at different m or M), TAU_ESTATE (not set up),
+ * TAU_EUNSUPPORTED (graph construction failed), TAU_ENOMEM. */
+typedef struct tau_batch tau_batch;
+tau_status tau_batch_create(tau_problem* const* problems, int count, void* stream, tau_batch** out);
+/* Advance every problem of the batch by `count` steps (asynchronous; one graph launch per step). */
+tau_status tau_batch_step(tau_batch* b, int64_t count);
+/* Wait for the batch's work; TAU_ENOTCONV if some problem's step hit its iteration cap. */
+tau_status tau_batch_sync(tau_batch* b);
+tau_status tau_batch_destroy(tau_batch* b);
 
 /* ---- allocation-free entry point (the paper has no counterpart).
  *

@@ -83,6 +83,20 @@ struct tau_problem {
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
   int64_t k_pro = 0, k_body = 0, k_epi = 0;  // kernels per prologue / GMRES iteration / epilogue
+  // mixed precision (FP64 refinement around an FP32 flexible GMRES)
+  bool mixed = false;
+  int kin = 0;                                 // inner iteration cap
+  double *X = nullptr;                         // FP64 iterate of the refinement
+  float *V32 = nullptr, *Z32 = nullptr, *A32 = nullptr, *C32 = nullptr, *invmu32 = nullptr;
+  double *Hin = nullptr, *csin = nullptr, *snin = nullptr, *gvin = nullptr, *h1in = nullptr, *h2in = nullptr,
+         *yin = nullptr;
+  GmresDev* gin = nullptr;
+  IRDev* ir = nullptr;
+  int* sweeps = nullptr;
+  float2 *spec32[3] = {nullptr, nullptr, nullptr}, *twK32[3] = {nullptr, nullptr, nullptr},
+         *twK2_32[3] = {nullptr, nullptr, nullptr};
+  float *s32[3] = {nullptr, nullptr, nullptr}, *sintab32[3] = {nullptr, nullptr, nullptr};
+  int64_t k_ir_pre = 0, k_ir_post = 0;         // kernels of one refinement sweep around the inner loop
   int64_t fields_m = -1;                      // step whose e and dt*F sit in E / Fdt
   int* h_done = nullptr;  // pinned flag for the host-loop fallback
   std::vector<void*> allocs;
@@ -133,27 +147,37 @@ FieldDev field_dev(const tau_problem* p) {
   return f;
 }
 
-Pass base_pass(const tau_problem* p, int ax) {
-  Pass P{};
+template <typename T>
+PassT<T> base_pass_t(const tau_problem* p, int ax) {
+  PassT<T> P{};
   P.ax = ax;
   P.len = p->n[ax];
   int64_t inner = 1;
   for (int i = 0; i < ax; ++i) inner *= p->n[i];
   P.inner = inner;
   P.nlines = p->n_tot / P.len;
-  DimData& D = P.dim;
+  DimDataT<T>& D = P.dim;
   D.n = p->n[ax];
   D.K = p->n[ax] + 1;
   D.route = p->route[ax];
-  D.bdiag = 1.0 - p->desc.alpha[ax] / 12.0;
-  D.boff = p->desc.alpha[ax] / 24.0;
+  D.bdiag = (T)(1.0 - p->desc.alpha[ax] / 12.0);
+  D.boff = (T)(p->desc.alpha[ax] / 24.0);
   D.eta = p->eta[ax];
-  D.spec = p->spec[ax];
-  D.s = p->s[ax];
-  D.sintab = p->sintab[ax];
-  D.twK = p->twK[ax];
-  D.twK2 = p->twK2[ax];
-  const size_t per_line = 16 * (size_t)P.len + (D.route == ROUTE_FFT ? 16 * (size_t)D.K : 0);
+  if constexpr (sizeof(T) == 8) {
+    D.spec = p->spec[ax];
+    D.s = p->s[ax];
+    D.sintab = p->sintab[ax];
+    D.twK = p->twK[ax];
+    D.twK2 = p->twK2[ax];
+    P.in_base = P.out_base = p->V;
+  } else {
+    D.spec = p->spec32[ax];
+    D.s = p->s32[ax];
+    D.sintab = p->sintab32[ax];
+    D.twK = p->twK32[ax];
+    D.twK2 = p->twK2_32[ax];
+  }
+  const size_t per_line = 2 * sizeof(T) * (size_t)P.len + (D.route == ROUTE_FFT ? 2 * sizeof(T) * (size_t)D.K : 0);
   int64_t lpb = (int64_t)(32768 / per_line);
   if (lpb < 1) lpb = 1;
   if (lpb > 16) lpb = 16;
@@ -162,38 +186,73 @@ Pass base_pass(const tau_problem* p, int ax) {
   P.lpb = (int)lpb;
   const int64_t outer = P.nlines / inner;
   P.ntiles = ax == 0 ? (P.nlines + lpb - 1) / lpb : outer * ((inner + lpb - 1) / lpb);
-  P.in_base = p->V;
-  P.out_base = p->V;
   P.vstride = p->n_tot;
   return P;
 }
 
-// I/O of a pass chain: plain pointers, or V_j / V_{j+1} selected on the device.
-struct ChainIO {
-  const double* x = nullptr;
-  double* out = nullptr;
+Pass base_pass(const tau_problem* p, int ax) { return base_pass_t<double>(p, ax); }
+
+// I/O of a pass chain: plain pointers, or vectors selected on the device by the Arnoldi index j
+// (sel 1: base + j * n_tot, sel 2: base + (j+1) * n_tot).
+template <typename T>
+struct ChainT {
+  const T* x = nullptr;
+  T* out = nullptr;
   int in_sel = 0, out_sel = 0;
+  T* in_base = nullptr;
+  T* out_base = nullptr;
   const GmresDev* g = nullptr;
 };
+using ChainIO = ChainT<double>;
 
-tau_status enq(const Pass& P, cudaStream_t st) {
+template <typename T>
+tau_status enq(const PassT<T>& P, cudaStream_t st) {
   KL(launch_pass(P, st));
   return TAU_OK;
 }
 
+template <typename T> const T* invmu_of(const tau_problem* p);
+template <> const double* invmu_of<double>(const tau_problem* p) { return p->invmu; }
+template <> const float* invmu_of<float>(const tau_problem* p) { return p->invmu32; }
+template <typename T> T* chanA(const tau_problem* p);
+template <typename T> T* chanC(const tau_problem* p);
+template <> double* chanA<double>(const tau_problem* p) { return p->A; }
+template <> double* chanC<double>(const tau_problem* p) { return p->C; }
+template <> float* chanA<float>(const tau_problem* p) { return p->A32; }
+template <> float* chanC<float>(const tau_problem* p) { return p->C32; }
+
+template <typename T>
+void wire_in(PassT<T>& P, const ChainT<T>& io, bool from_x) {
+  if (from_x) {
+    P.in_a = io.x;
+    P.in_sel = io.in_sel;
+    if (io.in_base) P.in_base = io.in_base;
+  } else {
+    P.in_a = io.out;
+    P.in_sel = io.out_sel;
+    if (io.out_base) P.in_base = io.out_base;
+  }
+}
+
+template <typename T>
+void wire_out(PassT<T>& P, const ChainT<T>& io) {
+  P.out_a = io.out;
+  P.out_sel = io.out_sel;
+  if (io.out_base) P.out_base = io.out_base;
+}
+
 // DST along dims top..1 (descending), DST·(1/mu)·DST along dim 0, DST along dims 1..d-1,
 // reading `x` in the first pass and working in place on `out` afterwards.
-tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainIO& io, int top, bool first_reads_x) {
+template <typename T>
+tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainT<T>& io, int top, bool first_reads_x) {
   bool rd = first_reads_x;
   auto dst_pass = [&](int ax, int post) -> tau_status {
-    Pass P = base_pass(p, ax);
+    PassT<T> P = base_pass_t<T>(p, ax);
     P.post = post;
-    P.invmu = p->invmu;
+    P.invmu = invmu_of<T>(p);
     P.g = io.g;
-    P.in_a = rd ? io.x : io.out;
-    P.in_sel = rd ? io.in_sel : io.out_sel;
-    P.out_a = io.out;
-    P.out_sel = io.out_sel;
+    wire_in(P, io, rd);
+    wire_out(P, io);
     rd = false;
     return enq(P, st);
   };
@@ -204,46 +263,43 @@ tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainIO& io, int
 }
 
 // out = finish( B(e∘x) + sgn*sum_i eta_i (..S_i..) x ), optionally followed by M^{-1}.
-tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainIO& io, double sgn, int finish, const double* src,
+template <typename T>
+tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double sgn, int finish, const T* src,
                   bool precond) {
   const int d = p->d;
   for (int ax = 0; ax < d; ++ax) {
-    Pass P = base_pass(p, ax);
+    PassT<T> P = base_pass_t<T>(p, ax);
     P.mv = 1;
     P.first = ax == 0;
     P.last = ax == d - 1;
     P.seta = sgn * p->eta[ax];
     P.g = io.g;
     if (ax == 0) {
-      P.in_a = io.x;
-      P.in_sel = io.in_sel;
+      wire_in(P, io, true);
       P.e = p->E;
     } else {
-      P.in_a = p->A;
-      P.in_c = p->C;
+      P.in_a = chanA<T>(p);
+      P.in_c = chanC<T>(p);
     }
     if (!P.last) {
-      P.out_a = p->A;
-      P.out_c = p->C;
+      P.out_a = chanA<T>(p);
+      P.out_c = chanC<T>(p);
     } else {
-      P.out_a = io.out;
-      P.out_sel = io.out_sel;
+      wire_out(P, io);
       P.finish = finish;
       P.src = src;
-      P.invmu = p->invmu;
+      P.invmu = invmu_of<T>(p);
       if (precond) P.post = d == 1 ? POST_DST_MU_DST : POST_DST;
     }
     TRY(enq(P, st));
   }
-  if (precond && d > 1) {
-    ChainIO t = io;
-    TRY(enq_minv_tail(p, st, t, d - 2, false));
-  }
+  if (precond && d > 1) TRY(enq_minv_tail<T>(p, st, io, d - 2, false));
   return TAU_OK;
 }
 
-tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainIO& io) {
-  return enq_minv_tail(p, st, io, p->d - 1, true);
+template <typename T>
+tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainT<T>& io) {
+  return enq_minv_tail<T>(p, st, io, p->d - 1, true);
 }
 
 tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
@@ -251,15 +307,15 @@ tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
   ChainIO rhs;
   rhs.x = p->u;
   rhs.out = p->b;
-  TRY(enq_mv(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
+  TRY(enq_mv<double>(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
   ChainIO r0;
   r0.out = p->V;
   if (p->desc.x0_mode == TAU_X0_PREV) {
     r0.x = p->u;
-    TRY(enq_mv(p, st, r0, 1.0, FIN_RESID, p->b, true));
+    TRY(enq_mv<double>(p, st, r0, 1.0, FIN_RESID, p->b, true));
   } else {
     r0.x = p->b;
-    TRY(enq_minv(p, st, r0));
+    TRY(enq_minv<double>(p, st, r0));
   }
   KL(launch_norm_partial(p->V, p->n_tot, p->g, p->pnorm, st));
   tl_launches += 1;
@@ -272,15 +328,82 @@ tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle 
   it.in_sel = 1;
   it.out_sel = 2;
   it.g = p->g;
-  TRY(enq_mv(p, st, it, 1.0, FIN_NONE, nullptr, true));
+  TRY(enq_mv<double>(p, st, it, 1.0, FIN_NONE, nullptr, true));
   const int ld = RED_BLOCKS;
-  KL(launch_dots(p->V, p->n_tot, p->g, p->pdots, ld, st));
+  KL(launch_dots<double>(p->V, p->n_tot, p->g, p->pdots, ld, st));
   KL(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
-  KL(launch_update_dots(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
+  KL(launch_update_dots<double>(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
   KL(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
-  KL(launch_update_dots(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
+  KL(launch_update_dots<double>(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
   KL(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
-  KL(launch_scale_next(p->V, p->n_tot, p->g, st));
+  KL(launch_scale_next<double>(p->V, p->n_tot, p->g, st));
+  return TAU_OK;
+}
+
+// ---- mixed precision: prologue, refinement sweep (before / after the inner loop), inner
+//      FGMRES iteration, epilogue
+tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
+  KL(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
+  ChainIO rhs;
+  rhs.x = p->u;
+  rhs.out = p->b;
+  TRY(enq_mv<double>(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
+  if (p->desc.x0_mode == TAU_X0_PREV)
+    CK(cudaMemcpyAsync(p->X, p->u, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else
+    CK(cudaMemsetAsync(p->X, 0, p->n_tot * sizeof(double), st));
+  KL(launch_ir_init(p->ir, st));
+  return TAU_OK;
+}
+
+tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalHandle h_in, int use_cond) {
+  ChainIO r;
+  r.x = p->X;
+  r.out = p->tmp;
+  TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false));   // r = b - A x, FP64
+  KL(launch_norm_partial(p->tmp, p->n_tot, p->g, p->pnorm, st));
+  KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, h, h_in, use_cond, st));
+  KL(launch_scale_to_f32(p->tmp, p->V32, p->n_tot, p->ir, st));
+  return TAU_OK;
+}
+
+tau_status enq_mx_inner(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+  // z_j = M^{-1} v_j (FP32), v_{j+1} = A z_j (FP32), CGS2, Givens: flexible GMRES
+  ChainT<float> pz;
+  pz.in_sel = 1;
+  pz.in_base = p->V32;
+  pz.out_sel = 1;
+  pz.out_base = p->Z32;
+  pz.g = p->gin;
+  TRY(enq_minv<float>(p, st, pz));
+  ChainT<float> av;
+  av.in_sel = 1;
+  av.in_base = p->Z32;
+  av.out_sel = 2;
+  av.out_base = p->V32;
+  av.g = p->gin;
+  TRY(enq_mv<float>(p, st, av, 1.0, FIN_NONE, nullptr, false));
+  const int ld = RED_BLOCKS;
+  KL(launch_dots<float>(p->V32, p->n_tot, p->gin, p->pdots, ld, st));
+  KL(launch_reduce_dots(p->pdots, ld, p->gin, p->h1in, st));
+  KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h1in, p->pdots, ld, 0, st));
+  KL(launch_reduce_dots(p->pdots, ld, p->gin, p->h2in, st));
+  KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h2in, p->pnorm, ld, 1, st));
+  KL(launch_givens(p->gin, p->Hin, p->csin, p->snin, p->gvin, p->h1in, p->h2in, p->pnorm, p->kin + 1, h, use_cond, st));
+  KL(launch_scale_next<float>(p->V32, p->n_tot, p->gin, st));
+  return TAU_OK;
+}
+
+tau_status enq_mx_sweep_post(tau_problem* p, cudaStream_t st) {
+  KL(launch_backsolve(p->gin, p->Hin, p->gvin, p->kin + 1, p->yin, st));
+  KL(launch_update_x(p->X, p->Z32, p->yin, p->n_tot, p->gin, p->ir, st));
+  return TAU_OK;
+}
+
+tau_status enq_mx_epilogue(tau_problem* p, cudaStream_t st) {
+  CK(cudaMemcpyAsync(p->u, p->X, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KL(launch_ir_finish(p->ir, p->g, p->iters, p->sweeps, st));
   return TAU_OK;
 }
 
@@ -291,79 +414,105 @@ tau_status enq_epilogue(tau_problem* p, cudaStream_t st) {
   return TAU_OK;
 }
 
-// Step graph: prologue -> WHILE(body; the Givens kernel sets the condition) -> epilogue.
+// Record fn(stream) into graph g after deps; leaves receives the capture's final dependencies.
+template <typename F>
+tau_status capture_into(tau_problem* p, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, F fn,
+                        std::vector<cudaGraphNode_t>& leaves) {
+  CK(cudaStreamBeginCaptureToGraph(p->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                   cudaStreamCaptureModeThreadLocal));
+  tl_launches = 0;
+  tau_status st = fn(p->cap);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* d = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(p->cap, &cst, nullptr, nullptr, &d, nullptr, &nd);
+  if (e == cudaSuccess) leaves.assign(d, d + nd);
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(p->cap, &out);
+  if (st != TAU_OK) return st;
+  if (e != cudaSuccess) return fail(TAU_EUNSUPPORTED, "capture info: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(TAU_EUNSUPPORTED, "end capture: %s", cudaGetErrorString(e2));
+  return TAU_OK;
+}
+
+// A conditional handle owned by g; its default value 1 is applied when the top-level graph is
+// launched (not when an enclosing conditional body starts again).
+tau_status make_handle(cudaGraph_t g, cudaGraphConditionalHandle* h) {
+  cudaError_t e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(TAU_EUNSUPPORTED, "conditional handle: %s", cudaGetErrorString(e));
+  return TAU_OK;
+}
+
+// A conditional WHILE node after deps, driven by handle h (created on g).
+tau_status add_while(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle* h,
+                     cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaError_t e;
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = *h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp);
+  if (e != cudaSuccess) return fail(TAU_EUNSUPPORTED, "conditional node: %s", cudaGetErrorString(e));
+  *body = cp.conditional.phGraph_out[0];
+  return TAU_OK;
+}
+
+// Plain step graph: prologue -> WHILE(GMRES iteration; the Givens kernel sets the condition) ->
+// epilogue.  Mixed step graph: prologue -> WHILE(FP64 residual and refinement control ->
+// WHILE(FP32 flexible GMRES iteration) -> correction of x) -> epilogue.
+tau_status build_graph_inner(tau_problem* p, cudaGraph_t G) {
+  std::vector<cudaGraphNode_t> none, leaves, tmp;
+  if (!p->mixed) {
+    TRY(capture_into(p, G, none, [&](cudaStream_t s) { return enq_prologue(p, s); }, leaves));
+    p->k_pro = tl_launches;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t w;
+    cudaGraph_t body;
+    TRY(make_handle(G, &h));
+    TRY(add_while(G, leaves, &h, &w, &body));
+    TRY(capture_into(p, body, none, [&](cudaStream_t s) { return enq_body(p, s, h, 1); }, tmp));
+    p->k_body = tl_launches;
+    TRY(capture_into(p, G, {w}, [&](cudaStream_t s) { return enq_epilogue(p, s); }, tmp));
+    p->k_epi = tl_launches;
+    return TAU_OK;
+  }
+  TRY(capture_into(p, G, none, [&](cudaStream_t s) { return enq_mx_prologue(p, s); }, leaves));
+  p->k_pro = tl_launches;
+  cudaGraphConditionalHandle ho, hi;
+  cudaGraphNode_t wo, wi;
+  cudaGraph_t bo, bi;
+  TRY(make_handle(G, &ho));
+  TRY(add_while(G, leaves, &ho, &wo, &bo));
+  TRY(make_handle(bo, &hi));
+  std::vector<cudaGraphNode_t> pre;
+  TRY(capture_into(p, bo, none, [&](cudaStream_t s) { return enq_mx_sweep_pre(p, s, ho, hi, 1); }, pre));
+  p->k_ir_pre = tl_launches;
+  TRY(add_while(bo, pre, &hi, &wi, &bi));
+  TRY(capture_into(p, bi, none, [&](cudaStream_t s) { return enq_mx_inner(p, s, hi, 1); }, tmp));
+  p->k_body = tl_launches;
+  TRY(capture_into(p, bo, {wi}, [&](cudaStream_t s) { return enq_mx_sweep_post(p, s); }, tmp));
+  p->k_ir_post = tl_launches;
+  TRY(capture_into(p, G, {wo}, [&](cudaStream_t s) { return enq_mx_epilogue(p, s); }, tmp));
+  p->k_epi = tl_launches;
+  return TAU_OK;
+}
+
 tau_status build_graph(tau_problem* p) {
   cudaGraph_t G = nullptr;
   CK(cudaGraphCreate(&G, 0));
-  cudaGraphConditionalHandle h;
-  cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(G);
-    cudaGetLastError();
-    return fail(TAU_EUNSUPPORTED, "conditional graph nodes unavailable: %s", cudaGetErrorString(e));
+  tau_status st = build_graph_inner(p, G);
+  if (st == TAU_OK) {
+    cudaError_t e = cudaGraphInstantiate(&p->exec, G, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(TAU_EUNSUPPORTED, "step graph: %s", cudaGetErrorString(e));
+    }
   }
-  tau_status st = TAU_OK;
-  std::vector<cudaGraphNode_t> leaves;
-  do {
-    e = cudaStreamBeginCaptureToGraph(p->cap, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    tl_launches = 0;
-    st = enq_prologue(p, p->cap);
-    p->k_pro = tl_launches;
-    {
-      cudaStreamCaptureStatus cst;
-      const cudaGraphNode_t* deps = nullptr;
-      size_t nd = 0;
-      e = cudaStreamGetCaptureInfo(p->cap, &cst, nullptr, nullptr, &deps, nullptr, &nd);
-      if (e == cudaSuccess) leaves.assign(deps, deps + nd);
-    }
-    cudaGraph_t Gout = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(p->cap, &Gout);
-    if (st != TAU_OK) break;
-    if (e == cudaSuccess) e = e2;
-    if (e != cudaSuccess) break;
-    alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
-    memset(cp_raw, 0, sizeof(cp_raw));
-    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t cnode;
-    e = cudaGraphAddNode(&cnode, G, leaves.data(), nullptr, leaves.size(), &cp);
-    if (e != cudaSuccess) break;
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(p->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    tl_launches = 0;
-    st = enq_body(p, p->cap, h, 1);
-    p->k_body = tl_launches;
-    e2 = cudaStreamEndCapture(p->cap, &Gout);
-    if (st != TAU_OK) break;
-    if (e2 != cudaSuccess) {
-      e = e2;
-      break;
-    }
-    e = cudaStreamBeginCaptureToGraph(p->cap, G, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    tl_launches = 0;
-    st = enq_epilogue(p, p->cap);
-    p->k_epi = tl_launches;
-    e2 = cudaStreamEndCapture(p->cap, &Gout);
-    if (st != TAU_OK) break;
-    if (e2 != cudaSuccess) {
-      e = e2;
-      break;
-    }
-    e = cudaGraphInstantiate(&p->exec, G, 0);
-  } while (0);
   cudaGraphDestroy(G);
-  if (st != TAU_OK) return st;
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(TAU_EUNSUPPORTED, "step graph: %s", cudaGetErrorString(e));
-  }
-  return TAU_OK;
+  return st;
 }
 
 // Host-loop fallback: one synchronisation per GMRES iteration.
@@ -382,6 +531,38 @@ tau_status run_step_hostloop(tau_problem* p) {
   }
   tl_launches = 0;
   TRY(enq_epilogue(p, p->st));
+  p->k_epi = tl_launches;
+  return TAU_OK;
+}
+
+// Host-loop fallback of the mixed-precision step.
+tau_status run_step_hostloop_mx(tau_problem* p) {
+  cudaGraphConditionalHandle dummy = 0;
+  tl_launches = 0;
+  TRY(enq_mx_prologue(p, p->st));
+  p->k_pro = tl_launches;
+  for (int sw = 0; sw <= p->desc.max_sweeps + 1; ++sw) {
+    tl_launches = 0;
+    TRY(enq_mx_sweep_pre(p, p->st, dummy, dummy, 0));
+    p->k_ir_pre = tl_launches;
+    int flags[2];
+    CK(cudaMemcpyAsync(&flags[0], &p->ir->done, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    if (flags[0]) break;
+    for (int it = 0; it < p->kin; ++it) {
+      CK(cudaMemcpyAsync(&flags[1], &p->gin->done, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+      CK(cudaStreamSynchronize(p->st));
+      if (flags[1]) break;
+      tl_launches = 0;
+      TRY(enq_mx_inner(p, p->st, dummy, 0));
+      p->k_body = tl_launches;
+    }
+    tl_launches = 0;
+    TRY(enq_mx_sweep_post(p, p->st));
+    p->k_ir_post = tl_launches;
+  }
+  tl_launches = 0;
+  TRY(enq_mx_epilogue(p, p->st));
   p->k_epi = tl_launches;
   return TAU_OK;
 }
@@ -434,7 +615,11 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (!(D.tol > 0) || D.max_iter < 1 || D.max_iter > MAX_ITER_CAP)
     return fail(TAU_EINVAL, "tol must be > 0 and 1 <= max_iter <= %d", MAX_ITER_CAP);
   if (D.x0_mode != TAU_X0_ZERO && D.x0_mode != TAU_X0_PREV) return fail(TAU_EINVAL, "x0_mode %d", D.x0_mode);
-  if (D.precision != TAU_FP64) return fail(TAU_EUNSUPPORTED, "precision %d", D.precision);
+  if (D.precision != TAU_FP64 && D.precision != TAU_MIXED) return fail(TAU_EINVAL, "precision %d", D.precision);
+  if (D.precision == TAU_MIXED &&
+      (D.refine_tol < 0 || D.inner_tol < 0 || D.inner_max_iter < 0 || D.inner_max_iter > MAX_ITER_CAP ||
+       D.max_sweeps < 0))
+    return fail(TAU_EINVAL, "mixed-precision parameters out of range");
   if (n_tot > (int64_t)1 << 31) return fail(TAU_EINVAL, "n_tot=%lld too large", (long long)n_tot);
 
   tau_problem* p = new (std::nothrow) tau_problem();
@@ -475,16 +660,36 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
   if (cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+  p->mixed = D.precision == TAU_MIXED;
+  if (p->mixed) {
+    if (p->desc.refine_tol == 0) p->desc.refine_tol = 1e-10;
+    if (p->desc.inner_max_iter == 0) p->desc.inner_max_iter = 30;
+    if (p->desc.max_sweeps == 0) p->desc.max_sweeps = 10;
+    if (p->desc.inner_tol == 0) p->desc.inner_tol = 1e-5;
+    p->kin = p->desc.inner_max_iter;
+  }
   const int mi = D.max_iter;
+  const int rows = (p->mixed ? (p->kin > mi ? p->kin : mi) : mi) + 1;
   tau_status s = TAU_OK;
   const size_t n = (size_t)n_tot;
-  if ((s = dalloc_n(p, &p->V, (size_t)(mi + 1) * n)) || (s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
+  if (!p->mixed && (s = dalloc_n(p, &p->V, (size_t)(mi + 1) * n))) return cleanup(s);
+  if (p->mixed) {
+    const int k = p->kin;
+    if ((s = dalloc_n(p, &p->X, n)) || (s = dalloc_n(p, &p->V32, (size_t)(k + 1) * n)) ||
+        (s = dalloc_n(p, &p->Z32, (size_t)k * n)) || (s = dalloc_n(p, &p->A32, n)) || (s = dalloc_n(p, &p->C32, n)) ||
+        (s = dalloc_n(p, &p->invmu32, n)) || (s = dalloc_n(p, &p->Hin, (size_t)(k + 1) * k)) ||
+        (s = dalloc_n(p, &p->csin, k)) || (s = dalloc_n(p, &p->snin, k)) || (s = dalloc_n(p, &p->gvin, k + 1)) ||
+        (s = dalloc_n(p, &p->h1in, k + 1)) || (s = dalloc_n(p, &p->h2in, k + 1)) || (s = dalloc_n(p, &p->yin, k + 1)) ||
+        (s = dalloc_n(p, &p->gin, 1)) || (s = dalloc_n(p, &p->ir, 1)) || (s = dalloc_n(p, &p->sweeps, (size_t)D.M)))
+      return cleanup(s);
+  }
+  if ((s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
       (s = dalloc_n(p, &p->A, n)) || (s = dalloc_n(p, &p->C, n)) || (s = dalloc_n(p, &p->E, n)) ||
       (s = dalloc_n(p, &p->Fdt, n)) || (s = dalloc_n(p, &p->invmu, n)) || (s = dalloc_n(p, &p->tmp, n)) ||
       (s = dalloc_n(p, &p->H, (size_t)(mi + 1) * mi)) || (s = dalloc_n(p, &p->cs, mi)) ||
       (s = dalloc_n(p, &p->sn, mi)) || (s = dalloc_n(p, &p->gv, mi + 1)) || (s = dalloc_n(p, &p->h1, mi + 1)) ||
       (s = dalloc_n(p, &p->h2, mi + 1)) || (s = dalloc_n(p, &p->y, mi + 1)) ||
-      (s = dalloc_n(p, &p->pdots, (size_t)(mi + 1) * RED_BLOCKS)) || (s = dalloc_n(p, &p->pnorm, RED_BLOCKS)) ||
+      (s = dalloc_n(p, &p->pdots, (size_t)rows * RED_BLOCKS)) || (s = dalloc_n(p, &p->pnorm, RED_BLOCKS)) ||
       (s = dalloc_n(p, &p->escan, 2 * RED_BLOCKS)) || (s = dalloc_n(p, &p->g, 1)) ||
       (s = dalloc_n(p, &p->iters, (size_t)D.M)))
     return cleanup(s);
@@ -627,6 +832,38 @@ tau_status tau_setup(tau_problem* p) {
   p->ebar = 0.5 * (p->ehat + p->echeck);
   KL(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
   KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->u, p->st));
+  if (p->mixed) {
+    auto conv = [&](const double* src, float** dst, size_t cnt) -> tau_status {
+      TRY(dalloc_n(p, dst, cnt));
+      KL(launch_f64_to_f32(src, *dst, (int64_t)cnt, p->st));
+      return TAU_OK;
+    };
+    for (int i = 0; i < d; ++i) {
+      const int N = p->n[i], K = N + 1;
+      TRY(conv(p->s[i], &p->s32[i], N));
+      TRY(conv(p->sintab[i], &p->sintab32[i], 2 * (size_t)K));
+      if (p->route[i] == ROUTE_FFT) {
+        float* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 2 * (size_t)(K / 2 + 1)));
+        p->spec32[i] = reinterpret_cast<float2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
+        p->twK32[i] = reinterpret_cast<float2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK2[i]), &f, 2 * (size_t)twp_size(K / 2)));
+        p->twK2_32[i] = reinterpret_cast<float2*>(f);
+      }
+    }
+    KL(launch_f64_to_f32(p->invmu, p->invmu32, p->n_tot, p->st));
+    IRDev ir{};
+    ir.tol = p->desc.refine_tol;
+    ir.max_sweeps = p->desc.max_sweeps;
+    CK(cudaMemcpyAsync(p->ir, &ir, sizeof(ir), cudaMemcpyHostToDevice, p->st));
+    GmresDev gi{};
+    gi.max_iter = p->kin;
+    gi.tol = p->desc.inner_tol;
+    gi.done = 1;
+    CK(cudaMemcpyAsync(p->gin, &gi, sizeof(gi), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemsetAsync(p->sweeps, 0, sizeof(int) * (size_t)p->desc.M, p->st));
+  }
   GmresDev g{};
   g.max_iter = p->desc.max_iter;
   g.tol = p->desc.tol;
@@ -655,6 +892,8 @@ tau_status tau_step(tau_problem* p, int64_t count) {
   for (int64_t c = 0; c < count; ++c) {
     if (p->graph_ok) {
       CK(cudaGraphLaunch(p->exec, p->st));
+    } else if (p->mixed) {
+      TRY(run_step_hostloop_mx(p));
     } else {
       TRY(run_step_hostloop(p));
     }
@@ -725,6 +964,20 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->kernels_prologue = p->k_pro;
   out->kernels_per_iter = p->k_body;
   out->kernels_epilogue = p->k_epi;
+  if (p->mixed) {
+    std::vector<int> sw((size_t)p->desc.M);
+    CK(cudaMemcpy(sw.data(), p->sweeps, sw.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    int64_t kt = 0, ts = 0;
+    for (int64_t m = 0; m < g.m && m < p->desc.M; ++m) {
+      ts += sw[m];
+      kt += p->k_pro + p->k_epi + (int64_t)(sw[m] + 1) * (p->k_ir_pre + p->k_ir_post) +
+            (int64_t)(it[m] + 1) * p->k_body;
+    }
+    out->kernels_total = kt;
+    out->total_sweeps = ts;
+  } else {
+    out->kernels_total = g.m * (p->k_pro + p->k_epi) + tot * p->k_body;
+  }
   out->device_bytes = p->bytes;
   if (g.notconv) return fail(TAU_ENOTCONV, "a step reached max_iter without meeting tol");
   return TAU_OK;
@@ -760,7 +1013,7 @@ tau_status tau_apply_A(tau_problem* p, int64_t m, const double* x, double* y) {
   ChainIO io;
   io.x = x;
   io.out = y;
-  return enq_mv(p, p->st, io, 1.0, FIN_NONE, nullptr, false);
+  return enq_mv<double>(p, p->st, io, 1.0, FIN_NONE, nullptr, false);
 }
 
 tau_status tau_apply_MinvA(tau_problem* p, int64_t m, const double* x, double* z) {
@@ -771,7 +1024,7 @@ tau_status tau_apply_MinvA(tau_problem* p, int64_t m, const double* x, double* z
   ChainIO io;
   io.x = x;
   io.out = z;
-  return enq_mv(p, p->st, io, 1.0, FIN_NONE, nullptr, true);
+  return enq_mv<double>(p, p->st, io, 1.0, FIN_NONE, nullptr, true);
 }
 
 tau_status tau_apply_Minv(tau_problem* p, const double* r, double* z) {
@@ -780,7 +1033,7 @@ tau_status tau_apply_Minv(tau_problem* p, const double* r, double* z) {
   ChainIO io;
   io.x = r;
   io.out = z;
-  return enq_minv(p, p->st, io);
+  return enq_minv<double>(p, p->st, io);
 }
 
 tau_status tau_rhs(tau_problem* p, int64_t m, const double* u, double* b) {
@@ -791,7 +1044,7 @@ tau_status tau_rhs(tau_problem* p, int64_t m, const double* u, double* b) {
   ChainIO io;
   io.x = u;
   io.out = b;
-  return enq_mv(p, p->st, io, -1.0, FIN_ADD_F, p->Fdt, false);
+  return enq_mv<double>(p, p->st, io, -1.0, FIN_ADD_F, p->Fdt, false);
 }
 
 tau_status tau_dst(tau_problem* p, const double* x, double* y) {
@@ -816,6 +1069,105 @@ tau_status tau_toeplitz_mode(tau_problem* p, int dim, const double* x, double* y
   P.in_a = x;
   P.out_a = y;
   return enq(P, p->st);
+}
+
+struct tau_batch {
+  std::vector<tau_problem*> probs;
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+tau_status tau_batch_create(tau_problem* const* problems, int count, void* stream, tau_batch** out) {
+  if (!problems || !out || count < 1) return fail(TAU_EINVAL, "tau_batch_create: bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    tau_problem* p = problems[i];
+    if (!p) return fail(TAU_EINVAL, "tau_batch_create: problem %d is NULL", i);
+    if (!p->setup_done) return fail(TAU_ESTATE, "tau_batch_create: problem %d not set up", i);
+    if (p->m_host != problems[0]->m_host || p->desc.M != problems[0]->desc.M)
+      return fail(TAU_EINVAL, "tau_batch_create: problems must stand at the same step m with the same M");
+    CK(cudaStreamSynchronize(p->st));
+  }
+  tau_batch* b = new (std::nothrow) tau_batch();
+  if (!b) return fail(TAU_ENOMEM, "host allocation");
+  b->probs.assign(problems, problems + count);
+  b->st = (cudaStream_t)stream;
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+    delete b;
+    return fail(TAU_ECUDA, "cudaGraphCreate");
+  }
+  tau_status st = TAU_OK;
+  for (int i = 0; i < count && st == TAU_OK; ++i) st = build_graph_inner(b->probs[i], G);
+  if (st == TAU_OK) {
+    cudaError_t e = cudaGraphInstantiate(&b->exec, G, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = fail(TAU_EUNSUPPORTED, "batch graph: %s", cudaGetErrorString(e));
+    }
+  }
+  cudaGraphDestroy(G);
+  if (st != TAU_OK) {
+    delete b;
+    return st;
+  }
+  *out = b;
+  return TAU_OK;
+}
+
+tau_status tau_batch_step(tau_batch* b, int64_t count) {
+  if (!b) return fail(TAU_EINVAL, "batch is NULL");
+  tau_problem* p0 = b->probs[0];
+  if (count < 0 || p0->m_host + count > p0->desc.M)
+    return fail(TAU_EINVAL, "count=%lld with m=%lld of M=%lld", (long long)count, (long long)p0->m_host,
+                (long long)p0->desc.M);
+  for (int64_t c = 0; c < count; ++c) CK(cudaGraphLaunch(b->exec, b->st));
+  for (tau_problem* p : b->probs) {
+    p->m_host += count;
+    if (count > 0) p->fields_m = -1;
+  }
+  return TAU_OK;
+}
+
+tau_status tau_batch_sync(tau_batch* b) {
+  if (!b) return fail(TAU_EINVAL, "batch is NULL");
+  CK(cudaStreamSynchronize(b->st));
+  tau_status worst = TAU_OK;
+  for (tau_problem* p : b->probs) {
+    tau_status s = sync_status(p);
+    if (s != TAU_OK) worst = s;
+  }
+  return worst;
+}
+
+tau_status tau_batch_destroy(tau_batch* b) {
+  if (!b) return TAU_OK;
+  cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  delete b;
+  return TAU_OK;
+}
+
+tau_status tau_apply_A_f32(tau_problem* p, int64_t m, const float* x, float* y) {
+  TRY(check_ready(p));
+  if (!p->mixed) return fail(TAU_ESTATE, "FP32 operators exist only for TAU_MIXED problems");
+  if (!x || !y) return fail(TAU_EINVAL, "NULL vector");
+  if (m < 0 || m >= p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M-1", (long long)m);
+  TRY(fields_for(p, m));
+  ChainT<float> io;
+  io.x = x;
+  io.out = y;
+  return enq_mv<float>(p, p->st, io, 1.0, FIN_NONE, nullptr, false);
+}
+
+tau_status tau_apply_Minv_f32(tau_problem* p, const float* r, float* z) {
+  TRY(check_ready(p));
+  if (!p->mixed) return fail(TAU_ESTATE, "FP32 operators exist only for TAU_MIXED problems");
+  if (!r || !z) return fail(TAU_EINVAL, "NULL vector");
+  ChainT<float> io;
+  io.x = r;
+  io.out = z;
+  return enq_minv<float>(p, p->st, io);
 }
 
 tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_check) {

@@ -146,17 +146,20 @@ cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const 
                          const double* const* q, const double* eta, double* invmu, cudaStream_t st);
 
 // GMRES building blocks
-// w = V_{j+1} (the slot of the next basis vector) in the CGS2 kernels below.
-cudaError_t launch_dots(const double* V, int64_t n, const GmresDev* g, double* partial, int ld_partial,
-                        cudaStream_t st);
+// w = V_{j+1} (the slot of the next basis vector) in the CGS2 kernels below; S is the storage
+// type of the basis (products in S, reductions in FP64).
+template <typename S>
+cudaError_t launch_dots(const S* V, int64_t n, const GmresDev* g, double* partial, int ld_partial, cudaStream_t st);
 cudaError_t launch_reduce_dots(const double* partial, int ld_partial, const GmresDev* g, double* h,
                                cudaStream_t st);
-cudaError_t launch_update_dots(double* V, int64_t n, const GmresDev* g, const double* h, double* partial,
-                               int ld_partial, int want_norm, cudaStream_t st);
+template <typename S>
+cudaError_t launch_update_dots(S* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld_partial,
+                               int want_norm, cudaStream_t st);
 cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* h1,
                           const double* h2, const double* partial_norm, int ldH,
                           cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
-cudaError_t launch_scale_next(double* V, int64_t n, const GmresDev* g, cudaStream_t st);
+template <typename S>
+cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st);
 cudaError_t launch_norm_partial(const double* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st);
 cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, double* V, int64_t n,
                              cudaStream_t st);
@@ -164,5 +167,27 @@ cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* 
                                     const double* V, int64_t n, double* u, int x0_prev, int* iters_log,
                                     cudaStream_t st);
 cudaError_t launch_fp64_peak(double* out, int blocks, int iters, cudaStream_t st);
+
+// Iterative-refinement state of the mixed-precision form (device memory).
+struct IRDev {
+  int sweep;         // corrections applied so far in this step
+  int done;
+  int max_sweeps;
+  int notconv;       // sticky: some step stopped at max_sweeps
+  int inner_total;   // inner FGMRES iterations of this step
+  int pad;
+  double tol;        // ||b - A x|| <= tol ||b - A x_0||
+  double rho0, rho, last_rel;
+};
+cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);
+cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm,
+                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
+                              cudaStream_t st);
+cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st);
+cudaError_t launch_update_x(double* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
+                            cudaStream_t st);
+cudaError_t launch_ir_finish(const IRDev* ir, GmresDev* g, int* iters_log, int* sweeps_log, cudaStream_t st);
+cudaError_t launch_backsolve(GmresDev* g, const double* H, const double* gv, int ldH, double* y, cudaStream_t st);
 
 }  // namespace tau

@@ -816,36 +816,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// partial[i * ld + blockIdx.x] = sum_{this block's elements} w * V_i, i = 0..j
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const double* __restrict__ V, int64_t n,
+// partial[i * ld + blockIdx.x] = sum_{this block's elements} w * V_i, i = 0..j, with w = V_{j+1}.
+// Per-element products and per-thread sums in the storage type S; block and grid sums in FP64.
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, int64_t n,
                                                       const GmresDev* __restrict__ g, double* partial, int ld) {
   __shared__ double sh[32];
   if (g->done) return;
   const int jj = g->j;
-  const double* __restrict__ w = V + (int64_t)(jj + 1) * n;
+  const S* __restrict__ w = V + (int64_t)(jj + 1) * n;
   for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
-    double acc[DOT_CHUNK] = {0.0, 0.0, 0.0, 0.0};
+    S acc[DOT_CHUNK] = {0, 0, 0, 0};
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-      const double wv = w[idx];
+      const S wv = w[idx];
 #pragma unroll
       for (int r = 0; r < DOT_CHUNK; ++r)
-        if (r < ni) acc[r] = fma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
+        if (r < ni) acc[r] = tfma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
-        const double s = block_sum(acc[r], sh);
+        const double s = block_sum((double)acc[r], sh);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
       }
     }
   }
 }
 
-cudaError_t launch_dots(const double* V, int64_t n, const GmresDev* g, double* partial, int ld, cudaStream_t st) {
-  k_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, partial, ld);
+template <typename S>
+cudaError_t launch_dots(const S* V, int64_t n, const GmresDev* g, double* partial, int ld, cudaStream_t st) {
+  k_dots<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, partial, ld);
   return cudaGetLastError();
 }
+template cudaError_t launch_dots<double>(const double*, int64_t, const GmresDev*, double*, int, cudaStream_t);
+template cudaError_t launch_dots<float>(const float*, int64_t, const GmresDev*, double*, int, cudaStream_t);
 
 // h[i] = sum_b partial[i * ld + b], i = 0..j (one warp per i)
 __global__ void k_reduce_dots(const double* __restrict__ partial, int ld, const GmresDev* __restrict__ g, double* h) {
@@ -866,55 +871,61 @@ cudaError_t launch_reduce_dots(const double* partial, int ld, const GmresDev* g,
   return cudaGetLastError();
 }
 
-// w -= sum_i h_i V_i; then either partial dots with V_i (CGS2 second pass) or partial ||w||^2.
-__global__ void __launch_bounds__(RED_THREADS) k_update_dots(double* V, int64_t n, const GmresDev* __restrict__ g,
+// w -= sum_i h_i V_i (w = V_{j+1}); then either partial dots with V_i (CGS2 second pass) or ||w||^2.
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, const GmresDev* __restrict__ g,
                                                              const double* __restrict__ h, double* partial, int ld,
                                                              int want_norm) {
   __shared__ double sh[32];
-  __shared__ double hs[MAX_ITER_CAP + 1];
+  __shared__ S hs[MAX_ITER_CAP + 1];
   if (g->done) return;
   const int jj = g->j;
-  double* w = V + (int64_t)(jj + 1) * n;
-  for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = h[i];
+  S* w = V + (int64_t)(jj + 1) * n;
+  for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = (S)h[i];
   __syncthreads();
-  double nacc = 0.0;
+  S nacc = 0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    double wv = w[idx];
-    for (int i = 0; i <= jj; ++i) wv = fma(-hs[i], V[(int64_t)i * n + idx], wv);
+    S wv = w[idx];
+    for (int i = 0; i <= jj; ++i) wv = tfma(-hs[i], V[(int64_t)i * n + idx], wv);
     w[idx] = wv;
-    nacc = fma(wv, wv, nacc);
+    nacc = tfma(wv, wv, nacc);
   }
   if (want_norm) {
-    const double s = block_sum(nacc, sh);
+    const double s = block_sum((double)nacc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
     return;
   }
   __syncthreads();
   // second Gram-Schmidt pass: dots of the updated w (this block's elements) with V_i
   for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
-    double acc[DOT_CHUNK] = {0.0, 0.0, 0.0, 0.0};
+    S acc[DOT_CHUNK] = {0, 0, 0, 0};
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-      const double wv = w[idx];
+      const S wv = w[idx];
 #pragma unroll
       for (int r = 0; r < DOT_CHUNK; ++r)
-        if (r < ni) acc[r] = fma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
+        if (r < ni) acc[r] = tfma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
-        const double s = block_sum(acc[r], sh);
+        const double s = block_sum((double)acc[r], sh);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
       }
     }
   }
 }
 
-cudaError_t launch_update_dots(double* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld,
+template <typename S>
+cudaError_t launch_update_dots(S* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld,
                                int want_norm, cudaStream_t st) {
-  k_update_dots<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, want_norm);
+  k_update_dots<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, want_norm);
   return cudaGetLastError();
 }
+template cudaError_t launch_update_dots<double>(double*, int64_t, const GmresDev*, const double*, double*, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_update_dots<float>(float*, int64_t, const GmresDev*, const double*, double*, int, int,
+                                               cudaStream_t);
 
 // Column j of the Hessenberg matrix: h1 + h2 (CGS2), ||w||; previous rotations, new rotation,
 // residual estimate |g_{j+1}|, stopping test ||r_j|| <= tol ||r_0|| (§4), cap and breakdown.
@@ -978,19 +989,23 @@ cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double
 
 // V_{j} <- w / ||w|| where w sits in the slot of V_j (after k_givens advanced j). When the
 // column closed the iteration (done), nothing is scaled.
-__global__ void k_scale_next(double* V, int64_t n, const GmresDev* __restrict__ g) {
+template <typename S>
+__global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
   if (g->done) return;
   const int j = g->j;
-  const double inv = 1.0 / g->hnorm;
-  double* v = V + (int64_t)j * n;
+  const S inv = (S)(1.0 / g->hnorm);
+  S* v = V + (int64_t)j * n;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     v[idx] *= inv;
 }
 
-cudaError_t launch_scale_next(double* V, int64_t n, const GmresDev* g, cudaStream_t st) {
-  k_scale_next<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+template <typename S>
+cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st) {
+  k_scale_next<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
   return cudaGetLastError();
 }
+template cudaError_t launch_scale_next<double>(double*, int64_t, const GmresDev*, cudaStream_t);
+template cudaError_t launch_scale_next<float>(float*, int64_t, const GmresDev*, cudaStream_t);
 
 __global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const double* __restrict__ w, int64_t n, double* partial) {
   __shared__ double sh[32];
@@ -1074,6 +1089,140 @@ cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* 
   k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, iters_log);
   k_update_solution<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
   k_advance<<<1, 32, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// mixed precision: FP64 iterative refinement around an FP32 flexible GMRES
+// ---------------------------------------------------------------------------
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_f64_to_f32<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_ir_init(IRDev* ir) {
+  if (threadIdx.x == 0) {
+    ir->sweep = 0;
+    ir->done = 0;
+    ir->inner_total = 0;
+    ir->rho0 = 0.0;
+    ir->rho = 0.0;
+  }
+}
+
+cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st) {
+  k_ir_init<<<1, 32, 0, st>>>(ir);
+  return cudaGetLastError();
+}
+
+// rho = ||b - A x|| (FP64); stop when rho <= tol rho_0 or after max_sweeps corrections; otherwise
+// start the inner flexible GMRES on v_0 = (b - A x)/rho (beta = 1).
+// In the step graph the inner WHILE node lives in the outer loop's body; a handle's default value
+// is applied only when the whole graph is launched, so this kernel sets the inner condition for
+// every sweep (cond_in) as well as the outer one (cond).
+__global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* __restrict__ pnorm,
+                             cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += pnorm[b];
+  s = block_sum(s, sh);
+  if (threadIdx.x != 0) return;
+  const double rho = sqrt(s);
+  if (ir->sweep == 0) ir->rho0 = rho;
+  ir->rho = rho;
+  ir->last_rel = ir->rho0 > 0.0 ? rho / ir->rho0 : 0.0;
+  const bool conv = !(rho > ir->tol * ir->rho0);
+  const bool cap = ir->sweep >= ir->max_sweeps;
+  if (conv || cap) {
+    ir->done = 1;
+    if (!conv) ir->notconv = 1;
+    gin->done = 1;
+    if (use_cond) {
+      cudaGraphSetConditional(cond, 0);
+      cudaGraphSetConditional(cond_in, 0);
+    }
+    return;
+  }
+  ir->sweep += 1;
+  gin->j = 0;
+  gin->k = 0;
+  gin->done = 0;
+  gin->beta = 1.0;
+  gin->hnorm = 1.0;
+  gv_in[0] = 1.0;
+  if (use_cond) {
+    cudaGraphSetConditional(cond, 1);
+    cudaGraphSetConditional(cond_in, 1);
+  }
+}
+
+cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm,
+                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
+                              cudaStream_t st) {
+  k_ir_control<<<1, 256, 0, st>>>(ir, gin, gv_in, pnorm, cond, cond_in, use_cond);
+  return cudaGetLastError();
+}
+
+// v_0 = (float)(r / rho)
+__global__ void k_scale_to_f32(const double* __restrict__ r, float* v, int64_t n, const IRDev* __restrict__ ir) {
+  if (ir->done) return;
+  const double inv = 1.0 / ir->rho;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (float)(r[i] * inv);
+}
+
+cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st) {
+  k_scale_to_f32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(r, v, n, ir);
+  return cudaGetLastError();
+}
+
+// x += rho * sum_{i<k} y_i Z_i (FP64 accumulation of the FP32 preconditioned directions)
+__global__ void k_update_x(double* x, const float* __restrict__ Z, const double* __restrict__ y, int64_t n,
+                           const GmresDev* __restrict__ gin, IRDev* ir) {
+  __shared__ double ys[MAX_ITER_CAP];
+  if (ir->done) return;
+  const int k = gin->k;
+  const double rho = ir->rho;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * y[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) ir->inner_total += k;
+  __syncthreads();
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    double v = x[idx];
+    for (int i = 0; i < k; ++i) v = fma(ys[i], (double)Z[(int64_t)i * n + idx], v);
+    x[idx] = v;
+  }
+}
+
+cudaError_t launch_update_x(double* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
+                            cudaStream_t st) {
+  k_update_x<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
+  return cudaGetLastError();
+}
+
+__global__ void k_ir_finish(const IRDev* __restrict__ ir, GmresDev* g, int* iters_log, int* sweeps_log) {
+  if (threadIdx.x != 0) return;
+  if (iters_log) iters_log[g->m] = ir->inner_total;
+  if (sweeps_log) sweeps_log[g->m] = ir->sweep;
+  if (ir->notconv) g->notconv = 1;
+  g->relres = ir->last_rel;
+  g->m += 1;
+}
+
+cudaError_t launch_ir_finish(const IRDev* ir, GmresDev* g, int* iters_log, int* sweeps_log, cudaStream_t st) {
+  k_ir_finish<<<1, 32, 0, st>>>(ir, g, iters_log, sweeps_log);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backsolve(GmresDev* g, const double* H, const double* gv, int ldH, double* y, cudaStream_t st) {
+  k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, nullptr);
   return cudaGetLastError();
 }
 

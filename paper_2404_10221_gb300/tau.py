@@ -29,6 +29,7 @@ TAU_ENOTCONV = -7
 TAU_X0_ZERO = 0
 TAU_X0_PREV = 1
 TAU_FP64 = 0
+TAU_MIXED = 1
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
@@ -51,6 +52,10 @@ class tau_problem_desc(C.Structure):
         ("route", C.c_int * 3),
         ("e_min", C.c_double),
         ("e_max", C.c_double),
+        ("refine_tol", C.c_double),
+        ("inner_max_iter", C.c_int),
+        ("max_sweeps", C.c_int),
+        ("inner_tol", C.c_double),
     ]
 
 
@@ -79,6 +84,8 @@ class tau_stats(C.Structure):
         ("kernels_prologue", C.c_int64),
         ("kernels_per_iter", C.c_int64),
         ("kernels_epilogue", C.c_int64),
+        ("kernels_total", C.c_int64),
+        ("total_sweeps", C.c_int64),
     ]
 
 
@@ -121,6 +128,12 @@ def lib():
             "tau_get_ebar": [P, D, D, D],
             "tau_measure_fp64_peak": [P, D],
             "tau_apply_A_noalloc": [C.POINTER(tau_problem_desc), P, P, P, P],
+            "tau_apply_A_f32": [P, C.c_int64, P, P],
+            "tau_batch_create": [C.POINTER(P), C.c_int, P, C.POINTER(P)],
+            "tau_batch_step": [P, C.c_int64],
+            "tau_batch_sync": [P],
+            "tau_batch_destroy": [P],
+            "tau_apply_Minv_f32": [P, P, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -139,11 +152,12 @@ def _check(status: int, allow=()):
     return status
 
 
-def _ptr(t) -> int:
-    """Device pointer of a contiguous FP64 CUDA tensor."""
+def _ptr(t, dtype: str = "float64") -> int:
+    """Device pointer of a contiguous CUDA tensor of the given dtype (float64 by default)."""
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-        raise TypeError("expected a contiguous float64 CUDA tensor")
+    dt = getattr(torch, dtype)
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous {dtype} CUDA tensor")
     return t.data_ptr()
 
 
@@ -155,7 +169,8 @@ def _stream(stream=None) -> int:
 
 
 def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
-              e_bounds: Optional[tuple] = None) -> tau_problem_desc:
+              e_bounds: Optional[tuple] = None, refine_tol: float = 0.0, inner_max_iter: int = 0,
+              max_sweeps: int = 0, inner_tol: float = 0.0) -> tau_problem_desc:
     """tau_problem_desc from a workloads.Problem."""
     d = tau_problem_desc()
     d.d = prob.d
@@ -176,6 +191,10 @@ def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
         d.e_min = d.e_max = math.nan
     else:
         d.e_min, d.e_max = float(e_bounds[0]), float(e_bounds[1])
+    d.refine_tol = float(refine_tol)
+    d.inner_max_iter = int(inner_max_iter)
+    d.max_sweeps = int(max_sweeps)
+    d.inner_tol = float(inner_tol)
     return d
 
 
@@ -277,6 +296,15 @@ def tau_toeplitz_mode(h: int, dim: int, x, y):
     _check(lib().tau_toeplitz_mode(C.c_void_p(h), C.c_int(dim), C.c_void_p(_ptr(x)), C.c_void_p(_ptr(y))))
 
 
+def tau_apply_A_f32(h: int, m: int, x, y):
+    _check(lib().tau_apply_A_f32(C.c_void_p(h), C.c_int64(m), C.c_void_p(_ptr(x, "float32")),
+                                 C.c_void_p(_ptr(y, "float32"))))
+
+
+def tau_apply_Minv_f32(h: int, r, z):
+    _check(lib().tau_apply_Minv_f32(C.c_void_p(h), C.c_void_p(_ptr(r, "float32")), C.c_void_p(_ptr(z, "float32"))))
+
+
 def tau_get_ebar(h: int):
     a, b, c = C.c_double(), C.c_double(), C.c_double()
     _check(lib().tau_get_ebar(C.c_void_p(h), C.byref(a), C.byref(b), C.byref(c)))
@@ -295,13 +323,32 @@ def tau_apply_A_noalloc(desc: tau_problem_desc, e, x, y, stream=None):
                                      C.c_void_p(_ptr(y)), C.c_void_p(_stream(stream))))
 
 
+def tau_batch_create(handles: Sequence[int], stream=None) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    b = C.c_void_p()
+    _check(lib().tau_batch_create(arr, C.c_int(len(handles)), C.c_void_p(_stream(stream)), C.byref(b)))
+    return b.value
+
+
+def tau_batch_step(b: int, count: int = 1):
+    _check(lib().tau_batch_step(C.c_void_p(b), C.c_int64(count)))
+
+
+def tau_batch_sync(b: int, allow_notconv: bool = False):
+    return _check(lib().tau_batch_sync(C.c_void_p(b)), (TAU_ENOTCONV,) if allow_notconv else ())
+
+
+def tau_batch_destroy(b: int):
+    _check(lib().tau_batch_destroy(C.c_void_p(b)))
+
+
 class Problem:
     """Owner of one tau_problem: create, set fields, set up; destroyed with the object."""
 
-    def __init__(self, workload, precision: int = TAU_FP64, route=(0, 0, 0), stream=None, e_bounds=None):
+    def __init__(self, workload, precision: int = TAU_FP64, route=(0, 0, 0), stream=None, e_bounds=None, **mixed):
         self.workload = workload
         self.prob = workload.prob
-        self.handle = tau_create(make_desc(self.prob, precision, route, e_bounds), stream)
+        self.handle = tau_create(make_desc(self.prob, precision, route, e_bounds, **mixed), stream)
         try:
             tau_set_fields(self.handle, workload.field_tables())
             tau_setup(self.handle)

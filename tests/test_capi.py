@@ -48,11 +48,12 @@ def test_struct_layout_matches_c_compiler(tmp_path):
         pytest.skip("no C compiler")
     checks = {
         "tau_problem_desc": ["d", "n", "L", "R", "alpha", "kappa", "T", "M", "tol", "max_iter", "x0_mode",
-                             "precision", "route", "e_min", "e_max"],
+                             "precision", "route", "e_min", "e_max", "refine_tol", "inner_max_iter",
+                             "max_sweeps", "inner_tol"],
         "tau_field": ["rank", "n_times", "time_coef", "space"],
         "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
                       "e_hat", "e_check", "route", "graph", "device_bytes", "kernels_prologue",
-                      "kernels_per_iter", "kernels_epilogue"],
+                      "kernels_per_iter", "kernels_epilogue", "kernels_total", "total_sweeps"],
     }
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "tau_rsfde.h"', "int main(void){"]
     for st, fields in checks.items():
