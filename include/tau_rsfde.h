@@ -221,6 +221,54 @@ tau_status tau_batch_step(tau_batch* b, int64_t count);
 tau_status tau_batch_sync(tau_batch* b);
 tau_status tau_batch_destroy(tau_batch* b);
 
+/* ---- serving: a continuous-batching request loop for whole time-marching solves.
+ *
+ * tau_server_create starts a worker thread on the current CUDA device.  tau_server_submit copies a
+ * request (problem description and field tables, as for tau_create / tau_set_fields) into a FIFO
+ * queue.  The worker admits queued requests while the estimated device memory of the admitted
+ * ones stays within `device_bytes_budget` and fewer than `max_active` are admitted; each admitted
+ * request gets its own stream and a tau_problem whose Krylov basis and solution stay on the
+ * device until its last step.  The worker keeps every admitted request's stream fed with
+ * `steps_per_launch` steps at a time, so requests that arrive while others run are admitted as
+ * memory frees up and their kernels overlap on the GPU.  A finished request's solution u^(M) is
+ * copied to host memory and its device memory returns to the budget.  A request whose estimate
+ * exceeds the whole budget fails at once with TAU_ENOMEM.  All host waits are bounded.
+ * Times are seconds since tau_server_create. */
+#define TAU_REQ_QUEUED 0
+#define TAU_REQ_RUNNING 1
+#define TAU_REQ_DONE 2
+#define TAU_REQ_FAILED 3
+typedef struct tau_server tau_server;
+typedef struct {
+  int64_t id;
+  int state;                  /* TAU_REQ_* */
+  tau_status status;          /* TAU_OK, TAU_ENOTCONV (done, some step hit its cap) or the failure */
+  double t_submit, t_admit, t_finish;
+  int64_t unknowns, steps, gmres_iters;
+  int64_t device_bytes;       /* device memory the request held while admitted */
+} tau_request_info;
+typedef struct {
+  int64_t completed, failed, queued, active;
+  int64_t device_bytes_in_use;    /* estimated bytes of the admitted requests */
+  double latency_p50_s, latency_p99_s, latency_mean_s;   /* submit -> u^(M) on the host, completed */
+  double unknowns_steps;          /* sum of n_tot * M over completed requests */
+  double span_s;                  /* first submit -> last completion */
+  double throughput;              /* unknowns_steps / span_s */
+} tau_server_stats;
+tau_status tau_server_create(int64_t device_bytes_budget, int max_active, int steps_per_launch, tau_server** out);
+tau_status tau_server_submit(tau_server* s, const tau_problem_desc* desc, const tau_field* e, const tau_field* f,
+                             const tau_field* psi, int64_t* id_out);
+tau_status tau_server_poll(tau_server* s, int64_t id, tau_request_info* info);
+/* Wait until the request is done or failed, at most timeout_s seconds (TAU_ETIMEOUT otherwise). */
+tau_status tau_server_wait(tau_server* s, int64_t id, double timeout_s, tau_request_info* info);
+/* Copy a finished request's solution (n doubles, host memory). */
+tau_status tau_server_result(tau_server* s, int64_t id, double* u_host, int64_t n);
+/* Forget a finished or failed request (frees its host copy of the solution). */
+tau_status tau_server_release(tau_server* s, int64_t id);
+tau_status tau_server_summary(tau_server* s, tau_server_stats* out);
+/* Cancel queued requests, let admitted ones finish, stop the worker, free everything. */
+tau_status tau_server_destroy(tau_server* s);
+
 /* ---- allocation-free entry point (the paper has no counterpart).
  *
  * y = A x = B_alpha (e ∘ x) + S_alpha x for the grid and coefficients of `desc` (d, n, L, R, alpha,

@@ -265,10 +265,11 @@ tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainT<T>& io, i
 // out = finish( B(e∘x) + sgn*sum_i eta_i (..S_i..) x ), optionally followed by M^{-1}.
 template <typename T>
 tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double sgn, int finish, const T* src,
-                  bool precond) {
+                  bool precond, const int* skip = nullptr) {
   const int d = p->d;
   for (int ax = 0; ax < d; ++ax) {
     PassT<T> P = base_pass_t<T>(p, ax);
+    P.skip = skip;
     P.mv = 1;
     P.first = ax == 0;
     P.last = ax == d - 1;
@@ -358,10 +359,12 @@ tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
 
 tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h,
                             cudaGraphConditionalHandle h_in, int use_cond) {
+  // r = b - A x in FP64; on the first sweep of a zero initial guess r = b and the passes are skipped
+  KL(launch_ir_first_resid(p->ir, p->b, p->tmp, p->n_tot, p->desc.x0_mode == TAU_X0_ZERO, st));
   ChainIO r;
   r.x = p->X;
   r.out = p->tmp;
-  TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false));   // r = b - A x, FP64
+  TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false, &p->ir->skip_resid));
   KL(launch_norm_partial(p->tmp, p->n_tot, p->g, p->pnorm, st));
   KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, h, h_in, use_cond, st));
   KL(launch_scale_to_f32(p->tmp, p->V32, p->n_tot, p->ir, st));

@@ -90,6 +90,7 @@ struct PassT {
   T* out_c;
   // Krylov wiring: pointers that depend on the device-side Arnoldi index j
   const GmresDev* g;    // non-null: skip the pass when g->done
+  const int* skip;      // non-null: skip the pass when *skip != 0
   T* in_base;           // in_sel: 1 -> in_base + j*vstride, 2 -> in_base + (j+1)*vstride
   T* out_base;          // out_sel: the same for the output
   int64_t vstride;
@@ -175,12 +176,15 @@ struct IRDev {
   int max_sweeps;
   int notconv;       // sticky: some step stopped at max_sweeps
   int inner_total;   // inner FGMRES iterations of this step
-  int pad;
+  int skip_resid;    // 1 while the first residual of a step equals b (zero initial guess)
   double tol;        // ||b - A x|| <= tol ||b - A x_0||
   double rho0, rho, last_rel;
 };
 cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);
+// Residual of the zero initial guess: r = b on the first sweep (the FP64 residual passes are
+// skipped through ir->skip_resid); later sweeps compute b - A x.
+cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st);
 cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
                               cudaStream_t st);

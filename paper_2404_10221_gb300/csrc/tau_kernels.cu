@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
   // ra and rc together hold an even number of elements, so cb starts aligned to sizeof(V)
   V* cb = reinterpret_cast<V*>(rc + lpb * N);
   if (P.g && P.g->done) return;
+  if (P.skip && *P.skip) return;
   const TileGeo tg = tile_geo(P, blockIdx.x);
   const int TH = blockDim.x, tid = threadIdx.x;
   const int NT = lpb * N;
@@ -1113,6 +1114,7 @@ __global__ void k_ir_init(IRDev* ir) {
     ir->sweep = 0;
     ir->done = 0;
     ir->inner_total = 0;
+    ir->skip_resid = 0;
     ir->rho0 = 0.0;
     ir->rho = 0.0;
   }
@@ -1120,6 +1122,20 @@ __global__ void k_ir_init(IRDev* ir) {
 
 cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st) {
   k_ir_init<<<1, 32, 0, st>>>(ir);
+  return cudaGetLastError();
+}
+
+__global__ void k_ir_first_resid(IRDev* ir, const double* __restrict__ b, double* r, int64_t n, int x0_zero) {
+  const bool first = x0_zero && ir->sweep == 0 && !ir->done;
+  if (first) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      r[i] = b[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ir->skip_resid = first ? 1 : 0;
+}
+
+cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st) {
+  k_ir_first_resid<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ir, b, r, n, x0_zero);
   return cudaGetLastError();
 }
 

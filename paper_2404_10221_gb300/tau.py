@@ -89,6 +89,40 @@ class tau_stats(C.Structure):
     ]
 
 
+TAU_REQ_QUEUED, TAU_REQ_RUNNING, TAU_REQ_DONE, TAU_REQ_FAILED = 0, 1, 2, 3
+
+
+class tau_request_info(C.Structure):
+    _fields_ = [
+        ("id", C.c_int64),
+        ("state", C.c_int),
+        ("status", C.c_int),
+        ("t_submit", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_finish", C.c_double),
+        ("unknowns", C.c_int64),
+        ("steps", C.c_int64),
+        ("gmres_iters", C.c_int64),
+        ("device_bytes", C.c_int64),
+    ]
+
+
+class tau_server_stats(C.Structure):
+    _fields_ = [
+        ("completed", C.c_int64),
+        ("failed", C.c_int64),
+        ("queued", C.c_int64),
+        ("active", C.c_int64),
+        ("device_bytes_in_use", C.c_int64),
+        ("latency_p50_s", C.c_double),
+        ("latency_p99_s", C.c_double),
+        ("latency_mean_s", C.c_double),
+        ("unknowns_steps", C.c_double),
+        ("span_s", C.c_double),
+        ("throughput", C.c_double),
+    ]
+
+
 class TauError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"tau status {status}: {msg}")
@@ -133,6 +167,15 @@ def lib():
             "tau_batch_step": [P, C.c_int64],
             "tau_batch_sync": [P],
             "tau_batch_destroy": [P],
+            "tau_server_create": [C.c_int64, C.c_int, C.c_int, C.POINTER(P)],
+            "tau_server_submit": [P, C.POINTER(tau_problem_desc), C.POINTER(tau_field), C.POINTER(tau_field),
+                                  C.POINTER(tau_field), C.POINTER(C.c_int64)],
+            "tau_server_poll": [P, C.c_int64, C.POINTER(tau_request_info)],
+            "tau_server_wait": [P, C.c_int64, C.c_double, C.POINTER(tau_request_info)],
+            "tau_server_result": [P, C.c_int64, P, C.c_int64],
+            "tau_server_release": [P, C.c_int64],
+            "tau_server_summary": [P, C.POINTER(tau_server_stats)],
+            "tau_server_destroy": [P],
             "tau_apply_Minv_f32": [P, P, P],
         }
         for name, args in sigs.items():
@@ -340,6 +383,56 @@ def tau_batch_sync(b: int, allow_notconv: bool = False):
 
 def tau_batch_destroy(b: int):
     _check(lib().tau_batch_destroy(C.c_void_p(b)))
+
+
+def tau_server_create(budget_bytes: int, max_active: int, steps_per_launch: int = 4) -> int:
+    h = C.c_void_p()
+    _check(lib().tau_server_create(C.c_int64(budget_bytes), C.c_int(max_active), C.c_int(steps_per_launch),
+                                   C.byref(h)))
+    return h.value
+
+
+def tau_server_submit(s: int, desc: tau_problem_desc, tables: dict) -> int:
+    e = _FieldHolder(tables["e_tc"], tables["e_sp"])
+    f = _FieldHolder(tables["f_tc"], tables["f_sp"])
+    p = _FieldHolder(tables["psi_tc"], tables["psi_sp"])
+    rid = C.c_int64()
+    _check(lib().tau_server_submit(C.c_void_p(s), C.byref(desc), C.byref(e.f), C.byref(f.f), C.byref(p.f),
+                                   C.byref(rid)))
+    return rid.value
+
+
+def tau_server_poll(s: int, rid: int) -> tau_request_info:
+    info = tau_request_info()
+    _check(lib().tau_server_poll(C.c_void_p(s), C.c_int64(rid), C.byref(info)))
+    return info
+
+
+def tau_server_wait(s: int, rid: int, timeout_s: float = 600.0) -> tau_request_info:
+    info = tau_request_info()
+    _check(lib().tau_server_wait(C.c_void_p(s), C.c_int64(rid), C.c_double(timeout_s), C.byref(info)))
+    return info
+
+
+def tau_server_result(s: int, rid: int, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _check(lib().tau_server_result(C.c_void_p(s), C.c_int64(rid), C.c_void_p(out.ctypes.data), C.c_int64(n)),
+           (TAU_ENOTCONV,))
+    return out
+
+
+def tau_server_release(s: int, rid: int):
+    _check(lib().tau_server_release(C.c_void_p(s), C.c_int64(rid)))
+
+
+def tau_server_summary(s: int) -> tau_server_stats:
+    out = tau_server_stats()
+    _check(lib().tau_server_summary(C.c_void_p(s), C.byref(out)))
+    return out
+
+
+def tau_server_destroy(s: int):
+    _check(lib().tau_server_destroy(C.c_void_p(s)))
 
 
 class Problem:
