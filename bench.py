@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision form measurements")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision/batched/served form measurements")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: set up the workload (2 Krylov slots) and run this many "
@@ -244,6 +247,130 @@ def run_forms(stream, dev):
     return out
 
 
+def plain_sequential_throughput(wls, stream, dev):
+    """unknowns*steps/s of solving the given problems one after another with the plain FP64 path
+    (each alone, steps of every problem, host waits excluded by CUDA events)."""
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+
+    ms = 0.0
+    work = 0.0
+    for wl in wls:
+        p = tau.Problem(wl, stream=stream.cuda_stream)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tau.tau_step(p.handle, wl.prob.M)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+        work += wl.prob.n_tot * wl.prob.M
+        p.close()
+    return work / (ms * 1e-3)
+
+
+def run_batched(args, stream, dev):
+    """512 independent 2-D instances (uneven n from {63,127,255,511}, random alpha, kappa, e), M = 20,
+    mixed precision, one graph launch per step for all instances."""
+    import numpy as np
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    rng = W.SplitMix64(10221)
+    wls = [W.random_2d(rng, sizes=(63, 127, 255, 511), M=20) for _ in range(args.batch_count)]
+    t0 = time.perf_counter()
+    probs = [tau.Problem(wl, precision=tau.TAU_MIXED, stream=stream.cuda_stream) for wl in wls]
+    b = tau.tau_batch_create([p.handle for p in probs], stream.cuda_stream)
+    t_setup = time.perf_counter() - t0
+    M = 20
+    warm = 2
+    tau.tau_batch_step(b, warm)
+    tau.tau_batch_sync(b, allow_notconv=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tau.tau_batch_step(b, M - warm)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    tau.tau_batch_sync(b, allow_notconv=True)
+    tau.tau_batch_destroy(b)
+    n_tot = sum(wl.prob.n_tot for wl in wls)
+    value = n_tot * (M - warm) / (ms * 1e-3)
+    # accuracy: a sample of instances against the plain FP64 path
+    errs = []
+    for i in range(0, len(wls), max(1, len(wls) // 4)):
+        ref = tau.Problem(wls[i], stream=stream.cuda_stream)
+        tau.tau_step(ref.handle, M)
+        ur = ref.solution()
+        um = probs[i].solution()
+        errs.append((torch.linalg.norm(um - ur) / torch.linalg.norm(ur)).item())
+        ref.close()
+    kernels = sum(int(tau.tau_get_stats(p.handle).kernels_total) for p in probs)
+    for p in probs:
+        p.close()
+    plain = plain_sequential_throughput(wls[:args.plain_sample], stream, dev)
+    return {"instances": len(wls), "unknowns_total": n_tot, "steps_timed": M - warm, "value": value,
+            "ms_per_step": ms / (M - warm), "setup_s": t_setup, "unit": UNIT,
+            "max_rel_err_vs_plain_fp64": max(errs), "plain_fp64_sequential_value": plain,
+            "plain_sample_instances": args.plain_sample, "speedup_vs_plain_fp64": value / plain,
+            "kernels_launched_all_steps": kernels,
+            "dtype": "f32 inner + f64 refinement", "launch": "one CUDA graph launch per step for all instances"}
+
+
+def run_serving(args, stream, dev):
+    """Continuous batching: saturation throughput (all requests submitted at once) and latency
+    under Poisson arrivals at half that throughput."""
+    import random
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    wls = W.serving_mix(args.serve_requests, 20240416)
+    tables = [wl.field_tables() for wl in wls]
+    descs = [tau.make_desc(wl.prob, precision=tau.TAU_MIXED) for wl in wls]
+    budget = 64 << 30
+
+    def run(arrivals):
+        s = tau.tau_server_create(budget, 64, 4)
+        t0 = time.perf_counter()
+        ids = []
+        for k, (d, tb) in enumerate(zip(descs, tables)):
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(tau.tau_server_submit(s, d, tb))
+        for i in ids:
+            tau.tau_server_wait(s, i, 600.0)
+        summ = tau.tau_server_summary(s)
+        tau.tau_server_destroy(s)
+        return summ
+
+    sat = run([0.0] * len(wls))
+    work = sum(wl.prob.n_tot * wl.prob.M for wl in wls)
+    rate = 0.5 * sat.throughput / (work / len(wls))        # requests per second at half saturation
+    rnd = random.Random(20240416)
+    t = 0.0
+    arr = []
+    for _ in wls:
+        t += rnd.expovariate(rate)
+        arr.append(t)
+    half = run(arr)
+    plain = plain_sequential_throughput(wls[:args.plain_sample], stream, dev)
+    return {"requests": len(wls), "unknowns_steps_total": work, "unit": UNIT,
+            "saturation": {"throughput": sat.throughput, "p50_s": sat.latency_p50_s, "p99_s": sat.latency_p99_s,
+                           "completed": sat.completed, "failed": sat.failed},
+            "poisson_half_rate": {"rate_req_per_s": rate, "throughput": half.throughput, "p50_s": half.latency_p50_s,
+                                  "p99_s": half.latency_p99_s, "completed": half.completed, "failed": half.failed},
+            "plain_fp64_sequential_value": plain, "plain_sample_requests": args.plain_sample,
+            "speedup_vs_plain_fp64": sat.throughput / plain,
+            "mix": "40% 1-D n in {1023,2047,4095}; 45% 2-D n in {127,255,511}^2; 15% 3-D n in {31,63,127}^3; "
+                   "M in [10,40]; mixed precision; latency = submit -> solution on the host"}
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -360,7 +487,11 @@ def run_native(args):
                "api": "tau_set_solution(host) + tau_step(1) + tau_get_solution(host), pinned buffers"}
         prob2.close()
 
-    forms = None if args.no_forms else run_forms(stream, dev)
+    forms = None
+    if not args.no_forms:
+        forms = run_forms(stream, dev)
+        forms["batched_2d_512"] = run_batched(args, stream, dev)
+        forms["served"] = run_serving(args, stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
         "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

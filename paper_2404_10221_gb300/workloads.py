@@ -296,3 +296,29 @@ def random_vector(n: int, seed: int) -> np.ndarray:
 def random_positive(n: int, seed: int, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, n)
+
+
+def serving_mix(count: int, seed: int = 20240416, M_range=(10, 40), precision_hint: str = "mixed") -> List[Workload]:
+    """Request mix of the served form: 40 % 1-D with n in {1023, 2047, 4095}, 45 % 2-D with n in
+    {127, 255, 511} per axis (uneven), 15 % 3-D with n in {31, 63, 127} per axis; M uniform in
+    M_range; alpha_i ~ U(1.1,1.9), kappa_i ~ U(0.2,1), e = 1 + a prod sin(pi x_i)(1+t), a ~ U(0.1,1).
+    Sizes are restricted to n+1 a power of two (the FFT route)."""
+    rng = SplitMix64(seed)
+    out = []
+    lo, hi = M_range
+    for _ in range(count):
+        u = rng.uniform()
+        M = lo + int(rng.uniform() * (hi - lo + 1))
+        if u < 0.40:
+            d, n = 1, [rng.choice((1023, 2047, 4095))]
+        elif u < 0.85:
+            d, n = 2, [rng.choice((127, 255, 511)), rng.choice((127, 255, 511))]
+        else:
+            d, n = 3, [rng.choice((31, 63, 127)) for _ in range(3)]
+        alpha = [rng.uniform(1.1, 1.9) for _ in range(d)]
+        kappa = [rng.uniform(0.2, 1.0) for _ in range(d)]
+        amp = rng.uniform(0.1, 1.0)
+        prob = Problem(d=d, n=n, alpha=alpha, kappa=kappa, T=1.0, M=M, tol=1e-12)
+        e_terms = [(_const(1.0), [_one] * d), (lambda t, a=amp: a * (1.0 + t), [_sinpi] * d)]
+        out.append(manufactured(f"req{d}d", prob, e_terms, 2, 2, 1.0))
+    return out
