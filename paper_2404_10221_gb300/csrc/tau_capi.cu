@@ -1187,7 +1187,7 @@ tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int blocks = sms * 8, iters = 6000;
+  const int blocks = sms * 2, iters = 20000;
   double* out = nullptr;
   CK(cudaMalloc(&out, sizeof(double) * blocks * 256));
   cudaEvent_t e0, e1;

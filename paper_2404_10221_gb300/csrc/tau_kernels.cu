@@ -1245,11 +1245,10 @@ cudaError_t launch_backsolve(GmresDev* g, const double* H, const double* gv, int
 // ---------------------------------------------------------------------------
 // FP64 FMA throughput probe (bounded loop; 8 independent chains per thread)
 // ---------------------------------------------------------------------------
-__global__ void k_fp64_peak(double* out, int iters) {
+__global__ void k_fp64_peak(double* out, int iters, double a, double b) {
   double x[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) x[c] = (double)(threadIdx.x + c);
-  const double a = 0.999999, b = 1e-7;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
@@ -1261,7 +1260,7 @@ __global__ void k_fp64_peak(double* out, int iters) {
 }
 
 cudaError_t launch_fp64_peak(double* out, int blocks, int iters, cudaStream_t st) {
-  k_fp64_peak<<<blocks, 256, 0, st>>>(out, iters);
+  k_fp64_peak<<<blocks, 256, 0, st>>>(out, iters, 0.999999, 1e-7);
   return cudaGetLastError();
 }
 
