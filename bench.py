@@ -374,6 +374,20 @@ def run_serving(args, stream, dev):
                    "M in [10,40]; mixed precision; latency = submit -> solution on the host"}
 
 
+def aggregate_over_ranks(local_seconds: float, units_per_rank: float, world: int, device=None) -> tuple:
+    """Whole-job throughput of independent replicas: every rank processed `units_per_rank`; the job
+    took as long as its slowest rank.  Returns (value, max_seconds).  Uses torch.distributed when
+    world > 1 (all_reduce MAX of the times; no data-path collective)."""
+    t = float(local_seconds)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * units_per_rank / t, t
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -423,16 +437,11 @@ def run_native(args):
         t_wall = time.perf_counter() - t_wall0
     barrier()
     ms = sum(starts[i].elapsed_time(ends[i]) for i in range(K))
-    t_dev = ms * 1e-3
-    if world > 1:
-        tt = torch.tensor([t_dev], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev = tt.item()
+    value, t_dev = aggregate_over_ranks(ms * 1e-3, n_tot * K, world, dev)
     st = tau.tau_get_stats(h)
     its = tau.tau_get_iters(h, pr.M)[Wm:Wm + K]
+    # kernels of the timed steps, from the library's per-step counts and iteration log
     kernels = int(K * (st.kernels_prologue + st.kernels_epilogue) + its.sum() * st.kernels_per_iter)
-    # (the steps' kernel count from the library's own log, timed steps only)
-    value = world * n_tot * K / t_dev
 
     # ---- live roofline of the dominant kernel: the line-pass kernel (4 launches per matvec)
     x = torch.randn(n_tot, dtype=torch.float64, device=dev)
@@ -481,12 +490,8 @@ def run_native(args):
             tau.tau_get_solution(h2, host_out.numpy(), False)
             host_in.copy_(host_out)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = tt.item()
-        e2e = {"value": world * n_tot * Ke / te, "unit": UNIT, "h2d_bytes_per_step": n_tot * 8 + 8,
+        e2e_value, te = aggregate_over_ranks(time.perf_counter() - t0, n_tot * Ke, world, dev)
+        e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n_tot * 8 + 8,
                "d2h_bytes_per_step": n_tot * 8, "steps": Ke,
                "api": "tau_set_solution(host) + tau_step(1) + tau_get_solution(host), pinned buffers"}
         prob2.close()
