@@ -120,6 +120,10 @@ typedef struct {
   int64_t kernels_total;    /* kernels launched by the completed steps */
   int64_t total_sweeps;     /* TAU_MIXED: refinement sweeps over the completed steps (iters count the
                                inner FGMRES iterations) */
+  int lines_per_cta[3];     /* grid lines per CTA of the line-pass kernel per dimension (FP64), chosen
+                               by the setup's autotuner (problems with >= 65536 unknowns, or
+                               TAU_AUTOTUNE=1; TAU_AUTOTUNE=0 keeps the shared-memory heuristic) */
+  int lines_per_cta_f32[3]; /* the same for the FP32 passes of a TAU_MIXED problem */
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of

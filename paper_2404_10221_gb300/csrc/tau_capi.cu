@@ -6,6 +6,9 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -97,6 +100,7 @@ struct tau_problem {
          *twK2_32[3] = {nullptr, nullptr, nullptr};
   float *s32[3] = {nullptr, nullptr, nullptr}, *sintab32[3] = {nullptr, nullptr, nullptr};
   int64_t k_ir_pre = 0, k_ir_post = 0;         // kernels of one refinement sweep around the inner loop
+  int lpb_tuned[2][3] = {{0, 0, 0}, {0, 0, 0}}; // lines per CTA chosen by the autotuner (FP64, FP32)
   int64_t fields_m = -1;                      // step whose e and dt*F sit in E / Fdt
   int* h_done = nullptr;  // pinned flag for the host-loop fallback
   std::vector<void*> allocs;
@@ -148,6 +152,13 @@ FieldDev field_dev(const tau_problem* p) {
 }
 
 template <typename T>
+void set_lpb(PassT<T>& P, int lpb) {
+  P.lpb = lpb;
+  const int64_t outer = P.nlines / P.inner;
+  P.ntiles = P.ax == 0 ? (P.nlines + lpb - 1) / lpb : outer * ((P.inner + lpb - 1) / lpb);
+}
+
+template <typename T>
 PassT<T> base_pass_t(const tau_problem* p, int ax) {
   PassT<T> P{};
   P.ax = ax;
@@ -182,10 +193,10 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   if (lpb < 1) lpb = 1;
   if (lpb > 16) lpb = 16;
   const int64_t cap = ax == 0 ? P.nlines : inner;
+  const int tuned = p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax];
+  if (tuned > 0) lpb = tuned;
   if (lpb > cap) lpb = cap;
-  P.lpb = (int)lpb;
-  const int64_t outer = P.nlines / inner;
-  P.ntiles = ax == 0 ? (P.nlines + lpb - 1) / lpb : outer * ((inner + lpb - 1) / lpb);
+  set_lpb(P, (int)lpb);
   P.vstride = p->n_tot;
   return P;
 }
@@ -578,6 +589,71 @@ tau_status fields_for(tau_problem* p, int64_t m) {
   return TAU_OK;
 }
 
+// ---- tile autotuner: lines per CTA for each dimension and element type.  Candidates are timed
+// on the real matvec pass (channels a, c in place) with CUDA events; results are cached per shape.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune_cache;
+
+template <typename T>
+tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
+  PassT<T> P = base_pass_t<T>(p, ax);
+  const auto key = std::make_tuple((int)sizeof(T), P.dim.route, P.len, P.inner, P.nlines);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax] = it->second;
+      return TAU_OK;
+    }
+  }
+  P.mv = 1;
+  P.seta = 1.0;
+  P.in_a = chA;
+  P.in_c = chC;
+  P.out_a = chA;
+  P.out_c = chC;
+  const int64_t cap = ax == 0 ? P.nlines : P.inner;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_lpb = P.lpb;
+  for (int lpb = 1; lpb <= 32 && lpb <= cap; lpb *= 2) {
+    set_lpb(P, lpb);
+    if (pass_smem_bytes(P) > 200 * 1024) break;
+    CK(launch_pass(P, p->st));
+    CK(cudaEventRecord(e0, p->st));
+    for (int r = 0; r < 3; ++r) CK(launch_pass(P, p->st));
+    CK(cudaEventRecord(e1, p->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best * 0.97f) {
+      best = ms;
+      best_lpb = lpb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax] = best_lpb;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best_lpb;
+  return TAU_OK;
+}
+
+tau_status autotune(tau_problem* p) {
+  CK(cudaMemsetAsync(p->A, 0, p->n_tot * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->C, 0, p->n_tot * sizeof(double), p->st));
+  for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<double>(p, ax, p->A, p->C));
+  if (p->mixed) {
+    CK(cudaMemsetAsync(p->A32, 0, p->n_tot * sizeof(float), p->st));
+    CK(cudaMemsetAsync(p->C32, 0, p->n_tot * sizeof(float), p->st));
+    for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<float>(p, ax, p->A32, p->C32));
+  }
+  CK(cudaStreamSynchronize(p->st));
+  return TAU_OK;
+}
+
 tau_status check_ready(tau_problem* p) {
   if (!p) return fail(TAU_EINVAL, "problem is NULL");
   if (!p->setup_done) return fail(TAU_ESTATE, "tau_setup has not run");
@@ -876,6 +952,9 @@ tau_status tau_setup(tau_problem* p) {
   CK(cudaMemcpyAsync(p->g, &g, sizeof(g), cudaMemcpyHostToDevice, p->st));
   CK(cudaStreamSynchronize(p->st));
   p->m_host = 0;
+  const char* tn = std::getenv("TAU_AUTOTUNE");
+  const bool tune = tn ? tn[0] == '1' : p->n_tot >= (1 << 16);
+  if (tune) TRY(autotune(p));
   p->setup_done = true;
   const char* nog = std::getenv("TAU_NO_GRAPH");
   if (!(nog && nog[0] == '1')) {
@@ -964,6 +1043,10 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->e_check = p->echeck;
   for (int i = 0; i < 3; ++i) out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE) : 0;
   out->graph = p->graph_ok ? 1 : 0;
+  for (int i = 0; i < 3; ++i) {
+    out->lines_per_cta[i] = i < p->d ? base_pass_t<double>(p, i).lpb : 0;
+    out->lines_per_cta_f32[i] = i < p->d && p->mixed ? base_pass_t<float>(p, i).lpb : 0;
+  }
   out->kernels_prologue = p->k_pro;
   out->kernels_per_iter = p->k_body;
   out->kernels_epilogue = p->k_epi;

@@ -86,6 +86,8 @@ class tau_stats(C.Structure):
         ("kernels_epilogue", C.c_int64),
         ("kernels_total", C.c_int64),
         ("total_sweeps", C.c_int64),
+        ("lines_per_cta", C.c_int * 3),
+        ("lines_per_cta_f32", C.c_int * 3),
     ]
 
 

@@ -53,7 +53,8 @@ def test_struct_layout_matches_c_compiler(tmp_path):
         "tau_field": ["rank", "n_times", "time_coef", "space"],
         "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
                       "e_hat", "e_check", "route", "graph", "device_bytes", "kernels_prologue",
-                      "kernels_per_iter", "kernels_epilogue", "kernels_total", "total_sweeps"],
+                      "kernels_per_iter", "kernels_epilogue", "kernels_total", "total_sweeps", "lines_per_cta",
+                      "lines_per_cta_f32"],
         "tau_request_info": ["id", "state", "status", "t_submit", "t_admit", "t_finish", "unknowns", "steps",
                              "gmres_iters", "device_bytes"],
         "tau_server_stats": ["completed", "failed", "queued", "active", "device_bytes_in_use", "latency_p50_s",
