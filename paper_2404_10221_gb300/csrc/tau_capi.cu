@@ -596,7 +596,7 @@ std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune_cache;
 
 template <typename T>
 tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
-  PassT<T> P = base_pass_t<T>(p, ax);
+  PassT<T> P = base_pass_t<T>(p, ax);   // heuristic tile (lpb_tuned not yet set for this axis)
   const auto key = std::make_tuple((int)sizeof(T), P.dim.route, P.len, P.inner, P.nlines);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -606,28 +606,46 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
       return TAU_OK;
     }
   }
-  P.mv = 1;
+  // representative work: one matvec pass (channels a, c in place) and one DST pass (on c)
   P.seta = 1.0;
   P.in_a = chA;
   P.in_c = chC;
   P.out_a = chA;
   P.out_c = chC;
+  PassT<T> Q = P;
+  P.mv = 1;
+  Q.post = POST_DST;
+  Q.in_a = chC;
+  Q.out_a = chC;
+  const int heur = P.lpb;
   const int64_t cap = ax == 0 ? P.nlines : P.inner;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_lpb = P.lpb;
-  for (int lpb = 1; lpb <= 32 && lpb <= cap; lpb *= 2) {
+  auto time_lpb = [&](int lpb, float* ms) -> tau_status {
     set_lpb(P, lpb);
-    if (pass_smem_bytes(P) > 200 * 1024) break;
+    set_lpb(Q, lpb);
     CK(launch_pass(P, p->st));
+    CK(launch_pass(Q, p->st));
     CK(cudaEventRecord(e0, p->st));
-    for (int r = 0; r < 3; ++r) CK(launch_pass(P, p->st));
+    for (int r = 0; r < 3; ++r) {
+      CK(launch_pass(P, p->st));
+      CK(launch_pass(Q, p->st));
+    }
     CK(cudaEventRecord(e1, p->st));
     CK(cudaEventSynchronize(e1));
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return TAU_OK;
+  };
+  float best = 0.0f;
+  TRY(time_lpb(heur, &best));
+  int best_lpb = heur;
+  for (int lpb = 1; lpb <= 32 && lpb <= cap; lpb *= 2) {
+    if (lpb == heur) continue;
+    set_lpb(P, lpb);
+    if (pass_smem_bytes(P) > 200 * 1024) break;
+    float ms = 0.0f;
+    TRY(time_lpb(lpb, &ms));
     if (ms < best * 0.97f) {
       best = ms;
       best_lpb = lpb;

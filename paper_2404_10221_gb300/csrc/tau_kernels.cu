@@ -51,9 +51,41 @@ __device__ __forceinline__ int dif_pos(int k, int K) {
   return pos;
 }
 
+// Radix-4 decimation-in-frequency butterfly on registers (span q, index i within the group).
+template <typename V>
+__device__ __forceinline__ void dif4(V& a0, V& a1, V& a2, V& a3, int i, int q, const V* __restrict__ tws) {
+  const V b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), b3 = mul_mi(csub(a1, a3));
+  a0 = cadd(b0, b2);
+  if (i == 0) {
+    a1 = cadd(b1, b3);
+    a2 = csub(b0, b2);
+    a3 = csub(b1, b3);
+  } else {
+    a1 = cmul(cadd(b1, b3), __ldg(&tws[i]));
+    a2 = cmul(csub(b0, b2), __ldg(&tws[q + i]));
+    a3 = cmul(csub(b1, b3), __ldg(&tws[2 * q + i]));
+  }
+}
+
+// Inverse radix-4 decimation-in-time butterfly on registers (conjugate twiddles, then 4-point).
+template <typename V>
+__device__ __forceinline__ void dit4_inv(V& y0, V& y1, V& y2, V& y3, int i, int q, const V* __restrict__ tws) {
+  if (i != 0) {
+    y1 = cmulc(y1, __ldg(&tws[i]));
+    y2 = cmulc(y2, __ldg(&tws[q + i]));
+    y3 = cmulc(y3, __ldg(&tws[2 * q + i]));
+  }
+  const V c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
+  y0 = cadd(c0, c2);
+  y1 = cadd(c1, c3);
+  y2 = csub(c0, c2);
+  y3 = csub(c1, c3);
+}
+
 // Forward complex DFT of length K (natural order in, digit-reversed out) on nl lines stored at
-// cb + l*cs, twiddles from the stage-packed table twp (twp_size(K) entries).  Caller
-// synchronises before; this synchronises after.
+// cb + l*cs, twiddles from the stage-packed table twp (twp_size(K) entries).  Each thread loads two
+// independent butterflies before computing either, so their shared-memory latencies overlap.
+// Caller synchronises before; this synchronises after.
 template <typename V>
 __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp) {
   const int T = blockDim.x, tid = threadIdx.x;
@@ -62,21 +94,42 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp)
     const int q = size >> 2;
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
-    for (int b = tid; b < nl * nb; b += T) {
-      const int l = b / nb, loc = b - l * nb;
-      const int g = loc / q, i = loc - g * q;
-      V* x = cb + l * cs + g * size + i;
-      const V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
-      const V b0 = cadd(a0, a2), b1 = csub(a0, a2), b2 = cadd(a1, a3), b3 = mul_mi(csub(a1, a3));
-      x[0] = cadd(b0, b2);
-      if (i == 0) {
-        x[q] = cadd(b1, b3);
-        x[2 * q] = csub(b0, b2);
-        x[3 * q] = csub(b1, b3);
-      } else {
-        x[q] = cmul(cadd(b1, b3), __ldg(&tws[i]));
-        x[2 * q] = cmul(csub(b0, b2), __ldg(&tws[q + i]));
-        x[3 * q] = cmul(csub(b1, b3), __ldg(&tws[2 * q + i]));
+    const int tot = nl * nb;
+    for (int b = tid; b < tot; b += 2 * T) {
+      const int bb = b + T;
+      const bool two = bb < tot;
+      int l = b / nb, loc = b - l * nb;
+      int g = loc / q;
+      const int i0 = loc - g * q;
+      V* x = cb + l * cs + g * size + i0;
+      int i1 = 0;
+      V* y = x;
+      if (two) {
+        l = bb / nb;
+        loc = bb - l * nb;
+        g = loc / q;
+        i1 = loc - g * q;
+        y = cb + l * cs + g * size + i1;
+      }
+      V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
+      V c0, c1, c2, c3;
+      if (two) {
+        c0 = y[0];
+        c1 = y[q];
+        c2 = y[2 * q];
+        c3 = y[3 * q];
+      }
+      dif4(a0, a1, a2, a3, i0, q, tws);
+      if (two) dif4(c0, c1, c2, c3, i1, q, tws);
+      x[0] = a0;
+      x[q] = a1;
+      x[2 * q] = a2;
+      x[3 * q] = a3;
+      if (two) {
+        y[0] = c0;
+        y[q] = c1;
+        y[2 * q] = c2;
+        y[3 * q] = c3;
       }
     }
     __syncthreads();
@@ -116,21 +169,43 @@ __device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ 
     const int q = size >> 2;
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
-    for (int b = tid; b < nl * nb; b += T) {
-      const int l = b / nb, loc = b - l * nb;
-      const int g = loc / q, i = loc - g * q;
-      V* x = cb + l * cs + g * size + i;
-      V y0 = x[0], y1 = x[q], y2 = x[2 * q], y3 = x[3 * q];
-      if (i != 0) {
-        y1 = cmulc(y1, __ldg(&tws[i]));
-        y2 = cmulc(y2, __ldg(&tws[q + i]));
-        y3 = cmulc(y3, __ldg(&tws[2 * q + i]));
+    const int tot = nl * nb;
+    for (int b = tid; b < tot; b += 2 * T) {
+      const int bb = b + T;
+      const bool two = bb < tot;
+      int l = b / nb, loc = b - l * nb;
+      int g = loc / q;
+      const int i0 = loc - g * q;
+      V* x = cb + l * cs + g * size + i0;
+      int i1 = 0;
+      V* y = x;
+      if (two) {
+        l = bb / nb;
+        loc = bb - l * nb;
+        g = loc / q;
+        i1 = loc - g * q;
+        y = cb + l * cs + g * size + i1;
       }
-      const V c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
-      x[0] = cadd(c0, c2);
-      x[q] = cadd(c1, c3);
-      x[2 * q] = csub(c0, c2);
-      x[3 * q] = csub(c1, c3);
+      V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
+      V c0, c1, c2, c3;
+      if (two) {
+        c0 = y[0];
+        c1 = y[q];
+        c2 = y[2 * q];
+        c3 = y[3 * q];
+      }
+      dit4_inv(a0, a1, a2, a3, i0, q, tws);
+      if (two) dit4_inv(c0, c1, c2, c3, i1, q, tws);
+      x[0] = a0;
+      x[q] = a1;
+      x[2 * q] = a2;
+      x[3 * q] = a3;
+      if (two) {
+        y[0] = c0;
+        y[q] = c1;
+        y[2 * q] = c2;
+        y[3 * q] = c3;
+      }
     }
     __syncthreads();
   }
