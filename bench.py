@@ -235,6 +235,17 @@ def run_forms(stream, dev):
     from paper_2404_10221_gb300 import workloads as W
 
     out = {}
+    # the plain method in double-float arithmetic on the FP32 pipes, same workload as the headline
+    wl = W.c2_2d()
+    v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, 2, 5, stream, dev)
+    vdf, msdf, udf, stdf, itdf = measure_steps(wl, tau.TAU_DF64, 2, 5, stream, dev)
+    out["2d_1023_df64"] = {
+        "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_compared": 7, "df64_value": vdf,
+        "df64_ms_per_step": msdf, "plain_fp64_value": v64, "plain_fp64_ms_per_step": ms64,
+        "speedup_vs_plain_fp64": vdf / v64,
+        "rel_err_vs_plain_fp64": (torch.linalg.norm(udf - u64) / torch.linalg.norm(u64)).item(),
+        "df64_iters_per_step": float(np.mean(itdf)), "plain_iters_per_step": float(np.mean(it64)),
+        "unit": UNIT, "dtype": "double-float (2 x f32) vectors, transforms and Arnoldi; f64 Givens/LSQ"}
     for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)

@@ -59,7 +59,11 @@ typedef int tau_status;
 #define TAU_FP64 0            /* plain FP64 arithmetic everywhere */
 #define TAU_MIXED 1           /* FP64 iterative refinement (residual b - A x, correction, stopping)
                                  around an inner flexible GMRES whose matvec, tau solve and Arnoldi
-                                 vectors are FP32 (SURVEY spec form 1) */
+                                 vectors are FP32 */
+#define TAU_DF64 2            /* the plain method with every solver vector, transform and Arnoldi
+                                 product in double-float arithmetic (pairs of FP32 numbers, ~48
+                                 significant bits) on the FP32 pipes; scalars (Givens, least squares)
+                                 in FP64; u, e and f cross the API in FP64 */
 
 #define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
@@ -79,7 +83,7 @@ typedef struct {
   double tol;           /* GMRES stop: ||r_k|| <= tol ||r_0|| on the preconditioned residual */
   int max_iter;         /* GMRES iteration cap per step, 1..1000 (no restart) */
   int x0_mode;          /* TAU_X0_ZERO or TAU_X0_PREV */
-  int precision;        /* TAU_FP64 or TAU_MIXED */
+  int precision;        /* TAU_FP64, TAU_MIXED or TAU_DF64 */
   int route[3];         /* TAU_ROUTE_* per dimension */
   double e_min, e_max;  /* bounds of e over the grid and all t_{m+1/2} for ebar (Eqs. (bard),
                            (dhat)); pass NaN for both to let tau_setup scan them */

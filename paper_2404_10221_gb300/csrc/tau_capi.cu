@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -90,7 +91,7 @@ struct tau_problem {
   bool mixed = false;
   int kin = 0;                                 // inner iteration cap
   double *X = nullptr;                         // FP64 iterate of the refinement
-  float *V32 = nullptr, *Z32 = nullptr, *A32 = nullptr, *C32 = nullptr, *invmu32 = nullptr;
+  float *V32 = nullptr, *Z32 = nullptr, *A32 = nullptr, *C32 = nullptr, *invmu32 = nullptr, *E32 = nullptr;
   double *Hin = nullptr, *csin = nullptr, *snin = nullptr, *gvin = nullptr, *h1in = nullptr, *h2in = nullptr,
          *yin = nullptr;
   GmresDev* gin = nullptr;
@@ -100,7 +101,14 @@ struct tau_problem {
          *twK2_32[3] = {nullptr, nullptr, nullptr};
   float *s32[3] = {nullptr, nullptr, nullptr}, *sintab32[3] = {nullptr, nullptr, nullptr};
   int64_t k_ir_pre = 0, k_ir_post = 0;         // kernels of one refinement sweep around the inner loop
-  int lpb_tuned[2][3] = {{0, 0, 0}, {0, 0, 0}}; // lines per CTA chosen by the autotuner (FP64, FP32)
+  int lpb_tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // lines per CTA chosen by the autotuner
+                                                          // (FP64, FP32, double-float)
+  // double-float precision (TAU_DF64): solver vectors live in the FP64 buffers above as df64 pairs
+  bool dfm = false;
+  df64 *Edf = nullptr, *Fdf = nullptr, *invmu_df = nullptr;
+  df64x2 *spec_df[3] = {nullptr, nullptr, nullptr}, *twK_df[3] = {nullptr, nullptr, nullptr},
+         *twK2_df[3] = {nullptr, nullptr, nullptr};
+  df64 *s_df[3] = {nullptr, nullptr, nullptr}, *sintab_df[3] = {nullptr, nullptr, nullptr};
   int64_t fields_m = -1;                      // step whose e and dt*F sit in E / Fdt
   int* h_done = nullptr;  // pinned flag for the host-loop fallback
   std::vector<void*> allocs;
@@ -151,6 +159,17 @@ FieldDev field_dev(const tau_problem* p) {
   return f;
 }
 
+// host-side conversion of a scalar to the element type (double-float: hi = fl(v), lo = fl(v - hi))
+template <typename T> T host_cast(double v) { return (T)v; }
+template <> df64 host_cast<df64>(double v) {
+  const float h = (float)v;
+  return df64{h, (float)(v - (double)h)};
+}
+
+template <typename T> constexpr int prec_index() {
+  return std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2);
+}
+
 template <typename T>
 void set_lpb(PassT<T>& P, int lpb) {
   P.lpb = lpb;
@@ -171,16 +190,23 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   D.n = p->n[ax];
   D.K = p->n[ax] + 1;
   D.route = p->route[ax];
-  D.bdiag = (T)(1.0 - p->desc.alpha[ax] / 12.0);
-  D.boff = (T)(p->desc.alpha[ax] / 24.0);
+  D.bdiag = host_cast<T>(1.0 - p->desc.alpha[ax] / 12.0);
+  D.boff = host_cast<T>(p->desc.alpha[ax] / 24.0);
   D.eta = p->eta[ax];
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, double>::value) {
     D.spec = p->spec[ax];
     D.s = p->s[ax];
     D.sintab = p->sintab[ax];
     D.twK = p->twK[ax];
     D.twK2 = p->twK2[ax];
     P.in_base = P.out_base = p->V;
+  } else if constexpr (std::is_same<T, df64>::value) {
+    D.spec = p->spec_df[ax];
+    D.s = p->s_df[ax];
+    D.sintab = p->sintab_df[ax];
+    D.twK = p->twK_df[ax];
+    D.twK2 = p->twK2_df[ax];
+    P.in_base = P.out_base = reinterpret_cast<df64*>(p->V);
   } else {
     D.spec = p->spec32[ax];
     D.s = p->s32[ax];
@@ -193,7 +219,7 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   if (lpb < 1) lpb = 1;
   if (lpb > 16) lpb = 16;
   const int64_t cap = ax == 0 ? P.nlines : inner;
-  const int tuned = p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax];
+  const int tuned = p->lpb_tuned[prec_index<T>()][ax];
   if (tuned > 0) lpb = tuned;
   if (lpb > cap) lpb = cap;
   set_lpb(P, (int)lpb);
@@ -225,12 +251,20 @@ tau_status enq(const PassT<T>& P, cudaStream_t st) {
 template <typename T> const T* invmu_of(const tau_problem* p);
 template <> const double* invmu_of<double>(const tau_problem* p) { return p->invmu; }
 template <> const float* invmu_of<float>(const tau_problem* p) { return p->invmu32; }
+template <> const df64* invmu_of<df64>(const tau_problem* p) { return p->invmu_df; }
 template <typename T> T* chanA(const tau_problem* p);
 template <typename T> T* chanC(const tau_problem* p);
 template <> double* chanA<double>(const tau_problem* p) { return p->A; }
 template <> double* chanC<double>(const tau_problem* p) { return p->C; }
 template <> float* chanA<float>(const tau_problem* p) { return p->A32; }
 template <> float* chanC<float>(const tau_problem* p) { return p->C32; }
+template <> df64* chanA<df64>(const tau_problem* p) { return reinterpret_cast<df64*>(p->A); }
+template <> df64* chanC<df64>(const tau_problem* p) { return reinterpret_cast<df64*>(p->C); }
+// coefficient e of the current step in the pass element type
+template <typename T> const T* e_of(const tau_problem* p);
+template <> const double* e_of<double>(const tau_problem* p) { return p->E; }
+template <> const df64* e_of<df64>(const tau_problem* p) { return p->Edf; }
+template <> const float* e_of<float>(const tau_problem* p) { return p->E32; }
 
 template <typename T>
 void wire_in(PassT<T>& P, const ChainT<T>& io, bool from_x) {
@@ -288,7 +322,7 @@ tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double s
     P.g = io.g;
     if (ax == 0) {
       wire_in(P, io, true);
-      P.e = p->E;
+      P.e = e_of<T>(p);
     } else {
       P.in_a = chanA<T>(p);
       P.in_c = chanC<T>(p);
@@ -314,48 +348,84 @@ tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainT<T>& io) {
   return enq_minv_tail<T>(p, st, io, p->d - 1, true);
 }
 
-tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
-  KL(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
-  ChainIO rhs;
-  rhs.x = p->u;
-  rhs.out = p->b;
-  TRY(enq_mv<double>(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
-  ChainIO r0;
-  r0.out = p->V;
-  if (p->desc.x0_mode == TAU_X0_PREV) {
-    r0.x = p->u;
-    TRY(enq_mv<double>(p, st, r0, 1.0, FIN_RESID, p->b, true));
-  } else {
-    r0.x = p->b;
-    TRY(enq_minv<double>(p, st, r0));
+// Fields of the current step (from g->m): E, dt F in FP64, plus their copies in the element type
+// of the solver (double-float: converted here; FP32 inner solve: e only).
+tau_status enq_fields(tau_problem* p, cudaStream_t st, int64_t m_override) {
+  KL(launch_fields(field_dev(p), p->g, m_override, p->E, p->Fdt, st));
+  if (p->dfm) {
+    KL(launch_d_to_df(p->E, p->Edf, p->n_tot, st));
+    KL(launch_d_to_df(p->Fdt, p->Fdf, p->n_tot, st));
   }
-  KL(launch_norm_partial(p->V, p->n_tot, p->g, p->pnorm, st));
-  tl_launches += 1;
-  KL(launch_init_beta(p->g, p->pnorm, p->gv, p->V, p->n_tot, st));
+  if (p->mixed) KL(launch_f64_to_f32(p->E, p->E32, p->n_tot, st));
   return TAU_OK;
 }
 
-tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
-  ChainIO it;
+template <typename T> T* as(double* v) { return reinterpret_cast<T*>(v); }
+template <typename T> const T* fdt_of(const tau_problem* p);
+template <> const double* fdt_of<double>(const tau_problem* p) { return p->Fdt; }
+template <> const df64* fdt_of<df64>(const tau_problem* p) { return p->Fdf; }
+
+// Plain GMRES step in element type T (double, or double-float pairs stored in the same buffers).
+template <typename T>
+tau_status enq_prologue_t(tau_problem* p, cudaStream_t st) {
+  TRY(enq_fields(p, st, -1));
+  ChainT<T> rhs;
+  rhs.x = as<T>(p->u);
+  rhs.out = as<T>(p->b);
+  TRY(enq_mv<T>(p, st, rhs, -1.0, FIN_ADD_F, fdt_of<T>(p), false));
+  ChainT<T> r0;
+  r0.out = as<T>(p->V);
+  if (p->desc.x0_mode == TAU_X0_PREV) {
+    r0.x = as<T>(p->u);
+    TRY(enq_mv<T>(p, st, r0, 1.0, FIN_RESID, as<T>(p->b), true));
+  } else {
+    r0.x = as<T>(p->b);
+    TRY(enq_minv<T>(p, st, r0));
+  }
+  KL(launch_norm_partial<T>(as<T>(p->V), p->n_tot, p->g, p->pnorm, st));
+  tl_launches += 1;
+  KL(launch_init_beta<T>(p->g, p->pnorm, p->gv, as<T>(p->V), p->n_tot, st));
+  return TAU_OK;
+}
+
+template <typename T>
+tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+  ChainT<T> it;
   it.in_sel = 1;
   it.out_sel = 2;
   it.g = p->g;
-  TRY(enq_mv<double>(p, st, it, 1.0, FIN_NONE, nullptr, true));
+  TRY(enq_mv<T>(p, st, it, 1.0, FIN_NONE, nullptr, true));
   const int ld = RED_BLOCKS;
-  KL(launch_dots<double>(p->V, p->n_tot, p->g, p->pdots, ld, st));
+  T* V = as<T>(p->V);
+  KL(launch_dots<T>(V, p->n_tot, p->g, p->pdots, ld, st));
   KL(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
-  KL(launch_update_dots<double>(p->V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
+  KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
   KL(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
-  KL(launch_update_dots<double>(p->V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
+  KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
   KL(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
-  KL(launch_scale_next<double>(p->V, p->n_tot, p->g, st));
+  KL(launch_scale_next<T>(V, p->n_tot, p->g, st));
   return TAU_OK;
+}
+
+template <typename T>
+tau_status enq_epilogue_t(tau_problem* p, cudaStream_t st) {
+  tl_launches += 2;
+  KL(launch_backsolve_update<T>(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, as<T>(p->V), p->n_tot, as<T>(p->u),
+                                p->desc.x0_mode == TAU_X0_PREV, p->iters, st));
+  return TAU_OK;
+}
+
+tau_status enq_prologue(tau_problem* p, cudaStream_t st) {
+  return p->dfm ? enq_prologue_t<df64>(p, st) : enq_prologue_t<double>(p, st);
+}
+tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
+  return p->dfm ? enq_body_t<df64>(p, st, h, use_cond) : enq_body_t<double>(p, st, h, use_cond);
 }
 
 // ---- mixed precision: prologue, refinement sweep (before / after the inner loop), inner
 //      FGMRES iteration, epilogue
 tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
-  KL(launch_fields(field_dev(p), p->g, -1, p->E, p->Fdt, st));
+  TRY(enq_fields(p, st, -1));
   ChainIO rhs;
   rhs.x = p->u;
   rhs.out = p->b;
@@ -422,10 +492,7 @@ tau_status enq_mx_epilogue(tau_problem* p, cudaStream_t st) {
 }
 
 tau_status enq_epilogue(tau_problem* p, cudaStream_t st) {
-  tl_launches += 2;
-  KL(launch_backsolve_update(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, p->V, p->n_tot, p->u,
-                             p->desc.x0_mode == TAU_X0_PREV, p->iters, st));
-  return TAU_OK;
+  return p->dfm ? enq_epilogue_t<df64>(p, st) : enq_epilogue_t<double>(p, st);
 }
 
 // Record fn(stream) into graph g after deps; leaves receives the capture's final dependencies.
@@ -584,7 +651,7 @@ tau_status run_step_hostloop_mx(tau_problem* p) {
 // e and dt*F of step m into E / Fdt for the operator entry points (skipped when already there).
 tau_status fields_for(tau_problem* p, int64_t m) {
   if (p->fields_m == m) return TAU_OK;
-  KL(launch_fields(field_dev(p), p->g, m, p->E, p->Fdt, p->st));
+  TRY(enq_fields(p, p->st, m));
   p->fields_m = m;
   return TAU_OK;
 }
@@ -597,12 +664,12 @@ std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune_cache;
 template <typename T>
 tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   PassT<T> P = base_pass_t<T>(p, ax);   // heuristic tile (lpb_tuned not yet set for this axis)
-  const auto key = std::make_tuple((int)sizeof(T), P.dim.route, P.len, P.inner, P.nlines);
+  const auto key = std::make_tuple(prec_index<T>(), P.dim.route, P.len, P.inner, P.nlines);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax] = it->second;
+      p->lpb_tuned[prec_index<T>()][ax] = it->second;
       return TAU_OK;
     }
   }
@@ -653,7 +720,7 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  p->lpb_tuned[sizeof(T) == 8 ? 0 : 1][ax] = best_lpb;
+  p->lpb_tuned[prec_index<T>()][ax] = best_lpb;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best_lpb;
   return TAU_OK;
@@ -663,6 +730,8 @@ tau_status autotune(tau_problem* p) {
   CK(cudaMemsetAsync(p->A, 0, p->n_tot * sizeof(double), p->st));
   CK(cudaMemsetAsync(p->C, 0, p->n_tot * sizeof(double), p->st));
   for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<double>(p, ax, p->A, p->C));
+  if (p->dfm)
+    for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<df64>(p, ax, as<df64>(p->A), as<df64>(p->C)));
   if (p->mixed) {
     CK(cudaMemsetAsync(p->A32, 0, p->n_tot * sizeof(float), p->st));
     CK(cudaMemsetAsync(p->C32, 0, p->n_tot * sizeof(float), p->st));
@@ -712,7 +781,8 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (!(D.tol > 0) || D.max_iter < 1 || D.max_iter > MAX_ITER_CAP)
     return fail(TAU_EINVAL, "tol must be > 0 and 1 <= max_iter <= %d", MAX_ITER_CAP);
   if (D.x0_mode != TAU_X0_ZERO && D.x0_mode != TAU_X0_PREV) return fail(TAU_EINVAL, "x0_mode %d", D.x0_mode);
-  if (D.precision != TAU_FP64 && D.precision != TAU_MIXED) return fail(TAU_EINVAL, "precision %d", D.precision);
+  if (D.precision != TAU_FP64 && D.precision != TAU_MIXED && D.precision != TAU_DF64)
+    return fail(TAU_EINVAL, "precision %d", D.precision);
   if (D.precision == TAU_MIXED &&
       (D.refine_tol < 0 || D.inner_tol < 0 || D.inner_max_iter < 0 || D.inner_max_iter > MAX_ITER_CAP ||
        D.max_sweeps < 0))
@@ -758,6 +828,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
   p->mixed = D.precision == TAU_MIXED;
+  p->dfm = D.precision == TAU_DF64;
   if (p->mixed) {
     if (p->desc.refine_tol == 0) p->desc.refine_tol = 1e-10;
     if (p->desc.inner_max_iter == 0) p->desc.inner_max_iter = 30;
@@ -774,12 +845,16 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     const int k = p->kin;
     if ((s = dalloc_n(p, &p->X, n)) || (s = dalloc_n(p, &p->V32, (size_t)(k + 1) * n)) ||
         (s = dalloc_n(p, &p->Z32, (size_t)k * n)) || (s = dalloc_n(p, &p->A32, n)) || (s = dalloc_n(p, &p->C32, n)) ||
-        (s = dalloc_n(p, &p->invmu32, n)) || (s = dalloc_n(p, &p->Hin, (size_t)(k + 1) * k)) ||
+        (s = dalloc_n(p, &p->invmu32, n)) || (s = dalloc_n(p, &p->E32, n)) ||
+        (s = dalloc_n(p, &p->Hin, (size_t)(k + 1) * k)) ||
         (s = dalloc_n(p, &p->csin, k)) || (s = dalloc_n(p, &p->snin, k)) || (s = dalloc_n(p, &p->gvin, k + 1)) ||
         (s = dalloc_n(p, &p->h1in, k + 1)) || (s = dalloc_n(p, &p->h2in, k + 1)) || (s = dalloc_n(p, &p->yin, k + 1)) ||
         (s = dalloc_n(p, &p->gin, 1)) || (s = dalloc_n(p, &p->ir, 1)) || (s = dalloc_n(p, &p->sweeps, (size_t)D.M)))
       return cleanup(s);
   }
+  if (p->dfm && ((s = dalloc_n(p, &p->Edf, n)) || (s = dalloc_n(p, &p->Fdf, n)) ||
+                 (s = dalloc_n(p, &p->invmu_df, n))))
+    return cleanup(s);
   if ((s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
       (s = dalloc_n(p, &p->A, n)) || (s = dalloc_n(p, &p->C, n)) || (s = dalloc_n(p, &p->E, n)) ||
       (s = dalloc_n(p, &p->Fdt, n)) || (s = dalloc_n(p, &p->invmu, n)) || (s = dalloc_n(p, &p->tmp, n)) ||
@@ -928,7 +1003,30 @@ tau_status tau_setup(tau_problem* p) {
     return fail(TAU_EINVAL, "e must be positive: min %g max %g", p->echeck, p->ehat);
   p->ebar = 0.5 * (p->ehat + p->echeck);
   KL(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
-  KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->u, p->st));
+  KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->dfm ? p->tmp : p->u, p->st));
+  if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
+  if (p->dfm) {
+    auto conv = [&](const double* src, df64** dst, size_t cnt) -> tau_status {
+      TRY(dalloc_n(p, dst, cnt));
+      KL(launch_d_to_df(src, *dst, (int64_t)cnt, p->st));
+      return TAU_OK;
+    };
+    for (int i = 0; i < d; ++i) {
+      const int N = p->n[i], K = N + 1;
+      TRY(conv(p->s[i], &p->s_df[i], N));
+      TRY(conv(p->sintab[i], &p->sintab_df[i], 2 * (size_t)K));
+      if (p->route[i] == ROUTE_FFT) {
+        df64* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 2 * (size_t)(K / 2 + 1)));
+        p->spec_df[i] = reinterpret_cast<df64x2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
+        p->twK_df[i] = reinterpret_cast<df64x2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK2[i]), &f, 2 * (size_t)twp_size(K / 2)));
+        p->twK2_df[i] = reinterpret_cast<df64x2*>(f);
+      }
+    }
+    KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
+  }
   if (p->mixed) {
     auto conv = [&](const double* src, float** dst, size_t cnt) -> tau_status {
       TRY(dalloc_n(p, dst, cnt));
@@ -1016,7 +1114,12 @@ tau_status tau_solve(tau_problem* p) {
 tau_status tau_get_solution(tau_problem* p, double* out, int is_device, int64_t* m_out) {
   TRY(check_ready(p));
   if (!out) return fail(TAU_EINVAL, "out is NULL");
-  CK(cudaMemcpyAsync(out, p->u, p->n_tot * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+  const double* src = p->u;
+  if (p->dfm) {
+    KL(launch_df_to_d(as<df64>(p->u), p->tmp, p->n_tot, p->st));
+    src = p->tmp;
+  }
+  CK(cudaMemcpyAsync(out, src, p->n_tot * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      p->st));
   if (!is_device) CK(cudaStreamSynchronize(p->st));
   if (m_out) *m_out = p->m_host;
@@ -1027,8 +1130,9 @@ tau_status tau_set_solution(tau_problem* p, const double* u, int is_device, int6
   TRY(check_ready(p));
   if (!u) return fail(TAU_EINVAL, "u is NULL");
   if (m < 0 || m > p->desc.M) return fail(TAU_EINVAL, "m=%lld outside 0..M", (long long)m);
-  CK(cudaMemcpyAsync(p->u, u, p->n_tot * sizeof(double), is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                     p->st));
+  CK(cudaMemcpyAsync(p->dfm ? p->tmp : p->u, u, p->n_tot * sizeof(double),
+                     is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->st));
+  if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
   // m lives in the device state read by the step graph
   CK(cudaMemcpyAsync(&p->g->m, &m, sizeof(int64_t), cudaMemcpyHostToDevice, p->st));
   CK(cudaStreamSynchronize(p->st));

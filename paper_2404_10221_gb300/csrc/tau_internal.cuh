@@ -34,10 +34,62 @@ enum Post : int {
 
 struct GmresDev;
 
+// Double-float number: value = hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits, computed
+// on the FP32 pipes.  Addition is Knuth's two-sum on the high parts followed by a renormalisation;
+// multiplication uses the FMA-exact product of the high parts (Dekker, "A floating-point technique
+// for extending the available precision", 1971; the FMA form of the product error).
+struct __align__(8) df64 {
+  float hi, lo;
+};
+struct __align__(16) df64x2 {
+  df64 x, y;
+};
+
 template <typename T> struct Vec2Of;
 template <> struct Vec2Of<double> { using type = double2; };
 template <> struct Vec2Of<float> { using type = float2; };
+template <> struct Vec2Of<df64> { using type = df64x2; };
 template <typename T> using vec2 = typename Vec2Of<T>::type;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return df64{h, e - (h - s)};
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64{-a.hi, -a.lo}; }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + df64{-b.hi, -b.lo}; }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float h = p + e;
+  return df64{h, e - (h - p)};
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+
+// conversions (the double <-> float ones run on the FP64 pipe: keep them off inner loops)
+template <typename T> __device__ __forceinline__ T from_d(double v) { return (T)v; }
+template <> __device__ __forceinline__ df64 from_d<df64>(double v) {
+  const float h = __double2float_rn(v);
+  return df64{h, __double2float_rn(v - (double)h)};
+}
+template <typename T> __device__ __forceinline__ T from_f(float v) { return (T)v; }
+template <> __device__ __forceinline__ df64 from_f<df64>(float v) { return df64{v, 0.0f}; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(df64 v) { return (double)v.hi + (double)v.lo; }
+// element conversion between storage and compute types
+template <typename T, typename S> __device__ __forceinline__ T cvt(S v) { return (T)v; }
+template <> __device__ __forceinline__ df64 cvt<df64, double>(double v) { return from_d<df64>(v); }
+template <> __device__ __forceinline__ df64 cvt<df64, df64>(df64 v) { return v; }
+template <> __device__ __forceinline__ double cvt<double, df64>(df64 v) { return to_d(v); }
+#endif
 
 // Per-dimension data resident on the device, in the element type T of the pass (FP64 for the
 // plain path, FP32 for the inner solve of the mixed-precision form).
@@ -83,7 +135,7 @@ struct PassT {
   int post;          // Post
   const T* in_a;        // first pass: x; else channel a
   const T* in_c;        // channel c (not read by the first pass)
-  const double* e;      // first pass: e at the interior nodes (FP64 storage)
+  const T* e;           // first pass: e at the interior nodes
   const T* src;         // FIN_RESID minuend or FIN_ADD_F addend (Fdt)
   const T* invmu;       // POST_DST_MU_DST
   T* out_a;
@@ -161,12 +213,15 @@ cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double
                           cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 template <typename S>
 cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st);
-cudaError_t launch_norm_partial(const double* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st);
-cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, double* V, int64_t n,
-                             cudaStream_t st);
-cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y,
-                                    const double* V, int64_t n, double* u, int x0_prev, int* iters_log,
-                                    cudaStream_t st);
+template <typename S>
+cudaError_t launch_norm_partial(const S* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st);
+template <typename S>
+cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, S* V, int64_t n, cudaStream_t st);
+template <typename S>
+cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y, const S* V,
+                                    int64_t n, S* u, int x0_prev, int* iters_log, cudaStream_t st);
+cudaError_t launch_d_to_df(const double* a, df64* b, int64_t n, cudaStream_t st);
+cudaError_t launch_df_to_d(const df64* a, double* b, int64_t n, cudaStream_t st);
 cudaError_t launch_fp64_peak(double* out, int blocks, int iters, cudaStream_t st);
 
 // Iterative-refinement state of the mixed-precision form (device memory).

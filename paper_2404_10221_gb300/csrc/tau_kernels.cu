@@ -26,7 +26,16 @@ constexpr int PASS_THREADS = 128;
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 tfma(df64 a, df64 b, df64 c) { return a * b + c; }
+__device__ __forceinline__ double shfl_up(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float shfl_up(float v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ df64 shfl_up(df64 v, int o) {
+  return df64{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
 template <typename V> __device__ __forceinline__ V mk(decltype(V::x) x, decltype(V::x) y) { return V{x, y}; }
+// read-only cached load for table entries (plain load for the double-float pair type)
+template <typename V> __device__ __forceinline__ V ldt(const V* p) { return __ldg(p); }
+template <> __device__ __forceinline__ df64x2 ldt<df64x2>(const df64x2* p) { return *p; }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk<V>(a.x + b.x, a.y + b.y); }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk<V>(a.x - b.x, a.y - b.y); }
 template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
@@ -61,9 +70,9 @@ __device__ __forceinline__ void dif4(V& a0, V& a1, V& a2, V& a3, int i, int q, c
     a2 = csub(b0, b2);
     a3 = csub(b1, b3);
   } else {
-    a1 = cmul(cadd(b1, b3), __ldg(&tws[i]));
-    a2 = cmul(csub(b0, b2), __ldg(&tws[q + i]));
-    a3 = cmul(csub(b1, b3), __ldg(&tws[2 * q + i]));
+    a1 = cmul(cadd(b1, b3), ldt(&tws[i]));
+    a2 = cmul(csub(b0, b2), ldt(&tws[q + i]));
+    a3 = cmul(csub(b1, b3), ldt(&tws[2 * q + i]));
   }
 }
 
@@ -71,9 +80,9 @@ __device__ __forceinline__ void dif4(V& a0, V& a1, V& a2, V& a3, int i, int q, c
 template <typename V>
 __device__ __forceinline__ void dit4_inv(V& y0, V& y1, V& y2, V& y3, int i, int q, const V* __restrict__ tws) {
   if (i != 0) {
-    y1 = cmulc(y1, __ldg(&tws[i]));
-    y2 = cmulc(y2, __ldg(&tws[q + i]));
-    y3 = cmulc(y3, __ldg(&tws[2 * q + i]));
+    y1 = cmulc(y1, ldt(&tws[i]));
+    y2 = cmulc(y2, ldt(&tws[q + i]));
+    y3 = cmulc(y3, ldt(&tws[2 * q + i]));
   }
   const V c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
   y0 = cadd(c0, c2);
@@ -227,12 +236,12 @@ __device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict_
     const V A = x[pk], B = x[pkk];
     const V E2 = mk<V>(A.x + B.x, A.y - B.y);
     const V O2 = mk<V>(A.y + B.y, B.x - A.x);
-    const V W = __ldg(&twp[K + k]);
+    const V W = ldt(&twp[K + k]);
     const V P = cmul(W, O2);
-    const V sd = __ldg(&spec[k]);
-    const V Ep = mk<V>(fma(sd.x, E2.x, sd.y * P.x), fma(sd.x, E2.y, sd.y * P.y));
+    const V sd = ldt(&spec[k]);
+    const V Ep = mk<V>(tfma(sd.x, E2.x, sd.y * P.x), tfma(sd.x, E2.y, sd.y * P.y));
     const V WcE = cmulc(E2, W);
-    const V Op = mk<V>(fma(sd.y, WcE.x, sd.x * O2.x), fma(sd.y, WcE.y, sd.x * O2.y));
+    const V Op = mk<V>(tfma(sd.y, WcE.x, sd.x * O2.x), tfma(sd.y, WcE.y, sd.x * O2.y));
     x[pk] = mk<V>(Ep.x - Op.y, Ep.y + Op.x);
     if (kk != k) x[pkk] = mk<V>(Ep.x + Op.y, Op.x - Ep.y);
   }
@@ -286,7 +295,7 @@ __device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, cons
       j = idx / lpb;
       l = idx - j * lpb;
     }
-    sm[l * N + j] = (l < t.nvalid) ? (T)g[t.base + l * t.lstep + (int64_t)j * t.jstep] : (T)0;
+    sm[l * N + j] = (l < t.nvalid) ? cvt<T, S>(g[t.base + l * t.lstep + (int64_t)j * t.jstep]) : from_f<T>(0.0f);
   }
 }
 
@@ -320,8 +329,8 @@ __device__ __forceinline__ int tile_index(const TileGeo& t, int N, int lpb, int 
 // B_{alpha} along the line (3-point stencil of 𝓗_alpha, zero beyond the interior).
 template <typename T>
 __device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
-  const T lft = j > 0 ? row[j - 1] : (T)0;
-  const T rgt = j + 1 < N ? row[j + 1] : (T)0;
+  const T lft = j > 0 ? row[j - 1] : from_f<T>(0.0f);
+  const T rgt = j + 1 < N ? row[j + 1] : from_f<T>(0.0f);
   return tfma(bd, row[j], bo * (lft + rgt));
 }
 
@@ -342,7 +351,8 @@ __device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* c
       const int l = b / K, jj = b - l * K;
       const int t0 = 2 * jj, t1 = 2 * jj + 1;
       const T* row = xs + l * N;
-      cb[l * K + jj] = mk<V>(t0 < N ? row[t0] : 0.0, t1 < N ? row[t1] : 0.0);
+      const T z0 = from_f<T>(0.0f);
+      cb[l * K + jj] = mk<V>(t0 < N ? row[t0] : z0, t1 < N ? row[t1] : z0);
     }
     __syncthreads();
     fft_dif(cb, K, lpb, K, P.dim.twK);
@@ -357,6 +367,7 @@ __device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* c
   } else {
     const T* __restrict__ s = P.dim.s;
     T acc[8];
+    const T z0 = from_f<T>(0.0f);
     // dense: (T x)_a = sum_b s_|a-b| x_b; each thread accumulates its outputs in registers first
     // so ts may alias xs.
     const int tot = lpb * N;
@@ -364,12 +375,12 @@ __device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* c
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int idx = base + r * TH + tid;
-        acc[r] = (T)0;
+        acc[r] = z0;
         if (idx < tot) {
           const int l = idx / N, a = idx - l * N;
           const T* row = xs + l * N;
-          T sacc = 0;
-          for (int bb = 0; bb < N; ++bb) sacc = tfma(__ldg(&s[abs(a - bb)]), row[bb], sacc);
+          T sacc = z0;
+          for (int bb = 0; bb < N; ++bb) sacc = tfma(s[abs(a - bb)], row[bb], sacc);
           acc[r] = sacc;
         }
       }
@@ -404,10 +415,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
         const int j = 2 * m + r;
-        T v = 0;
+        T v = from_f<T>(0.0f);
         if (j > 0) {
           const T xj = row[j - 1], xk = row[K - j - 1];
-          v = tfma(__ldg(&sn[j]), xj + xk, (T)0.5 * (xj - xk));
+          v = tfma(sn[j], xj + xk, from_f<T>(0.5f) * (xj - xk));
         }
         w[r] = v;
       }
@@ -417,7 +428,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     fft_dif(cb, K2, lpb, K2, tw2);
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
-    const T sc = (T)sqrt(2.0 / (double)K);
+    const T sc = from_d<T>(sqrt(2.0 / (double)K));
     const int np = K2 / 2 + 1;
     for (int b = tid; b < lpb * np; b += TH) {
       const int l = b / np, k = b - l * np;
@@ -426,9 +437,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
       const V A = z[dif_pos(k, K2)], B = z[dif_pos(kk, K2)];
       const V E2 = mk<V>(A.x + B.x, A.y - B.y);
       const V O2 = mk<V>(A.y + B.y, B.x - A.x);
-      const V Pw = cmul(__ldg(&tw2[K2 + k]), O2);
+      const V Pw = cmul(tw2[K2 + k], O2);
       T* row = xs + l * N;
-      const T h = (T)0.5 * sc;
+      const T h = from_f<T>(0.5f) * sc;
       row[2 * k] = h * (E2.x + Pw.x);                       // sc Re W_k
       if (k > 0) row[2 * k - 1] = -h * (E2.y + Pw.y);       // y_{2k} = -Im W_k
       if (kk != k) {
@@ -450,9 +461,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     const int l = tid / spl, sg = tid - l * spl;
     const bool act = l < lpb;
     T* row = xs + (act ? l : 0) * N;
-    T acc = 0;
+    T acc = from_f<T>(0.0f);
     if (act) {
-      if (sg == 0) line_half0[l] = (T)0.5 * row[0];
+      if (sg == 0) line_half0[l] = from_f<T>(0.5f) * row[0];
       for (int k = sg * seg; k < (sg + 1) * seg; ++k) {
         acc += row[2 * k];
         row[2 * k] = acc;
@@ -462,7 +473,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     T v = acc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const T t = __shfl_up_sync(0xffffffffu, v, o);
+      const T t = shfl_up(v, o);
       if (lane >= o) v += t;
     }
     if (lane == 31) warp_tot[wp] = v;
@@ -471,7 +482,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     scan_incl[tid] = v;
     __syncthreads();
     if (act) {
-      const T base = l * spl > 0 ? scan_incl[l * spl - 1] : (T)0;
+      const T base = l * spl > 0 ? scan_incl[l * spl - 1] : from_f<T>(0.0f);
       const T off = v - acc - base - line_half0[l];
       for (int k = sg * seg; k < (sg + 1) * seg; ++k) row[2 * k] += off;
     }
@@ -479,21 +490,22 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
   } else {
     const int K = P.dim.K;
     const T* __restrict__ st = P.dim.sintab;
-    const T sc = (T)sqrt(2.0 / (double)K);
+    const T sc = from_d<T>(sqrt(2.0 / (double)K));
+    const T z0 = from_f<T>(0.0f);
     T acc[8];
     const int tot = lpb * N;
     for (int base = 0; base < tot; base += 8 * TH) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int idx = base + r * TH + tid;
-        acc[r] = (T)0;
+        acc[r] = z0;
         if (idx < tot) {
           const int l = idx / N, k = idx - l * N + 1;
           const T* row = xs + l * N;
-          T sacc = 0;
+          T sacc = z0;
           int ph = k;  // (j * k) mod 2K for j = 1
           for (int j = 1; j <= N; ++j) {
-            sacc = tfma(__ldg(&st[ph]), row[j - 1], sacc);
+            sacc = tfma(st[ph], row[j - 1], sacc);
             ph += k;
             if (ph >= 2 * K) ph -= 2 * K;
           }
@@ -548,6 +560,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
     else tile_load(tg, N, lpb, P.in_c, rc);
     __syncthreads();
     const T bd = P.dim.bdiag, bo = P.dim.boff;
+    const T seta = from_d<T>(P.seta);
     if (P.first) {
       // ra = x, rc = e  ->  ra = e∘x (kept), rc = x (Toeplitz input), c_out = B x
       for (int idx = tid; idx < NT; idx += TH) {
@@ -575,7 +588,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
     for (int idx = tid; idx < NT; idx += TH) {
       const int l = idx / N, j = idx - l * N;
       const T ba = stencil_B(ra + l * N, j, N, bd, bo);
-      rc[idx] = tfma((T)P.seta, rc[idx], ba);
+      rc[idx] = tfma(seta, rc[idx], ba);
     }
     __syncthreads();
     if (!P.last) {
@@ -623,6 +636,8 @@ cudaError_t init_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -636,8 +651,10 @@ cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
 
 template size_t pass_smem_bytes<double>(const PassT<double>&);
 template size_t pass_smem_bytes<float>(const PassT<float>&);
+template size_t pass_smem_bytes<df64>(const PassT<df64>&);
 template cudaError_t launch_pass<double>(const PassT<double>&, cudaStream_t);
 template cudaError_t launch_pass<float>(const PassT<float>&, cudaStream_t);
+template cudaError_t launch_pass<df64>(const PassT<df64>&, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // setup: circulant spectrum lambda_k = DFT_{2K}(c)_k, k = 0..K (c real symmetric)
@@ -902,7 +919,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, i
   const int jj = g->j;
   const S* __restrict__ w = V + (int64_t)(jj + 1) * n;
   for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
-    S acc[DOT_CHUNK] = {0, 0, 0, 0};
+    S acc[DOT_CHUNK];
+#pragma unroll
+    for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
       const S wv = w[idx];
@@ -913,7 +932,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, i
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
-        const double s = block_sum((double)acc[r], sh);
+        const double s = block_sum(to_d(acc[r]), sh);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
       }
     }
@@ -927,6 +946,7 @@ cudaError_t launch_dots(const S* V, int64_t n, const GmresDev* g, double* partia
 }
 template cudaError_t launch_dots<double>(const double*, int64_t, const GmresDev*, double*, int, cudaStream_t);
 template cudaError_t launch_dots<float>(const float*, int64_t, const GmresDev*, double*, int, cudaStream_t);
+template cudaError_t launch_dots<df64>(const df64*, int64_t, const GmresDev*, double*, int, cudaStream_t);
 
 // h[i] = sum_b partial[i * ld + b], i = 0..j (one warp per i)
 __global__ void k_reduce_dots(const double* __restrict__ partial, int ld, const GmresDev* __restrict__ g, double* h) {
@@ -957,9 +977,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, co
   if (g->done) return;
   const int jj = g->j;
   S* w = V + (int64_t)(jj + 1) * n;
-  for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = (S)h[i];
+  for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = from_d<S>(h[i]);
   __syncthreads();
-  S nacc = 0;
+  S nacc = from_f<S>(0.0f);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
     S wv = w[idx];
     for (int i = 0; i <= jj; ++i) wv = tfma(-hs[i], V[(int64_t)i * n + idx], wv);
@@ -967,14 +987,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, co
     nacc = tfma(wv, wv, nacc);
   }
   if (want_norm) {
-    const double s = block_sum((double)nacc, sh);
+    const double s = block_sum(to_d(nacc), sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
     return;
   }
   __syncthreads();
   // second Gram-Schmidt pass: dots of the updated w (this block's elements) with V_i
   for (int i0 = 0; i0 <= jj; i0 += DOT_CHUNK) {
-    S acc[DOT_CHUNK] = {0, 0, 0, 0};
+    S acc[DOT_CHUNK];
+#pragma unroll
+    for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
       const S wv = w[idx];
@@ -985,7 +1007,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, co
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
-        const double s = block_sum((double)acc[r], sh);
+        const double s = block_sum(to_d(acc[r]), sh);
         if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
       }
     }
@@ -1002,6 +1024,8 @@ template cudaError_t launch_update_dots<double>(double*, int64_t, const GmresDev
                                                 cudaStream_t);
 template cudaError_t launch_update_dots<float>(float*, int64_t, const GmresDev*, const double*, double*, int, int,
                                                cudaStream_t);
+template cudaError_t launch_update_dots<df64>(df64*, int64_t, const GmresDev*, const double*, double*, int, int,
+                                              cudaStream_t);
 
 // Column j of the Hessenberg matrix: h1 + h2 (CGS2), ||w||; previous rotations, new rotation,
 // residual estimate |g_{j+1}|, stopping test ||r_j|| <= tol ||r_0|| (§4), cap and breakdown.
@@ -1069,7 +1093,7 @@ template <typename S>
 __global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
   if (g->done) return;
   const int j = g->j;
-  const S inv = (S)(1.0 / g->hnorm);
+  const S inv = from_d<S>(1.0 / g->hnorm);
   S* v = V + (int64_t)j * n;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     v[idx] *= inv;
@@ -1082,21 +1106,26 @@ cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t s
 }
 template cudaError_t launch_scale_next<double>(double*, int64_t, const GmresDev*, cudaStream_t);
 template cudaError_t launch_scale_next<float>(float*, int64_t, const GmresDev*, cudaStream_t);
+template cudaError_t launch_scale_next<df64>(df64*, int64_t, const GmresDev*, cudaStream_t);
 
-__global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const double* __restrict__ w, int64_t n, double* partial) {
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const S* __restrict__ w, int64_t n, double* partial) {
   __shared__ double sh[32];
-  double acc = 0.0;
+  S acc = from_f<S>(0.0f);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
-    acc = fma(w[idx], w[idx], acc);
-  const double s = block_sum(acc, sh);
+    acc = tfma(w[idx], w[idx], acc);
+  const double s = block_sum(to_d(acc), sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-cudaError_t launch_norm_partial(const double* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st) {
+template <typename S>
+cudaError_t launch_norm_partial(const S* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st) {
   (void)g;
-  k_norm_partial<<<RED_BLOCKS, RED_THREADS, 0, st>>>(w, n, partial);
+  k_norm_partial<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(w, n, partial);
   return cudaGetLastError();
 }
+template cudaError_t launch_norm_partial<double>(const double*, int64_t, const GmresDev*, double*, cudaStream_t);
+template cudaError_t launch_norm_partial<df64>(const df64*, int64_t, const GmresDev*, double*, cudaStream_t);
 
 // beta = ||r_0||, g_0 = beta, j = 0; done if beta == 0.
 __global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, double* gv) {
@@ -1116,18 +1145,22 @@ __global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, dou
   }
 }
 
-__global__ void k_scale_first(double* V, int64_t n, const GmresDev* __restrict__ g) {
+template <typename S>
+__global__ void k_scale_first(S* V, int64_t n, const GmresDev* __restrict__ g) {
   if (g->done) return;
-  const double inv = 1.0 / g->beta;
+  const S inv = from_d<S>(1.0 / g->beta);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     V[idx] *= inv;
 }
 
-cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, double* V, int64_t n, cudaStream_t st) {
+template <typename S>
+cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, S* V, int64_t n, cudaStream_t st) {
   k_init_beta<<<1, 256, 0, st>>>(g, partial, gv);
-  k_scale_first<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+  k_scale_first<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
   return cudaGetLastError();
 }
+template cudaError_t launch_init_beta<double>(GmresDev*, const double*, double*, double*, int64_t, cudaStream_t);
+template cudaError_t launch_init_beta<df64>(GmresDev*, const double*, double*, df64*, int64_t, cudaStream_t);
 
 // y = R^{-1} g (upper triangular k x k in H after the rotations), then u = x0 + V_k y.
 __global__ void k_backsolve(GmresDev* g, const double* __restrict__ H, const double* __restrict__ gv, int ldH,
@@ -1142,15 +1175,16 @@ __global__ void k_backsolve(GmresDev* g, const double* __restrict__ H, const dou
   if (iters_log) iters_log[g->m] = k;
 }
 
+template <typename S>
 __global__ void k_update_solution(const GmresDev* __restrict__ g, const double* __restrict__ y,
-                                  const double* __restrict__ V, int64_t n, double* u, int x0_prev) {
-  __shared__ double ys[MAX_ITER_CAP];
+                                  const S* __restrict__ V, int64_t n, S* u, int x0_prev) {
+  __shared__ S ys[MAX_ITER_CAP];
   const int k = g->k;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = y[i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = from_d<S>(y[i]);
   __syncthreads();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    double v = x0_prev ? u[idx] : 0.0;
-    for (int i = 0; i < k; ++i) v = fma(ys[i], V[(int64_t)i * n + idx], v);
+    S v = x0_prev ? u[idx] : from_f<S>(0.0f);
+    for (int i = 0; i < k; ++i) v = tfma(ys[i], V[(int64_t)i * n + idx], v);
     u[idx] = v;
   }
 }
@@ -1159,12 +1193,42 @@ __global__ void k_advance(GmresDev* g) {
   if (threadIdx.x == 0) g->m += 1;
 }
 
-cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y,
-                                    const double* V, int64_t n, double* u, int x0_prev, int* iters_log,
-                                    cudaStream_t st) {
+template <typename S>
+cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y, const S* V,
+                                    int64_t n, S* u, int x0_prev, int* iters_log, cudaStream_t st) {
   k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, iters_log);
-  k_update_solution<<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
+  k_update_solution<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
   k_advance<<<1, 32, 0, st>>>(g);
+  return cudaGetLastError();
+}
+template cudaError_t launch_backsolve_update<double>(GmresDev*, const double*, const double*, int, double*,
+                                                     const double*, int64_t, double*, int, int*, cudaStream_t);
+template cudaError_t launch_backsolve_update<df64>(GmresDev*, const double*, const double*, int, double*, const df64*,
+                                                   int64_t, df64*, int, int*, cudaStream_t);
+
+// double <-> double-float conversion of whole vectors (setup, per-step fields, API boundary)
+__global__ void k_d_to_df(const double* __restrict__ a, df64* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = from_d<df64>(a[i]);
+}
+__global__ void k_df_to_d(const df64* __restrict__ a, double* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = to_d(a[i]);
+}
+
+cudaError_t launch_d_to_df(const double* a, df64* b, int64_t n, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_d_to_df<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_d(const df64* a, double* b, int64_t n, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_df_to_d<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ TAU_X0_ZERO = 0
 TAU_X0_PREV = 1
 TAU_FP64 = 0
 TAU_MIXED = 1
+TAU_DF64 = 2
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
