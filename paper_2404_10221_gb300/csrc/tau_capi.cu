@@ -214,8 +214,10 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.twK = p->twK32[ax];
     D.twK2 = p->twK2_32[ax];
   }
-  const size_t per_line = 2 * sizeof(T) * (size_t)P.len + (D.route == ROUTE_FFT ? 2 * sizeof(T) * (size_t)D.K : 0);
-  int64_t lpb = (int64_t)(32768 / per_line);
+  // shared memory per line: the line (N reals) plus the transform line (2K reals, FFT route) or a
+  // second copy (N, dense route).  24 KB of lines per CTA lets 8 CTAs of 128 threads share an SM.
+  const size_t per_line = sizeof(T) * ((size_t)P.len + (D.route == ROUTE_FFT ? 2 * (size_t)D.K : (size_t)P.len));
+  int64_t lpb = (int64_t)(24576 / per_line);
   if (lpb < 1) lpb = 1;
   if (lpb > 16) lpb = 16;
   const int64_t cap = ax == 0 ? P.nlines : inner;

@@ -282,9 +282,9 @@ __device__ __forceinline__ TileGeo tile_geo(const PT& P, int64_t tile) {
   return t;
 }
 
-// sm[l*N + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
+// sm[l*ss + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
 template <typename S, typename T>
-__device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const S* __restrict__ g, T* sm) {
+__device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const S* __restrict__ g, T* sm, int ss) {
   const int tot = lpb * N;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
@@ -295,12 +295,12 @@ __device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, cons
       j = idx / lpb;
       l = idx - j * lpb;
     }
-    sm[l * N + j] = (l < t.nvalid) ? cvt<T, S>(g[t.base + l * t.lstep + (int64_t)j * t.jstep]) : from_f<T>(0.0f);
+    sm[l * ss + j] = (l < t.nvalid) ? cvt<T, S>(g[t.base + l * t.lstep + (int64_t)j * t.jstep]) : from_f<T>(0.0f);
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const T* sm, T* g) {
+__device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const T* sm, int ss, T* g) {
   const int tot = lpb * N;
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
@@ -311,7 +311,7 @@ __device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, con
       j = idx / lpb;
       l = idx - j * lpb;
     }
-    if (l < t.nvalid) g[t.base + l * t.lstep + (int64_t)j * t.jstep] = sm[l * N + j];
+    if (l < t.nvalid) g[t.base + l * t.lstep + (int64_t)j * t.jstep] = sm[l * ss + j];
   }
 }
 
@@ -337,39 +337,33 @@ __device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
 // ---------------------------------------------------------------------------
 // per-line transforms on shared memory
 // ---------------------------------------------------------------------------
-// Toeplitz product T x for every line: x in xs[l*N + j], result written to ts[l*N + j].
-// ts may alias xs.  FFT route uses cb (lpb lines of K complex).
+// Toeplitz product T x in place for every line: x_j at xs[l*xst + j].  FFT route: xst = 2K and
+// the line's 2K reals are the packed complex sequence z_j = (y_2j, y_2j+1) of the zero-padded
+// y (y_t = x_t for t < N, 0 otherwise), so packing is only the zero fill of [N, 2K) and the
+// product comes back in [0, N).  Dense route: xst = N.
 template <typename T>
-__device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* cb) {
+__device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
   const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_FFT) {
     const int K = P.dim.K;
-    // pack y_t = x_t (t < N), 0 otherwise, as z_j = (y_2j, y_2j+1)
-    for (int b = tid; b < lpb * K; b += TH) {
-      const int l = b / K, jj = b - l * K;
-      const int t0 = 2 * jj, t1 = 2 * jj + 1;
-      const T* row = xs + l * N;
-      const T z0 = from_f<T>(0.0f);
-      cb[l * K + jj] = mk<V>(t0 < N ? row[t0] : z0, t1 < N ? row[t1] : z0);
+    const int pad = 2 * K - N;
+    for (int b = tid; b < lpb * pad; b += TH) {
+      const int l = b / pad, t = N + (b - l * pad);
+      xs[l * xst + t] = from_f<T>(0.0f);
     }
     __syncthreads();
+    V* cb = reinterpret_cast<V*>(xs);
     fft_dif(cb, K, lpb, K, P.dim.twK);
     toep_spectral(cb, K, lpb, K, P.dim.spec, P.dim.twK);
     fft_dit_inv(cb, K, lpb, K, P.dim.twK);
-    for (int b = tid; b < lpb * N; b += TH) {
-      const int l = b / N, t = b - l * N;
-      const V z = cb[l * K + (t >> 1)];
-      ts[l * N + t] = (t & 1) ? z.y : z.x;
-    }
-    __syncthreads();
   } else {
     const T* __restrict__ s = P.dim.s;
     T acc[8];
     const T z0 = from_f<T>(0.0f);
     // dense: (T x)_a = sum_b s_|a-b| x_b; each thread accumulates its outputs in registers first
-    // so ts may alias xs.
+    // and writes them after a barrier (in place).
     const int tot = lpb * N;
     for (int base = 0; base < tot; base += 8 * TH) {
 #pragma unroll
@@ -378,7 +372,7 @@ __device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* c
         acc[r] = z0;
         if (idx < tot) {
           const int l = idx / N, a = idx - l * N;
-          const T* row = xs + l * N;
+          const T* row = xs + l * xst;
           T sacc = z0;
           for (int bb = 0; bb < N; ++bb) sacc = tfma(s[abs(a - bb)], row[bb], sacc);
           acc[r] = sacc;
@@ -388,16 +382,21 @@ __device__ void toeplitz_lines(const PassT<T>& P, const T* xs, T* ts, vec2<T>* c
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int idx = base + r * TH + tid;
-        if (idx < tot) ts[idx] = acc[r];
+        if (idx < tot) {
+          const int l = idx / N;
+          xs[l * xst + idx - l * N] = acc[r];
+        }
       }
       __syncthreads();
     }
   }
 }
 
-// Orthonormal DST-I of every line in place: xs[l*N + j] holds x_{j+1}; result y_{k} at xs[l*N + k-1].
+// Orthonormal DST-I of every line in place: xs[l*xst + j] holds x_{j+1}; result y_{k} at
+// xs[l*xst + k-1].  FFT route: xst = 2K; the half-length complex FFT works in the line's upper
+// half [K, 2K), which holds no data (N < K).  Dense route: xst = N.
 template <typename T>
-__device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
+__device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
   using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
   const int TH = blockDim.x, tid = threadIdx.x;
@@ -408,9 +407,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     const int K = P.dim.K, K2 = K >> 1;
     const T* __restrict__ sn = P.dim.sintab;
     const V* __restrict__ tw2 = P.dim.twK2;
+    V* cb = reinterpret_cast<V*>(xs + K);   // line l at cb + l*K (complex)
     for (int b = tid; b < lpb * K2; b += TH) {
       const int l = b / K2, m = b - l * K2;
-      const T* row = xs + l * N;
+      const T* row = xs + l * xst;
       T w[2];
 #pragma unroll
       for (int r = 0; r < 2; ++r) {
@@ -422,10 +422,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
         }
         w[r] = v;
       }
-      cb[l * K2 + m] = mk<V>(w[0], w[1]);
+      cb[l * K + m] = mk<V>(w[0], w[1]);
     }
     __syncthreads();
-    fft_dif(cb, K2, lpb, K2, tw2);
+    fft_dif(cb, K, lpb, K2, tw2);
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
     const T sc = from_d<T>(sqrt(2.0 / (double)K));
@@ -433,12 +433,12 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     for (int b = tid; b < lpb * np; b += TH) {
       const int l = b / np, k = b - l * np;
       const int kk = (K2 - k) & (K2 - 1);
-      const V* z = cb + l * K2;
+      const V* z = cb + l * K;
       const V A = z[dif_pos(k, K2)], B = z[dif_pos(kk, K2)];
       const V E2 = mk<V>(A.x + B.x, A.y - B.y);
       const V O2 = mk<V>(A.y + B.y, B.x - A.x);
       const V Pw = cmul(tw2[K2 + k], O2);
-      T* row = xs + l * N;
+      T* row = xs + l * xst;
       const T h = from_f<T>(0.5f) * sc;
       row[2 * k] = h * (E2.x + Pw.x);                       // sc Re W_k
       if (k > 0) row[2 * k - 1] = -h * (E2.y + Pw.y);       // y_{2k} = -Im W_k
@@ -452,7 +452,6 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     // spl threads per line scan contiguous segments; segment offsets by a block-wide shuffle scan.
     __shared__ T scan_incl[PASS_THREADS];
     __shared__ T warp_tot[PASS_THREADS / 32];
-    __shared__ T line_half0[PASS_THREADS];
     int spl = TH / lpb;
     if (spl < 1) spl = 1;
     spl = 1 << (31 - __clz(spl));
@@ -460,10 +459,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     const int seg = K2 / spl;
     const int l = tid / spl, sg = tid - l * spl;
     const bool act = l < lpb;
-    T* row = xs + (act ? l : 0) * N;
+    T* row = xs + (act ? l : 0) * xst;
     T acc = from_f<T>(0.0f);
     if (act) {
-      if (sg == 0) line_half0[l] = from_f<T>(0.5f) * row[0];
       for (int k = sg * seg; k < (sg + 1) * seg; ++k) {
         acc += row[2 * k];
         row[2 * k] = acc;
@@ -478,12 +476,15 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
     }
     if (lane == 31) warp_tot[wp] = v;
     __syncthreads();
+    // row[0] (sc Re W_0) is left unchanged by the segment scans and read before the barrier that
+    // precedes the offset loop, which is the only writer of it.
+    const T half0 = from_f<T>(0.5f) * row[0];
     for (int w2 = 0; w2 < wp; ++w2) v += warp_tot[w2];
     scan_incl[tid] = v;
     __syncthreads();
     if (act) {
       const T base = l * spl > 0 ? scan_incl[l * spl - 1] : from_f<T>(0.0f);
-      const T off = v - acc - base - line_half0[l];
+      const T off = v - acc - base - half0;
       for (int k = sg * seg; k < (sg + 1) * seg; ++k) row[2 * k] += off;
     }
     __syncthreads();
@@ -501,7 +502,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
         acc[r] = z0;
         if (idx < tot) {
           const int l = idx / N, k = idx - l * N + 1;
-          const T* row = xs + l * N;
+          const T* row = xs + l * xst;
           T sacc = z0;
           int ph = k;  // (j * k) mod 2K for j = 1
           for (int j = 1; j <= N; ++j) {
@@ -516,7 +517,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int idx = base + r * TH + tid;
-        if (idx < tot) xs[idx] = acc[r];
+        if (idx < tot) {
+          const int l = idx / N;
+          xs[l * xst + idx - l * N] = acc[r];
+        }
       }
       __syncthreads();
     }
@@ -526,16 +530,26 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, vec2<T>* cb) {
 // ---------------------------------------------------------------------------
 // the line-pass kernel
 // ---------------------------------------------------------------------------
-// Shared memory: ra, rc (lpb*N doubles each) then cb (lpb*K complex, FFT route, 16-byte aligned).
+// Shared memory: ra (lpb*N reals, rounded up to even) then rc (lpb lines of rs reals; rs = 2K on
+// the FFT route, whose transforms run in place in the padded line, rs = N on the dense route).
 template <typename T>
-__global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
-  using V = vec2<T>;
+__device__ __forceinline__ int rc_stride(const PassT<T>& P) {
+  return P.dim.route == ROUTE_FFT ? 2 * P.dim.K : P.len;
+}
+
+// 8 resident CTAs of 128 threads per SM (64 registers a thread) for FP64 and FP32; the
+// double-float type keeps 6 (85 registers) to avoid spills.
+template <typename T> struct PassOcc { static constexpr int ctas = 7; };
+template <> struct PassOcc<df64> { static constexpr int ctas = 6; };
+
+template <typename T>
+__global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const PassT<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = P.len, lpb = P.lpb;
+  const int RS = rc_stride(P);
   T* ra = reinterpret_cast<T*>(smraw);
-  T* rc = ra + lpb * N;
-  // ra and rc together hold an even number of elements, so cb starts aligned to sizeof(V)
-  V* cb = reinterpret_cast<V*>(rc + lpb * N);
+  // an even count of reals before rc keeps every line of rc (and its upper half) aligned for vec2<T>
+  T* rc = ra + ((lpb * N + 1) & ~1);
   if (P.g && P.g->done) return;
   if (P.skip && *P.skip) return;
   const TileGeo tg = tile_geo(P, blockIdx.x);
@@ -547,86 +561,90 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(const PassT<T> P) {
   if (P.out_sel) out_a = P.out_base + (int64_t)(P.g->j + P.out_sel - 1) * P.vstride;
 
   if (P.toep_only) {
-    tile_load(tg, N, lpb, in_a, ra);
+    tile_load(tg, N, lpb, in_a, rc, RS);
     __syncthreads();
-    toeplitz_lines(P, ra, ra, cb);
-    tile_store(tg, N, lpb, ra, out_a);
+    toeplitz_lines(P, rc, RS);
+    tile_store(tg, N, lpb, rc, RS, out_a);
     return;
   }
 
   if (P.mv) {
-    tile_load(tg, N, lpb, in_a, ra);
-    if (P.first) tile_load(tg, N, lpb, P.e, rc);
-    else tile_load(tg, N, lpb, P.in_c, rc);
+    tile_load(tg, N, lpb, in_a, ra, N);
+    if (P.first) tile_load(tg, N, lpb, P.e, rc, RS);
+    else tile_load(tg, N, lpb, P.in_c, rc, RS);
     __syncthreads();
     const T bd = P.dim.bdiag, bo = P.dim.boff;
     const T seta = from_d<T>(P.seta);
     if (P.first) {
       // ra = x, rc = e  ->  ra = e∘x (kept), rc = x (Toeplitz input), c_out = B x
       for (int idx = tid; idx < NT; idx += TH) {
+        const int l = idx / N, j = idx - l * N;
         const T x = ra[idx];
-        const T e = rc[idx];
-        rc[idx] = x;
+        const T e = rc[l * RS + j];
+        rc[l * RS + j] = x;
         ra[idx] = e * x;
       }
       __syncthreads();
     }
-    // Toeplitz of channel c into cb-backed scratch: result t_j kept in registers below.
-    // First compute c_out = B c (needs c before it is overwritten), stream it to global.
+    // c_out = B c needs c before the Toeplitz product overwrites it; stream it to global.
     if (!P.last) {
       for (int idx = tid; idx < NT; idx += TH) {
         int l, j;
         tile_index(tg, N, lpb, idx, l, j);
-        const T v = stencil_B(rc + l * N, j, N, bd, bo);
+        const T v = stencil_B(rc + l * RS, j, N, bd, bo);
         if (l < tg.nvalid) P.out_c[tg.base + l * tg.lstep + (int64_t)j * tg.jstep] = v;
       }
     }
-    // value = B a + seta * T c; computed in register batches, then written into rc.
     __syncthreads();
-    // T c in place (rc <- T c); B a needs ra intact.
-    toeplitz_lines(P, rc, rc, cb);
+    // rc <- T c in place, then rc <- B a + seta * T c (B a needs ra intact).
+    toeplitz_lines(P, rc, RS);
     for (int idx = tid; idx < NT; idx += TH) {
       const int l = idx / N, j = idx - l * N;
       const T ba = stencil_B(ra + l * N, j, N, bd, bo);
-      rc[idx] = tfma(seta, rc[idx], ba);
+      rc[l * RS + j] = tfma(seta, rc[l * RS + j], ba);
     }
     __syncthreads();
     if (!P.last) {
-      tile_store(tg, N, lpb, rc, out_a);
+      tile_store(tg, N, lpb, rc, RS, out_a);
       return;
     }
     if (P.finish == FIN_ADD_F || P.finish == FIN_RESID) {
-      tile_load(tg, N, lpb, P.src, ra);
+      tile_load(tg, N, lpb, P.src, ra, N);
       __syncthreads();
-      for (int idx = tid; idx < NT; idx += TH)
-        rc[idx] = (P.finish == FIN_ADD_F) ? rc[idx] + ra[idx] : ra[idx] - rc[idx];
+      for (int idx = tid; idx < NT; idx += TH) {
+        const int l = idx / N, j = idx - l * N;
+        T& r = rc[l * RS + j];
+        r = (P.finish == FIN_ADD_F) ? r + ra[idx] : ra[idx] - r;
+      }
       __syncthreads();
     }
     // fall through to post-processing of rc
   } else {
-    tile_load(tg, N, lpb, in_a, rc);
+    tile_load(tg, N, lpb, in_a, rc, RS);
     __syncthreads();
   }
 
   if (P.post == POST_DST || P.post == POST_DST_MU_DST) {
-    dst_lines(P, rc, cb);
+    dst_lines(P, rc, RS);
     if (P.post == POST_DST_MU_DST) {
-      tile_load(tg, N, lpb, P.invmu, ra);
+      tile_load(tg, N, lpb, P.invmu, ra, N);
       __syncthreads();
-      for (int idx = tid; idx < NT; idx += TH) rc[idx] *= ra[idx];
+      for (int idx = tid; idx < NT; idx += TH) {
+        const int l = idx / N, j = idx - l * N;
+        rc[l * RS + j] *= ra[idx];
+      }
       __syncthreads();
-      dst_lines(P, rc, cb);
+      dst_lines(P, rc, RS);
     }
   }
-  tile_store(tg, N, lpb, rc, out_a);
+  tile_store(tg, N, lpb, rc, RS, out_a);
 }
 
 template <typename T>
 size_t pass_smem_bytes(const PassT<T>& p) {
-  const size_t real = (size_t)p.lpb * p.len;
-  size_t bytes = 2 * real * sizeof(T);
-  if (p.dim.route == ROUTE_FFT) bytes += (size_t)p.lpb * p.dim.K * sizeof(vec2<T>);
-  return bytes;
+  const size_t ra = ((size_t)p.lpb * p.len + 1) & ~(size_t)1;
+  const size_t rs = p.dim.route == ROUTE_FFT ? 2 * (size_t)p.dim.K : (size_t)p.len;
+  return (ra + (size_t)p.lpb * rs) * sizeof(T);
 }
 
 __global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ twK);

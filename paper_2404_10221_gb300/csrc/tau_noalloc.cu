@@ -169,8 +169,8 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     P.inner = inner;
     P.nlines = n_tot / P.len;
     P.dim = dims[ax];
-    const size_t per_line = 16 * (size_t)P.len + (P.dim.route == ROUTE_FFT ? 16 * (size_t)P.dim.K : 0);
-    int64_t lpb = (int64_t)(32768 / per_line);
+    const size_t per_line = 8 * ((size_t)P.len + (P.dim.route == ROUTE_FFT ? 2 * (size_t)P.dim.K : (size_t)P.len));
+    int64_t lpb = (int64_t)(24576 / per_line);
     if (lpb < 1) lpb = 1;
     if (lpb > 16) lpb = 16;
     const int64_t cap = ax == 0 ? P.nlines : inner;
