@@ -91,7 +91,9 @@ typedef struct {
   double refine_tol;    /* stop refining at ||b - A x||_2 <= refine_tol ||b - A x_0||_2 (FP64); 1e-10 */
   int inner_max_iter;   /* inner FGMRES iterations per refinement sweep, 1..1000; 30 */
   int max_sweeps;       /* refinement sweeps per step; 10 */
-  double inner_tol;     /* inner FGMRES relative residual target; 1e-5 */
+  double inner_tol;     /* inner FGMRES relative residual target of the first sweep; 1e-5.  A later
+                           sweep targets the reduction still needed, 0.3 refine_tol rho_0 / rho,
+                           kept within [min(1e-6, inner_tol), inner_tol] */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
@@ -288,7 +290,7 @@ tau_status tau_server_destroy(tau_server* s);
  *   e, x: device pointers to n_tot doubles (e = e(x_J, t) at the interior nodes); y: device
  *   output of n_tot doubles (must not alias x or e).  Enqueued on `stream` (cudaStream_t or NULL).
  * Scratch (FCD weights, circulant spectra, twiddles, the two Kronecker channels) lives in one
- * static device array of about 4.8 MB that every GPU loading the library holds until process
+ * static device array of about 5.2 MB that every GPU loading the library holds until process
  * exit; it is rebuilt on each call.  Limits: n_i <= 4095 per dimension and n_tot <= 262,144;
  * larger problems return TAU_EINVAL.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before any

@@ -960,10 +960,11 @@ tau_status tau_setup(tau_problem* p) {
       std::vector<double> lam(K + 1);
       CK(cudaMemcpyAsync(lam.data(), dl, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
-      std::vector<double2> spec(K / 2 + 1);
+      std::vector<double2> spec(4 * (size_t)(K / 2 + 1));
       for (int k = 0; k <= K / 2; ++k) {
-        const double lk = lam[k], lkk = lam[K - k];
-        spec[k] = make_double2((lk + lkk) / (4.0 * K), (lk - lkk) / (4.0 * K));
+        double abcd[8];
+        toep_pack_coeffs(lam[k], lam[K - k], std::cos(M_PI * k / K), -std::sin(M_PI * k / K), K, abcd);
+        for (int r = 0; r < 4; ++r) spec[4 * (size_t)k + r] = make_double2(abcd[2 * r], abcd[2 * r + 1]);
       }
       TRY(upload(p, &p->spec[i], spec.data(), spec.size()));
       for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
@@ -1019,7 +1020,7 @@ tau_status tau_setup(tau_problem* p) {
       TRY(conv(p->sintab[i], &p->sintab_df[i], 2 * (size_t)K));
       if (p->route[i] == ROUTE_FFT) {
         df64* f = nullptr;
-        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 2 * (size_t)(K / 2 + 1)));
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(K / 2 + 1)));
         p->spec_df[i] = reinterpret_cast<df64x2*>(f);
         TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
         p->twK_df[i] = reinterpret_cast<df64x2*>(f);
@@ -1041,7 +1042,7 @@ tau_status tau_setup(tau_problem* p) {
       TRY(conv(p->sintab[i], &p->sintab32[i], 2 * (size_t)K));
       if (p->route[i] == ROUTE_FFT) {
         float* f = nullptr;
-        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 2 * (size_t)(K / 2 + 1)));
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(K / 2 + 1)));
         p->spec32[i] = reinterpret_cast<float2*>(f);
         TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
         p->twK32[i] = reinterpret_cast<float2*>(f);
@@ -1053,6 +1054,7 @@ tau_status tau_setup(tau_problem* p) {
     IRDev ir{};
     ir.tol = p->desc.refine_tol;
     ir.max_sweeps = p->desc.max_sweeps;
+    ir.inner_tol = p->desc.inner_tol;
     CK(cudaMemcpyAsync(p->ir, &ir, sizeof(ir), cudaMemcpyHostToDevice, p->st));
     GmresDev gi{};
     gi.max_iter = p->kin;

@@ -100,8 +100,8 @@ struct DimDataT {
   int route;          // Route
   T bdiag, boff;      // B_{alpha_i}: 1 - alpha/12, alpha/24
   double eta;         // kappa_i dt / (2 h_i^alpha_i)
-  const vec2<T>* spec;  // FFT route: (sigma_k, delta_k), k = 0..K/2, Toeplitz spectrum folded
-                        // for the packed real FFT, scaled by 1/K (no eta)
+  const vec2<T>* spec;  // FFT route: (a, b, c, d)_k, k = 0..K/2 (toep_pack_coeffs): the Toeplitz
+                        // spectrum folded for the packed real FFT, scaled by 1/K (no eta)
   const T* s;           // FCD weights s_0..s_{n-1}
   const T* sintab;      // sin(pi t / K), t = 0..2K-1
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
@@ -114,6 +114,31 @@ using DimData = DimDataT<double>;
 //   with w_s = exp(-2 pi i / s); then at offset S: exp(-2 pi i k / (2S)), k = 0..S.
 // Consecutive butterflies of a stage read consecutive entries.
 __host__ __device__ inline int twp_size(int S) { return 2 * S + 1; }
+
+// Coefficients (a, b, c, d) of the spectral step of the Toeplitz product for the pair (k, K-k):
+// with Z the packed half-length DFT of the zero-padded line, Z'_k = a Z_k + b conj(Z_{K-k}) and
+// Z'_{K-k} = c conj(Z_k) + d Z_{K-k}.  The map unpacks the length-2K real DFT at k,
+// Y_k = (E + W_k O)/2 with E = Z_k + conj Z_{K-k}, O = -i (Z_k - conj Z_{K-k}) and
+// W_k = (wx, wy) = exp(-i pi k / K), multiplies by lambda_k, lambda_{K-k} and repacks for the
+// unnormalised inverse (1/K); it is evaluated on the basis inputs (Z_k, Z_{K-k}) = (1, 0), (0, 1).
+// out: 8 reals (a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y).
+__host__ __device__ inline void toep_pack_coeffs(double lk, double lkk, double wx, double wy, int K, double* out) {
+  const double sg = (lk + lkk) / (4.0 * K), dl = (lk - lkk) / (4.0 * K);
+  for (int basis = 0; basis < 2; ++basis) {
+    const double ax = basis == 0 ? 1.0 : 0.0, bx = basis == 1 ? 1.0 : 0.0;   // imaginary parts 0
+    const double e2x = ax + bx, e2y = 0.0;
+    const double o2x = 0.0, o2y = bx - ax;
+    const double px = wx * o2x - wy * o2y, py = wx * o2y + wy * o2x;
+    const double epx = sg * e2x + dl * px, epy = sg * e2y + dl * py;
+    const double wcx = e2x * wx + e2y * wy, wcy = e2y * wx - e2x * wy;
+    const double opx = dl * wcx + sg * o2x, opy = dl * wcy + sg * o2y;
+    // basis 0 gives a (Z'_k) and c (Z'_{K-k}); basis 1 gives b and d
+    out[2 * basis + 0] = epx - opy;
+    out[2 * basis + 1] = epy + opx;
+    out[4 + 2 * basis + 0] = epx + opy;
+    out[4 + 2 * basis + 1] = opx - epy;
+  }
+}
 
 // One line pass over an array of shape (n_{d-1}, ..., n_0) along dimension ax.
 template <typename T>
@@ -234,6 +259,7 @@ struct IRDev {
   int skip_resid;    // 1 while the first residual of a step equals b (zero initial guess)
   double tol;        // ||b - A x|| <= tol ||b - A x_0||
   double rho0, rho, last_rel;
+  double inner_tol;  // inner FGMRES target of the first sweep (later sweeps: k_ir_control)
 };
 cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);

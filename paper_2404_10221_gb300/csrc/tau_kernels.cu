@@ -76,27 +76,86 @@ __device__ __forceinline__ void dif4(V& a0, V& a1, V& a2, V& a3, int i, int q, c
   }
 }
 
-// Inverse radix-4 decimation-in-time butterfly on registers (conjugate twiddles, then 4-point).
+// The same butterfly when a2 = a3 = 0 (upper half of a zero-padded input, first stage only).
 template <typename V>
-__device__ __forceinline__ void dit4_inv(V& y0, V& y1, V& y2, V& y3, int i, int q, const V* __restrict__ tws) {
-  if (i != 0) {
-    y1 = cmulc(y1, ldt(&tws[i]));
-    y2 = cmulc(y2, ldt(&tws[q + i]));
-    y3 = cmulc(y3, ldt(&tws[2 * q + i]));
+__device__ __forceinline__ void dif4_lo(V& a0, V& a1, V& a2, V& a3, int i, int q, const V* __restrict__ tws) {
+  const V b3 = mul_mi(a1);
+  const V s0 = cadd(a0, a1), s1 = cadd(a0, b3), s2 = csub(a0, a1), s3 = csub(a0, b3);
+  a0 = s0;
+  if (i == 0) {
+    a1 = s1;
+    a2 = s2;
+    a3 = s3;
+  } else {
+    a1 = cmul(s1, ldt(&tws[i]));
+    a2 = cmul(s2, ldt(&tws[q + i]));
+    a3 = cmul(s3, ldt(&tws[2 * q + i]));
   }
-  const V c0 = cadd(y0, y2), c1 = csub(y0, y2), c2 = cadd(y1, y3), c3 = mul_pi(csub(y1, y3));
-  y0 = cadd(c0, c2);
-  y1 = cadd(c1, c3);
-  y2 = csub(c0, c2);
-  y3 = csub(c1, c3);
+}
+
+// a + w b and a - w b in six FMAs: the difference is formed as 2a - (a + w b).
+template <typename V>
+__device__ __forceinline__ void bfly2w(V& a, V& b, const V w) {
+  using T = decltype(V::x);
+  const T two = from_f<T>(2.0f);
+  const T px = tfma(-w.y, b.y, tfma(w.x, b.x, a.x));
+  const T py = tfma(w.y, b.x, tfma(w.x, b.y, a.y));
+  b = mk<V>(tfma(two, a.x, -px), tfma(two, a.y, -py));
+  a = mk<V>(px, py);
+}
+// a + w b only (four FMAs)
+template <typename V>
+__device__ __forceinline__ V bfly2w_sum(const V a, const V b, const V w) {
+  return mk<V>(tfma(-w.y, b.y, tfma(w.x, b.x, a.x)), tfma(w.y, b.x, tfma(w.x, b.y, a.y)));
+}
+
+// Radix-4 decimation-in-time butterfly on registers, split as radix-2 x 2 so every twiddle
+// multiply folds into the butterfly's additions (24 FMAs instead of 28 operations):
+//   c = y0 +- w2 y2,  e = y1 +- w2 y3,  out0/2 = c0 +- w1 e0,  out1/3 = c1 +- (-+i w1) e1
+// with w1 = w^i, w2 = w^2i (w = exp(-+2 pi i / size); INV conjugates).  Outputs land at offsets
+// 0, q, 2q, 3q in y0, y1, y2, y3.  HALF computes out0 and out1 only.
+template <bool INV, bool HALF, typename V>
+__device__ __forceinline__ void dit4(V& y0, V& y1, V& y2, V& y3, int i, int q, const V* __restrict__ tws) {
+  if (i == 0) {
+    const V c0 = cadd(y0, y2), c1 = csub(y0, y2), e0 = cadd(y1, y3);
+    const V e1 = INV ? mul_pi(csub(y1, y3)) : mul_mi(csub(y1, y3));
+    y0 = cadd(c0, e0);
+    y1 = cadd(c1, e1);
+    if (!HALF) {
+      y2 = csub(c0, e0);
+      y3 = csub(c1, e1);
+    }
+    return;
+  }
+  V w1 = ldt(&tws[i]), w2 = ldt(&tws[q + i]);
+  if (INV) {
+    w1.y = -w1.y;
+    w2.y = -w2.y;
+  }
+  // -i w1 (forward) or +i conj(w1) (inverse)
+  const V wj = INV ? mk<V>(-w1.y, w1.x) : mk<V>(w1.y, -w1.x);
+  bfly2w(y0, y2, w2);   // y0 = c0, y2 = c1
+  bfly2w(y1, y3, w2);   // y1 = e0, y3 = e1
+  if (HALF) {
+    const V o0 = bfly2w_sum(y0, y1, w1);
+    y1 = bfly2w_sum(y2, y3, wj);
+    y0 = o0;
+    return;
+  }
+  bfly2w(y0, y1, w1);   // y0 = out0, y1 = out2
+  bfly2w(y2, y3, wj);   // y2 = out1, y3 = out3
+  const V o2 = y1;
+  y1 = y2;
+  y2 = o2;
 }
 
 // Forward complex DFT of length K (natural order in, digit-reversed out) on nl lines stored at
 // cb + l*cs, twiddles from the stage-packed table twp (twp_size(K) entries).  Each thread loads two
 // independent butterflies before computing either, so their shared-memory latencies overlap.
+// zero_hi: entries [K/2, K) are zero and not read (the first stage skips them).
 // Caller synchronises before; this synchronises after.
 template <typename V>
-__device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp) {
+__device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool zero_hi = false) {
   const int T = blockDim.x, tid = threadIdx.x;
   int size = K;
   for (; size >= 4; size >>= 2) {
@@ -119,6 +178,27 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp)
         g = loc / q;
         i1 = loc - g * q;
         y = cb + l * cs + g * size + i1;
+      }
+      if (zero_hi && size == K) {
+        V a0 = x[0], a1 = x[q], a2, a3;
+        V c0, c1, c2, c3;
+        if (two) {
+          c0 = y[0];
+          c1 = y[q];
+        }
+        dif4_lo(a0, a1, a2, a3, i0, q, tws);
+        if (two) dif4_lo(c0, c1, c2, c3, i1, q, tws);
+        x[0] = a0;
+        x[q] = a1;
+        x[2 * q] = a2;
+        x[3 * q] = a3;
+        if (two) {
+          y[0] = c0;
+          y[q] = c1;
+          y[2 * q] = c2;
+          y[3 * q] = c3;
+        }
+        continue;
       }
       V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
       V c0, c1, c2, c3;
@@ -156,9 +236,11 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp)
   }
 }
 
-// Unnormalised inverse DFT (times K): digit-reversed in, natural order out (same table as fft_dif).
-template <typename V>
-__device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ twp) {
+// Complex DFT of length K by decimation in time: digit-reversed in (the order fft_dif leaves and
+// dif_pos() describes), natural order out, same twiddle table as fft_dif.  INV: the unnormalised
+// inverse (times K).  half_out: only outputs [0, K/2) are needed (the last stage skips the rest).
+template <bool INV, typename V>
+__device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool half_out = false) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int lg = 31 - __clz(K);
   int size = 4;
@@ -179,6 +261,7 @@ __device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ 
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
     const int tot = nl * nb;
+    const bool half = half_out && size == K;
     for (int b = tid; b < tot; b += 2 * T) {
       const int bb = b + T;
       const bool two = bb < tot;
@@ -203,8 +286,19 @@ __device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ 
         c2 = y[2 * q];
         c3 = y[3 * q];
       }
-      dit4_inv(a0, a1, a2, a3, i0, q, tws);
-      if (two) dit4_inv(c0, c1, c2, c3, i1, q, tws);
+      if (half) {
+        dit4<INV, true>(a0, a1, a2, a3, i0, q, tws);
+        if (two) dit4<INV, true>(c0, c1, c2, c3, i1, q, tws);
+        x[0] = a0;
+        x[q] = a1;
+        if (two) {
+          y[0] = c0;
+          y[q] = c1;
+        }
+        continue;
+      }
+      dit4<INV, false>(a0, a1, a2, a3, i0, q, tws);
+      if (two) dit4<INV, false>(c0, c1, c2, c3, i1, q, tws);
       x[0] = a0;
       x[q] = a1;
       x[2 * q] = a2;
@@ -220,12 +314,15 @@ __device__ void fft_dit_inv(V* cb, int cs, int nl, int K, const V* __restrict__ 
   }
 }
 
-// Multiply the length-2K real DFT Y of the packed sequence by the real symmetric circulant
-// spectrum lambda, working on the packed half-length DFT Z in place:
-//   E2 = Z_k + conj Z_{K-k},  O2 = -i (Z_k - conj Z_{K-k}),  Y_k = (E2 + W_k O2)/2,
-//   W_k = exp(-i pi k / K).  spec[k] = ((lam_k + lam_{K-k})/(4K), (lam_k - lam_{K-k})/(4K)).
+// Multiply the length-2K real DFT of the packed sequence by the real symmetric circulant
+// spectrum, working on the packed half-length DFT Z in place (digit-reversed layout of fft_dif).
+// For each pair (k, K-k) the step is the linear map
+//   Z'_k = a_k Z_k + b_k conj(Z_{K-k}),   Z'_{K-k} = c_k conj(Z_k) + d_k Z_{K-k}
+// whose coefficients spec[4k..4k+3] = (a, b, c, d) fold the unpacking (E = Z_k + conj Z_{K-k},
+// O = -i (Z_k - conj Z_{K-k}), Y_k = (E + W_k O)/2, W_k = exp(-i pi k/K)), the multiply by lambda
+// and the repacking, scaled by 1/K for the unnormalised inverse (toep_pack_coeffs).
 template <typename V>
-__device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict__ spec, const V* __restrict__ twp) {
+__device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict__ spec) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int np = K / 2 + 1;
   for (int b = tid; b < nl * np; b += T) {
@@ -234,16 +331,14 @@ __device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict_
     V* x = cb + l * cs;
     const int pk = dif_pos(k, K), pkk = dif_pos(kk, K);
     const V A = x[pk], B = x[pkk];
-    const V E2 = mk<V>(A.x + B.x, A.y - B.y);
-    const V O2 = mk<V>(A.y + B.y, B.x - A.x);
-    const V W = ldt(&twp[K + k]);
-    const V P = cmul(W, O2);
-    const V sd = ldt(&spec[k]);
-    const V Ep = mk<V>(tfma(sd.x, E2.x, sd.y * P.x), tfma(sd.x, E2.y, sd.y * P.y));
-    const V WcE = cmulc(E2, W);
-    const V Op = mk<V>(tfma(sd.y, WcE.x, sd.x * O2.x), tfma(sd.y, WcE.y, sd.x * O2.y));
-    x[pk] = mk<V>(Ep.x - Op.y, Ep.y + Op.x);
-    if (kk != k) x[pkk] = mk<V>(Ep.x + Op.y, Op.x - Ep.y);
+    const V ca = ldt(&spec[4 * k]), cbv = ldt(&spec[4 * k + 1]);
+    x[pk] = mk<V>(tfma(ca.x, A.x, tfma(-ca.y, A.y, tfma(cbv.x, B.x, cbv.y * B.y))),
+                  tfma(ca.x, A.y, tfma(ca.y, A.x, tfma(cbv.y, B.x, -cbv.x * B.y))));
+    if (kk != k) {
+      const V cc = ldt(&spec[4 * k + 2]), cd = ldt(&spec[4 * k + 3]);
+      x[pkk] = mk<V>(tfma(cc.x, A.x, tfma(cc.y, A.y, tfma(cd.x, B.x, -cd.y * B.y))),
+                     tfma(cc.y, A.x, tfma(-cc.x, A.y, tfma(cd.x, B.y, cd.y * B.x))));
+    }
   }
   __syncthreads();
 }
@@ -339,8 +434,8 @@ __device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
 // ---------------------------------------------------------------------------
 // Toeplitz product T x in place for every line: x_j at xs[l*xst + j].  FFT route: xst = 2K and
 // the line's 2K reals are the packed complex sequence z_j = (y_2j, y_2j+1) of the zero-padded
-// y (y_t = x_t for t < N, 0 otherwise), so packing is only the zero fill of [N, 2K) and the
-// product comes back in [0, N).  Dense route: xst = N.
+// y (y_t = x_t for t < N, 0 otherwise), so packing is only y_N = 0 (the upper half is zero by
+// construction and skipped) and the product comes back in [0, N).  Dense route: xst = N.
 template <typename T>
 __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   using V = vec2<T>;
@@ -348,16 +443,19 @@ __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_FFT) {
     const int K = P.dim.K;
-    const int pad = 2 * K - N;
-    for (int b = tid; b < lpb * pad; b += TH) {
-      const int l = b / pad, t = N + (b - l * pad);
-      xs[l * xst + t] = from_f<T>(0.0f);
+    // y_N = 0 completes z_{K/2-1}; z_j for j >= K/2 is zero and, for K >= 4, never read (the
+    // first DIF stage skips it); K = 2 has no radix-4 stage and zeroes it.
+    const int zn = K >= 4 ? 1 : 2 * K - N;
+    for (int b = tid; b < lpb * zn; b += TH) {
+      const int l = b / zn;
+      xs[l * xst + N + (b - l * zn)] = from_f<T>(0.0f);
     }
     __syncthreads();
     V* cb = reinterpret_cast<V*>(xs);
-    fft_dif(cb, K, lpb, K, P.dim.twK);
-    toep_spectral(cb, K, lpb, K, P.dim.spec, P.dim.twK);
-    fft_dit_inv(cb, K, lpb, K, P.dim.twK);
+    fft_dif(cb, K, lpb, K, P.dim.twK, K >= 4);
+    toep_spectral(cb, K, lpb, K, P.dim.spec);
+    // outputs y_t, t < N, are z_j for j < K/2
+    fft_dit<true>(cb, K, lpb, K, P.dim.twK, true);
   } else {
     const T* __restrict__ s = P.dim.s;
     T acc[8];
@@ -422,10 +520,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
         }
         w[r] = v;
       }
-      cb[l * K + m] = mk<V>(w[0], w[1]);
+      cb[l * K + dif_pos(m, K2)] = mk<V>(w[0], w[1]);
     }
     __syncthreads();
-    fft_dif(cb, K, lpb, K2, tw2);
+    fft_dit<false>(cb, K, lpb, K2, tw2);
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
     const T sc = from_d<T>(sqrt(2.0 / (double)K));
@@ -434,7 +532,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
       const int l = b / np, k = b - l * np;
       const int kk = (K2 - k) & (K2 - 1);
       const V* z = cb + l * K;
-      const V A = z[dif_pos(k, K2)], B = z[dif_pos(kk, K2)];
+      const V A = z[k], B = z[kk];
       const V E2 = mk<V>(A.x + B.x, A.y - B.y);
       const V O2 = mk<V>(A.y + B.y, B.x - A.x);
       const V Pw = cmul(tw2[K2 + k], O2);
@@ -1325,6 +1423,16 @@ __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const doub
     return;
   }
   ir->sweep += 1;
+  // Inner target: the first sweep solves to inner_tol; a later one asks only for the reduction
+  // still needed, with a factor 0.3 of margin, rho0 tol / rho, kept within [1e-6, inner_tol]
+  // (an FP32 solve cannot resolve much below 1e-6 of its right-hand side).
+  double itol = ir->inner_tol;
+  if (ir->sweep > 1) {
+    const double need = 0.3 * ir->tol * ir->rho0 / rho;
+    itol = need < itol ? need : itol;
+    if (itol < 1e-6) itol = 1e-6 < ir->inner_tol ? 1e-6 : ir->inner_tol;
+  }
+  gin->tol = itol;
   gin->j = 0;
   gin->k = 0;
   gin->done = 0;

@@ -35,10 +35,10 @@ constexpr size_t NA_DIM0 = NA_CHAN_C + NA_MAX_UNKNOWNS;       // per-dimension t
 constexpr size_t NA_DIM_S = 0;                                // weights s_0..s_{n-1}
 constexpr size_t NA_DIM_C = NA_DIM_S + KMAX;                  // circulant first column, 2K
 constexpr size_t NA_DIM_LAM = NA_DIM_C + 2 * (size_t)KMAX;    // spectrum lambda_0..lambda_K
-constexpr size_t NA_DIM_SPEC = NA_DIM_LAM + KMAX + 2;         // (sigma, delta) pairs, K/2+1
-constexpr size_t NA_DIM_TWK = NA_DIM_SPEC + KMAX + 2;         // stage-packed twiddles, 2K+1 pairs
+constexpr size_t NA_DIM_SPEC = NA_DIM_LAM + KMAX + 2;         // (a, b, c, d) complex, K/2+1
+constexpr size_t NA_DIM_TWK = NA_DIM_SPEC + 4 * (size_t)KMAX + 8;  // stage-packed twiddles, 2K+1 pairs
 constexpr size_t NA_DIM_STRIDE = NA_DIM_TWK + 4 * (size_t)KMAX + 2;
-constexpr size_t NA_TOTAL = NA_DIM0 + 3 * NA_DIM_STRIDE;      // ~4.8 MB
+constexpr size_t NA_TOTAL = NA_DIM0 + 3 * NA_DIM_STRIDE;      // ~5.2 MB
 
 static __device__ __align__(256) double g_tau_noalloc_scratch[NA_TOTAL];
 
@@ -64,10 +64,15 @@ __global__ void k_na_weights(double alpha, int n, double* s, double* c) {
   }
 }
 
-// (sigma_k, delta_k) = ((lam_k + lam_{K-k})/(4K), (lam_k - lam_{K-k})/(4K)), k = 0..K/2
-__global__ void k_na_spec(int K, const double* lam, double2* spec) {
-  for (int k = threadIdx.x; k <= K / 2; k += blockDim.x)
-    spec[k] = make_double2((lam[k] + lam[K - k]) / (4.0 * K), (lam[k] - lam[K - k]) / (4.0 * K));
+// coefficients (a, b, c, d)_k, k = 0..K/2, of the packed spectral step (toep_pack_coeffs);
+// W_k = exp(-i pi k / K) is entry K + k of the twiddle table
+__global__ void k_na_spec(int K, const double* lam, const double2* twK, double2* spec) {
+  for (int k = threadIdx.x; k <= K / 2; k += blockDim.x) {
+    double abcd[8];
+    const double2 w = twK[K + k];
+    toep_pack_coeffs(lam[k], lam[K - k], w.x, w.y, K, abcd);
+    for (int r = 0; r < 4; ++r) spec[4 * k + r] = make_double2(abcd[2 * r], abcd[2 * r + 1]);
+  }
 }
 
 tau_status na_fail(tau_status st, const char* msg) {
@@ -152,7 +157,7 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
       if ((ce = launch_twp(K, twk, st)) != cudaSuccess) return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
       if ((ce = launch_spectrum(K, dimb + NA_DIM_C, dimb + NA_DIM_LAM, twk, st)) != cudaSuccess)
         return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
-      k_na_spec<<<1, 256, 0, st>>>(K, dimb + NA_DIM_LAM, reinterpret_cast<double2*>(dimb + NA_DIM_SPEC));
+      k_na_spec<<<1, 256, 0, st>>>(K, dimb + NA_DIM_LAM, twk, reinterpret_cast<double2*>(dimb + NA_DIM_SPEC));
     }
     if ((ce = cudaGetLastError()) != cudaSuccess) return na_fail(TAU_ECUDA, cudaGetErrorString(ce));
   }
