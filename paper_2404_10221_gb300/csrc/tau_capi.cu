@@ -172,6 +172,9 @@ template <typename T> constexpr int prec_index() {
 
 template <typename T>
 void set_lpb(PassT<T>& P, int lpb) {
+  // the line-pass kernel maps threads to lines with shifts: a power of two
+  if (lpb < 1) lpb = 1;
+  while (lpb & (lpb - 1)) lpb &= lpb - 1;
   P.lpb = lpb;
   const int64_t outer = P.nlines / P.inner;
   P.ntiles = P.ax == 0 ? (P.nlines + lpb - 1) / lpb : outer * ((P.inner + lpb - 1) / lpb);

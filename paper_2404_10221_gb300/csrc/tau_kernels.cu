@@ -48,16 +48,23 @@ template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
 template <typename V> __device__ __forceinline__ V mul_mi(V a) { return mk<V>(a.y, -a.x); }  // -i a
 template <typename V> __device__ __forceinline__ V mul_pi(V a) { return mk<V>(-a.y, a.x); }  // +i a
 
-// Position of DFT output k after the in-place radix-4 (final radix-2 when log2 K is odd) DIF.
+// Base-4 digit reversal of an nb-bit number (nb even): bit reversal, then a swap inside every
+// pair of bits.
+__device__ __forceinline__ int rev4(int x, int nb) {
+  if (nb == 0) return 0;
+  const unsigned r = __brev((unsigned)x) >> (32 - nb);
+  return (int)(((r & 0x55555555u) << 1) | ((r >> 1) & 0x55555555u));
+}
+
+// Position of DFT output k after the in-place radix-4 (final radix-2 when log2 K is odd) DIF:
+// the base-4 digits of k reversed; for odd log2 K the top bit of k is the last (radix-2) digit.
 __device__ __forceinline__ int dif_pos(int k, int K) {
-  int pos = 0, size = K;
-  while (size > 2) {
-    pos += (k & 3) * (size >> 2);
-    k >>= 2;
-    size >>= 2;
+  const int lg = __ffs(K) - 1;
+  if (lg & 1) {
+    const int lo = lg - 1;
+    return (rev4(k & ((1 << lo) - 1), lo) << 1) | (k >> lo);
   }
-  if (size == 2) pos += k;
-  return pos;
+  return rev4(k, lg);
 }
 
 // Radix-4 decimation-in-frequency butterfly on registers (span q, index i within the group).
@@ -157,27 +164,28 @@ __device__ __forceinline__ void dit4(V& y0, V& y1, V& y2, V& y3, int i, int q, c
 template <typename V>
 __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool zero_hi = false) {
   const int T = blockDim.x, tid = threadIdx.x;
-  int size = K;
-  for (; size >= 4; size >>= 2) {
-    const int q = size >> 2;
+  const int lgK = __ffs(K) - 1;
+  int size = K, lgs = lgK;
+  for (; size >= 4; size >>= 2, lgs -= 2) {
+    const int q = size >> 2, lq = lgs - 2, lnb = lgK - 2;
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
     const int tot = nl * nb;
     for (int b = tid; b < tot; b += 2 * T) {
       const int bb = b + T;
       const bool two = bb < tot;
-      int l = b / nb, loc = b - l * nb;
-      int g = loc / q;
-      const int i0 = loc - g * q;
-      V* x = cb + l * cs + g * size + i0;
+      int l = b >> lnb, loc = b & (nb - 1);
+      int g = loc >> lq;
+      const int i0 = loc & (q - 1);
+      V* x = cb + l * cs + (g << lgs) + i0;
       int i1 = 0;
       V* y = x;
       if (two) {
-        l = bb / nb;
-        loc = bb - l * nb;
-        g = loc / q;
-        i1 = loc - g * q;
-        y = cb + l * cs + g * size + i1;
+        l = bb >> lnb;
+        loc = bb & (nb - 1);
+        g = loc >> lq;
+        i1 = loc & (q - 1);
+        y = cb + l * cs + (g << lgs) + i1;
       }
       if (zero_hi && size == K) {
         V a0 = x[0], a1 = x[q], a2, a3;
@@ -226,7 +234,7 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
   if (size == 2) {
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
-      const int l = b / nb, loc = b - l * nb;
+      const int l = b >> (lgK - 1), loc = b & (nb - 1);
       V* x = cb + l * cs + 2 * loc;
       const V a0 = x[0], a1 = x[1];
       x[0] = cadd(a0, a1);
@@ -242,12 +250,12 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
 template <bool INV, typename V>
 __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool half_out = false) {
   const int T = blockDim.x, tid = threadIdx.x;
-  const int lg = 31 - __clz(K);
-  int size = 4;
-  if (lg & 1) {
+  const int lgK = __ffs(K) - 1;
+  int size = 4, lgs = 2;
+  if (lgK & 1) {
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
-      const int l = b / nb, loc = b - l * nb;
+      const int l = b >> (lgK - 1), loc = b & (nb - 1);
       V* x = cb + l * cs + 2 * loc;
       const V a0 = x[0], a1 = x[1];
       x[0] = cadd(a0, a1);
@@ -255,9 +263,10 @@ __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
     }
     __syncthreads();
     size = 8;
+    lgs = 3;
   }
-  for (; size <= K; size <<= 2) {
-    const int q = size >> 2;
+  for (; size <= K; size <<= 2, lgs += 2) {
+    const int q = size >> 2, lq = lgs - 2, lnb = lgK - 2;
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
     const int tot = nl * nb;
@@ -265,18 +274,18 @@ __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
     for (int b = tid; b < tot; b += 2 * T) {
       const int bb = b + T;
       const bool two = bb < tot;
-      int l = b / nb, loc = b - l * nb;
-      int g = loc / q;
-      const int i0 = loc - g * q;
-      V* x = cb + l * cs + g * size + i0;
+      int l = b >> lnb, loc = b & (nb - 1);
+      int g = loc >> lq;
+      const int i0 = loc & (q - 1);
+      V* x = cb + l * cs + (g << lgs) + i0;
       int i1 = 0;
       V* y = x;
       if (two) {
-        l = bb / nb;
-        loc = bb - l * nb;
-        g = loc / q;
-        i1 = loc - g * q;
-        y = cb + l * cs + g * size + i1;
+        l = bb >> lnb;
+        loc = bb & (nb - 1);
+        g = loc >> lq;
+        i1 = loc & (q - 1);
+        y = cb + l * cs + (g << lgs) + i1;
       }
       V a0 = x[0], a1 = x[q], a2 = x[2 * q], a3 = x[3 * q];
       V c0, c1, c2, c3;
@@ -322,23 +331,30 @@ __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
 // O = -i (Z_k - conj Z_{K-k}), Y_k = (E + W_k O)/2, W_k = exp(-i pi k/K)), the multiply by lambda
 // and the repacking, scaled by 1/K for the unnormalised inverse (toep_pack_coeffs).
 template <typename V>
+__device__ __forceinline__ void toep_pair(V* x, int k, int K, const V* __restrict__ spec) {
+  const int kk = (K - k) & (K - 1);
+  const int pk = dif_pos(k, K), pkk = dif_pos(kk, K);
+  const V A = x[pk], B = x[pkk];
+  const V ca = ldt(&spec[4 * k]), cbv = ldt(&spec[4 * k + 1]);
+  x[pk] = mk<V>(tfma(ca.x, A.x, tfma(-ca.y, A.y, tfma(cbv.x, B.x, cbv.y * B.y))),
+                tfma(ca.x, A.y, tfma(ca.y, A.x, tfma(cbv.y, B.x, -cbv.x * B.y))));
+  if (kk != k) {
+    const V cc = ldt(&spec[4 * k + 2]), cd = ldt(&spec[4 * k + 3]);
+    x[pkk] = mk<V>(tfma(cc.x, A.x, tfma(cc.y, A.y, tfma(cd.x, B.x, -cd.y * B.y))),
+                   tfma(cc.y, A.x, tfma(-cc.x, A.y, tfma(cd.x, B.y, cd.y * B.x))));
+  }
+}
+
+template <typename V>
 __device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict__ spec) {
   const int T = blockDim.x, tid = threadIdx.x;
-  const int np = K / 2 + 1;
-  for (int b = tid; b < nl * np; b += T) {
-    const int l = b / np, k = b - l * np;
-    const int kk = (K - k) & (K - 1);
+  // slot k in [0, K/2) of each line: the pair (k, K-k); slot 0 also takes the pair (K/2, K/2)
+  const int H = K > 1 ? K >> 1 : 1, lh = __ffs(H) - 1;
+  for (int b = tid; b < (nl << lh); b += T) {
+    const int l = b >> lh, k = b & (H - 1);
     V* x = cb + l * cs;
-    const int pk = dif_pos(k, K), pkk = dif_pos(kk, K);
-    const V A = x[pk], B = x[pkk];
-    const V ca = ldt(&spec[4 * k]), cbv = ldt(&spec[4 * k + 1]);
-    x[pk] = mk<V>(tfma(ca.x, A.x, tfma(-ca.y, A.y, tfma(cbv.x, B.x, cbv.y * B.y))),
-                  tfma(ca.x, A.y, tfma(ca.y, A.x, tfma(cbv.y, B.x, -cbv.x * B.y))));
-    if (kk != k) {
-      const V cc = ldt(&spec[4 * k + 2]), cd = ldt(&spec[4 * k + 3]);
-      x[pkk] = mk<V>(tfma(cc.x, A.x, tfma(cc.y, A.y, tfma(cd.x, B.x, -cd.y * B.y))),
-                     tfma(cc.y, A.x, tfma(-cc.x, A.y, tfma(cd.x, B.y, cd.y * B.x))));
-    }
+    toep_pair(x, k, K, spec);
+    if (k == 0 && K > 1) toep_pair(x, K >> 1, K, spec);
   }
   __syncthreads();
 }
@@ -377,48 +393,44 @@ __device__ __forceinline__ TileGeo tile_geo(const PT& P, int64_t tile) {
   return t;
 }
 
+// Flat thread index -> (line l, position j) inside a tile.  Lines along x_1 (jstep 1): slots of
+// 2^lgnp >= N per line (consecutive threads walk a line; slots j >= N are idle).  Lines along a
+// strided dimension: consecutive threads take consecutive lines (lpb is a power of two).
+__device__ __forceinline__ int tile_total(const TileGeo& t, int N, int lpb, int lgnp) {
+  return t.jstep == 1 ? (lpb << lgnp) : N * lpb;
+}
+__device__ __forceinline__ bool tile_lj(const TileGeo& t, int N, int lpb, int lgnp, int idx, int& l, int& j) {
+  if (t.jstep == 1) {
+    l = idx >> lgnp;
+    j = idx & ((1 << lgnp) - 1);
+    return j < N;
+  }
+  const int llpb = __ffs(lpb) - 1;
+  j = idx >> llpb;
+  l = idx & (lpb - 1);
+  return true;
+}
+__device__ __forceinline__ int lg_pad(int N) { return N > 1 ? 32 - __clz(N - 1) : 0; }
+
 // sm[l*ss + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
 template <typename S, typename T>
 __device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const S* __restrict__ g, T* sm, int ss) {
-  const int tot = lpb * N;
+  const int lgnp = lg_pad(N), tot = tile_total(t, N, lpb, lgnp);
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
-    if (t.jstep == 1) {
-      l = idx / N;
-      j = idx - l * N;
-    } else {
-      j = idx / lpb;
-      l = idx - j * lpb;
-    }
+    if (!tile_lj(t, N, lpb, lgnp, idx, l, j)) continue;
     sm[l * ss + j] = (l < t.nvalid) ? cvt<T, S>(g[t.base + l * t.lstep + (int64_t)j * t.jstep]) : from_f<T>(0.0f);
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void tile_store(const TileGeo& t, int N, int lpb, const T* sm, int ss, T* g) {
-  const int tot = lpb * N;
+  const int lgnp = lg_pad(N), tot = tile_total(t, N, lpb, lgnp);
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int l, j;
-    if (t.jstep == 1) {
-      l = idx / N;
-      j = idx - l * N;
-    } else {
-      j = idx / lpb;
-      l = idx - j * lpb;
-    }
+    if (!tile_lj(t, N, lpb, lgnp, idx, l, j)) continue;
     if (l < t.nvalid) g[t.base + l * t.lstep + (int64_t)j * t.jstep] = sm[l * ss + j];
   }
-}
-
-__device__ __forceinline__ int tile_index(const TileGeo& t, int N, int lpb, int idx, int& l, int& j) {
-  if (t.jstep == 1) {
-    l = idx / N;
-    j = idx - l * N;
-  } else {
-    j = idx / lpb;
-    l = idx - j * lpb;
-  }
-  return l;
 }
 
 // B_{alpha} along the line (3-point stencil of 𝓗_alpha, zero beyond the interior).
@@ -506,8 +518,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     const T* __restrict__ sn = P.dim.sintab;
     const V* __restrict__ tw2 = P.dim.twK2;
     V* cb = reinterpret_cast<V*>(xs + K);   // line l at cb + l*K (complex)
-    for (int b = tid; b < lpb * K2; b += TH) {
-      const int l = b / K2, m = b - l * K2;
+    const int lk2 = __ffs(K2) - 1;
+    for (int b = tid; b < (lpb << lk2); b += TH) {
+      const int l = b >> lk2, m = b & (K2 - 1);
       const T* row = xs + l * xst;
       T w[2];
 #pragma unroll
@@ -527,23 +540,28 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
     const T sc = from_d<T>(sqrt(2.0 / (double)K));
-    const int np = K2 / 2 + 1;
-    for (int b = tid; b < lpb * np; b += TH) {
-      const int l = b / np, k = b - l * np;
+    const T h = from_f<T>(0.5f) * sc;
+    auto recombine = [&](int l, int k) {
       const int kk = (K2 - k) & (K2 - 1);
       const V* z = cb + l * K;
       const V A = z[k], B = z[kk];
       const V E2 = mk<V>(A.x + B.x, A.y - B.y);
       const V O2 = mk<V>(A.y + B.y, B.x - A.x);
-      const V Pw = cmul(tw2[K2 + k], O2);
+      const V Pw = cmul(ldt(&tw2[K2 + k]), O2);
       T* row = xs + l * xst;
-      const T h = from_f<T>(0.5f) * sc;
       row[2 * k] = h * (E2.x + Pw.x);                       // sc Re W_k
       if (k > 0) row[2 * k - 1] = -h * (E2.y + Pw.y);       // y_{2k} = -Im W_k
       if (kk != k) {
         row[2 * kk] = h * (E2.x - Pw.x);                    // sc Re W_{K2-k}
         row[2 * kk - 1] = h * (E2.y - Pw.y);                // y_{2(K2-k)} = -Im W_{K2-k}
       }
+    };
+    // slot k in [0, K2/2) of each line: the pair (k, K2-k); slot 0 also takes k = K2/2
+    const int H2 = K2 > 1 ? K2 >> 1 : 1, lh2 = __ffs(H2) - 1;
+    for (int b = tid; b < (lpb << lh2); b += TH) {
+      const int l = b >> lh2, k = b & (H2 - 1);
+      recombine(l, k);
+      if (k == 0 && K2 > 1) recombine(l, K2 >> 1);
     }
     __syncthreads();
     // prefix sums over the even slots of each line: y_{2k+1} = sum_{i<=k} sc Re W_i - sc Re W_0 / 2.
@@ -554,8 +572,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     if (spl < 1) spl = 1;
     spl = 1 << (31 - __clz(spl));
     if (spl > K2) spl = K2;
-    const int seg = K2 / spl;
-    const int l = tid / spl, sg = tid - l * spl;
+    const int lspl = __ffs(spl) - 1;
+    const int seg = K2 >> lspl;
+    const int l = tid >> lspl, sg = tid & (spl - 1);
     const bool act = l < lpb;
     T* row = xs + (act ? l : 0) * xst;
     T acc = from_f<T>(0.0f);
@@ -635,9 +654,11 @@ __device__ __forceinline__ int rc_stride(const PassT<T>& P) {
   return P.dim.route == ROUTE_FFT ? 2 * P.dim.K : P.len;
 }
 
-// 8 resident CTAs of 128 threads per SM (64 registers a thread) for FP64 and FP32; the
-// double-float type keeps 6 (85 registers) to avoid spills.
+// Resident CTAs of 128 threads per SM the register budget allows: 7 for FP64 (72 registers; a
+// 1023-line pass fits one wave on 152 SMs), 10 for FP32 (48 registers; its passes are latency
+// bound, so more warps help), 6 for the double-float type (85 registers, no spills).
 template <typename T> struct PassOcc { static constexpr int ctas = 7; };
+template <> struct PassOcc<float> { static constexpr int ctas = 10; };
 template <> struct PassOcc<df64> { static constexpr int ctas = 6; };
 
 template <typename T>
@@ -652,7 +673,8 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
   if (P.skip && *P.skip) return;
   const TileGeo tg = tile_geo(P, blockIdx.x);
   const int TH = blockDim.x, tid = threadIdx.x;
-  const int NT = lpb * N;
+  // element loops run over lpb lines of 2^lgnp >= N slots (shift and mask, no division)
+  const int lgnp = lg_pad(N), NP = 1 << lgnp, NTP = lpb << lgnp;
   const T* in_a = P.in_a;
   T* out_a = P.out_a;
   if (P.in_sel) in_a = P.in_base + (int64_t)(P.g->j + P.in_sel - 1) * P.vstride;
@@ -675,20 +697,22 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     const T seta = from_d<T>(P.seta);
     if (P.first) {
       // ra = x, rc = e  ->  ra = e∘x (kept), rc = x (Toeplitz input), c_out = B x
-      for (int idx = tid; idx < NT; idx += TH) {
-        const int l = idx / N, j = idx - l * N;
-        const T x = ra[idx];
+      for (int idx = tid; idx < NTP; idx += TH) {
+        const int l = idx >> lgnp, j = idx & (NP - 1);
+        if (j >= N) continue;
+        const T x = ra[l * N + j];
         const T e = rc[l * RS + j];
         rc[l * RS + j] = x;
-        ra[idx] = e * x;
+        ra[l * N + j] = e * x;
       }
       __syncthreads();
     }
     // c_out = B c needs c before the Toeplitz product overwrites it; stream it to global.
     if (!P.last) {
-      for (int idx = tid; idx < NT; idx += TH) {
+      const int tot = tile_total(tg, N, lpb, lgnp);
+      for (int idx = tid; idx < tot; idx += TH) {
         int l, j;
-        tile_index(tg, N, lpb, idx, l, j);
+        if (!tile_lj(tg, N, lpb, lgnp, idx, l, j)) continue;
         const T v = stencil_B(rc + l * RS, j, N, bd, bo);
         if (l < tg.nvalid) P.out_c[tg.base + l * tg.lstep + (int64_t)j * tg.jstep] = v;
       }
@@ -696,8 +720,9 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     __syncthreads();
     // rc <- T c in place, then rc <- B a + seta * T c (B a needs ra intact).
     toeplitz_lines(P, rc, RS);
-    for (int idx = tid; idx < NT; idx += TH) {
-      const int l = idx / N, j = idx - l * N;
+    for (int idx = tid; idx < NTP; idx += TH) {
+      const int l = idx >> lgnp, j = idx & (NP - 1);
+      if (j >= N) continue;
       const T ba = stencil_B(ra + l * N, j, N, bd, bo);
       rc[l * RS + j] = tfma(seta, rc[l * RS + j], ba);
     }
@@ -709,10 +734,11 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     if (P.finish == FIN_ADD_F || P.finish == FIN_RESID) {
       tile_load(tg, N, lpb, P.src, ra, N);
       __syncthreads();
-      for (int idx = tid; idx < NT; idx += TH) {
-        const int l = idx / N, j = idx - l * N;
+      for (int idx = tid; idx < NTP; idx += TH) {
+        const int l = idx >> lgnp, j = idx & (NP - 1);
+        if (j >= N) continue;
         T& r = rc[l * RS + j];
-        r = (P.finish == FIN_ADD_F) ? r + ra[idx] : ra[idx] - r;
+        r = (P.finish == FIN_ADD_F) ? r + ra[l * N + j] : ra[l * N + j] - r;
       }
       __syncthreads();
     }
@@ -727,9 +753,10 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     if (P.post == POST_DST_MU_DST) {
       tile_load(tg, N, lpb, P.invmu, ra, N);
       __syncthreads();
-      for (int idx = tid; idx < NT; idx += TH) {
-        const int l = idx / N, j = idx - l * N;
-        rc[l * RS + j] *= ra[idx];
+      for (int idx = tid; idx < NTP; idx += TH) {
+        const int l = idx >> lgnp, j = idx & (NP - 1);
+        if (j >= N) continue;
+        rc[l * RS + j] *= ra[l * N + j];
       }
       __syncthreads();
       dst_lines(P, rc, RS);

@@ -180,6 +180,7 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     if (lpb > 16) lpb = 16;
     const int64_t cap = ax == 0 ? P.nlines : inner;
     if (lpb > cap) lpb = cap;
+    while (lpb & (lpb - 1)) lpb &= lpb - 1;   // a power of two (the kernel maps lines by shifts)
     P.lpb = (int)lpb;
     P.ntiles = ax == 0 ? (P.nlines + lpb - 1) / lpb : (P.nlines / inner) * ((inner + lpb - 1) / lpb);
     P.mv = 1;
