@@ -21,7 +21,8 @@ __all__ = [
     "apply_B", "apply_A", "apply_S", "apply_Minv", "mu_tensor", "ebar_from_tables",
     "eval_field", "eval_field_interior", "rhs_F", "rhs_b", "gmres", "GmresResult",
     "step_direct", "time_march", "l2_error", "OracleSolver", "fcd_apply_line",
-    "gmres_paper_form", "theorem_c", "two_sided_gmres",
+    "gmres_paper_form", "theorem_c", "two_sided_gmres", "two_sided_structured", "beta_tensor",
+    "apply_sine_diag",
 ]
 
 
@@ -290,6 +291,49 @@ def apply_Minv(prob, ebar: float, r: np.ndarray, mu: Optional[np.ndarray] = None
     return X.reshape(-1)
 
 
+def beta_tensor(prob) -> np.ndarray:
+    """Eigenvalues of B_alpha = B_{alpha_d} ⊗ ... ⊗ B_{alpha_1} on the d-dimensional sine basis
+    (Lemma le:eig with Lemma Heig): prod_i beta^{(i)}_{k_i}."""
+    betas = [beta_eigs(prob.alpha[i], prob.n[i]) for i in range(prob.d)]
+    out = betas[0]
+    for v in betas[1:]:
+        out = np.multiply.outer(v, out)
+    return out.reshape(-1)
+
+
+def apply_sine_diag(prob, r: np.ndarray, dvec: np.ndarray) -> np.ndarray:
+    """S_d diag(dvec) S_d r with the orthonormal d-dimensional DST-I S_d (Eq. (diag))."""
+    X = r.reshape(_shape(prob))
+    Ss = [sine_matrix(prob.n[i]) for i in range(prob.d)]
+    for i in range(prob.d):
+        X = mode_product(X, Ss[i], _axis(prob, i))
+    X = X * dvec.reshape(_shape(prob))
+    for i in range(prob.d):
+        X = mode_product(X, Ss[i], _axis(prob, i))
+    return X.reshape(-1)
+
+
+def two_sided_structured(prob, e_vec: np.ndarray, b: np.ndarray, ebar: float, tol: float, max_iter: int,
+                         u0: Optional[np.ndarray] = None, toeps=None) -> GmresResult:
+    """Two-sided τ-preconditioned GMRES (TPGM), Eq. (Pls), with the structured operators.
+
+    P_alpha = ebar I + B^{-1} tau(S) (Eq. (Pa)) is a τ-matrix: on the sine basis its eigenvalues
+    are ebar + tau_k / beta_k = mu_k / beta_k (mu_tensor, beta_tensor), so
+    P^{-1/2} = S_d diag((beta/mu)^{1/2}) S_d and P^{-1/2} B^{-1} = S_d diag((beta mu)^{-1/2}) S_d.
+    GMRES runs on P^{-1/2} Ã P^{-1/2} ũ = P^{-1/2} b̃ with Ã = B^{-1} A, b̃ = B^{-1} b (Eq. (equi)),
+    from ũ_0 = P^{1/2} u0 (zero without u0); the returned x is u = P^{-1/2} ũ."""
+    mu = mu_tensor(prob, ebar)
+    beta = beta_tensor(prob)
+    d_pmh = np.sqrt(beta / mu)
+    d_pmhb = 1.0 / np.sqrt(beta * mu)
+    op = lambda v: apply_sine_diag(prob, apply_A(prob, e_vec, apply_sine_diag(prob, v, d_pmh), toeps), d_pmhb)
+    rhs = apply_sine_diag(prob, b, d_pmhb)
+    x0 = np.zeros_like(b) if u0 is None else apply_sine_diag(prob, u0, 1.0 / d_pmh)
+    res = gmres(op, rhs, x0, tol, max_iter)
+    res.x = apply_sine_diag(prob, res.x, d_pmh)
+    return res
+
+
 # --------------------------------------------------------------------------
 # fields and right-hand side (Eq. (tls), Appendix A)
 # --------------------------------------------------------------------------
@@ -455,11 +499,13 @@ def l2_error(prob, u, u_exact) -> float:
 
 
 class OracleSolver:
-    """Whole time-march with one-sided τ-preconditioned GMRES in the A-form
-    (M = ebar B + tau(S)), structured tier."""
+    """Whole time-march with τ-preconditioned GMRES, structured tier: one-sided in the A-form
+    (M = ebar B + tau(S)) or two-sided (Eq. (Pls))."""
 
-    def __init__(self, prob, tables: dict, ebar: Optional[float] = None):
+    def __init__(self, prob, tables: dict, ebar: Optional[float] = None, sided: int = 1):
+        """sided 1: one-sided (OPGM, Eq. (one-sided)); 2: two-sided (TPGM, Eq. (Pls))."""
         self.prob = prob
+        self.sided = sided
         self.t = tables
         if ebar is None:
             ebar = ebar_from_tables(prob, tables["e_tc"], tables["e_sp"])[0]
@@ -486,8 +532,12 @@ class OracleSolver:
             self.m += 1
             return None
         x0 = np.zeros_like(b) if p.x0_mode == 0 else self.u.copy()
-        res = gmres(lambda v: apply_A(p, e, v, self.toeps), b, x0, p.tol, p.max_iter,
-                    lambda v: apply_Minv(p, self.ebar, v, self.mu))
+        if self.sided == 2:
+            res = two_sided_structured(p, e, b, self.ebar, p.tol, p.max_iter,
+                                       None if p.x0_mode == 0 else x0, self.toeps)
+        else:
+            res = gmres(lambda v: apply_A(p, e, v, self.toeps), b, x0, p.tol, p.max_iter,
+                        lambda v: apply_Minv(p, self.ebar, v, self.mu))
         self.u = res.x
         self.iters.append(res.iters)
         self.m += 1

@@ -85,3 +85,47 @@ def test_iteration_count_mesh_independent():
         s.run(steps=2)
         its.append(max(s.iters))
     assert max(its) - min(its) <= 1
+
+
+@pytest.mark.parametrize("d,n", [(1, (9,)), (2, (6, 5)), (3, (3, 4, 3))])
+def test_pmh_squares_to_P_inverse(d, n):
+    # P^{-1/2} on the sine basis, applied twice, is P^{-1} of the dense assembly of Eq. (Pa)
+    p, e, b, ebar, _ = _system(d, n)
+    mu, beta = O.mu_tensor(p, ebar), O.beta_tensor(p)
+    half = np.sqrt(beta / mu)
+    r = O.apply_sine_diag(p, O.apply_sine_diag(p, b, half), half)
+    ref = np.linalg.solve(O.dense_P(p, ebar), b)
+    assert np.linalg.norm(r - ref) <= 1e-12 * np.linalg.norm(ref)
+    # P^{-1/2} B^{-1} on the sine basis equals the dense eigh-based P^{-1/2} times B^{-1}
+    pb = O.apply_sine_diag(p, b, 1.0 / np.sqrt(beta * mu))
+    Bm = O.dense_B(p)
+    w, Q = np.linalg.eigh(0.5 * (O.dense_P(p, ebar) + O.dense_P(p, ebar).T))
+    ref2 = (Q * w ** -0.5) @ Q.T @ np.linalg.solve(Bm, b)
+    assert np.linalg.norm(pb - ref2) <= 1e-11 * np.linalg.norm(ref2)
+
+
+@pytest.mark.parametrize("d,n", [(1, (9,)), (2, (6, 5)), (3, (3, 4, 3))])
+def test_two_sided_structured_equals_dense_form(d, n):
+    # the structured TPGM runs the same Krylov iteration as the dense eigh-based form of Eq. (Pls)
+    p, e, b, ebar, _ = _system(d, n)
+    s = O.two_sided_structured(p, e, b, ebar, 1e-12, 60)
+    q = O.two_sided_gmres(p, e, b, ebar, 1e-12, 60)
+    assert s.iters == q.iters
+    assert np.allclose(s.res, q.res, rtol=1e-8, atol=1e-13 * q.res[0])
+    w, Q = np.linalg.eigh(0.5 * (O.dense_P(p, ebar) + O.dense_P(p, ebar).T))
+    u_dense = (Q * w ** -0.5) @ Q.T @ q.x
+    assert np.linalg.norm(s.x - u_dense) <= 1e-10 * np.linalg.norm(u_dense)
+    x_dir = np.linalg.solve(O.dense_A(p, e), b)
+    assert np.linalg.norm(s.x - x_dir) <= 1e-10 * np.linalg.norm(x_dir)
+
+
+def test_two_sided_time_march_matches_one_sided():
+    # both solvers converge to the same u^(m) (A^{-1} b each step); iteration counts are close
+    # (Tables 2-4: OPGM and TPGM take similar iteration numbers)
+    wl = W.paper_example(2, [1.3, 1.5], 15, 64)
+    one = O.OracleSolver(wl.prob, wl.field_tables())
+    two = O.OracleSolver(wl.prob, wl.field_tables(), sided=2)
+    one.run(steps=3)
+    two.run(steps=3)
+    assert np.linalg.norm(one.u - two.u) <= 1e-10 * np.linalg.norm(one.u)
+    assert all(abs(a - b) <= 2 for a, b in zip(one.iters, two.iters))
