@@ -198,13 +198,13 @@ def pass_flops_2d(n: int) -> float:
     return lines * sum(per_line.values())
 
 
-def measure_steps(wl, precision, warm, timed, stream, dev):
+def measure_steps(wl, precision, warm, timed, stream, dev, method=0):
     """Time `timed` steps (CUDA events per step, L2 flushed between steps) after `warm` steps."""
     import torch
 
     from paper_2404_10221_gb300 import tau
 
-    prob = tau.Problem(wl, precision=precision, stream=stream.cuda_stream)
+    prob = tau.Problem(wl, precision=precision, stream=stream.cuda_stream, method=method)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tau.tau_step(prob.handle, warm)
     tau.tau_sync(prob.handle, allow_notconv=True)
@@ -246,6 +246,16 @@ def run_forms(stream, dev):
         "rel_err_vs_plain_fp64": (torch.linalg.norm(udf - u64) / torch.linalg.norm(u64)).item(),
         "df64_iters_per_step": float(np.mean(itdf)), "plain_iters_per_step": float(np.mean(it64)),
         "unit": UNIT, "dtype": "double-float (2 x f32) vectors, transforms and Arnoldi; f64 Givens/LSQ"}
+    # two-sided method (Eq. (Pls)) on the headline workload: one more τ solve per iteration
+    wl = W.c2_2d()
+    vt, mst, ut, stt, itt = measure_steps(wl, tau.TAU_FP64, 2, 5, stream, dev, method=tau.TAU_TPGM)
+    out["2d_1023_tpgm"] = {
+        "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_compared": 7, "tpgm_value": vt,
+        "tpgm_ms_per_step": mst, "opgm_value": v64, "opgm_ms_per_step": ms64,
+        "tpgm_over_opgm_time": mst / ms64,
+        "rel_err_vs_opgm": (torch.linalg.norm(ut - u64) / torch.linalg.norm(u64)).item(),
+        "tpgm_iters_per_step": float(np.mean(itt)), "opgm_iters_per_step": float(np.mean(it64)),
+        "unit": UNIT, "dtype": "f64"}
     for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)

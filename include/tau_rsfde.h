@@ -65,6 +65,13 @@ typedef int tau_status;
                                  significant bits) on the FP32 pipes; scalars (Givens, least squares)
                                  in FP64; u, e and f cross the API in FP64 */
 
+#define TAU_OPGM 0            /* one-sided: GMRES on P^{-1} Ã u = P^{-1} b̃ (§3), run in the equivalent
+                                 A-form M^{-1} A u = M^{-1} b with M = ebar B + tau(S) */
+#define TAU_TPGM 1            /* two-sided: GMRES on P^{-1/2} Ã P^{-1/2} ũ = P^{-1/2} b̃ (Eq. (Pls)),
+                                 u = P^{-1/2} ũ; both P^{-1/2} and P^{-1/2} B^{-1} are DST-diag-DST
+                                 products, so an iteration costs one more τ solve than OPGM.
+                                 TAU_FP64 only */
+
 #define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
 #define TAU_ROUTE_DENSE 2     /* explicit n_i x n_i mode products (any n_i <= 8192) */
@@ -94,6 +101,7 @@ typedef struct {
   double inner_tol;     /* inner FGMRES relative residual target of the first sweep; 1e-5.  A later
                            sweep targets the reduction still needed, 0.3 refine_tol rho_0 / rho,
                            kept within [min(1e-6, inner_tol), inner_tol] */
+  int method;           /* TAU_OPGM (0, default) or TAU_TPGM */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,

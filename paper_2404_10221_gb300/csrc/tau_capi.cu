@@ -106,6 +106,9 @@ struct tau_problem {
   // double-float precision (TAU_DF64): solver vectors live in the FP64 buffers above as df64 pairs
   bool dfm = false;
   df64 *Edf = nullptr, *Fdf = nullptr, *invmu_df = nullptr;
+  // two-sided method (TAU_TPGM): sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1}
+  int tpgm = 0;
+  double *pmh = nullptr, *pmhb = nullptr;
   df64x2 *spec_df[3] = {nullptr, nullptr, nullptr}, *twK_df[3] = {nullptr, nullptr, nullptr},
          *twK2_df[3] = {nullptr, nullptr, nullptr};
   df64 *s_df[3] = {nullptr, nullptr, nullptr}, *sintab_df[3] = {nullptr, nullptr, nullptr};
@@ -244,6 +247,7 @@ struct ChainT {
   T* in_base = nullptr;
   T* out_base = nullptr;
   const GmresDev* g = nullptr;
+  const T* diag = nullptr;   // sine-basis diagonal of the DST-diag-DST tail (default 1/mu)
 };
 using ChainIO = ChainT<double>;
 
@@ -299,7 +303,7 @@ tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainT<T>& io, i
   auto dst_pass = [&](int ax, int post) -> tau_status {
     PassT<T> P = base_pass_t<T>(p, ax);
     P.post = post;
-    P.invmu = invmu_of<T>(p);
+    P.invmu = io.diag ? io.diag : invmu_of<T>(p);
     P.g = io.g;
     wire_in(P, io, rd);
     wire_out(P, io);
@@ -339,7 +343,7 @@ tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double s
       wire_out(P, io);
       P.finish = finish;
       P.src = src;
-      P.invmu = invmu_of<T>(p);
+      P.invmu = io.diag ? io.diag : invmu_of<T>(p);
       if (precond) P.post = d == 1 ? POST_DST_MU_DST : POST_DST;
     }
     TRY(enq(P, st));
@@ -380,6 +384,8 @@ tau_status enq_prologue_t(tau_problem* p, cudaStream_t st) {
   TRY(enq_mv<T>(p, st, rhs, -1.0, FIN_ADD_F, fdt_of<T>(p), false));
   ChainT<T> r0;
   r0.out = as<T>(p->V);
+  // two-sided: r_0 = P^{-1/2} B^{-1} (b - A u_0), the residual of Eq. (Pls) at ũ_0 = P^{1/2} u_0
+  if (p->tpgm) r0.diag = as<T>(p->pmhb);
   if (p->desc.x0_mode == TAU_X0_PREV) {
     r0.x = as<T>(p->u);
     TRY(enq_mv<T>(p, st, r0, 1.0, FIN_RESID, as<T>(p->b), true));
@@ -399,6 +405,18 @@ tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandl
   it.in_sel = 1;
   it.out_sel = 2;
   it.g = p->g;
+  if (p->tpgm) {
+    // two-sided operator of Eq. (Pls): v_{j+1} = P^{-1/2} B^{-1} A P^{-1/2} v_j, with P^{-1/2} v_j in tmp
+    ChainT<T> half;
+    half.in_sel = 1;
+    half.out = as<T>(p->tmp);
+    half.g = p->g;
+    half.diag = as<T>(p->pmh);
+    TRY(enq_minv<T>(p, st, half));
+    it.in_sel = 0;
+    it.x = as<T>(p->tmp);
+    it.diag = as<T>(p->pmhb);
+  }
   TRY(enq_mv<T>(p, st, it, 1.0, FIN_NONE, nullptr, true));
   const int ld = RED_BLOCKS;
   T* V = as<T>(p->V);
@@ -415,6 +433,18 @@ tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandl
 template <typename T>
 tau_status enq_epilogue_t(tau_problem* p, cudaStream_t st) {
   tl_launches += 2;
+  if (p->tpgm) {
+    // ũ = ũ_0 + V y and u = P^{-1/2} ũ = u_0 + P^{-1/2} (V y)
+    KL(launch_backsolve_update<T>(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, as<T>(p->V), p->n_tot,
+                                  as<T>(p->tmp), 0, p->iters, st));
+    ChainT<T> half;
+    half.x = as<T>(p->tmp);
+    half.out = as<T>(p->A);
+    half.diag = as<T>(p->pmh);
+    TRY(enq_minv<T>(p, st, half));
+    KL(launch_add_into(p->u, p->A, p->n_tot, p->desc.x0_mode == TAU_X0_PREV, st));
+    return TAU_OK;
+  }
   KL(launch_backsolve_update<T>(p->g, p->H, p->gv, p->desc.max_iter + 1, p->y, as<T>(p->V), p->n_tot, as<T>(p->u),
                                 p->desc.x0_mode == TAU_X0_PREV, p->iters, st));
   return TAU_OK;
@@ -788,6 +818,9 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (D.x0_mode != TAU_X0_ZERO && D.x0_mode != TAU_X0_PREV) return fail(TAU_EINVAL, "x0_mode %d", D.x0_mode);
   if (D.precision != TAU_FP64 && D.precision != TAU_MIXED && D.precision != TAU_DF64)
     return fail(TAU_EINVAL, "precision %d", D.precision);
+  if (D.method != TAU_OPGM && D.method != TAU_TPGM) return fail(TAU_EINVAL, "method %d", D.method);
+  if (D.method == TAU_TPGM && D.precision != TAU_FP64)
+    return fail(TAU_EUNSUPPORTED, "the two-sided method runs in TAU_FP64 only");
   if (D.precision == TAU_MIXED &&
       (D.refine_tol < 0 || D.inner_tol < 0 || D.inner_max_iter < 0 || D.inner_max_iter > MAX_ITER_CAP ||
        D.max_sweeps < 0))
@@ -834,6 +867,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
   p->mixed = D.precision == TAU_MIXED;
   p->dfm = D.precision == TAU_DF64;
+  p->tpgm = D.method == TAU_TPGM;
   if (p->mixed) {
     if (p->desc.refine_tol == 0) p->desc.refine_tol = 1e-10;
     if (p->desc.inner_max_iter == 0) p->desc.inner_max_iter = 30;
@@ -860,6 +894,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (p->dfm && ((s = dalloc_n(p, &p->Edf, n)) || (s = dalloc_n(p, &p->Fdf, n)) ||
                  (s = dalloc_n(p, &p->invmu_df, n))))
     return cleanup(s);
+  if (p->tpgm && ((s = dalloc_n(p, &p->pmh, n)) || (s = dalloc_n(p, &p->pmhb, n)))) return cleanup(s);
   if ((s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
       (s = dalloc_n(p, &p->A, n)) || (s = dalloc_n(p, &p->C, n)) || (s = dalloc_n(p, &p->E, n)) ||
       (s = dalloc_n(p, &p->Fdt, n)) || (s = dalloc_n(p, &p->invmu, n)) || (s = dalloc_n(p, &p->tmp, n)) ||
@@ -1009,6 +1044,7 @@ tau_status tau_setup(tau_problem* p) {
     return fail(TAU_EINVAL, "e must be positive: min %g max %g", p->echeck, p->ehat);
   p->ebar = 0.5 * (p->ehat + p->echeck);
   KL(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
+  if (p->tpgm) KL(launch_tpgm_diag(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->pmh, p->pmhb, p->st));
   KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->dfm ? p->tmp : p->u, p->st));
   if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
   if (p->dfm) {

@@ -222,6 +222,11 @@ cudaError_t launch_psi(int d, const int* n, int64_t n_tot, int rank, const doubl
 cudaError_t launch_escan(const FieldDev& f, int64_t M, double* partial /*2*RED_BLOCKS*/, cudaStream_t st);
 cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
                          const double* const* q, const double* eta, double* invmu, cudaStream_t st);
+// Two-sided preconditioning (Eq. (Pls)): pmh = sqrt(beta/mu), pmhb = 1/sqrt(beta mu) per sine mode.
+cudaError_t launch_tpgm_diag(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
+                             const double* const* q, const double* eta, double* pmh, double* pmhb, cudaStream_t st);
+// u = t (keep 0) or u += t (keep 1)
+cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cudaStream_t st);
 
 // GMRES building blocks
 // w = V_{j+1} (the slot of the next basis vector) in the CGS2 kernels below; S is the storage

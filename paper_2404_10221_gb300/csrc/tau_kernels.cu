@@ -1032,6 +1032,60 @@ cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const 
   return cudaGetLastError();
 }
 
+// Two-sided preconditioning (Eq. (Pls)): P = ebar I + B^{-1} tau(S) has the eigenvalues mu_k / beta_k
+// on the sine basis (beta_k = prod_i beta^{(i)}_{k_i}), so P^{-1/2} = S diag(sqrt(beta/mu)) S and
+// P^{-1/2} B^{-1} = S diag(1/sqrt(beta mu)) S.
+__global__ void k_tpgm_diag(const MuArgs a, double* pmh, double* pmhb) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.n_tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    unflatten(idx, a.d, a.n, j);
+    double bprod = 1.0;
+    for (int i = 0; i < a.d; ++i) bprod *= a.beta[i][j[i]];
+    double mu = a.ebar * bprod;
+    for (int i = 0; i < a.d; ++i) {
+      double p = a.eta[i] * a.q[i][j[i]];
+      for (int l = 0; l < a.d; ++l)
+        if (l != i) p *= a.beta[l][j[l]];
+      mu += p;
+    }
+    pmh[idx] = sqrt(bprod / mu);
+    pmhb[idx] = 1.0 / sqrt(bprod * mu);
+  }
+}
+
+cudaError_t launch_tpgm_diag(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
+                             const double* const* q, const double* eta, double* pmh, double* pmhb, cudaStream_t st) {
+  MuArgs a;
+  a.d = d;
+  a.n_tot = n_tot;
+  a.ebar = ebar;
+  for (int i = 0; i < 3; ++i) {
+    a.n[i] = i < d ? n[i] : 1;
+    a.beta[i] = i < d ? beta[i] : nullptr;
+    a.q[i] = i < d ? q[i] : nullptr;
+    a.eta[i] = i < d ? eta[i] : 0.0;
+  }
+  int64_t blocks = (n_tot + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_tpgm_diag<<<(unsigned)blocks, 256, 0, st>>>(a, pmh, pmhb);
+  return cudaGetLastError();
+}
+
+// u = t (keep = 0) or u += t (keep = 1)
+__global__ void k_add_into(double* u, const double* __restrict__ t, int64_t n, int keep) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = keep ? u[i] + t[i] : t[i];
+}
+
+cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_add_into<<<(unsigned)blocks, 256, 0, st>>>(u, t, n, keep);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // GMRES: classical Gram-Schmidt with one re-orthogonalisation (CGS2), Givens rotations
 // ---------------------------------------------------------------------------

@@ -31,6 +31,8 @@ TAU_X0_PREV = 1
 TAU_FP64 = 0
 TAU_MIXED = 1
 TAU_DF64 = 2
+TAU_OPGM = 0
+TAU_TPGM = 1
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
@@ -57,6 +59,7 @@ class tau_problem_desc(C.Structure):
         ("inner_max_iter", C.c_int),
         ("max_sweeps", C.c_int),
         ("inner_tol", C.c_double),
+        ("method", C.c_int),
     ]
 
 
@@ -216,7 +219,7 @@ def _stream(stream=None) -> int:
 
 def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
               e_bounds: Optional[tuple] = None, refine_tol: float = 0.0, inner_max_iter: int = 0,
-              max_sweeps: int = 0, inner_tol: float = 0.0) -> tau_problem_desc:
+              max_sweeps: int = 0, inner_tol: float = 0.0, method: int = TAU_OPGM) -> tau_problem_desc:
     """tau_problem_desc from a workloads.Problem."""
     d = tau_problem_desc()
     d.d = prob.d
@@ -233,6 +236,7 @@ def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
     d.max_iter = int(prob.max_iter)
     d.x0_mode = int(prob.x0_mode)
     d.precision = precision
+    d.method = int(method)
     if e_bounds is None:
         d.e_min = d.e_max = math.nan
     else:
