@@ -198,6 +198,7 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   D.route = p->route[ax];
   D.bdiag = host_cast<T>(1.0 - p->desc.alpha[ax] / 12.0);
   D.boff = host_cast<T>(p->desc.alpha[ax] / 24.0);
+  D.dsc = host_cast<T>(std::sqrt(2.0 / (double)(p->n[ax] + 1)));
   D.eta = p->eta[ax];
   if constexpr (std::is_same<T, double>::value) {
     D.spec = p->spec[ax];

@@ -99,6 +99,7 @@ struct DimDataT {
   int K;              // n + 1 (FFT route: power of two)
   int route;          // Route
   T bdiag, boff;      // B_{alpha_i}: 1 - alpha/12, alpha/24
+  T dsc;              // sqrt(2 / K): scale of the orthonormal DST-I of length n
   double eta;         // kappa_i dt / (2 h_i^alpha_i)
   const vec2<T>* spec;  // FFT route: (a, b, c, d)_k, k = 0..K/2 (toep_pack_coeffs): the Toeplitz
                         // spectrum folded for the packed real FFT, scaled by 1/K (no eta)

@@ -413,13 +413,29 @@ __device__ __forceinline__ bool tile_lj(const TileGeo& t, int N, int lpb, int lg
 __device__ __forceinline__ int lg_pad(int N) { return N > 1 ? 32 - __clz(N - 1) : 0; }
 
 // sm[l*ss + j] = g[base + l*lstep + j*jstep]; consecutive threads take consecutive addresses.
+// Each thread issues a batch of independent loads (8 of 4 bytes, 4 of 8) before the shared-memory
+// stores, so one memory latency covers the batch instead of one per element.
 template <typename S, typename T>
 __device__ __forceinline__ void tile_load(const TileGeo& t, int N, int lpb, const S* __restrict__ g, T* sm, int ss) {
+  constexpr int TILE_BATCH = sizeof(S) >= 8 ? 4 : 8;
   const int lgnp = lg_pad(N), tot = tile_total(t, N, lpb, lgnp);
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    int l, j;
-    if (!tile_lj(t, N, lpb, lgnp, idx, l, j)) continue;
-    sm[l * ss + j] = (l < t.nvalid) ? cvt<T, S>(g[t.base + l * t.lstep + (int64_t)j * t.jstep]) : from_f<T>(0.0f);
+  const int TH = blockDim.x;
+  for (int base = threadIdx.x; base < tot; base += TILE_BATCH * TH) {
+    S v[TILE_BATCH];
+    int dst[TILE_BATCH];
+#pragma unroll
+    for (int r = 0; r < TILE_BATCH; ++r) {
+      const int idx = base + r * TH;
+      int l = 0, j = 0;
+      dst[r] = -1;
+      if (idx < tot && tile_lj(t, N, lpb, lgnp, idx, l, j)) {
+        dst[r] = l * ss + j;
+        v[r] = (l < t.nvalid) ? g[t.base + l * t.lstep + (int64_t)j * t.jstep] : from_f<S>(0.0f);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < TILE_BATCH; ++r)
+      if (dst[r] >= 0) sm[dst[r]] = cvt<T, S>(v[r]);
   }
 }
 
@@ -539,7 +555,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     fft_dit<false>(cb, K, lpb, K2, tw2);
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
-    const T sc = from_d<T>(sqrt(2.0 / (double)K));
+    const T sc = P.dim.dsc;   // sqrt(2/K), precomputed per dimension
     const T h = from_f<T>(0.5f) * sc;
     auto recombine = [&](int l, int k) {
       const int kk = (K2 - k) & (K2 - 1);
@@ -608,7 +624,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
   } else {
     const int K = P.dim.K;
     const T* __restrict__ st = P.dim.sintab;
-    const T sc = from_d<T>(sqrt(2.0 / (double)K));
+    const T sc = P.dim.dsc;   // sqrt(2/K), precomputed per dimension
     const T z0 = from_f<T>(0.0f);
     T acc[8];
     const int tot = lpb * N;
@@ -1092,15 +1108,16 @@ cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cud
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 4;
 
+// Block sum in FP64 (sh: at least blockDim.x doubles).  Every thread's value goes to shared memory
+// and warp 0 adds them, so the FP64 additions (a slow pipe on this part) number ~12 per lane of
+// one warp instead of a shuffle tree in every warp.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
   __syncthreads();
-  if (ln == 0) sh[w] = v;
+  sh[threadIdx.x] = v;
   __syncthreads();
   double r = 0.0;
   if (threadIdx.x < 32) {
-    r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int t = threadIdx.x; t < blockDim.x; t += 32) r += sh[t];
     for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
   }
   return r;  // valid in thread 0
@@ -1111,7 +1128,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename S>
 __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, int64_t n,
                                                       const GmresDev* __restrict__ g, double* partial, int ld) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   if (g->done) return;
   const int jj = g->j;
   const S* __restrict__ w = V + (int64_t)(jj + 1) * n;
@@ -1169,7 +1186,7 @@ template <typename S>
 __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, const GmresDev* __restrict__ g,
                                                              const double* __restrict__ h, double* partial, int ld,
                                                              int want_norm) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   __shared__ S hs[MAX_ITER_CAP + 1];
   if (g->done) return;
   const int jj = g->j;
@@ -1229,7 +1246,7 @@ template cudaError_t launch_update_dots<df64>(df64*, int64_t, const GmresDev*, c
 __global__ void k_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* __restrict__ h1,
                          const double* __restrict__ h2, const double* __restrict__ pnorm, int ldH,
                          cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   if (g->done) {
     if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
@@ -1290,7 +1307,10 @@ template <typename S>
 __global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
   if (g->done) return;
   const int j = g->j;
-  const S inv = from_d<S>(1.0 / g->hnorm);
+  __shared__ double sinv;   // one FP64 division per block
+  if (threadIdx.x == 0) sinv = 1.0 / g->hnorm;
+  __syncthreads();
+  const S inv = from_d<S>(sinv);
   S* v = V + (int64_t)j * n;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     v[idx] *= inv;
@@ -1307,7 +1327,7 @@ template cudaError_t launch_scale_next<df64>(df64*, int64_t, const GmresDev*, cu
 
 template <typename S>
 __global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const S* __restrict__ w, int64_t n, double* partial) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   S acc = from_f<S>(0.0f);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     acc = tfma(w[idx], w[idx], acc);
@@ -1326,7 +1346,7 @@ template cudaError_t launch_norm_partial<df64>(const df64*, int64_t, const Gmres
 
 // beta = ||r_0||, g_0 = beta, j = 0; done if beta == 0.
 __global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, double* gv) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   double s = 0.0;
   for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += partial[b];
   s = block_sum(s, sh);
@@ -1345,7 +1365,10 @@ __global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, dou
 template <typename S>
 __global__ void k_scale_first(S* V, int64_t n, const GmresDev* __restrict__ g) {
   if (g->done) return;
-  const S inv = from_d<S>(1.0 / g->beta);
+  __shared__ double sinv;   // one FP64 division per block
+  if (threadIdx.x == 0) sinv = 1.0 / g->beta;
+  __syncthreads();
+  const S inv = from_d<S>(sinv);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
     V[idx] *= inv;
 }
@@ -1482,7 +1505,7 @@ cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t
 // every sweep (cond_in) as well as the outer one (cond).
 __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* __restrict__ pnorm,
                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond) {
-  __shared__ double sh[32];
+  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   double s = 0.0;
   for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += pnorm[b];
   s = block_sum(s, sh);
@@ -1536,7 +1559,10 @@ cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const dou
 // v_0 = (float)(r / rho)
 __global__ void k_scale_to_f32(const double* __restrict__ r, float* v, int64_t n, const IRDev* __restrict__ ir) {
   if (ir->done) return;
-  const double inv = 1.0 / ir->rho;
+  __shared__ double sinv;   // one FP64 division per block
+  if (threadIdx.x == 0) sinv = 1.0 / ir->rho;
+  __syncthreads();
+  const double inv = sinv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[i] = (float)(r[i] * inv);
 }
@@ -1546,20 +1572,22 @@ cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDe
   return cudaGetLastError();
 }
 
-// x += rho * sum_{i<k} y_i Z_i (FP64 accumulation of the FP32 preconditioned directions)
+// x += rho * sum_{i<k} y_i Z_i: the correction is summed over the FP32 preconditioned directions in
+// FP32 (it needs only the inner solve's accuracy, and the Z_i are FP32 already) and added to x in
+// FP64, so FP64 work is one addition per element.
 __global__ void k_update_x(double* x, const float* __restrict__ Z, const double* __restrict__ y, int64_t n,
                            const GmresDev* __restrict__ gin, IRDev* ir) {
-  __shared__ double ys[MAX_ITER_CAP];
+  __shared__ float ys[MAX_ITER_CAP];
   if (ir->done) return;
   const int k = gin->k;
   const double rho = ir->rho;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * y[i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = (float)(rho * y[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) ir->inner_total += k;
   __syncthreads();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    double v = x[idx];
-    for (int i = 0; i < k; ++i) v = fma(ys[i], (double)Z[(int64_t)i * n + idx], v);
-    x[idx] = v;
+    float d = 0.0f;
+    for (int i = 0; i < k; ++i) d = fmaf(ys[i], Z[(int64_t)i * n + idx], d);
+    x[idx] += (double)d;
   }
 }
 

@@ -144,6 +144,7 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     Dd.route = fft ? ROUTE_FFT : ROUTE_DENSE;
     Dd.bdiag = 1.0 - D.alpha[i] / 12.0;
     Dd.boff = D.alpha[i] / 24.0;
+    Dd.dsc = sqrt(2.0 / (double)(D.n[i] + 1));
     const double h = (D.R[i] - D.L[i]) / (double)(n + 1);
     Dd.eta = D.kappa[i] * dt / (2.0 * std::pow(h, D.alpha[i]));
     Dd.s = dimb + NA_DIM_S;
