@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--profile-step", default="", choices=["", "2d_1023_fp64", "3d_255_mixed"],
+                    help="profiling driver: set up the workload, run one step, then one more step inside "
+                         "the NVTX range 'step' (ncu --nvtx --nvtx-include step/)")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: set up the workload (2 Krylov slots) and run this many "
                          "preconditioned matvecs (4 line-pass launches each), then exit")
@@ -179,6 +182,33 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": rows[0][1], "reasons": reasons, "samples": len(rows)}
+
+
+# DRAM bytes (read + write) of the four line-pass launches of one preconditioned matvec on the
+# 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
+# kernel sources that capture measured (sha256 below), else the bench reports null.
+TRAFFIC_CAPTURE = {
+    "bytes_per_matvec": 16916992 + 512 + 16963072 + 256 + 16904192 + 8493056,
+    "sha256": {
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "31a512ac5b26211486a8a5f85976b42cacc01929cacba8d2d14d2550cbd938b2",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "560712c93ceb7636f5091836efc22873f05bcc0c746db788161f4b03a7904597",
+    },
+}
+
+
+def captured_traffic():
+    """TRAFFIC_CAPTURE's bytes if the kernel sources are the captured ones, else None."""
+    import hashlib
+
+    root = os.path.dirname(os.path.abspath(__file__))
+    for rel, want in TRAFFIC_CAPTURE["sha256"].items():
+        try:
+            with open(os.path.join(root, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+        except OSError:
+            return None
+    return TRAFFIC_CAPTURE["bytes_per_matvec"]
 
 
 def pass_flops_2d(n: int) -> float:
@@ -483,7 +513,9 @@ def run_native(args):
     achieved = flops / t_chain / 1e12
     roof = {"bound": "alu", "kernel": "tau::k_pass (4 launches per preconditioned matvec)",
             "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / (fp64_peak / 1e12), "traffic": None,
+            "frac": achieved / (fp64_peak / 1e12), "traffic": captured_traffic(),
+            "traffic_unit": "DRAM bytes read + written by the 4 launches of one preconditioned matvec "
+                            "(ncu capture of this kernel source; null if the source changed since)",
             "peak_kind": "measured FP64 FMA throughput (in-process probe, best of two runs); nominal 1.25 TFLOP/s",
             "matvec_ms": t_chain * 1e3, "algorithmic_flops_per_matvec": flops}
 
@@ -570,6 +602,31 @@ def run_matvec_only(args):
     return 0
 
 
+def run_profile_step(args):
+    import torch
+
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+
+    if args.profile_step == "2d_1023_fp64":
+        wl, prec = W.c2_2d(), tau.TAU_FP64
+    else:
+        wl, prec = W.c3_3d(), tau.TAU_MIXED
+    p = tau.Problem(wl, precision=prec)
+    p.step(1)
+    tau.tau_sync(p.handle)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("step")
+    p.step(1)
+    tau.tau_sync(p.handle)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    st = tau.tau_get_stats(p.handle)
+    p.close()
+    print(json.dumps({"profile_step": args.profile_step, "iters": int(st.last_iters), "graph": bool(st.graph)}))
+    return 0
+
+
 def run_matvec_f32_3d(args):
     import torch
 
@@ -600,6 +657,8 @@ def main():
         return run_matvec_only(args)
     if args.matvec_f32_3d:
         return run_matvec_f32_3d(args)
+    if args.profile_step:
+        return run_profile_step(args)
     return run_native(args)
 
 
