@@ -976,9 +976,11 @@ tau_status tau_setup(tau_problem* p) {
     TRY(upload(p, &p->beta[i], beta.data(), beta.size()));
     std::vector<double> q(N);
     {
-      // sin(pi t / K), t = 0..2K-1 (dense DST route and the half-length DST of the FFT route)
+      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: the half-length DST's input weights
+      // with the orthonormal scale folded in, (1/2) sqrt(2/K) sin(pi t / K), t = 0..K-1
       std::vector<double> st(2 * (size_t)K);
-      for (int t = 0; t < 2 * K; ++t) st[t] = std::sin(M_PI * t / K);
+      const double hs = p->route[i] == ROUTE_FFT ? 0.5 * std::sqrt(2.0 / K) : 1.0;
+      for (int t = 0; t < 2 * K; ++t) st[t] = hs * std::sin(M_PI * t / K);
       TRY(upload(p, &p->sintab[i], st.data(), st.size()));
     }
     if (p->route[i] == ROUTE_FFT) {

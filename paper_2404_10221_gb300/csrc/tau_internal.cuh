@@ -104,7 +104,7 @@ struct DimDataT {
   const vec2<T>* spec;  // FFT route: (a, b, c, d)_k, k = 0..K/2 (toep_pack_coeffs): the Toeplitz
                         // spectrum folded for the packed real FFT, scaled by 1/K (no eta)
   const T* s;           // FCD weights s_0..s_{n-1}
-  const T* sintab;      // sin(pi t / K), t = 0..2K-1
+  const T* sintab;      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: (1/2) sqrt(2/K) sin(pi t / K)
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
   const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I
 };

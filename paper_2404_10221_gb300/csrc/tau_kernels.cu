@@ -530,11 +530,14 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     // DST-I through a real FFT of length K = N+1 (complex FFT of length K2 = K/2):
     //   w_j = sin(pi j/K)(x_j + x_{K-j}) + (x_j - x_{K-j})/2  (x_0 = x_K = 0),  W = DFT_K(w):
     //   y_{2k} = -Im W_k,   y_{2k+1} - y_{2k-1} = Re W_k,  y_1 = Re W_0 / 2.
+    // The orthonormal scale h = sqrt(2/K)/2 of the packed outputs is folded into w (sn holds
+    // h sin(pi j/K)), so the recombination needs no multiplies.
     const int K = P.dim.K, K2 = K >> 1;
     const T* __restrict__ sn = P.dim.sintab;
     const V* __restrict__ tw2 = P.dim.twK2;
     V* cb = reinterpret_cast<V*>(xs + K);   // line l at cb + l*K (complex)
     const int lk2 = __ffs(K2) - 1;
+    const T hh = from_f<T>(0.25f) * P.dim.dsc;   // h / 2 = sqrt(2/K) / 4
     for (int b = tid; b < (lpb << lk2); b += TH) {
       const int l = b >> lk2, m = b & (K2 - 1);
       const T* row = xs + l * xst;
@@ -545,7 +548,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
         T v = from_f<T>(0.0f);
         if (j > 0) {
           const T xj = row[j - 1], xk = row[K - j - 1];
-          v = tfma(sn[j], xj + xk, from_f<T>(0.5f) * (xj - xk));
+          v = tfma(sn[j], xj + xk, hh * (xj - xk));
         }
         w[r] = v;
       }
@@ -555,8 +558,6 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     fft_dit<false>(cb, K, lpb, K2, tw2);
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
-    const T sc = P.dim.dsc;   // sqrt(2/K), precomputed per dimension
-    const T h = from_f<T>(0.5f) * sc;
     auto recombine = [&](int l, int k) {
       const int kk = (K2 - k) & (K2 - 1);
       const V* z = cb + l * K;
@@ -565,11 +566,11 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
       const V O2 = mk<V>(A.y + B.y, B.x - A.x);
       const V Pw = cmul(ldt(&tw2[K2 + k]), O2);
       T* row = xs + l * xst;
-      row[2 * k] = h * (E2.x + Pw.x);                       // sc Re W_k
-      if (k > 0) row[2 * k - 1] = -h * (E2.y + Pw.y);       // y_{2k} = -Im W_k
+      row[2 * k] = E2.x + Pw.x;                             // sc Re W_k
+      if (k > 0) row[2 * k - 1] = -(E2.y + Pw.y);           // y_{2k} = -Im W_k
       if (kk != k) {
-        row[2 * kk] = h * (E2.x - Pw.x);                    // sc Re W_{K2-k}
-        row[2 * kk - 1] = h * (E2.y - Pw.y);                // y_{2(K2-k)} = -Im W_{K2-k}
+        row[2 * kk] = E2.x - Pw.x;                          // sc Re W_{K2-k}
+        row[2 * kk - 1] = E2.y - Pw.y;                      // y_{2(K2-k)} = -Im W_{K2-k}
       }
     };
     // slot k in [0, K2/2) of each line: the pair (k, K2-k); slot 0 also takes k = K2/2
