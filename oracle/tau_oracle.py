@@ -22,7 +22,7 @@ __all__ = [
     "eval_field", "eval_field_interior", "rhs_F", "rhs_b", "gmres", "GmresResult",
     "step_direct", "time_march", "l2_error", "OracleSolver", "fcd_apply_line",
     "gmres_paper_form", "theorem_c", "two_sided_gmres", "two_sided_structured", "beta_tensor",
-    "apply_sine_diag",
+    "apply_sine_diag", "numerical_range_bounds", "spectral_summary",
 ]
 
 
@@ -472,6 +472,40 @@ def two_sided_gmres(prob, e_vec, b, ebar, tol, max_iter, u0_tilde=None) -> Gmres
     Abr = Pmh @ At @ Pmh
     x0 = np.zeros_like(b) if u0_tilde is None else u0_tilde
     return gmres(lambda v: Abr @ v, Pmh @ bt, x0, tol, max_iter)
+
+
+def numerical_range_bounds(A: np.ndarray, n_angles: int = 720):
+    """(v, r) of Eq. (numrag): the distance of the numerical range W(A) from the origin and the
+    numerical radius.  W(A) is convex; its support function in the direction e^{-i phi} is the largest
+    eigenvalue of the Hermitian part of e^{i phi} A, so r = max_phi lambda_max(H(e^{i phi} A)) and,
+    when 0 is not in W(A), v = max_phi lambda_min(H(e^{i phi} A)) (sampled on n_angles angles)."""
+    vmax, rmax = -np.inf, 0.0
+    for phi in np.linspace(0.0, 2 * np.pi, n_angles, endpoint=False):
+        R = np.exp(1j * phi) * A
+        w = np.linalg.eigvalsh(0.5 * (R + R.conj().T))
+        vmax = max(vmax, float(w[0]))
+        rmax = max(rmax, float(w[-1]))
+    return vmax, rmax
+
+
+def spectral_summary(prob, e_vec: np.ndarray, ebar: float) -> dict:
+    """Spectral diagnostics of §3 at small N (Figs. 1–3, Theorem GMRES), dense tier: the spread
+    max|lambda| / min|lambda| of Ã = E + B^{-1} S and of P^{-1} Ã (Eqs. (equi), (Pa)), and the
+    numerical-range angle of Ă = P^{-1/2} Ã P^{-1/2} (Eq. (Pls)): cos(theta) = v / r."""
+    B = dense_B(prob)
+    At = np.diag(e_vec) + np.linalg.solve(B, dense_S(prob))
+    P = dense_P(prob, ebar)
+    lam_a = np.linalg.eigvals(At)
+    lam_p = np.linalg.eigvals(np.linalg.solve(P, At))
+    w, Q = np.linalg.eigh(0.5 * (P + P.T))
+    Pmh = (Q * w ** -0.5) @ Q.T
+    v, r = numerical_range_bounds(Pmh @ At @ Pmh)
+    cos_t = v / r
+    return {"spread_A": float(np.abs(lam_a).max() / np.abs(lam_a).min()),
+            "spread_PA": float(np.abs(lam_p).max() / np.abs(lam_p).min()),
+            "re_PA_min": float(lam_p.real.min()), "re_PA_max": float(lam_p.real.max()),
+            "im_PA_absmax": float(np.abs(lam_p.imag).max()),
+            "v": v, "r": r, "sin_theta": float(math.sqrt(max(0.0, 1.0 - cos_t * cos_t)))}
 
 
 def theorem_c(ehat: float, echeck: float) -> float:

@@ -55,6 +55,16 @@ def test_example1_iterations_table2(row):
     assert abs(np.mean(s.iters) - it_paper) <= 1.0
 
 
+@pytest.mark.parametrize("row", _load("table2_example1.txt"))
+def test_example1_two_sided_iterations_table2(row):
+    # the TPGM column of Table 2: GMRES on Eq. (Pls)
+    alpha, M, Np1, _, _, it_paper = row
+    wl = W.paper_example(1, [alpha], int(Np1) - 1, int(M))
+    s = O.OracleSolver(wl.prob, wl.field_tables(), sided=2)
+    s.run(steps=40)
+    assert abs(np.mean(s.iters) - it_paper) <= 1.0
+
+
 @pytest.mark.parametrize("row", _load("table3_example2.txt"))
 def test_example2_iterations_table3(row):
     a1, a2, M, Np1, _, it_paper = row
