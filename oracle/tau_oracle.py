@@ -22,7 +22,8 @@ __all__ = [
     "eval_field", "eval_field_interior", "rhs_F", "rhs_b", "gmres", "GmresResult",
     "step_direct", "time_march", "l2_error", "OracleSolver", "fcd_apply_line",
     "gmres_paper_form", "theorem_c", "two_sided_gmres", "two_sided_structured", "beta_tensor",
-    "apply_sine_diag", "numerical_range_bounds", "spectral_summary",
+    "apply_sine_diag", "numerical_range_bounds", "spectral_summary", "strang_circulant",
+    "circulant_dense", "strang_pc_eigs", "dense_Pc", "apply_Pc_inv", "spgm",
 ]
 
 
@@ -474,6 +475,93 @@ def two_sided_gmres(prob, e_vec, b, ebar, tol, max_iter, u0_tilde=None) -> Gmres
     return gmres(lambda v: Abr @ v, Pmh @ bt, x0, tol, max_iter)
 
 
+def strang_circulant(t: np.ndarray) -> np.ndarray:
+    """First column of the Strang circulant s(T) of the symmetric Toeplitz T with first column t
+    (§4, Eq. (Pcir)): the central diagonals of T kept, wrapped around: c_k = t_k for k <= N/2,
+    c_k = t_{N-k} otherwise."""
+    N = t.shape[0]
+    c = np.array(t, dtype=np.float64)
+    for k in range(N // 2 + 1, N):
+        c[k] = t[N - k]
+    return c
+
+
+def circulant_dense(c: np.ndarray) -> np.ndarray:
+    """Dense circulant with first column c: C_{jk} = c_{(j-k) mod N}."""
+    N = c.shape[0]
+    j = np.arange(N)
+    return c[(j[:, None] - j[None, :]) % N]
+
+
+def _strang_eigs(prob):
+    """Per-dimension DFT eigenvalues of s(B_{alpha_i}) and s(S_{alpha_i}) (real: symmetric circulants)."""
+    bs, ss = [], []
+    for i in range(prob.d):
+        n, a = prob.n[i], prob.alpha[i]
+        tb = np.zeros(n)
+        tb[0] = 1.0 - a / 12.0
+        if n > 1:
+            tb[1] = a / 24.0
+        bs.append(np.fft.fft(strang_circulant(tb)).real)
+        ss.append(np.fft.fft(strang_circulant(fcd_weights(a, n))).real)
+    return bs, ss
+
+
+def strang_pc_eigs(prob, ebar: float) -> np.ndarray:
+    """Eigenvalues of P_c = ebar I + c(B)^{-1} c(S) (Eq. (Pcir); circulants commute) on the
+    d-dimensional Fourier basis, as an array of shape (N_d, ..., N_1)."""
+    bs, ss = _strang_eigs(prob)
+    eta = etas(prob)
+
+    def outer(vs):
+        out = vs[0]
+        for v in vs[1:]:
+            out = np.multiply.outer(v, out)
+        return out
+
+    cb = outer(bs)
+    cs = 0.0
+    for i in range(prob.d):
+        cs = cs + eta[i] * outer([ss[l] if l == i else bs[l] for l in range(prob.d)])
+    return ebar + cs / cb
+
+
+def dense_Pc(prob, ebar: float) -> np.ndarray:
+    """P_c = ebar I + c(B)^{-1/2} c(S) c(B)^{-1/2} = ebar I + c(B)^{-1} c(S), assembled densely from
+    the Strang circulants of every factor (Eq. (Pcir))."""
+    d = prob.d
+    sB = [circulant_dense(strang_circulant(np.r_[1.0 - prob.alpha[i] / 12.0, prob.alpha[i] / 24.0,
+                                                 np.zeros(max(prob.n[i] - 2, 0))][: prob.n[i]]))
+          for i in range(d)]
+    sS = [circulant_dense(strang_circulant(fcd_weights(prob.alpha[i], prob.n[i]))) for i in range(d)]
+    eta = etas(prob)
+    cB = kron_all([sB[i] for i in reversed(range(d))])
+    cS = 0.0
+    for i in range(d):
+        cS = cS + eta[i] * kron_all([sS[l] if l == i else sB[l] for l in reversed(range(d))])
+    return ebar * np.eye(cB.shape[0]) + np.linalg.solve(cB, cS)
+
+
+def apply_Pc_inv(prob, ebar: float, r: np.ndarray, pc: Optional[np.ndarray] = None) -> np.ndarray:
+    """P_c^{-1} r by the d-dimensional DFT (numpy FFT as the transform step)."""
+    if pc is None:
+        pc = strang_pc_eigs(prob, ebar)
+    X = np.fft.fftn(r.reshape(_shape(prob)))
+    return np.fft.ifftn(X / pc).real.reshape(-1)
+
+
+def spgm(prob, e_vec: np.ndarray, b: np.ndarray, ebar: float, tol: float, max_iter: int,
+         x0: Optional[np.ndarray] = None, toeps=None) -> GmresResult:
+    """SPGM (Table 1): GMRES on P_c^{-1} Ã u = P_c^{-1} b̃ with Ã = B^{-1} A, b̃ = B^{-1} b (Eq. (equi)),
+    i.e. the one-sided method with the τ preconditioner replaced by the Strang circulant one (the
+    reading of "one-sided Strang PGMRES"; B^{-1} by the DST, P_c^{-1} by the DFT)."""
+    binv = 1.0 / beta_tensor(prob)
+    pc = strang_pc_eigs(prob, ebar)
+    op = lambda v: apply_sine_diag(prob, apply_A(prob, e_vec, v, toeps), binv)
+    x0 = np.zeros_like(b) if x0 is None else x0
+    return gmres(op, apply_sine_diag(prob, b, binv), x0, tol, max_iter, lambda v: apply_Pc_inv(prob, ebar, v, pc))
+
+
 def numerical_range_bounds(A: np.ndarray, n_angles: int = 720):
     """(v, r) of Eq. (numrag): the distance of the numerical range W(A) from the origin and the
     numerical radius.  W(A) is convex; its support function in the direction e^{-i phi} is the largest
@@ -537,7 +625,8 @@ class OracleSolver:
     (M = ebar B + tau(S)) or two-sided (Eq. (Pls))."""
 
     def __init__(self, prob, tables: dict, ebar: Optional[float] = None, sided: int = 1):
-        """sided 1: one-sided (OPGM, Eq. (one-sided)); 2: two-sided (TPGM, Eq. (Pls))."""
+        """sided 1: one-sided (OPGM, Eq. (one-sided)); 2: two-sided (TPGM, Eq. (Pls));
+        3: the Strang circulant comparison method (SPGM, Table 1)."""
         self.prob = prob
         self.sided = sided
         self.t = tables
@@ -569,6 +658,8 @@ class OracleSolver:
         if self.sided == 2:
             res = two_sided_structured(p, e, b, self.ebar, p.tol, p.max_iter,
                                        None if p.x0_mode == 0 else x0, self.toeps)
+        elif self.sided == 3:
+            res = spgm(p, e, b, self.ebar, p.tol, p.max_iter, x0, self.toeps)
         else:
             res = gmres(lambda v: apply_A(p, e, v, self.toeps), b, x0, p.tol, p.max_iter,
                         lambda v: apply_Minv(p, self.ebar, v, self.mu))
