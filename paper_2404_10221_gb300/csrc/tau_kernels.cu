@@ -17,6 +17,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace tau {
 
 constexpr int PASS_THREADS = 128;
@@ -31,6 +33,11 @@ __device__ __forceinline__ double shfl_up(double v, int o) { return __shfl_up_sy
 __device__ __forceinline__ float shfl_up(float v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ df64 shfl_up(df64 v, int o) {
   return df64{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double shfl_idx(double v, int s) { return __shfl_sync(0xffffffffu, v, s); }
+__device__ __forceinline__ float shfl_idx(float v, int s) { return __shfl_sync(0xffffffffu, v, s); }
+__device__ __forceinline__ df64 shfl_idx(df64 v, int s) {
+  return df64{__shfl_sync(0xffffffffu, v.hi, s), __shfl_sync(0xffffffffu, v.lo, s)};
 }
 template <typename V> __device__ __forceinline__ V mk(decltype(V::x) x, decltype(V::x) y) { return V{x, y}; }
 // read-only cached load for table entries (plain load for the double-float pair type)
@@ -518,6 +525,112 @@ __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   }
 }
 
+// Prefix sums over the even slots of each line of the DST recombination:
+//   row[2k] <- sum_{i<=k} row[2i] - row[0]/2,  k < K2,
+// which turns the stored sc Re W_k into the odd outputs y_{2k+1}.  row[0] itself is left unchanged
+// by any partial scan, so it can be read until the final pass writes it.
+//
+// FP64: each thread scans a contiguous segment of K2 / spl slots sequentially (one addition per
+// slot; FP64 additions are the scarce resource), segment offsets by a block-wide shuffle scan.
+template <typename T>
+__device__ void prefix_segments(T* xs, int xst, int lpb, int K2) {
+  const int TH = blockDim.x, tid = threadIdx.x;
+  __shared__ T scan_incl[PASS_THREADS];
+  __shared__ T warp_tot[PASS_THREADS / 32];
+  int spl = TH / lpb;
+  if (spl < 1) spl = 1;
+  spl = 1 << (31 - __clz(spl));
+  if (spl > K2) spl = K2;
+  const int lspl = __ffs(spl) - 1;
+  const int seg = K2 >> lspl;
+  const int l = tid >> lspl, sg = tid & (spl - 1);
+  const bool act = l < lpb;
+  T* row = xs + (act ? l : 0) * xst;
+  T acc = from_f<T>(0.0f);
+  if (act) {
+    for (int k = sg * seg; k < (sg + 1) * seg; ++k) {
+      acc += row[2 * k];
+      row[2 * k] = acc;
+    }
+  }
+  const int lane = tid & 31, wp = tid >> 5;
+  T v = acc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T t = shfl_up(v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) warp_tot[wp] = v;
+  __syncthreads();
+  // read before the barrier that precedes the offset loop, the only writer of row[0]
+  const T half0 = from_f<T>(0.5f) * row[0];
+  for (int w2 = 0; w2 < wp; ++w2) v += warp_tot[w2];
+  scan_incl[tid] = v;
+  __syncthreads();
+  if (act) {
+    const T base = l * spl > 0 ? scan_incl[l * spl - 1] : from_f<T>(0.0f);
+    const T off = v - acc - base - half0;
+    for (int k = sg * seg; k < (sg + 1) * seg; ++k) row[2 * k] += off;
+  }
+  __syncthreads();
+}
+
+// FP32 pipes (float, double-float): warps scan 32 consecutive slots at a time with shuffles and a
+// running carry, so consecutive lanes touch consecutive slots (no bank conflicts) and a line owned
+// by one warp needs no block barrier.  A line shared by wpl > 1 warps (fewer lines than warps) is
+// split into wpl portions whose totals are combined through shared memory.
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T t = shfl_up(v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ void prefix_warps(T* xs, int xst, int lpb, int K2) {
+  const int NW = blockDim.x >> 5, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T half = from_f<T>(0.5f), z0 = from_f<T>(0.0f);
+  int wpl = lpb >= NW ? 1 : NW / lpb;
+  if (K2 < 32 * wpl) wpl = 1;
+  if (wpl == 1) {
+    for (int l = wid; l < lpb; l += NW) {
+      T* row = xs + l * xst;
+      const T h0 = half * row[0];
+      T carry = z0;
+      for (int c = 0; c < K2; c += 32) {
+        const int k = c + lane;
+        T v = k < K2 ? row[2 * k] : z0;
+        v = warp_incl_scan(v, lane) + carry;
+        if (k < K2) row[2 * k] = v - h0;
+        carry = shfl_idx(v, 31);
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  __shared__ T part_tot[PASS_THREADS / 32];
+  const int l = wid / wpl, pw = wid - l * wpl;
+  const int part = K2 / wpl, k0 = pw * part;
+  T* row = xs + l * xst;
+  T carry = z0;
+  for (int c = 0; c < part; c += 32) {
+    const int k = k0 + c + lane;
+    const T v = warp_incl_scan(row[2 * k], lane) + carry;
+    if (k != 0) row[2 * k] = v;   // the prefix at slot 0 is row[0] itself
+    carry = shfl_idx(v, 31);
+  }
+  if (lane == 0) part_tot[wid] = carry;
+  const T h0 = half * row[0];   // no warp writes row[0] before the barrier below
+  __syncthreads();
+  T off = -h0;
+  for (int q = l * wpl; q < wid; ++q) off += part_tot[q];
+  for (int c = 0; c < part; c += 32) row[2 * (k0 + c + lane)] += off;
+  __syncthreads();
+}
+
 // Orthonormal DST-I of every line in place: xs[l*xst + j] holds x_{j+1}; result y_{k} at
 // xs[l*xst + k-1].  FFT route: xst = 2K; the half-length complex FFT works in the line's upper
 // half [K, 2K), which holds no data (N < K).  Dense route: xst = N.
@@ -583,45 +696,11 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     __syncthreads();
     // prefix sums over the even slots of each line: y_{2k+1} = sum_{i<=k} sc Re W_i - sc Re W_0 / 2.
     // spl threads per line scan contiguous segments; segment offsets by a block-wide shuffle scan.
-    __shared__ T scan_incl[PASS_THREADS];
-    __shared__ T warp_tot[PASS_THREADS / 32];
-    int spl = TH / lpb;
-    if (spl < 1) spl = 1;
-    spl = 1 << (31 - __clz(spl));
-    if (spl > K2) spl = K2;
-    const int lspl = __ffs(spl) - 1;
-    const int seg = K2 >> lspl;
-    const int l = tid >> lspl, sg = tid & (spl - 1);
-    const bool act = l < lpb;
-    T* row = xs + (act ? l : 0) * xst;
-    T acc = from_f<T>(0.0f);
-    if (act) {
-      for (int k = sg * seg; k < (sg + 1) * seg; ++k) {
-        acc += row[2 * k];
-        row[2 * k] = acc;
-      }
+    if constexpr (std::is_same<T, double>::value) {
+      prefix_segments(xs, xst, lpb, K2);
+    } else {
+      prefix_warps(xs, xst, lpb, K2);
     }
-    const int lane = tid & 31, wp = tid >> 5;
-    T v = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T t = shfl_up(v, o);
-      if (lane >= o) v += t;
-    }
-    if (lane == 31) warp_tot[wp] = v;
-    __syncthreads();
-    // row[0] (sc Re W_0) is left unchanged by the segment scans and read before the barrier that
-    // precedes the offset loop, which is the only writer of it.
-    const T half0 = from_f<T>(0.5f) * row[0];
-    for (int w2 = 0; w2 < wp; ++w2) v += warp_tot[w2];
-    scan_incl[tid] = v;
-    __syncthreads();
-    if (act) {
-      const T base = l * spl > 0 ? scan_incl[l * spl - 1] : from_f<T>(0.0f);
-      const T off = v - acc - base - half0;
-      for (int k = sg * seg; k < (sg + 1) * seg; ++k) row[2 * k] += off;
-    }
-    __syncthreads();
   } else {
     const int K = P.dim.K;
     const T* __restrict__ st = P.dim.sintab;
