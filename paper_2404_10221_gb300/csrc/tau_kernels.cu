@@ -166,14 +166,17 @@ __device__ __forceinline__ void dit4(V& y0, V& y1, V& y2, V& y3, int i, int q, c
 // Forward complex DFT of length K (natural order in, digit-reversed out) on nl lines stored at
 // cb + l*cs, twiddles from the stage-packed table twp (twp_size(K) entries).  Each thread loads two
 // independent butterflies before computing either, so their shared-memory latencies overlap.
-// zero_hi: entries [K/2, K) are zero and not read (the first stage skips them).
+// zero_hi: entries [K/2, K) are zero and not read (the first stage skips them).  stop_last: the
+// last stage (size 4, or 2 for odd log2 K) is left to the caller (toep_mid).
 // Caller synchronises before; this synchronises after.
 template <typename V>
-__device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool zero_hi = false) {
+__device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool zero_hi = false,
+                        bool stop_last = false) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int lgK = __ffs(K) - 1;
+  const int min_r4 = (stop_last && !(lgK & 1)) ? 16 : 4;
   int size = K, lgs = lgK;
-  for (; size >= 4; size >>= 2, lgs -= 2) {
+  for (; size >= min_r4; size >>= 2, lgs -= 2) {
     const int q = size >> 2, lq = lgs - 2, lnb = lgK - 2;
     const V* __restrict__ tws = twp + (K - size);
     const int nb = K >> 2;
@@ -238,7 +241,7 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
     }
     __syncthreads();
   }
-  if (size == 2) {
+  if (size == 2 && !stop_last) {
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b >> (lgK - 1), loc = b & (nb - 1);
@@ -255,11 +258,19 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
 // dif_pos() describes), natural order out, same twiddle table as fft_dif.  INV: the unnormalised
 // inverse (times K).  half_out: only outputs [0, K/2) are needed (the last stage skips the rest).
 template <bool INV, typename V>
-__device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool half_out = false) {
+__device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool half_out = false,
+                        bool skip_first = false) {
   const int T = blockDim.x, tid = threadIdx.x;
   const int lgK = __ffs(K) - 1;
   int size = 4, lgs = 2;
-  if (lgK & 1) {
+  if (skip_first && !(lgK & 1)) {
+    size = 16;
+    lgs = 4;
+  }
+  if ((lgK & 1) && skip_first) {
+    size = 8;
+    lgs = 3;
+  } else if (lgK & 1) {
     const int nb = K >> 1;
     for (int b = tid; b < nl * nb; b += T) {
       const int l = b >> (lgK - 1), loc = b & (nb - 1);
@@ -330,13 +341,8 @@ __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
   }
 }
 
-// Multiply the length-2K real DFT of the packed sequence by the real symmetric circulant
-// spectrum, working on the packed half-length DFT Z in place (digit-reversed layout of fft_dif).
-// For each pair (k, K-k) the step is the linear map
-//   Z'_k = a_k Z_k + b_k conj(Z_{K-k}),   Z'_{K-k} = c_k conj(Z_k) + d_k Z_{K-k}
-// whose coefficients spec[4k..4k+3] = (a, b, c, d) fold the unpacking (E = Z_k + conj Z_{K-k},
-// O = -i (Z_k - conj Z_{K-k}), Y_k = (E + W_k O)/2, W_k = exp(-i pi k/K)), the multiply by lambda
-// and the repacking, scaled by 1/K for the unnormalised inverse (toep_pack_coeffs).
+// FP64 route of the spectral step: one pass over the pairs (k, K-k) in the digit-reversed layout
+// (the fused toep_mid below raises the FP64 kernel's register pressure more than it saves).
 template <typename V>
 __device__ __forceinline__ void toep_pair(V* x, int k, int K, const V* __restrict__ spec) {
   const int kk = (K - k) & (K - 1);
@@ -362,6 +368,127 @@ __device__ void toep_spectral(V* cb, int cs, int nl, int K, const V* __restrict_
     V* x = cb + l * cs;
     toep_pair(x, k, K, spec);
     if (k == 0 && K > 1) toep_pair(x, K >> 1, K, spec);
+  }
+  __syncthreads();
+}
+
+// Spectral step of the Toeplitz product: multiply the length-2K real DFT of the packed sequence by
+// the real symmetric circulant spectrum, working on the packed half-length DFT Z.  For each pair
+// (k, K-k) the step is the linear map
+//   Z'_k = a_k Z_k + b_k conj(Z_{K-k}),   Z'_{K-k} = c_k conj(Z_k) + d_k Z_{K-k}
+// whose coefficients spec[4k..4k+3] = (a, b, c, d) fold the unpacking (E = Z_k + conj Z_{K-k},
+// O = -i (Z_k - conj Z_{K-k}), Y_k = (E + W_k O)/2, W_k = exp(-i pi k/K)), the multiply by lambda
+// and the repacking, scaled by 1/K for the unnormalised inverse (toep_pack_coeffs).
+// One pair in registers: A = Z_k, B = Z_{K-k}, k <= K/2; a self-paired k (0 or K/2) updates A alone.
+template <typename V>
+__device__ __forceinline__ void spec_apply(V& A, V& B, int k, bool self, const V* __restrict__ spec) {
+  const V ca = ldt(&spec[4 * k]), cbv = ldt(&spec[4 * k + 1]);
+  const V Bv = self ? A : B;
+  const V nA = mk<V>(tfma(ca.x, A.x, tfma(-ca.y, A.y, tfma(cbv.x, Bv.x, cbv.y * Bv.y))),
+                     tfma(ca.x, A.y, tfma(ca.y, A.x, tfma(cbv.y, Bv.x, -cbv.x * Bv.y))));
+  if (!self) {
+    const V cc = ldt(&spec[4 * k + 2]), cd = ldt(&spec[4 * k + 3]);
+    B = mk<V>(tfma(cc.x, A.x, tfma(cc.y, A.y, tfma(cd.x, B.x, -cd.y * B.y))),
+              tfma(cc.y, A.x, tfma(-cc.x, A.y, tfma(cd.x, B.y, cd.y * B.x))));
+  }
+  A = nA;
+}
+
+// u holds Z_{k1}, w holds Z_{K-k1}: apply the pair's map whichever of the two has the lower index.
+template <typename V>
+__device__ __forceinline__ void spec_pairup(V& u, V& w, int k1, int K, const V* __restrict__ spec) {
+  const int k2 = (K - k1) & (K - 1);
+  if (k1 == k2) spec_apply(u, u, k1, true, spec);
+  else if (k1 < k2) spec_apply(u, w, k1, false, spec);
+  else spec_apply(w, u, k2, false, spec);
+}
+
+// The forward DIF's last stage, the spectral map and the inverse DIT's first stage in one pass.
+// The last DIF stage (radix R = 4, or 2 for odd log2 K; no twiddles) leaves in the R consecutive
+// slots of group g the frequencies k_lo + r K/R, r < R, with g the digit reversal of k_lo; the
+// partners K - k of a group's frequencies fill group g' = rev(K/R - k_lo) in reversed slot order.
+// One thread takes both groups from shared memory (two contiguous runs, no bank conflicts),
+// finishes the forward transform, applies the R 2x2 maps and starts the inverse transform.
+template <typename V>
+__device__ __forceinline__ void toep_mid_r4(V* x, int klo, int lgG, int K, const V* __restrict__ spec) {
+  const int G = 1 << lgG;
+  const int g = rev4(klo, lgG), g2 = rev4((G - klo) & (G - 1), lgG);
+  const V* __restrict__ none = nullptr;
+  V a0 = x[4 * g], a1 = x[4 * g + 1], a2 = x[4 * g + 2], a3 = x[4 * g + 3];
+  dif4(a0, a1, a2, a3, 0, 1, none);
+  if (g2 != g) {
+    V b0 = x[4 * g2], b1 = x[4 * g2 + 1], b2 = x[4 * g2 + 2], b3 = x[4 * g2 + 3];
+    dif4(b0, b1, b2, b3, 0, 1, none);
+    spec_pairup(a0, b3, klo, K, spec);
+    spec_pairup(a1, b2, klo + G, K, spec);
+    spec_pairup(a2, b1, klo + 2 * G, K, spec);
+    spec_pairup(a3, b0, klo + 3 * G, K, spec);
+    dit4<true, false>(b0, b1, b2, b3, 0, 1, none);
+    x[4 * g2] = b0;
+    x[4 * g2 + 1] = b1;
+    x[4 * g2 + 2] = b2;
+    x[4 * g2 + 3] = b3;
+  } else if (klo == 0) {
+    spec_pairup(a0, a0, 0, K, spec);
+    spec_pairup(a2, a2, 2 * G, K, spec);
+    spec_pairup(a1, a3, G, K, spec);
+  } else {  // klo = G/2: the group pairs with itself, slot r with slot 3 - r
+    spec_pairup(a0, a3, klo, K, spec);
+    spec_pairup(a1, a2, klo + G, K, spec);
+  }
+  dit4<true, false>(a0, a1, a2, a3, 0, 1, none);
+  x[4 * g] = a0;
+  x[4 * g + 1] = a1;
+  x[4 * g + 2] = a2;
+  x[4 * g + 3] = a3;
+}
+
+template <typename V>
+__device__ __forceinline__ void toep_mid_r2(V* x, int klo, int lgG, int K, const V* __restrict__ spec) {
+  const int G = 1 << lgG;
+  const int g = rev4(klo, lgG), g2 = rev4((G - klo) & (G - 1), lgG);
+  const V p0 = x[2 * g], p1 = x[2 * g + 1];
+  V a0 = cadd(p0, p1), a1 = csub(p0, p1);
+  if (g2 != g) {
+    const V q0 = x[2 * g2], q1 = x[2 * g2 + 1];
+    V b0 = cadd(q0, q1), b1 = csub(q0, q1);
+    spec_pairup(a0, b1, klo, K, spec);
+    spec_pairup(a1, b0, klo + G, K, spec);
+    x[2 * g2] = cadd(b0, b1);
+    x[2 * g2 + 1] = csub(b0, b1);
+  } else if (klo == 0) {
+    spec_pairup(a0, a0, 0, K, spec);
+    spec_pairup(a1, a1, G, K, spec);
+  } else {  // klo = G/2
+    spec_pairup(a0, a1, klo, K, spec);
+  }
+  x[2 * g] = cadd(a0, a1);
+  x[2 * g + 1] = csub(a0, a1);
+}
+
+// The forward DIF's last stage, the spectral map and the inverse DIT's first stage in one pass.
+// The last DIF stage (radix R = 4, or 2 for odd log2 K; no twiddles) leaves in the R consecutive
+// slots of group g the frequencies k_lo + r K/R, r < R, with g the digit reversal of k_lo; the
+// partners K - k of a group's frequencies fill group g' = rev(K/R - k_lo) in reversed slot order.
+// Work item k_lo in [0, G/2] (G = K/R) takes both groups from shared memory (two contiguous runs),
+// finishes the forward transform, applies the R 2x2 maps and starts the inverse transform; item
+// slot 0 also takes the self-paired k_lo = G/2, so every lane has work.
+template <typename V>
+__device__ void toep_mid(V* cb, int cs, int nl, int K, const V* __restrict__ spec) {
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int lgK = __ffs(K) - 1;
+  const int lgG = (lgK & 1) ? lgK - 1 : lgK - 2, G = 1 << lgG;
+  const int H = G > 1 ? G >> 1 : 1, lh = __ffs(H) - 1;
+  for (int t = tid; t < (nl << lh); t += T) {
+    const int l = t >> lh, klo = t & (H - 1);
+    V* x = cb + l * cs;
+    const int items = (klo == 0 && G > 1) ? 2 : 1;
+#pragma unroll 1
+    for (int it = 0; it < items; ++it) {
+      const int kl = it ? G >> 1 : klo;
+      if (lgK & 1) toep_mid_r2(x, kl, lgG, K, spec);
+      else toep_mid_r4(x, kl, lgG, K, spec);
+    }
   }
   __syncthreads();
 }
@@ -478,19 +605,26 @@ __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_FFT) {
     const int K = P.dim.K;
-    // y_N = 0 completes z_{K/2-1}; z_j for j >= K/2 is zero and, for K >= 4, never read (the
-    // first DIF stage skips it); K = 2 has no radix-4 stage and zeroes it.
-    const int zn = K >= 4 ? 1 : 2 * K - N;
+    // y_N = 0 completes z_{K/2-1}; z_j for j >= K/2 is zero and never read when the first DIF
+    // stage skips it (K >= 4, or K > 4 where the last DIF stage is fused into toep_mid).
+    constexpr bool fused = !std::is_same<T, double>::value;
+    const int zn = (fused ? K > 4 : K >= 4) ? 1 : 2 * K - N;
     for (int b = tid; b < lpb * zn; b += TH) {
       const int l = b / zn;
       xs[l * xst + N + (b - l * zn)] = from_f<T>(0.0f);
     }
     __syncthreads();
     V* cb = reinterpret_cast<V*>(xs);
-    fft_dif(cb, K, lpb, K, P.dim.twK, K >= 4);
-    toep_spectral(cb, K, lpb, K, P.dim.spec);
-    // outputs y_t, t < N, are z_j for j < K/2
-    fft_dit<true>(cb, K, lpb, K, P.dim.twK, true);
+    // outputs y_t, t < N, are z_j for j < K/2 (half_out of the inverse's last stage)
+    if constexpr (fused) {
+      fft_dif(cb, K, lpb, K, P.dim.twK, K > 4, true);
+      toep_mid(cb, K, lpb, K, P.dim.spec);
+      fft_dit<true>(cb, K, lpb, K, P.dim.twK, true, true);
+    } else {
+      fft_dif(cb, K, lpb, K, P.dim.twK, K >= 4);
+      toep_spectral(cb, K, lpb, K, P.dim.spec);
+      fft_dit<true>(cb, K, lpb, K, P.dim.twK, true);
+    }
   } else {
     const T* __restrict__ s = P.dim.s;
     T acc[8];
