@@ -1,4 +1,5 @@
-// CUDA kernels of the τ-preconditioned GMRES solver (sm_103a, FP64).
+// CUDA kernels of the τ-preconditioned GMRES solver (sm_103a; FP64, with FP32 and double-float
+// instantiations of the line passes and Gram-Schmidt kernels for the other precisions).
 //
 // Line passes: the matvec A x = B_alpha (e∘x) + sum_i eta_i (⊗_{l!=i} B_l ⊗ S_i) x of Eq. (tls),
 // the right-hand side of Eq. (tls) and the DST-I based τ solve of Eqs. (Pa), (diag) are applied
@@ -8,11 +9,13 @@
 //     a = (B_i ... B_1)(e∘x) + sum_{l<=i} eta_l (B_i..S_l..B_1) x,      c = (B_i ... B_1) x,
 // so the pass over dimension i+1 computes a' = B_{i+1} a + eta_{i+1} S_{i+1} c, c' = B_{i+1} c.
 //
-// FFT route (n_i + 1 = K = 2^p): the Toeplitz product S_i x uses the circulant embedding of
-// length 2K and the DST-I of length n_i the odd extension of length 2K; both real transforms of
-// length 2K run as one complex FFT of length K (in-place radix-4 decimation in frequency, whose
-// digit-reversed output is read through dif_pos(); the inverse is the mirrored decimation in
-// time, so no reordering pass is needed).  Dense route (any n_i): explicit O(n_i) sums per output.
+// FFT route (n_i + 1 = K = 2^p): the Toeplitz product S_i x uses the circulant embedding of length
+// 2K, whose real transforms run as one complex FFT of length K in place in the padded line (radix-4
+// decimation in frequency, digit-reversed output located by dif_pos(); the spectral step works in
+// that layout; the inverse is the mirrored decimation in time, so no reordering pass is needed).
+// The DST-I of length n_i is a real FFT of length K: a complex FFT of length K/2 (decimation in time
+// fed by a digit-reversed scatter), a pair recombination and a prefix sum.  Dense route (any n_i):
+// explicit O(n_i) sums per output.
 #include "tau_internal.cuh"
 
 #include <math.h>
@@ -24,7 +27,7 @@ namespace tau {
 constexpr int PASS_THREADS = 128;
 
 // ---------------------------------------------------------------------------
-// complex helpers (FP64)
+// element-type helpers (double, float, double-float) and complex arithmetic
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
@@ -257,6 +260,7 @@ __device__ void fft_dif(V* cb, int cs, int nl, int K, const V* __restrict__ twp,
 // Complex DFT of length K by decimation in time: digit-reversed in (the order fft_dif leaves and
 // dif_pos() describes), natural order out, same twiddle table as fft_dif.  INV: the unnormalised
 // inverse (times K).  half_out: only outputs [0, K/2) are needed (the last stage skips the rest).
+// skip_first: the first stage (size 4, or 2 for odd log2 K) was done by the caller (toep_mid).
 template <bool INV, typename V>
 __device__ void fft_dit(V* cb, int cs, int nl, int K, const V* __restrict__ twp, bool half_out = false,
                         bool skip_first = false) {

@@ -76,3 +76,28 @@ def test_batch_rejects_mismatched_steps():
         tau.tau_batch_create([a.handle, c.handle])
     a.close()
     c.close()
+
+
+def test_batch_of_uneven_3d_instances():
+    # d = 3 with uneven n_i per axis, FFT and dense routes mixed, in one batch
+    tau = _tau()
+    shapes = [(15, 7, 31), (7, 15, 3), (31, 3, 7), (12, 7, 15)]
+    wls = []
+    for k, n in enumerate(shapes):
+        base = W.c3_3d(n=n[0], M=3)
+        base.prob.n = list(n)
+        base.prob.alpha = [1.2 + 0.1 * k, 1.5, 1.8 - 0.1 * k]
+        wls.append(W.manufactured(f"3d_{n}", base.prob, base.e.terms, 2, 2, 1.0))
+    alone = [_alone(wl, 0) for wl in wls]
+    probs = [tau.Problem(wl) for wl in wls]
+    b = tau.tau_batch_create([p.handle for p in probs])
+    tau.tau_batch_step(b, 3)
+    assert tau.tau_batch_sync(b) == tau.TAU_OK
+    tau.tau_batch_destroy(b)
+    for wl, (ua, ia), p in zip(wls, alone, probs):
+        ub = p.solution().cpu().numpy()
+        assert np.array_equal(ua, ub)
+        ref = O.OracleSolver(wl.prob, wl.field_tables())
+        ref.run()
+        assert np.linalg.norm(ub - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+        p.close()
