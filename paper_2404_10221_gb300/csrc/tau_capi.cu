@@ -421,12 +421,10 @@ tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandl
   TRY(enq_mv<T>(p, st, it, 1.0, FIN_NONE, nullptr, true));
   const int ld = RED_BLOCKS;
   T* V = as<T>(p->V);
-  KL(launch_dots<T>(V, p->n_tot, p->g, p->pdots, ld, st));
-  KL(launch_reduce_dots(p->pdots, ld, p->g, p->h1, st));
-  KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h1, p->pdots, ld, 0, st));
-  KL(launch_reduce_dots(p->pdots, ld, p->g, p->h2, st));
-  KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h2, p->pnorm, ld, 1, st));
-  KL(launch_givens(p->g, p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->pnorm, p->desc.max_iter + 1, h, use_cond, st));
+  KL(launch_dots<T>(V, p->n_tot, p->g, p->pdots, ld, p->h1, st));
+  KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h1, p->pdots, ld, p->h2, st));
+  const GivensArgs ga{p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->desc.max_iter + 1, use_cond, h};
+  KL(launch_update_norm_givens<T>(V, p->n_tot, p->g, p->h2, p->pnorm, ga, st));
   KL(launch_scale_next<T>(V, p->n_tot, p->g, st));
   return TAU_OK;
 }
@@ -483,7 +481,7 @@ tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditiona
   r.out = p->tmp;
   TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false, &p->ir->skip_resid));
   KL(launch_norm_partial(p->tmp, p->n_tot, p->g, p->pnorm, st));
-  KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, h, h_in, use_cond, st));
+  KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, st));
   KL(launch_scale_to_f32(p->tmp, p->V32, p->n_tot, p->ir, st));
   return TAU_OK;
 }
@@ -505,12 +503,10 @@ tau_status enq_mx_inner(tau_problem* p, cudaStream_t st, cudaGraphConditionalHan
   av.g = p->gin;
   TRY(enq_mv<float>(p, st, av, 1.0, FIN_NONE, nullptr, false));
   const int ld = RED_BLOCKS;
-  KL(launch_dots<float>(p->V32, p->n_tot, p->gin, p->pdots, ld, st));
-  KL(launch_reduce_dots(p->pdots, ld, p->gin, p->h1in, st));
-  KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h1in, p->pdots, ld, 0, st));
-  KL(launch_reduce_dots(p->pdots, ld, p->gin, p->h2in, st));
-  KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h2in, p->pnorm, ld, 1, st));
-  KL(launch_givens(p->gin, p->Hin, p->csin, p->snin, p->gvin, p->h1in, p->h2in, p->pnorm, p->kin + 1, h, use_cond, st));
+  KL(launch_dots<float>(p->V32, p->n_tot, p->gin, p->pdots, ld, p->h1in, st));
+  KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h1in, p->pdots, ld, p->h2in, st));
+  const GivensArgs ga{p->Hin, p->csin, p->snin, p->gvin, p->h1in, p->h2in, p->kin + 1, use_cond, h};
+  KL(launch_update_norm_givens<float>(p->V32, p->n_tot, p->gin, p->h2in, p->pnorm, ga, st));
   KL(launch_scale_next<float>(p->V32, p->n_tot, p->gin, st));
   return TAU_OK;
 }

@@ -16,6 +16,15 @@ constexpr int MAX_ITER_CAP = 1000;
 // Blocks used by the reduction kernels (partials per reduction).
 constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
 
+// Blocks of 256 threads for a vector kernel over n elements: about 8 elements a thread, at most
+// RED_BLOCKS, so the kernels of a small problem leave the rest of the GPU to the problems running
+// beside it (batched and served forms).  Producers and consumers of per-block partial sums use the
+// same count.
+__host__ __device__ inline int red_blocks(int64_t n) {
+  const int64_t b = (n + 2047) / 2048;
+  return b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : (int)b);
+}
+
 enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2 };
 
 // What the value computed by a matvec pass becomes at the last dimension.
@@ -183,7 +192,7 @@ struct GmresDev {
   int k;             // iterations of the finished step
   int notconv;       // sticky: some step hit max_iter
   int max_iter;
-  int pad;
+  unsigned int tickets;  // last-block counter of the fused Gram-Schmidt reductions (0 between launches)
   double tol;
   double beta;       // ||r_0||
   double relres;
@@ -231,17 +240,31 @@ cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cud
 
 // GMRES building blocks
 // w = V_{j+1} (the slot of the next basis vector) in the CGS2 kernels below; S is the storage
-// type of the basis (products in S, reductions in FP64).
+// type of the basis (products in S, reductions in FP64).  Each kernel's per-block partial sums are
+// finished by the block that completes last (a ticket counter in GmresDev), so a CGS2 iteration is
+// three launches: h1 = V^T w; w -= V h1 and h2 = V^T w; w -= V h2, ||w|| and the Givens column.
 template <typename S>
-cudaError_t launch_dots(const S* V, int64_t n, const GmresDev* g, double* partial, int ld_partial, cudaStream_t st);
-cudaError_t launch_reduce_dots(const double* partial, int ld_partial, const GmresDev* g, double* h,
-                               cudaStream_t st);
+cudaError_t launch_dots(const S* V, int64_t n, GmresDev* g, double* partial, int ld_partial, double* h,
+                        cudaStream_t st);
 template <typename S>
-cudaError_t launch_update_dots(S* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld_partial,
-                               int want_norm, cudaStream_t st);
-cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* h1,
-                          const double* h2, const double* partial_norm, int ldH,
-                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+cudaError_t launch_update_dots(S* V, int64_t n, GmresDev* g, const double* h_in, double* partial, int ld_partial,
+                               double* h_out, cudaStream_t st);
+// Arguments of the Givens step that closes an Arnoldi column (Hessenberg column j = h1 + h2 and
+// ||w||, rotations, residual estimate, stop test, graph condition).
+struct GivensArgs {
+  double* H;
+  double* cs;
+  double* sn;
+  double* gv;
+  const double* h1;
+  const double* h2;
+  int ldH;
+  int use_cond;
+  cudaGraphConditionalHandle cond;
+};
+template <typename S>
+cudaError_t launch_update_norm_givens(S* V, int64_t n, GmresDev* g, const double* h2, double* partial_norm,
+                                      const GivensArgs& ga, cudaStream_t st);
 template <typename S>
 cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st);
 template <typename S>
@@ -272,7 +295,7 @@ cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);
 // Residual of the zero initial guess: r = b on the first sweep (the FP64 residual passes are
 // skipped through ir->skip_resid); later sweeps compute b - A x.
 cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st);
-cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm,
+cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm, int64_t n,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
                               cudaStream_t st);
 cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st);

@@ -1341,11 +1341,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// partial[i * ld + blockIdx.x] = sum_{this block's elements} w * V_i, i = 0..j, with w = V_{j+1}.
-// Per-element products and per-thread sums in the storage type S; block and grid sums in FP64.
+// Last-block completion: every block publishes its partial results, fences, and draws a ticket;
+// the block that draws the last one sees all partials and finishes the reduction.  The counter is
+// the problem's own (GmresDev.tickets), so concurrent problems never share it; the last block
+// resets it for the next launch.
+__device__ __forceinline__ bool last_block(unsigned int* tickets) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(tickets, 1u);
+    s_last = (t == gridDim.x - 1);
+    if (s_last) *tickets = 0u;
+  }
+  __syncthreads();
+  return s_last;
+}
+
+// h[i] = sum_b partial[i * ld + b], i = 0..jj, by one block (a warp per i); the partials come from
+// other SMs, so they are read through L2.
+__device__ void reduce_partials(const double* partial, int ld, int jj, double* h) {
+  const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i <= jj; i += nw) {
+    double s = 0.0;
+    for (int b = ln; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[(int64_t)i * ld + b]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (ln == 0) h[i] = s;
+  }
+}
+
+// partial[i * ld + blockIdx.x] = sum_{this block's elements} w * V_i, i = 0..j, with w = V_{j+1};
+// the last block sums them into h.  Per-element products and per-thread sums in the storage type
+// S; block and grid sums in FP64.
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, int64_t n,
-                                                      const GmresDev* __restrict__ g, double* partial, int ld) {
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, int64_t n, GmresDev* g,
+                                                      double* partial, int ld, double* h) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   if (g->done) return;
   const int jj = g->j;
@@ -1369,44 +1399,75 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, i
       }
     }
   }
+  if (last_block(&g->tickets)) reduce_partials(partial, ld, jj, h);
 }
 
 template <typename S>
-cudaError_t launch_dots(const S* V, int64_t n, const GmresDev* g, double* partial, int ld, cudaStream_t st) {
-  k_dots<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, partial, ld);
+cudaError_t launch_dots(const S* V, int64_t n, GmresDev* g, double* partial, int ld, double* h, cudaStream_t st) {
+  k_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, partial, ld, h);
   return cudaGetLastError();
 }
-template cudaError_t launch_dots<double>(const double*, int64_t, const GmresDev*, double*, int, cudaStream_t);
-template cudaError_t launch_dots<float>(const float*, int64_t, const GmresDev*, double*, int, cudaStream_t);
-template cudaError_t launch_dots<df64>(const df64*, int64_t, const GmresDev*, double*, int, cudaStream_t);
+template cudaError_t launch_dots<double>(const double*, int64_t, GmresDev*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_dots<float>(const float*, int64_t, GmresDev*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_dots<df64>(const df64*, int64_t, GmresDev*, double*, int, double*, cudaStream_t);
 
-// h[i] = sum_b partial[i * ld + b], i = 0..j (one warp per i)
-__global__ void k_reduce_dots(const double* __restrict__ partial, int ld, const GmresDev* __restrict__ g, double* h) {
-  if (g->done) return;
-  const int jj = g->j;
-  const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31;
-  const int nw = blockDim.x >> 5;
-  for (int i = warp; i <= jj; i += nw) {
-    double s = 0.0;
-    for (int b = ln; b < RED_BLOCKS; b += 32) s += partial[(int64_t)i * ld + b];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (ln == 0) h[i] = s;
+// The Givens step closing Arnoldi column j (one thread): H(:, j) = h1 + h2 with H(j+1, j) = ||w||
+// (nsq = ||w||^2), earlier rotations applied, the new rotation, the residual estimate |g_{j+1}|,
+// the stop test ||r_j|| <= tol ||r_0|| (or the iteration cap, or breakdown) and the graph condition.
+__device__ void givens_column(GmresDev* g, const GivensArgs& a, double nsq) {
+  const int j = g->j;
+  const double hn = sqrt(nsq);
+  double* col = a.H + (int64_t)j * a.ldH;
+  for (int i = 0; i <= j; ++i) col[i] = a.h1[i] + a.h2[i];
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
+    col[i + 1] = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double rr = hypot(col[j], col[j + 1]);
+  double c = 1.0, sgv = 0.0;
+  if (rr > 0.0) {
+    c = col[j] / rr;
+    sgv = col[j + 1] / rr;
+  }
+  a.cs[j] = c;
+  a.sn[j] = sgv;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  a.gv[j + 1] = -sgv * a.gv[j];
+  a.gv[j] = c * a.gv[j];
+  const double res = fabs(a.gv[j + 1]);
+  g->hnorm = hn;
+  g->relres = res / g->beta;
+  const bool conv = res <= g->tol * g->beta;
+  const bool cap = (j + 1) >= g->max_iter;
+  const bool brk = !(hn > 0.0);
+  if (conv || cap || brk) {
+    g->done = 1;
+    g->k = j + 1;
+    if (!conv && !brk) g->notconv = 1;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+  } else {
+    g->j = j + 1;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, 1);
   }
 }
 
-cudaError_t launch_reduce_dots(const double* partial, int ld, const GmresDev* g, double* h, cudaStream_t st) {
-  k_reduce_dots<<<1, 1024, 0, st>>>(partial, ld, g, h);
-  return cudaGetLastError();
-}
-
-// w -= sum_i h_i V_i (w = V_{j+1}); then either partial dots with V_i (CGS2 second pass) or ||w||^2.
+// w -= sum_i h_i V_i (w = V_{j+1}); then, with norm_only = false, partial dots of the updated w with
+// V_i (CGS2 second pass) finished into h_out by the last block, or, with norm_only = true, ||w||^2
+// finished by the last block, which then runs the Givens step.
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, const GmresDev* __restrict__ g,
+__global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, GmresDev* g,
                                                              const double* __restrict__ h, double* partial, int ld,
-                                                             int want_norm) {
+                                                             double* h_out, int norm_only, const GivensArgs ga) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   __shared__ S hs[MAX_ITER_CAP + 1];
-  if (g->done) return;
+  if (g->done) {
+    // a finished step: the loop body still runs once after the prologue found r_0 = 0
+    if (norm_only && ga.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ga.cond, 0);
+    return;
+  }
   const int jj = g->j;
   S* w = V + (int64_t)(jj + 1) * n;
   for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = from_d<S>(h[i]);
@@ -1418,9 +1479,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, co
     w[idx] = wv;
     nacc = tfma(wv, wv, nacc);
   }
-  if (want_norm) {
+  if (norm_only) {
     const double s = block_sum(to_d(nacc), sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (last_block(&g->tickets)) {
+      double t = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&partial[b]);
+      t = block_sum(t, sh);
+      if (threadIdx.x == 0) givens_column(g, ga, t);
+    }
     return;
   }
   __syncthreads();
@@ -1444,82 +1511,33 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, co
       }
     }
   }
+  if (last_block(&g->tickets)) reduce_partials(partial, ld, jj, h_out);
 }
 
 template <typename S>
-cudaError_t launch_update_dots(S* V, int64_t n, const GmresDev* g, const double* h, double* partial, int ld,
-                               int want_norm, cudaStream_t st) {
-  k_update_dots<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, want_norm);
+cudaError_t launch_update_dots(S* V, int64_t n, GmresDev* g, const double* h, double* partial, int ld,
+                               double* h_out, cudaStream_t st) {
+  GivensArgs none{};
+  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, h_out, 0, none);
   return cudaGetLastError();
 }
-template cudaError_t launch_update_dots<double>(double*, int64_t, const GmresDev*, const double*, double*, int, int,
-                                                cudaStream_t);
-template cudaError_t launch_update_dots<float>(float*, int64_t, const GmresDev*, const double*, double*, int, int,
-                                               cudaStream_t);
-template cudaError_t launch_update_dots<df64>(df64*, int64_t, const GmresDev*, const double*, double*, int, int,
-                                              cudaStream_t);
-
-// Column j of the Hessenberg matrix: h1 + h2 (CGS2), ||w||; previous rotations, new rotation,
-// residual estimate |g_{j+1}|, stopping test ||r_j|| <= tol ||r_0|| (§4), cap and breakdown.
-__global__ void k_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* __restrict__ h1,
-                         const double* __restrict__ h2, const double* __restrict__ pnorm, int ldH,
-                         cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
-  if (g->done) {
-    if (use_cond && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
-    return;
-  }
-  const int j = g->j;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += pnorm[b];
-  s = block_sum(s, sh);
-  if (threadIdx.x != 0) return;
-  const double hn = sqrt(s);
-  double* col = H + (int64_t)j * ldH;
-  for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
-  col[j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-    col[i] = t;
-  }
-  const double rr = hypot(col[j], col[j + 1]);
-  double c = 1.0, sgv = 0.0;
-  if (rr > 0.0) {
-    c = col[j] / rr;
-    sgv = col[j + 1] / rr;
-  }
-  cs[j] = c;
-  sn[j] = sgv;
-  col[j] = rr;
-  col[j + 1] = 0.0;
-  gv[j + 1] = -sgv * gv[j];
-  gv[j] = c * gv[j];
-  const double res = fabs(gv[j + 1]);
-  g->hnorm = hn;
-  g->relres = res / g->beta;
-  const bool conv = res <= g->tol * g->beta;
-  const bool cap = (j + 1) >= g->max_iter;
-  const bool brk = !(hn > 0.0);
-  if (conv || cap || brk) {
-    g->done = 1;
-    g->k = j + 1;
-    if (!conv && !brk) g->notconv = 1;
-    if (use_cond) cudaGraphSetConditional(cond, 0);
-  } else {
-    g->j = j + 1;
-    if (use_cond) cudaGraphSetConditional(cond, 1);
-  }
-}
-
-cudaError_t launch_givens(GmresDev* g, double* H, double* cs, double* sn, double* gv, const double* h1,
-                          const double* h2, const double* pnorm, int ldH, cudaGraphConditionalHandle cond,
-                          int use_cond, cudaStream_t st) {
-  k_givens<<<1, 256, 0, st>>>(g, H, cs, sn, gv, h1, h2, pnorm, ldH, cond, use_cond);
+template <typename S>
+cudaError_t launch_update_norm_givens(S* V, int64_t n, GmresDev* g, const double* h2, double* partial_norm,
+                                      const GivensArgs& ga, cudaStream_t st) {
+  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, h2, partial_norm, 0, nullptr, 1, ga);
   return cudaGetLastError();
 }
+#define TAU_CGS_INST(S)                                                                                          \
+  template cudaError_t launch_update_dots<S>(S*, int64_t, GmresDev*, const double*, double*, int, double*,         \
+                                             cudaStream_t);                                                       \
+  template cudaError_t launch_update_norm_givens<S>(S*, int64_t, GmresDev*, const double*, double*,               \
+                                                    const GivensArgs&, cudaStream_t);
+TAU_CGS_INST(double)
+TAU_CGS_INST(float)
+TAU_CGS_INST(df64)
+#undef TAU_CGS_INST
 
-// V_{j} <- w / ||w|| where w sits in the slot of V_j (after k_givens advanced j). When the
+// V_{j} <- w / ||w|| where w sits in the slot of V_j (after the Givens step advanced j). When the
 // column closed the iteration (done), nothing is scaled.
 template <typename S>
 __global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
@@ -1536,7 +1554,7 @@ __global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
 
 template <typename S>
 cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st) {
-  k_scale_next<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+  k_scale_next<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g);
   return cudaGetLastError();
 }
 template cudaError_t launch_scale_next<double>(double*, int64_t, const GmresDev*, cudaStream_t);
@@ -1556,17 +1574,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const S* __restric
 template <typename S>
 cudaError_t launch_norm_partial(const S* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st) {
   (void)g;
-  k_norm_partial<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(w, n, partial);
+  k_norm_partial<S><<<red_blocks(n), RED_THREADS, 0, st>>>(w, n, partial);
   return cudaGetLastError();
 }
 template cudaError_t launch_norm_partial<double>(const double*, int64_t, const GmresDev*, double*, cudaStream_t);
 template cudaError_t launch_norm_partial<df64>(const df64*, int64_t, const GmresDev*, double*, cudaStream_t);
 
 // beta = ||r_0||, g_0 = beta, j = 0; done if beta == 0.
-__global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, double* gv) {
+__global__ void k_init_beta(GmresDev* g, const double* __restrict__ partial, int nblk, double* gv) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   double s = 0.0;
-  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += partial[b];
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) {
     const double beta = sqrt(s);
@@ -1593,8 +1611,8 @@ __global__ void k_scale_first(S* V, int64_t n, const GmresDev* __restrict__ g) {
 
 template <typename S>
 cudaError_t launch_init_beta(GmresDev* g, const double* partial, double* gv, S* V, int64_t n, cudaStream_t st) {
-  k_init_beta<<<1, 256, 0, st>>>(g, partial, gv);
-  k_scale_first<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, n, g);
+  k_init_beta<<<1, 256, 0, st>>>(g, partial, red_blocks(n), gv);   // partials of launch_norm_partial(n)
+  k_scale_first<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g);
   return cudaGetLastError();
 }
 template cudaError_t launch_init_beta<double>(GmresDev*, const double*, double*, double*, int64_t, cudaStream_t);
@@ -1635,7 +1653,7 @@ template <typename S>
 cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y, const S* V,
                                     int64_t n, S* u, int x0_prev, int* iters_log, cudaStream_t st) {
   k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, iters_log);
-  k_update_solution<S><<<RED_BLOCKS, RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
+  k_update_solution<S><<<red_blocks(n), RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
   k_advance<<<1, 32, 0, st>>>(g);
   return cudaGetLastError();
 }
@@ -1712,7 +1730,7 @@ __global__ void k_ir_first_resid(IRDev* ir, const double* __restrict__ b, double
 }
 
 cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st) {
-  k_ir_first_resid<<<RED_BLOCKS, RED_THREADS, 0, st>>>(ir, b, r, n, x0_zero);
+  k_ir_first_resid<<<red_blocks(n), RED_THREADS, 0, st>>>(ir, b, r, n, x0_zero);
   return cudaGetLastError();
 }
 
@@ -1721,11 +1739,11 @@ cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t
 // In the step graph the inner WHILE node lives in the outer loop's body; a handle's default value
 // is applied only when the whole graph is launched, so this kernel sets the inner condition for
 // every sweep (cond_in) as well as the outer one (cond).
-__global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* __restrict__ pnorm,
+__global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* __restrict__ pnorm, int nblk,
                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   double s = 0.0;
-  for (int b = threadIdx.x; b < RED_BLOCKS; b += blockDim.x) s += pnorm[b];
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += pnorm[b];
   s = block_sum(s, sh);
   if (threadIdx.x != 0) return;
   const double rho = sqrt(s);
@@ -1767,10 +1785,10 @@ __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const doub
   }
 }
 
-cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm,
+cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm, int64_t n,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
                               cudaStream_t st) {
-  k_ir_control<<<1, 256, 0, st>>>(ir, gin, gv_in, pnorm, cond, cond_in, use_cond);
+  k_ir_control<<<1, 256, 0, st>>>(ir, gin, gv_in, pnorm, red_blocks(n), cond, cond_in, use_cond);
   return cudaGetLastError();
 }
 
@@ -1786,7 +1804,7 @@ __global__ void k_scale_to_f32(const double* __restrict__ r, float* v, int64_t n
 }
 
 cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st) {
-  k_scale_to_f32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(r, v, n, ir);
+  k_scale_to_f32<<<red_blocks(n), RED_THREADS, 0, st>>>(r, v, n, ir);
   return cudaGetLastError();
 }
 
@@ -1811,7 +1829,7 @@ __global__ void k_update_x(double* x, const float* __restrict__ Z, const double*
 
 cudaError_t launch_update_x(double* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
                             cudaStream_t st) {
-  k_update_x<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
+  k_update_x<<<red_blocks(n), RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
   return cudaGetLastError();
 }
 
