@@ -286,6 +286,17 @@ def run_forms(stream, dev):
         "rel_err_vs_opgm": (torch.linalg.norm(ut - u64) / torch.linalg.norm(u64)).item(),
         "tpgm_iters_per_step": float(np.mean(itt)), "opgm_iters_per_step": float(np.mean(it64)),
         "unit": UNIT, "dtype": "f64"}
+    # the paper's comparison preconditioner (Strang circulant, Table 1) against the τ one on
+    # Example 2 with alpha = (1.7, 1.9), N + 1 = 128 (Table 3 prints 40.6 and 7.0 iterations at M = 2^14)
+    wl = W.paper_example(2, [1.7, 1.9], 127, 4096)
+    vo, mso, uo, _, ito = measure_steps(wl, tau.TAU_FP64, 2, 5, stream, dev)
+    vsp, mssp, usp, _, itsp = measure_steps(wl, tau.TAU_FP64, 2, 5, stream, dev, method=tau.TAU_SPGM)
+    out["2d_127_example2_spgm"] = {
+        "workload": "Example 2 of the paper, alpha = (1.7, 1.9), n = 127^2, M = 4096, tol 1e-9",
+        "spgm_value": vsp, "spgm_ms_per_step": mssp, "opgm_value": vo, "opgm_ms_per_step": mso,
+        "spgm_iters_per_step": float(np.mean(itsp)), "opgm_iters_per_step": float(np.mean(ito)),
+        "rel_diff_vs_opgm": (torch.linalg.norm(usp - uo) / torch.linalg.norm(uo)).item(),
+        "unit": UNIT, "dtype": "f64"}
     for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)

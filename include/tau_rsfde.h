@@ -71,6 +71,11 @@ typedef int tau_status;
                                  u = P^{-1/2} ũ; both P^{-1/2} and P^{-1/2} B^{-1} are DST-diag-DST
                                  products, so an iteration costs one more τ solve than OPGM.
                                  TAU_FP64 only */
+#define TAU_SPGM 2            /* the paper's comparison method (Table 1, Eq. (Pcir)): GMRES on
+                                 P_c^{-1} Ã u = P_c^{-1} b̃ with the Strang circulant preconditioner
+                                 P_c = ebar I + c(B)^{-1} c(S); P_c^{-1} by the separable orthonormal
+                                 Hartley transform (dense, O(n_i) per element), B^{-1} by the DST.
+                                 TAU_FP64 only; meant for comparisons at small n */
 
 #define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
@@ -101,7 +106,7 @@ typedef struct {
   double inner_tol;     /* inner FGMRES relative residual target of the first sweep; 1e-5.  A later
                            sweep targets the reduction still needed, 0.3 refine_tol rho_0 / rho,
                            kept within [min(1e-6, inner_tol), inner_tol] */
-  int method;           /* TAU_OPGM (0, default) or TAU_TPGM */
+  int method;           /* TAU_OPGM (0, default), TAU_TPGM or TAU_SPGM */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,

@@ -109,6 +109,12 @@ struct tau_problem {
   // two-sided method (TAU_TPGM): sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1}
   int tpgm = 0;
   double *pmh = nullptr, *pmhb = nullptr;
+  // Strang circulant comparison method (TAU_SPGM): Fourier-basis diagonal 1/p_c, sine-basis 1/beta,
+  // and per dimension the Hartley table and the DFT eigenvalues of s(B_i), s(S_i)
+  int spgm = 0;
+  double *pcinv = nullptr, *binv = nullptr;
+  double *cas[3] = {nullptr, nullptr, nullptr}, *sb[3] = {nullptr, nullptr, nullptr},
+         *ss[3] = {nullptr, nullptr, nullptr};
   df64x2 *spec_df[3] = {nullptr, nullptr, nullptr}, *twK_df[3] = {nullptr, nullptr, nullptr},
          *twK2_df[3] = {nullptr, nullptr, nullptr};
   df64 *s_df[3] = {nullptr, nullptr, nullptr}, *sintab_df[3] = {nullptr, nullptr, nullptr};
@@ -206,6 +212,7 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.sintab = p->sintab[ax];
     D.twK = p->twK[ax];
     D.twK2 = p->twK2[ax];
+    D.cas = p->cas[ax];
     P.in_base = P.out_base = p->V;
   } else if constexpr (std::is_same<T, df64>::value) {
     D.spec = p->spec_df[ax];
@@ -353,6 +360,28 @@ tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double s
   return TAU_OK;
 }
 
+// P_c^{-1} of the Strang circulant method: Hartley along dims d-1..1, Hartley·(1/p_c)·Hartley along
+// dim 0, Hartley along 1..d-1 (the separable orthonormal Hartley transform is its own inverse and
+// diagonalises every factor's Strang circulant), reading io's input and working in place after.
+template <typename T>
+tau_status enq_hartley(tau_problem* p, cudaStream_t st, const ChainT<T>& io) {
+  bool rd = true;
+  auto pass = [&](int ax, int post) -> tau_status {
+    PassT<T> P = base_pass_t<T>(p, ax);
+    P.post = post;
+    P.invmu = reinterpret_cast<const T*>(p->pcinv);
+    P.g = io.g;
+    wire_in(P, io, rd);
+    wire_out(P, io);
+    rd = false;
+    return enq(P, st);
+  };
+  for (int ax = p->d - 1; ax >= 1; --ax) TRY(pass(ax, POST_HT));
+  TRY(pass(0, POST_HT_D_HT));
+  for (int ax = 1; ax < p->d; ++ax) TRY(pass(ax, POST_HT));
+  return TAU_OK;
+}
+
 template <typename T>
 tau_status enq_minv(tau_problem* p, cudaStream_t st, const ChainT<T>& io) {
   return enq_minv_tail<T>(p, st, io, p->d - 1, true);
@@ -387,12 +416,20 @@ tau_status enq_prologue_t(tau_problem* p, cudaStream_t st) {
   r0.out = as<T>(p->V);
   // two-sided: r_0 = P^{-1/2} B^{-1} (b - A u_0), the residual of Eq. (Pls) at ũ_0 = P^{1/2} u_0
   if (p->tpgm) r0.diag = as<T>(p->pmhb);
+  // Strang circulant method: r_0 = P_c^{-1} B^{-1} (b - A u_0), B^{-1} on the sine basis
+  if (p->spgm) r0.diag = as<T>(p->binv);
   if (p->desc.x0_mode == TAU_X0_PREV) {
     r0.x = as<T>(p->u);
     TRY(enq_mv<T>(p, st, r0, 1.0, FIN_RESID, as<T>(p->b), true));
   } else {
     r0.x = as<T>(p->b);
     TRY(enq_minv<T>(p, st, r0));
+  }
+  if (p->spgm) {
+    ChainT<T> hc;
+    hc.x = as<T>(p->V);
+    hc.out = as<T>(p->V);
+    TRY(enq_hartley<T>(p, st, hc));
   }
   KL(launch_norm_partial<T>(as<T>(p->V), p->n_tot, p->g, p->pnorm, st));
   tl_launches += 1;
@@ -418,7 +455,16 @@ tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandl
     it.x = as<T>(p->tmp);
     it.diag = as<T>(p->pmhb);
   }
+  if (p->spgm) it.diag = as<T>(p->binv);
   TRY(enq_mv<T>(p, st, it, 1.0, FIN_NONE, nullptr, true));
+  if (p->spgm) {
+    // v_{j+1} = P_c^{-1} (B^{-1} A v_j), in place in the slot of v_{j+1}
+    ChainT<T> hc;
+    hc.in_sel = 2;
+    hc.out_sel = 2;
+    hc.g = p->g;
+    TRY(enq_hartley<T>(p, st, hc));
+  }
   const int ld = RED_BLOCKS;
   T* V = as<T>(p->V);
   KL(launch_dots<T>(V, p->n_tot, p->g, p->pdots, ld, p->h1, st));
@@ -815,9 +861,10 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (D.x0_mode != TAU_X0_ZERO && D.x0_mode != TAU_X0_PREV) return fail(TAU_EINVAL, "x0_mode %d", D.x0_mode);
   if (D.precision != TAU_FP64 && D.precision != TAU_MIXED && D.precision != TAU_DF64)
     return fail(TAU_EINVAL, "precision %d", D.precision);
-  if (D.method != TAU_OPGM && D.method != TAU_TPGM) return fail(TAU_EINVAL, "method %d", D.method);
-  if (D.method == TAU_TPGM && D.precision != TAU_FP64)
-    return fail(TAU_EUNSUPPORTED, "the two-sided method runs in TAU_FP64 only");
+  if (D.method != TAU_OPGM && D.method != TAU_TPGM && D.method != TAU_SPGM)
+    return fail(TAU_EINVAL, "method %d", D.method);
+  if (D.method != TAU_OPGM && D.precision != TAU_FP64)
+    return fail(TAU_EUNSUPPORTED, "the two-sided and Strang circulant methods run in TAU_FP64 only");
   if (D.precision == TAU_MIXED &&
       (D.refine_tol < 0 || D.inner_tol < 0 || D.inner_max_iter < 0 || D.inner_max_iter > MAX_ITER_CAP ||
        D.max_sweeps < 0))
@@ -865,6 +912,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   p->mixed = D.precision == TAU_MIXED;
   p->dfm = D.precision == TAU_DF64;
   p->tpgm = D.method == TAU_TPGM;
+  p->spgm = D.method == TAU_SPGM;
   if (p->mixed) {
     if (p->desc.refine_tol == 0) p->desc.refine_tol = 1e-10;
     if (p->desc.inner_max_iter == 0) p->desc.inner_max_iter = 30;
@@ -892,6 +940,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
                  (s = dalloc_n(p, &p->invmu_df, n))))
     return cleanup(s);
   if (p->tpgm && ((s = dalloc_n(p, &p->pmh, n)) || (s = dalloc_n(p, &p->pmhb, n)))) return cleanup(s);
+  if (p->spgm && ((s = dalloc_n(p, &p->pcinv, n)) || (s = dalloc_n(p, &p->binv, n)))) return cleanup(s);
   if ((s = dalloc_n(p, &p->u, n)) || (s = dalloc_n(p, &p->b, n)) ||
       (s = dalloc_n(p, &p->A, n)) || (s = dalloc_n(p, &p->C, n)) || (s = dalloc_n(p, &p->E, n)) ||
       (s = dalloc_n(p, &p->Fdt, n)) || (s = dalloc_n(p, &p->invmu, n)) || (s = dalloc_n(p, &p->tmp, n)) ||
@@ -970,6 +1019,38 @@ tau_status tau_setup(tau_problem* p) {
       beta[k - 1] = 1.0 - (a / 6.0) * sn * sn;
     }
     TRY(upload(p, &p->beta[i], beta.data(), beta.size()));
+    if (p->spgm) {
+      // Strang circulants of B_{alpha_i} and S_{alpha_i} (first column t, entries k > N/2 wrapped to
+      // t_{N-k}) and their DFT eigenvalues lambda_m = sum_k c_k cos(2 pi k m / N) (real: symmetric);
+      // the orthonormal Hartley table cas(2 pi t / N) / sqrt(N)
+      std::vector<double> tb(N, 0.0);
+      tb[0] = 1.0 - a / 12.0;
+      if (N > 1) tb[1] = a / 24.0;
+      auto strang = [&](const std::vector<double>& t) {
+        std::vector<double> c(t);
+        for (int k = N / 2 + 1; k < N; ++k) c[k] = t[N - k];
+        return c;
+      };
+      const std::vector<double> cb = strang(tb), cs = strang(s);
+      std::vector<double> cosN(N), lb(N), ls(N), ct(N);
+      for (int t = 0; t < N; ++t) cosN[t] = std::cos(2.0 * M_PI * t / N);
+      for (int m = 0; m < N; ++m) {
+        double xb = 0.0, xs = 0.0;
+        int ph = 0;
+        for (int k = 0; k < N; ++k) {
+          xb += cb[k] * cosN[ph];
+          xs += cs[k] * cosN[ph];
+          ph += m;
+          if (ph >= N) ph -= N;
+        }
+        lb[m] = xb;
+        ls[m] = xs;
+      }
+      for (int t = 0; t < N; ++t) ct[t] = (cosN[t] + std::sin(2.0 * M_PI * t / N)) / std::sqrt((double)N);
+      TRY(upload(p, &p->sb[i], lb.data(), lb.size()));
+      TRY(upload(p, &p->ss[i], ls.data(), ls.size()));
+      TRY(upload(p, &p->cas[i], ct.data(), ct.size()));
+    }
     std::vector<double> q(N);
     {
       // dense route: sin(pi t / K), t = 0..2K-1; FFT route: the half-length DST's input weights
@@ -1044,6 +1125,8 @@ tau_status tau_setup(tau_problem* p) {
   p->ebar = 0.5 * (p->ehat + p->echeck);
   KL(launch_invmu(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->invmu, p->st));
   if (p->tpgm) KL(launch_tpgm_diag(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->pmh, p->pmhb, p->st));
+  if (p->spgm)
+    KL(launch_spgm_diag(d, p->n, p->n_tot, p->ebar, p->sb, p->ss, p->eta, p->beta, p->pcinv, p->binv, p->st));
   KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->dfm ? p->tmp : p->u, p->st));
   if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
   if (p->dfm) {

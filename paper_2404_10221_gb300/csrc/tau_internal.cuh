@@ -39,6 +39,8 @@ enum Post : int {
   POST_NONE = 0,
   POST_DST = 1,        // orthonormal DST-I along this dimension
   POST_DST_MU_DST = 2, // DST-I, multiply by 1/mu, DST-I  (only on dimension 0)
+  POST_HT = 3,         // orthonormal Hartley transform along this dimension (dense, any n)
+  POST_HT_D_HT = 4,    // Hartley, multiply by the diagonal in `invmu`, Hartley (only on dimension 0)
 };
 
 struct GmresDev;
@@ -114,6 +116,7 @@ struct DimDataT {
                         // spectrum folded for the packed real FFT, scaled by 1/K (no eta)
   const T* s;           // FCD weights s_0..s_{n-1}
   const T* sintab;      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: (1/2) sqrt(2/K) sin(pi t / K)
+  const T* cas;         // Strang circulant method: cas(2 pi t / n) / sqrt(n), t = 0..n-1
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
   const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I
 };
@@ -235,6 +238,12 @@ cudaError_t launch_invmu(int d, const int* n, int64_t n_tot, double ebar, const 
 // Two-sided preconditioning (Eq. (Pls)): pmh = sqrt(beta/mu), pmhb = 1/sqrt(beta mu) per sine mode.
 cudaError_t launch_tpgm_diag(int d, const int* n, int64_t n_tot, double ebar, const double* const* beta,
                              const double* const* q, const double* eta, double* pmh, double* pmhb, cudaStream_t st);
+// Strang circulant method (Eq. (Pcir)): pcinv = 1/p_k with p_k = ebar + c(S)_k / c(B)_k on the
+// Fourier basis (bs, ss: per-dimension DFT eigenvalues of s(B_i), s(S_i)); binv = 1/prod_i beta_k
+// (B^{-1} on the sine basis).
+cudaError_t launch_spgm_diag(int d, const int* n, int64_t n_tot, double ebar, const double* const* bs,
+                             const double* const* ss, const double* eta, const double* const* beta, double* pcinv,
+                             double* binv, cudaStream_t st);
 // u = t (keep 0) or u += t (keep 1)
 cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cudaStream_t st);
 

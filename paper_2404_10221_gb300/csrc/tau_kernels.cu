@@ -663,6 +663,48 @@ __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   }
 }
 
+// Orthonormal Hartley transform of every line in place (dense, any n): y_k = sum_j c_{jk mod n} x_j
+// with c_t = cas(2 pi t / n) / sqrt(n), x_j at xs[l*xst + j], j, k = 0..n-1.  It is its own inverse and
+// diagonalises the Strang circulants of the comparison preconditioner P_c (their spectra are even).
+template <typename T>
+__device__ void hartley_lines(const PassT<T>& P, T* xs, int xst) {
+  const int N = P.len, lpb = P.lpb;
+  const int TH = blockDim.x, tid = threadIdx.x;
+  const T* __restrict__ ct = P.dim.cas;
+  const T z0 = from_f<T>(0.0f);
+  T acc[8];
+  const int tot = lpb * N;
+  for (int base = 0; base < tot; base += 8 * TH) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = base + r * TH + tid;
+      acc[r] = z0;
+      if (idx < tot) {
+        const int l = idx / N, k = idx - l * N;
+        const T* row = xs + l * xst;
+        T sacc = z0;
+        int ph = 0;  // (j * k) mod N
+        for (int j = 0; j < N; ++j) {
+          sacc = tfma(ct[ph], row[j], sacc);
+          ph += k;
+          if (ph >= N) ph -= N;
+        }
+        acc[r] = sacc;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = base + r * TH + tid;
+      if (idx < tot) {
+        const int l = idx / N;
+        xs[l * xst + idx - l * N] = acc[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Prefix sums over the even slots of each line of the DST recombination:
 //   row[2k] <- sum_{i<=k} row[2i] - row[0]/2,  k < K2,
 // which turns the stored sc Re W_k into the odd outputs y_{2k+1}.  row[0] itself is left unchanged
@@ -982,6 +1024,20 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     __syncthreads();
   }
 
+  if (P.post == POST_HT || P.post == POST_HT_D_HT) {
+    hartley_lines(P, rc, RS);
+    if (P.post == POST_HT_D_HT) {
+      tile_load(tg, N, lpb, P.invmu, ra, N);
+      __syncthreads();
+      for (int idx = tid; idx < NTP; idx += TH) {
+        const int l = idx >> lgnp, j = idx & (NP - 1);
+        if (j >= N) continue;
+        rc[l * RS + j] *= ra[l * N + j];
+      }
+      __syncthreads();
+      hartley_lines(P, rc, RS);
+    }
+  }
   if (P.post == POST_DST || P.post == POST_DST_MU_DST) {
     dst_lines(P, rc, RS);
     if (P.post == POST_DST_MU_DST) {
@@ -1303,6 +1359,51 @@ cudaError_t launch_tpgm_diag(int d, const int* n, int64_t n_tot, double ebar, co
   int64_t blocks = (n_tot + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   k_tpgm_diag<<<(unsigned)blocks, 256, 0, st>>>(a, pmh, pmhb);
+  return cudaGetLastError();
+}
+
+// Strang circulant method: pcinv = prod b / (ebar prod b + sum_i eta_i s_i prod_{l!=i} b_l) = 1/p_c
+// with b, s the Fourier-basis eigenvalues of s(B_i), s(S_i); binv = 1/prod_i beta^{(i)}.
+__global__ void k_spgm_diag(const MuArgs strang, const MuArgs tau_b, double* pcinv, double* binv) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < strang.n_tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int j[3] = {0, 0, 0};
+    unflatten(idx, strang.d, strang.n, j);
+    double bprod = 1.0, tprod = 1.0;
+    for (int i = 0; i < strang.d; ++i) {
+      bprod *= strang.beta[i][j[i]];
+      tprod *= tau_b.beta[i][j[i]];
+    }
+    double mu = strang.ebar * bprod;
+    for (int i = 0; i < strang.d; ++i) {
+      double p = strang.eta[i] * strang.q[i][j[i]];
+      for (int l = 0; l < strang.d; ++l)
+        if (l != i) p *= strang.beta[l][j[l]];
+      mu += p;
+    }
+    pcinv[idx] = bprod / mu;
+    binv[idx] = 1.0 / tprod;
+  }
+}
+
+cudaError_t launch_spgm_diag(int d, const int* n, int64_t n_tot, double ebar, const double* const* bs,
+                             const double* const* ss, const double* eta, const double* const* beta, double* pcinv,
+                             double* binv, cudaStream_t st) {
+  MuArgs a, t;
+  a.d = t.d = d;
+  a.n_tot = t.n_tot = n_tot;
+  a.ebar = t.ebar = ebar;
+  for (int i = 0; i < 3; ++i) {
+    a.n[i] = t.n[i] = i < d ? n[i] : 1;
+    a.beta[i] = i < d ? bs[i] : nullptr;
+    a.q[i] = i < d ? ss[i] : nullptr;
+    a.eta[i] = t.eta[i] = i < d ? eta[i] : 0.0;
+    t.beta[i] = i < d ? beta[i] : nullptr;
+    t.q[i] = nullptr;
+  }
+  int64_t blocks = (n_tot + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_spgm_diag<<<(unsigned)blocks, 256, 0, st>>>(a, t, pcinv, binv);
   return cudaGetLastError();
 }
 

@@ -83,7 +83,7 @@ int64_t estimate_bytes(const tau_problem_desc& d, int64_t n) {
     return (2 * k + 4) * n * 4 + 12 * n * 8 + (1 << 20);
   }
   // two-sided: two more vectors (the sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1})
-  return ((int64_t)d.max_iter + 11 + (d.method == TAU_TPGM ? 2 : 0)) * n * 8 + (1 << 20);
+  return ((int64_t)d.max_iter + 11 + (d.method != TAU_OPGM ? 2 : 0)) * n * 8 + (1 << 20);
 }
 
 void finish(tau_server* s, const std::shared_ptr<Req>& r, tau_status st, const char* msg) {

@@ -33,6 +33,7 @@ TAU_MIXED = 1
 TAU_DF64 = 2
 TAU_OPGM = 0
 TAU_TPGM = 1
+TAU_SPGM = 2
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
