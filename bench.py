@@ -188,10 +188,10 @@ class ClockSampler:
 # 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
 # kernel sources that capture measured (sha256 below), else the bench reports null.
 TRAFFIC_CAPTURE = {
-    "bytes_per_matvec": 16916992 + 512 + 16963072 + 256 + 16904192 + 8493056,
+    "bytes_per_matvec": 16916736 + 768 + 16967936 + 1280 + 16902656 + 8497664,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "31a512ac5b26211486a8a5f85976b42cacc01929cacba8d2d14d2550cbd938b2",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "560712c93ceb7636f5091836efc22873f05bcc0c746db788161f4b03a7904597",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "826c9eee3c347dc21b4ec96973199dacecadb1aa6eef462247f80d3360a3551d",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "3f2e0566c04a95edb61c853cf1f49320093af56d2a7fca21f4a5aef5f79629ce",
     },
 }
 
