@@ -811,6 +811,24 @@ __device__ void prefix_warps(T* xs, int xst, int lpb, int K2) {
   __syncthreads();
 }
 
+// Packed input z_m = (w_2m, w_2m+1) of the DST's half-length FFT (FP32 fused input stage):
+// w_j = sn_j (x_j + x_{K-j}) + hh (x_j - x_{K-j}), w_0 = 0, x_j at row[j-1].
+__device__ __forceinline__ float2 dst_packed_input(const float* row, int m, int K, const float* __restrict__ sn,
+                                                   float hh) {
+  float w[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = 2 * m + r;
+    float v = 0.0f;
+    if (j > 0) {
+      const float xj = row[j - 1], xk = row[K - j - 1];
+      v = fmaf(sn[j], xj + xk, hh * (xj - xk));
+    }
+    w[r] = v;
+  }
+  return make_float2(w[0], w[1]);
+}
+
 // Orthonormal DST-I of every line in place: xs[l*xst + j] holds x_{j+1}; result y_{k} at
 // xs[l*xst + k-1].  FFT route: xst = 2K; the half-length complex FFT works in the line's upper
 // half [K, 2K), which holds no data (N < K).  Dense route: xst = N.
@@ -831,6 +849,38 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     V* cb = reinterpret_cast<V*>(xs + K);   // line l at cb + l*K (complex)
     const int lk2 = __ffs(K2) - 1;
     const T hh = from_f<T>(0.25f) * P.dim.dsc;   // h / 2 = sqrt(2/K) / 4
+    bool input_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (K2 >= 2) {
+        // FP32: the input stage and the twiddle-free first DIT stage in one pass.  The R slots of
+        // group g (R = 2 for odd log2 K2, else 4) hold z_m for m = m_lo + r K2/R with g the digit
+        // reversal of m_lo; work item m_lo reads its inputs (consecutive lanes, consecutive x),
+        // applies the first stage and writes the group as one contiguous run.
+        const int R = (lk2 & 1) ? 2 : 4, lgG = lk2 - ((lk2 & 1) ? 1 : 2), G = 1 << lgG;
+        for (int b = tid; b < (lpb << lgG); b += TH) {
+          const int l = b >> lgG, mlo = b & (G - 1);
+          const float* row = xs + l * xst;
+          V* x = cb + l * K + R * rev4(mlo, lgG);
+          if (R == 2) {
+            const V a0 = dst_packed_input(row, mlo, K, sn, hh), a1 = dst_packed_input(row, mlo + G, K, sn, hh);
+            x[0] = cadd(a0, a1);
+            x[1] = csub(a0, a1);
+          } else {
+            V a0 = dst_packed_input(row, mlo, K, sn, hh), a1 = dst_packed_input(row, mlo + G, K, sn, hh),
+              a2 = dst_packed_input(row, mlo + 2 * G, K, sn, hh), a3 = dst_packed_input(row, mlo + 3 * G, K, sn, hh);
+            dit4<false, false>(a0, a1, a2, a3, 0, 1, static_cast<const V*>(nullptr));
+            x[0] = a0;
+            x[1] = a1;
+            x[2] = a2;
+            x[3] = a3;
+          }
+        }
+        __syncthreads();
+        fft_dit<false>(cb, K, lpb, K2, tw2, false, true);
+        input_done = true;
+      }
+    }
+    if (!input_done) {
     for (int b = tid; b < (lpb << lk2); b += TH) {
       const int l = b >> lk2, m = b & (K2 - 1);
       const T* row = xs + l * xst;
@@ -849,6 +899,7 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
     }
     __syncthreads();
     fft_dit<false>(cb, K, lpb, K2, tw2);
+    }
     // recombine pairs (k, K2-k) into W_k, W_{K2-k}; even outputs go to row[2k-1] (odd slots),
     // sc * Re W_k to row[2k] (even slots) for the prefix sum of the odd outputs.
     auto recombine = [&](int l, int k) {
@@ -1024,20 +1075,6 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
     __syncthreads();
   }
 
-  if (P.post == POST_HT || P.post == POST_HT_D_HT) {
-    hartley_lines(P, rc, RS);
-    if (P.post == POST_HT_D_HT) {
-      tile_load(tg, N, lpb, P.invmu, ra, N);
-      __syncthreads();
-      for (int idx = tid; idx < NTP; idx += TH) {
-        const int l = idx >> lgnp, j = idx & (NP - 1);
-        if (j >= N) continue;
-        rc[l * RS + j] *= ra[l * N + j];
-      }
-      __syncthreads();
-      hartley_lines(P, rc, RS);
-    }
-  }
   if (P.post == POST_DST || P.post == POST_DST_MU_DST) {
     dst_lines(P, rc, RS);
     if (P.post == POST_DST_MU_DST) {
@@ -1051,6 +1088,40 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
       __syncthreads();
       dst_lines(P, rc, RS);
     }
+  }
+  tile_store(tg, N, lpb, rc, RS, out_a);
+}
+
+// Hartley passes of the Strang circulant method (POST_HT, POST_HT_D_HT): a kernel of their own, so
+// the dense Hartley loop does not weigh on the register allocation of the line-pass kernel.
+template <typename T>
+__global__ void __launch_bounds__(PASS_THREADS) k_ht_pass(const PassT<T> P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = P.len, lpb = P.lpb;
+  const int RS = rc_stride(P);
+  T* ra = reinterpret_cast<T*>(smraw);
+  T* rc = ra + ((lpb * N + 1) & ~1);
+  if (P.g && P.g->done) return;
+  const TileGeo tg = tile_geo(P, blockIdx.x);
+  const int TH = blockDim.x, tid = threadIdx.x;
+  const int lgnp = lg_pad(N), NP = 1 << lgnp, NTP = lpb << lgnp;
+  const T* in_a = P.in_a;
+  T* out_a = P.out_a;
+  if (P.in_sel) in_a = P.in_base + (int64_t)(P.g->j + P.in_sel - 1) * P.vstride;
+  if (P.out_sel) out_a = P.out_base + (int64_t)(P.g->j + P.out_sel - 1) * P.vstride;
+  tile_load(tg, N, lpb, in_a, rc, RS);
+  __syncthreads();
+  hartley_lines(P, rc, RS);
+  if (P.post == POST_HT_D_HT) {
+    tile_load(tg, N, lpb, P.invmu, ra, N);
+    __syncthreads();
+    for (int idx = tid; idx < NTP; idx += TH) {
+      const int l = idx >> lgnp, j = idx & (NP - 1);
+      if (j >= N) continue;
+      rc[l * RS + j] *= ra[l * N + j];
+    }
+    __syncthreads();
+    hartley_lines(P, rc, RS);
   }
   tile_store(tg, N, lpb, rc, RS, out_a);
 }
@@ -1071,6 +1142,8 @@ cudaError_t init_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_pass<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_ht_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
@@ -1078,6 +1151,13 @@ template <typename T>
 cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
   if (p.ntiles <= 0) return cudaSuccess;
   const size_t smem = pass_smem_bytes(p);
+  if (p.post == POST_HT || p.post == POST_HT_D_HT) {
+    if constexpr (std::is_same<T, double>::value) {
+      k_ht_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
+      return cudaGetLastError();
+    }
+    return cudaErrorNotSupported;   // the Strang circulant method runs in FP64 only
+  }
   k_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }
