@@ -188,9 +188,9 @@ class ClockSampler:
 # 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
 # kernel sources that capture measured (sha256 below), else the bench reports null.
 TRAFFIC_CAPTURE = {
-    "bytes_per_matvec": 16916736 + 768 + 16967936 + 1280 + 16902656 + 8497664,
+    "bytes_per_matvec": 16916736 + 768 + 16961024 + 512 + 16901632 + 8492032,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "826c9eee3c347dc21b4ec96973199dacecadb1aa6eef462247f80d3360a3551d",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "3be7fb33e2125f2c11203f69caedbc8300d29724ee747079d99d6b84254963f9",
         "paper_2404_10221_gb300/csrc/tau_internal.cuh": "3f2e0566c04a95edb61c853cf1f49320093af56d2a7fca21f4a5aef5f79629ce",
     },
 }
