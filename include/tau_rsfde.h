@@ -77,9 +77,19 @@ typedef int tau_status;
                                  Hartley transform (dense, O(n_i) per element), B^{-1} by the DST.
                                  TAU_FP64 only; meant for comparisons at small n */
 
-#define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else dense */
+#define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else chirp
+                                 for 128 <= n_i < 4096 (when one line fits in shared memory), else
+                                 dense */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
 #define TAU_ROUTE_DENSE 2     /* explicit n_i x n_i mode products (any n_i <= 8192) */
+#define TAU_ROUTE_CHIRP 3     /* any n_i < 4096: Toeplitz products through a power-of-two circulant
+                                 embedding, DST-I through a chirp-z convolution of power-of-two
+                                 length >= 2 n_i (O(log n_i) per element).
+                                 Every route needs one line (the n_i values plus the route's work
+                                 row) in at most 200 KB of shared memory: TAU_DF64 (16-byte
+                                 elements) fits the chirp route up to n_i = 2048 and the dense
+                                 route up to n_i = 6400; otherwise tau_create returns
+                                 TAU_EUNSUPPORTED for a forced route */
 
 typedef struct tau_problem tau_problem;
 
@@ -130,7 +140,7 @@ typedef struct {
   int max_iters_step;       /* largest per-step count so far */
   double last_relres;       /* |g_k| / ||r_0|| of the last step (preconditioned, Givens estimate) */
   double ebar, e_hat, e_check; /* Eqs. (bard), (dhat) */
-  int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT or TAU_ROUTE_DENSE) */
+  int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT, _DENSE or _CHIRP) */
   int graph;                /* 1 if steps run as CUDA-graph launches with device-side loop control */
   int64_t device_bytes;     /* device memory held by the problem */
   int64_t kernels_prologue; /* kernels of one step: prologue + iters * per_iter + epilogue */

@@ -75,6 +75,15 @@ struct tau_problem {
   GmresDev* g = nullptr;
   int* iters = nullptr;
   double2* spec[3] = {nullptr, nullptr, nullptr};
+  // CHIRP route: Toeplitz transform length KT (power of two >= n+1), DST convolution length MC
+  // (power of two >= 2n), the chirp w_m, the kernel spectrum and the length-MC twiddles
+  int KT[3] = {0, 0, 0}, MC[3] = {0, 0, 0};
+  double2 *chirp[3] = {nullptr, nullptr, nullptr}, *bhat[3] = {nullptr, nullptr, nullptr},
+          *twM[3] = {nullptr, nullptr, nullptr};
+  float2 *chirp32[3] = {nullptr, nullptr, nullptr}, *bhat32[3] = {nullptr, nullptr, nullptr},
+         *twM32[3] = {nullptr, nullptr, nullptr};
+  df64x2 *chirp_df[3] = {nullptr, nullptr, nullptr}, *bhat_df[3] = {nullptr, nullptr, nullptr},
+         *twM_df[3] = {nullptr, nullptr, nullptr};
   double2 *twK[3] = {nullptr, nullptr, nullptr}, *twK2[3] = {nullptr, nullptr, nullptr};
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
@@ -213,6 +222,9 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.twK = p->twK[ax];
     D.twK2 = p->twK2[ax];
     D.cas = p->cas[ax];
+    D.chirp = p->chirp[ax];
+    D.bhat = p->bhat[ax];
+    D.twM = p->twM[ax];
     P.in_base = P.out_base = p->V;
   } else if constexpr (std::is_same<T, df64>::value) {
     D.spec = p->spec_df[ax];
@@ -220,6 +232,9 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.sintab = p->sintab_df[ax];
     D.twK = p->twK_df[ax];
     D.twK2 = p->twK2_df[ax];
+    D.chirp = p->chirp_df[ax];
+    D.bhat = p->bhat_df[ax];
+    D.twM = p->twM_df[ax];
     P.in_base = P.out_base = reinterpret_cast<df64*>(p->V);
   } else {
     D.spec = p->spec32[ax];
@@ -227,10 +242,20 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.sintab = p->sintab32[ax];
     D.twK = p->twK32[ax];
     D.twK2 = p->twK2_32[ax];
+    D.chirp = p->chirp32[ax];
+    D.bhat = p->bhat32[ax];
+    D.twM = p->twM32[ax];
+  }
+  if (D.route == ROUTE_CHIRP) {
+    D.K = p->KT[ax];
+    D.M = p->MC[ax];
   }
   // shared memory per line: the line (N reals) plus the transform line (2K reals, FFT route) or a
   // second copy (N, dense route).  24 KB of lines per CTA lets 8 CTAs of 128 threads share an SM.
-  const size_t per_line = sizeof(T) * ((size_t)P.len + (D.route == ROUTE_FFT ? 2 * (size_t)D.K : (size_t)P.len));
+  size_t rs = (size_t)P.len;
+  if (D.route == ROUTE_FFT) rs = 2 * (size_t)D.K;
+  if (D.route == ROUTE_CHIRP) rs = (((size_t)P.len + 1) & ~(size_t)1) + 2 * (size_t)D.M;
+  const size_t per_line = sizeof(T) * ((size_t)P.len + rs);
   int64_t lpb = (int64_t)(24576 / per_line);
   if (lpb < 1) lpb = 1;
   if (lpb > 16) lpb = 16;
@@ -885,7 +910,26 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     const int64_t K = D.n[i] + 1;
     int r = D.route[i];
     const bool fft_ok = is_pow2(K) && K >= 2 && K <= KMAX;
-    if (r == TAU_ROUTE_AUTO) r = fft_ok ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE;
+    // shared memory one line of the pass kernel needs on each route (the kernel's dynamic limit is
+    // 200 KB): the line plus its transform row (2K on the FFT route, the data then 2 MC reals of
+    // chirp-z work on the chirp route, a second copy on the dense route)
+    const size_t esz = D.precision == TAU_DF64 ? 16 : 8;
+    const size_t nn = (size_t)D.n[i], npad = (nn + 1) & ~(size_t)1;
+    size_t kt = 2, mc = 2;
+    while (kt < nn + 1) kt <<= 1;
+    while (mc < 2 * nn) mc <<= 1;
+    auto fits = [&](int route) {
+      const size_t rs = route == TAU_ROUTE_FFT ? 2 * (nn + 1) : (route == TAU_ROUTE_CHIRP ? npad + 2 * mc : nn);
+      return esz * (npad + rs) <= 200 * 1024;
+    };
+    if (r == TAU_ROUTE_AUTO) {
+      r = fft_ok ? TAU_ROUTE_FFT : (D.n[i] >= 128 && D.n[i] < KMAX ? TAU_ROUTE_CHIRP : TAU_ROUTE_DENSE);
+      if (r == TAU_ROUTE_CHIRP && !fits(r)) r = TAU_ROUTE_DENSE;
+    }
+    if (r == TAU_ROUTE_CHIRP && D.n[i] >= KMAX) {
+      delete p;
+      return fail(TAU_EUNSUPPORTED, "chirp route limited to n < %d (dim %d, n=%lld)", KMAX, i, (long long)D.n[i]);
+    }
     if (r == TAU_ROUTE_FFT && !fft_ok) {
       delete p;
       return fail(TAU_EUNSUPPORTED, "FFT route needs n+1 a power of two in [2, %d] (dim %d, n=%lld)", KMAX, i,
@@ -895,11 +939,20 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
       delete p;
       return fail(TAU_EUNSUPPORTED, "dense route limited to n <= 8192 (dim %d, n=%lld)", i, (long long)D.n[i]);
     }
-    if (r != TAU_ROUTE_FFT && r != TAU_ROUTE_DENSE) {
+    if (r != TAU_ROUTE_FFT && r != TAU_ROUTE_DENSE && r != TAU_ROUTE_CHIRP) {
       delete p;
       return fail(TAU_EINVAL, "route[%d]=%d", i, D.route[i]);
     }
-    p->route[i] = r == TAU_ROUTE_FFT ? ROUTE_FFT : ROUTE_DENSE;
+    if (!fits(r)) {
+      delete p;
+      return fail(TAU_EUNSUPPORTED, "one line of dim %d (n=%lld) does not fit in shared memory on route %d", i,
+                  (long long)D.n[i], r);
+    }
+    p->route[i] = r == TAU_ROUTE_FFT ? ROUTE_FFT : (r == TAU_ROUTE_CHIRP ? ROUTE_CHIRP : ROUTE_DENSE);
+    if (p->route[i] == ROUTE_CHIRP) {
+      p->KT[i] = (int)kt;
+      p->MC[i] = (int)mc;
+    }
   }
   auto cleanup = [&](tau_status s) {
     tau_destroy(p);
@@ -1060,33 +1113,40 @@ tau_status tau_setup(tau_problem* p) {
       for (int t = 0; t < 2 * K; ++t) st[t] = hs * std::sin(M_PI * t / K);
       TRY(upload(p, &p->sintab[i], st.data(), st.size()));
     }
-    if (p->route[i] == ROUTE_FFT) {
-      TRY(dalloc_n(p, &p->twK[i], (size_t)twp_size(K)));
-      TRY(dalloc_n(p, &p->twK2[i], (size_t)twp_size(K / 2)));
-      KL(launch_twp(K, p->twK[i], p->st));
-      KL(launch_twp(K / 2, p->twK2[i], p->st));
-      // circulant embedding c of length 2K: c_0 = s_0, c_k = c_{2K-k} = s_k (1 <= k < N), zeros
-      // elsewhere.  Its real spectrum lambda_k gives the Toeplitz product and, at k = 1..N, the
-      // eigenvalues q_k of tau(S) (Eq. (q)).
-      std::vector<double> c(2 * (size_t)K, 0.0);
+    const bool chirp = p->route[i] == ROUTE_CHIRP;
+    if (p->route[i] != ROUTE_DENSE) {
+      // Toeplitz product: circulant embedding c of length 2KK (KK = K on the FFT route, the power
+      // of two >= n+1 on the chirp route): c_0 = s_0, c_k = c_{2KK-k} = s_k (1 <= k < N), zeros
+      // elsewhere.  On the FFT route its real spectrum at k = 1..N is also the eigenvalues q_k of
+      // tau(S) (Eq. (q)).
+      const int KK = chirp ? p->KT[i] : K;
+      TRY(dalloc_n(p, &p->twK[i], (size_t)twp_size(KK)));
+      KL(launch_twp(KK, p->twK[i], p->st));
+      if (!chirp) {
+        TRY(dalloc_n(p, &p->twK2[i], (size_t)twp_size(K / 2)));
+        KL(launch_twp(K / 2, p->twK2[i], p->st));
+      }
+      std::vector<double> c(2 * (size_t)KK, 0.0);
       c[0] = s[0];
-      for (int k = 1; k < N; ++k) c[k] = c[2 * K - k] = s[k];
+      for (int k = 1; k < N; ++k) c[k] = c[2 * KK - k] = s[k];
       double *dc = nullptr, *dl = nullptr;
       TRY(upload(p, &dc, c.data(), c.size()));
-      TRY(dalloc_n(p, &dl, (size_t)K + 1));
-      KL(launch_spectrum(K, dc, dl, p->twK[i], p->st));
-      std::vector<double> lam(K + 1);
-      CK(cudaMemcpyAsync(lam.data(), dl, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+      TRY(dalloc_n(p, &dl, (size_t)KK + 1));
+      KL(launch_spectrum(KK, dc, dl, p->twK[i], p->st));
+      std::vector<double> lam(KK + 1);
+      CK(cudaMemcpyAsync(lam.data(), dl, (KK + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
       CK(cudaStreamSynchronize(p->st));
-      std::vector<double2> spec(4 * (size_t)(K / 2 + 1));
-      for (int k = 0; k <= K / 2; ++k) {
+      std::vector<double2> spec(4 * (size_t)(KK / 2 + 1));
+      for (int k = 0; k <= KK / 2; ++k) {
         double abcd[8];
-        toep_pack_coeffs(lam[k], lam[K - k], std::cos(M_PI * k / K), -std::sin(M_PI * k / K), K, abcd);
+        toep_pack_coeffs(lam[k], lam[KK - k], std::cos(M_PI * k / KK), -std::sin(M_PI * k / KK), KK, abcd);
         for (int r = 0; r < 4; ++r) spec[4 * (size_t)k + r] = make_double2(abcd[2 * r], abcd[2 * r + 1]);
       }
       TRY(upload(p, &p->spec[i], spec.data(), spec.size()));
-      for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
-    } else {
+      if (!chirp)
+        for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
+    }
+    if (p->route[i] != ROUTE_FFT) {
       // q_k = s_0 + 2 sum_j s_j cos(pi j k / K) (Eq. (q)) with a cosine table
       std::vector<double> ct(2 * (size_t)K);
       for (int t = 0; t < 2 * K; ++t) ct[t] = std::cos(M_PI * t / K);
@@ -1102,6 +1162,31 @@ tau_status tau_setup(tau_problem* p) {
       }
     }
     TRY(upload(p, &p->q[i], q.data(), q.size()));
+    if (chirp) {
+      // chirp-z DST-I tables: w_m = exp(i pi m^2/(2L)), m = 0..N, L = N+1 (m^2 reduced mod 4L, the
+      // period of the phase); kernel b_m = conj(w_|m|) for |m| < N placed at m mod MC; its FFT in
+      // fft_dif's order times sqrt(2/L)/MC
+      const int MCi = p->MC[i];
+      const int64_t L = N + 1;
+      auto wph = [&](int64_t m) {
+        const int64_t r = (m * m) % (4 * L);
+        return make_double2(std::cos(M_PI * (double)r / (2.0 * (double)L)),
+                            std::sin(M_PI * (double)r / (2.0 * (double)L)));
+      };
+      std::vector<double2> w(N + 1), bk(MCi, make_double2(0.0, 0.0));
+      for (int m = 0; m <= N; ++m) w[m] = wph(m);
+      for (int m = -(N - 1); m <= N - 1; ++m) {
+        const double2 v = wph(m < 0 ? -m : m);
+        bk[((m % MCi) + MCi) % MCi] = make_double2(v.x, -v.y);
+      }
+      TRY(upload(p, &p->chirp[i], w.data(), w.size()));
+      TRY(dalloc_n(p, &p->twM[i], (size_t)twp_size(MCi)));
+      KL(launch_twp(MCi, p->twM[i], p->st));
+      double2* db = nullptr;
+      TRY(upload(p, &db, bk.data(), bk.size()));
+      TRY(dalloc_n(p, &p->bhat[i], (size_t)MCi));
+      KL(launch_chirp_spectrum(MCi, db, p->bhat[i], p->twM[i], std::sqrt(2.0 / (double)L) / MCi, p->st));
+    }
   }
   // ebar (Eqs. (bard), (dhat))
   if (std::isnan(p->desc.e_min) || std::isnan(p->desc.e_max)) {
@@ -1139,14 +1224,27 @@ tau_status tau_setup(tau_problem* p) {
       const int N = p->n[i], K = N + 1;
       TRY(conv(p->s[i], &p->s_df[i], N));
       TRY(conv(p->sintab[i], &p->sintab_df[i], 2 * (size_t)K));
+      if (p->route[i] != ROUTE_DENSE) {
+        const int KK = p->route[i] == ROUTE_CHIRP ? p->KT[i] : K;
+        df64* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(KK / 2 + 1)));
+        p->spec_df[i] = reinterpret_cast<df64x2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(KK)));
+        p->twK_df[i] = reinterpret_cast<df64x2*>(f);
+      }
       if (p->route[i] == ROUTE_FFT) {
         df64* f = nullptr;
-        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(K / 2 + 1)));
-        p->spec_df[i] = reinterpret_cast<df64x2*>(f);
-        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
-        p->twK_df[i] = reinterpret_cast<df64x2*>(f);
         TRY(conv(reinterpret_cast<const double*>(p->twK2[i]), &f, 2 * (size_t)twp_size(K / 2)));
         p->twK2_df[i] = reinterpret_cast<df64x2*>(f);
+      }
+      if (p->route[i] == ROUTE_CHIRP) {
+        df64* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->chirp[i]), &f, 2 * (size_t)(N + 1)));
+        p->chirp_df[i] = reinterpret_cast<df64x2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->bhat[i]), &f, 2 * (size_t)p->MC[i]));
+        p->bhat_df[i] = reinterpret_cast<df64x2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
+        p->twM_df[i] = reinterpret_cast<df64x2*>(f);
       }
     }
     KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
@@ -1161,14 +1259,27 @@ tau_status tau_setup(tau_problem* p) {
       const int N = p->n[i], K = N + 1;
       TRY(conv(p->s[i], &p->s32[i], N));
       TRY(conv(p->sintab[i], &p->sintab32[i], 2 * (size_t)K));
+      if (p->route[i] != ROUTE_DENSE) {
+        const int KK = p->route[i] == ROUTE_CHIRP ? p->KT[i] : K;
+        float* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(KK / 2 + 1)));
+        p->spec32[i] = reinterpret_cast<float2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(KK)));
+        p->twK32[i] = reinterpret_cast<float2*>(f);
+      }
       if (p->route[i] == ROUTE_FFT) {
         float* f = nullptr;
-        TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(K / 2 + 1)));
-        p->spec32[i] = reinterpret_cast<float2*>(f);
-        TRY(conv(reinterpret_cast<const double*>(p->twK[i]), &f, 2 * (size_t)twp_size(K)));
-        p->twK32[i] = reinterpret_cast<float2*>(f);
         TRY(conv(reinterpret_cast<const double*>(p->twK2[i]), &f, 2 * (size_t)twp_size(K / 2)));
         p->twK2_32[i] = reinterpret_cast<float2*>(f);
+      }
+      if (p->route[i] == ROUTE_CHIRP) {
+        float* f = nullptr;
+        TRY(conv(reinterpret_cast<const double*>(p->chirp[i]), &f, 2 * (size_t)(N + 1)));
+        p->chirp32[i] = reinterpret_cast<float2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->bhat[i]), &f, 2 * (size_t)p->MC[i]));
+        p->bhat32[i] = reinterpret_cast<float2*>(f);
+        TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
+        p->twM32[i] = reinterpret_cast<float2*>(f);
       }
     }
     KL(launch_f64_to_f32(p->invmu, p->invmu32, p->n_tot, p->st));
@@ -1288,7 +1399,10 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->ebar = p->ebar;
   out->e_hat = p->ehat;
   out->e_check = p->echeck;
-  for (int i = 0; i < 3; ++i) out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT : TAU_ROUTE_DENSE) : 0;
+  for (int i = 0; i < 3; ++i)
+    out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT
+                                                         : (p->route[i] == ROUTE_CHIRP ? TAU_ROUTE_CHIRP : TAU_ROUTE_DENSE))
+                             : 0;
   out->graph = p->graph_ok ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     out->lines_per_cta[i] = i < p->d ? base_pass_t<double>(p, i).lpb : 0;

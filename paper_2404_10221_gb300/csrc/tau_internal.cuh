@@ -25,7 +25,10 @@ __host__ __device__ inline int red_blocks(int64_t n) {
   return b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : (int)b);
 }
 
-enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2 };
+// FFT: n + 1 = K a power of two.  CHIRP: any n; the Toeplitz product uses a power-of-two circulant
+// embedding of length 2K >= 2(n+1), the DST-I a chirp-z convolution of power-of-two length M >= 2n.
+// DENSE: explicit O(n) sums per output.
+enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2, ROUTE_CHIRP = 3 };
 
 // What the value computed by a matvec pass becomes at the last dimension.
 enum Finish : int {
@@ -117,6 +120,13 @@ struct DimDataT {
   const T* s;           // FCD weights s_0..s_{n-1}
   const T* sintab;      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: (1/2) sqrt(2/K) sin(pi t / K)
   const T* cas;         // Strang circulant method: cas(2 pi t / n) / sqrt(n), t = 0..n-1
+  // CHIRP route DST-I: y_k = Im(w_k z_k) sqrt(2/L), z = a * conj(w) (linear convolution, L = n+1),
+  // a_j = w_j x_j, w_m = exp(i pi m^2 / (2L)); M = convolution length (power of two >= 2n)
+  int M;
+  const vec2<T>* chirp;  // w_m, m = 0..n
+  const vec2<T>* bhat;   // FFT_M of conj(w_|m|) placed at m mod M, in the digit-reversed order fft_dif
+                         // leaves, times sqrt(2/L)/M
+  const vec2<T>* twM;    // stage-packed twiddles of the length-M FFT
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
   const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I
 };
@@ -213,6 +223,9 @@ void set_last_error(const char* msg);
 template <typename T> size_t pass_smem_bytes(const PassT<T>& p);
 template <typename T> cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st);
 cudaError_t launch_spectrum(int K, const double* c, double* lam, const double2* twK, cudaStream_t st);
+// out[p] = scale * (DFT_M b) in the digit-reversed layout of fft_dif (one block, M <= 8192)
+cudaError_t launch_chirp_spectrum(int M, const double2* b, double2* out, const double2* twM, double scale,
+                                  cudaStream_t st);
 // Fill a stage-packed twiddle table (twp_size(S) entries) on the device.
 cudaError_t launch_twp(int S, double2* twp, cudaStream_t st);
 

@@ -601,33 +601,38 @@ __device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
 // Toeplitz product T x in place for every line: x_j at xs[l*xst + j].  FFT route: xst = 2K and
 // the line's 2K reals are the packed complex sequence z_j = (y_2j, y_2j+1) of the zero-padded
 // y (y_t = x_t for t < N, 0 otherwise), so packing is only y_N = 0 (the upper half is zero by
-// construction and skipped) and the product comes back in [0, N).  Dense route: xst = N.
+// construction and skipped) and the product comes back in [0, N).  Chirp route: the same with K the
+// power of two >= N + 1 and xst >= 2K.  Dense route: xst = N.
 template <typename T>
 __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
   using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
   const int TH = blockDim.x, tid = threadIdx.x;
-  if (P.dim.route == ROUTE_FFT) {
+  if (P.dim.route != ROUTE_DENSE) {
     const int K = P.dim.K;
-    // y_N = 0 completes z_{K/2-1}; z_j for j >= K/2 is zero and never read when the first DIF
+    // y_t = 0 for t in [N, K) (one slot on the FFT route, where K = N + 1); z_j for j >= K/2 is
+    // zero and never read when the first DIF
     // stage skips it (K >= 4, or K > 4 where the last DIF stage is fused into toep_mid).
     constexpr bool fused = !std::is_same<T, double>::value;
-    const int zn = (fused ? K > 4 : K >= 4) ? 1 : 2 * K - N;
+    const int zn = (fused ? K > 4 : K >= 4) ? K - N : 2 * K - N;
     for (int b = tid; b < lpb * zn; b += TH) {
       const int l = b / zn;
       xs[l * xst + N + (b - l * zn)] = from_f<T>(0.0f);
     }
     __syncthreads();
+    // line l's packed sequence starts at xs + l*xst (xst = 2K on the FFT route; on the chirp route
+    // the row is longer than the 2K reals the product uses)
     V* cb = reinterpret_cast<V*>(xs);
+    const int cs = xst >> 1;
     // outputs y_t, t < N, are z_j for j < K/2 (half_out of the inverse's last stage)
     if constexpr (fused) {
-      fft_dif(cb, K, lpb, K, P.dim.twK, K > 4, true);
-      toep_mid(cb, K, lpb, K, P.dim.spec);
-      fft_dit<true>(cb, K, lpb, K, P.dim.twK, true, true);
+      fft_dif(cb, cs, lpb, K, P.dim.twK, K > 4, true);
+      toep_mid(cb, cs, lpb, K, P.dim.spec);
+      fft_dit<true>(cb, cs, lpb, K, P.dim.twK, true, true);
     } else {
-      fft_dif(cb, K, lpb, K, P.dim.twK, K >= 4);
-      toep_spectral(cb, K, lpb, K, P.dim.spec);
-      fft_dit<true>(cb, K, lpb, K, P.dim.twK, true);
+      fft_dif(cb, cs, lpb, K, P.dim.twK, K >= 4);
+      toep_spectral(cb, cs, lpb, K, P.dim.spec);
+      fft_dit<true>(cb, cs, lpb, K, P.dim.twK, true);
     }
   } else {
     const T* __restrict__ s = P.dim.s;
@@ -829,6 +834,54 @@ __device__ __forceinline__ float2 dst_packed_input(const float* row, int m, int 
   return make_float2(w[0], w[1]);
 }
 
+// Orthonormal DST-I of every line in place for any n (CHIRP route), by the chirp-z identity
+// jk = (j^2 + k^2 - (k-j)^2)/2:  sum_j x_j exp(i pi jk/L) = w_k sum_j (w_j x_j) conj(w_{k-j}),
+// w_m = exp(i pi m^2/(2L)), L = n + 1, so y_k = sqrt(2/L) Im(w_k z_k) with z the linear convolution
+// of a_j = w_j x_j (j = 1..n) and conj(w_m) (|m| < n), computed as a circular one of length M >= 2n:
+// forward FFT of a (upper half zero), pointwise product with bhat (the kernel's FFT in the same
+// digit-reversed order, scaled by sqrt(2/L)/M), inverse FFT (only [0, M/2) needed).  a_j sits at
+// position j-1 and z_k comes out at k-1, so both stay inside [0, M/2) even when M = 2n.  The line's
+// data occupy xs[l*xst + 0..n-1]; the complex work buffer follows them (xst = npad + 2M).
+template <typename T>
+__device__ void dst_chirp_lines(const PassT<T>& P, T* xs, int xst) {
+  using V = vec2<T>;
+  const int N = P.len, lpb = P.lpb, M = P.dim.M;
+  const int TH = blockDim.x, tid = threadIdx.x;
+  const int npad = (N + 1) & ~1, cs = xst >> 1, lgM = __ffs(M) - 1;
+  V* cb = reinterpret_cast<V*>(xs + npad);   // line l at cb + l*cs (complex)
+  const V* __restrict__ w = P.dim.chirp;
+  const V* __restrict__ bh = P.dim.bhat;
+  const V z0 = mk<V>(from_f<T>(0.0f), from_f<T>(0.0f));
+  // position m holds a_{m+1} = w_{m+1} x_{m+1} for m < N; zero elsewhere in [0, M/2) (and in
+  // [M/2, M) when M <= 4, where the first DIF stage reads the whole line)
+  const int fill = M > 4 ? M >> 1 : M, lgf = __ffs(fill) - 1;
+  for (int b = tid; b < (lpb << lgf); b += TH) {
+    const int l = b >> lgf, m = b & (fill - 1);
+    V a = z0;
+    if (m < N) {
+      const T x = xs[l * xst + m];
+      const V wm = ldt(&w[m + 1]);
+      a = mk<V>(x * wm.x, x * wm.y);
+    }
+    cb[l * cs + m] = a;
+  }
+  __syncthreads();
+  fft_dif(cb, cs, lpb, M, P.dim.twM, M > 4);
+  for (int b = tid; b < (lpb << lgM); b += TH) {
+    const int l = b >> lgM, pos = b & (M - 1);
+    V* x = cb + l * cs + pos;
+    *x = cmul(*x, ldt(&bh[pos]));
+  }
+  __syncthreads();
+  fft_dit<true>(cb, cs, lpb, M, P.dim.twM, M > 4);
+  for (int b = tid; b < lpb * N; b += TH) {
+    const int l = b / N, k = b - l * N + 1;
+    const V z = cb[l * cs + k - 1], wk = ldt(&w[k]);
+    xs[l * xst + k - 1] = tfma(wk.x, z.y, wk.y * z.x);   // Im(w_k z_k)
+  }
+  __syncthreads();
+}
+
 // Orthonormal DST-I of every line in place: xs[l*xst + j] holds x_{j+1}; result y_{k} at
 // xs[l*xst + k-1].  FFT route: xst = 2K; the half-length complex FFT works in the line's upper
 // half [K, 2K), which holds no data (N < K).  Dense route: xst = N.
@@ -837,6 +890,10 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
   using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
   const int TH = blockDim.x, tid = threadIdx.x;
+  if (P.dim.route == ROUTE_CHIRP) {
+    dst_chirp_lines(P, xs, xst);
+    return;
+  }
   if (P.dim.route == ROUTE_FFT) {
     // DST-I through a real FFT of length K = N+1 (complex FFT of length K2 = K/2):
     //   w_j = sin(pi j/K)(x_j + x_{K-j}) + (x_j - x_{K-j})/2  (x_0 = x_K = 0),  W = DFT_K(w):
@@ -978,7 +1035,9 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
 // the FFT route, whose transforms run in place in the padded line, rs = N on the dense route).
 template <typename T>
 __device__ __forceinline__ int rc_stride(const PassT<T>& P) {
-  return P.dim.route == ROUTE_FFT ? 2 * P.dim.K : P.len;
+  if (P.dim.route == ROUTE_FFT) return 2 * P.dim.K;
+  if (P.dim.route == ROUTE_CHIRP) return ((P.len + 1) & ~1) + 2 * P.dim.M;   // data, then M complex
+  return P.len;
 }
 
 // Resident CTAs of 128 threads per SM the register budget allows: 7 for FP64 (72 registers; a
@@ -1129,11 +1188,15 @@ __global__ void __launch_bounds__(PASS_THREADS) k_ht_pass(const PassT<T> P) {
 template <typename T>
 size_t pass_smem_bytes(const PassT<T>& p) {
   const size_t ra = ((size_t)p.lpb * p.len + 1) & ~(size_t)1;
-  const size_t rs = p.dim.route == ROUTE_FFT ? 2 * (size_t)p.dim.K : (size_t)p.len;
+  size_t rs = (size_t)p.len;
+  if (p.dim.route == ROUTE_FFT) rs = 2 * (size_t)p.dim.K;
+  if (p.dim.route == ROUTE_CHIRP) rs = (((size_t)p.len + 1) & ~(size_t)1) + 2 * (size_t)p.dim.M;
   return (ra + (size_t)p.lpb * rs) * sizeof(T);
 }
 
 __global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ twK);
+__global__ void k_chirp_spectrum(int M, const double2* __restrict__ b, double2* out, const double2* __restrict__ twM,
+                                 double scale);
 
 cudaError_t init_kernel_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1143,6 +1206,8 @@ cudaError_t init_kernel_attributes() {
   e = cudaFuncSetAttribute(k_pass<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ht_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_chirp_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -1225,6 +1290,25 @@ __global__ void k_twp(int S, double2* twp) {
 
 cudaError_t launch_twp(int S, double2* twp, cudaStream_t st) {
   k_twp<<<(twp_size(S) + 255) / 256, 256, 0, st>>>(S, twp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// setup: spectrum of the chirp kernel of the CHIRP-route DST, left in fft_dif's digit-reversed order
+// ---------------------------------------------------------------------------
+__global__ void k_chirp_spectrum(int M, const double2* __restrict__ b, double2* out, const double2* __restrict__ twM,
+                                 double scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double2* cb = reinterpret_cast<double2*>(smraw);
+  for (int j = threadIdx.x; j < M; j += blockDim.x) cb[j] = b[j];
+  __syncthreads();
+  fft_dif(cb, M, 1, M, twM);
+  for (int j = threadIdx.x; j < M; j += blockDim.x) out[j] = make_double2(scale * cb[j].x, scale * cb[j].y);
+}
+
+cudaError_t launch_chirp_spectrum(int M, const double2* b, double2* out, const double2* twM, double scale,
+                                  cudaStream_t st) {
+  k_chirp_spectrum<<<1, PASS_THREADS, (size_t)M * sizeof(double2), st>>>(M, b, out, twM, scale);
   return cudaGetLastError();
 }
 

@@ -133,7 +133,7 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
   }
 
   const double dt = D.T / (double)D.M;
-  DimData dims[3];
+  DimData dims[3] = {};
   for (int i = 0; i < D.d; ++i) {
     const int n = (int)D.n[i], K = n + 1;
     double* dimb = base + NA_DIM0 + i * NA_DIM_STRIDE;

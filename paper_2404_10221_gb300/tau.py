@@ -37,6 +37,7 @@ TAU_SPGM = 2
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
+TAU_ROUTE_CHIRP = 3
 
 
 class tau_problem_desc(C.Structure):
