@@ -188,10 +188,10 @@ class ClockSampler:
 # 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
 # kernel sources that capture measured (sha256 below), else the bench reports null.
 TRAFFIC_CAPTURE = {
-    "bytes_per_matvec": 16916736 + 768 + 16961024 + 512 + 16901632 + 8492032,
+    "bytes_per_matvec": 16916992 + 768 + 16962816 + 768 + 16904960 + 8492800,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "3be7fb33e2125f2c11203f69caedbc8300d29724ee747079d99d6b84254963f9",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "3f2e0566c04a95edb61c853cf1f49320093af56d2a7fca21f4a5aef5f79629ce",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "b5b37da3abff65c627ccc7c863f19303717bc08e4f442fee67eae6111c6bdf09",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "37715cbea3afdeca8f91a423b37fe0b1be24b79efa5a627d1291ece0b2a456bc",
     },
 }
 
@@ -228,13 +228,13 @@ def pass_flops_2d(n: int) -> float:
     return lines * sum(per_line.values())
 
 
-def measure_steps(wl, precision, warm, timed, stream, dev, method=0):
+def measure_steps(wl, precision, warm, timed, stream, dev, method=0, route=(0, 0, 0)):
     """Time `timed` steps (CUDA events per step, L2 flushed between steps) after `warm` steps."""
     import torch
 
     from paper_2404_10221_gb300 import tau
 
-    prob = tau.Problem(wl, precision=precision, stream=stream.cuda_stream, method=method)
+    prob = tau.Problem(wl, precision=precision, route=route, stream=stream.cuda_stream, method=method)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tau.tau_step(prob.handle, warm)
     tau.tau_sync(prob.handle, allow_notconv=True)
@@ -297,6 +297,18 @@ def run_forms(stream, dev):
         "spgm_iters_per_step": float(np.mean(itsp)), "opgm_iters_per_step": float(np.mean(ito)),
         "rel_diff_vs_opgm": (torch.linalg.norm(usp - uo) / torch.linalg.norm(uo)).item(),
         "unit": UNIT, "dtype": "f64"}
+    # a grid whose n + 1 is not a power of two: 1000^2 on the chirp route against the same grid on
+    # the dense route and against the 1023^2 FFT-route headline (per-unknown throughput)
+    wl = W.c2_2d(n=1000)
+    vc, msc, uc, stc, itc = measure_steps(wl, tau.TAU_FP64, 2, 3, stream, dev)
+    vd, msd, ud, _, itd = measure_steps(wl, tau.TAU_FP64, 2, 3, stream, dev, route=(tau.TAU_ROUTE_DENSE,) * 3)
+    out["2d_1000_chirp"] = {
+        "workload": wl.name, "unknowns": wl.prob.n_tot, "route": [int(r) for r in stc.route[:2]],
+        "chirp_value": vc, "chirp_ms_per_step": msc, "dense_route_value": vd, "dense_route_ms_per_step": msd,
+        "chirp_over_dense_speedup": vc / vd, "chirp_over_fft_1023_value": vc / v64,
+        "rel_diff_vs_dense_route": (torch.linalg.norm(uc - ud) / torch.linalg.norm(ud)).item(),
+        "chirp_iters_per_step": float(np.mean(itc)), "dense_iters_per_step": float(np.mean(itd)),
+        "steps_compared": 5, "unit": UNIT, "dtype": "f64"}
     for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)
@@ -432,8 +444,9 @@ def run_serving(args, stream, dev):
                                   "p99_s": half.latency_p99_s, "completed": half.completed, "failed": half.failed},
             "plain_fp64_sequential_value": plain, "plain_sample_requests": args.plain_sample,
             "speedup_vs_plain_fp64": sat.throughput / plain,
-            "mix": "40% 1-D n in {1023,2047,4095}; 45% 2-D n in {127,255,511}^2; 15% 3-D n in {31,63,127}^3; "
-                   "M in [10,40]; mixed precision; latency = submit -> solution on the host"}
+            "mix": "40% 1-D n ~ U[1023,4095]; 45% 2-D n ~ U[127,2047] per axis; 15% 3-D n ~ U[63,255] per axis; "
+                   "M ~ U[10,40]; any n (FFT, chirp and dense routes); mixed precision; "
+                   "latency = submit -> solution on the host"}
 
 
 def aggregate_over_ranks(local_seconds: float, units_per_rank: float, world: int, device=None) -> tuple:

@@ -298,23 +298,29 @@ def random_positive(n: int, seed: int, lo: float = 0.5, hi: float = 2.0) -> np.n
     return rng.uniform(lo, hi, n)
 
 
-def serving_mix(count: int, seed: int = 20240416, M_range=(10, 40), precision_hint: str = "mixed") -> List[Workload]:
-    """Request mix of the served form: 40 % 1-D with n in {1023, 2047, 4095}, 45 % 2-D with n in
-    {127, 255, 511} per axis (uneven), 15 % 3-D with n in {31, 63, 127} per axis; M uniform in
-    M_range; alpha_i ~ U(1.1,1.9), kappa_i ~ U(0.2,1), e = 1 + a prod sin(pi x_i)(1+t), a ~ U(0.1,1).
-    Sizes are restricted to n+1 a power of two (the FFT route)."""
+def serving_mix(count: int, seed: int = 20240416, M_range=(10, 40), precision_hint: str = "mixed",
+                n1_range=(1023, 4095), n2_range=(127, 2047), n3_range=(63, 255)) -> List[Workload]:
+    """Request mix of the served form: 40 % 1-D with n uniform on n1_range, 45 % 2-D with n uniform on
+    n2_range per axis (uneven), 15 % 3-D with n uniform on n3_range per axis; M uniform in M_range;
+    alpha_i ~ U(1.1,1.9), kappa_i ~ U(0.2,1), e = 1 + a prod sin(pi x_i)(1+t), a ~ U(0.1,1).
+    Any integer n: lines whose n + 1 is a power of two take the FFT route, the others the chirp
+    route (n >= 128) or the dense one.  1-D lines are limited to n <= 4095 (one CTA per line)."""
     rng = SplitMix64(seed)
     out = []
     lo, hi = M_range
+
+    def draw(r):
+        return r[0] + int(rng.next_u64() % (r[1] - r[0] + 1))
+
     for _ in range(count):
         u = rng.uniform()
         M = lo + int(rng.uniform() * (hi - lo + 1))
         if u < 0.40:
-            d, n = 1, [rng.choice((1023, 2047, 4095))]
+            d, n = 1, [draw(n1_range)]
         elif u < 0.85:
-            d, n = 2, [rng.choice((127, 255, 511)), rng.choice((127, 255, 511))]
+            d, n = 2, [draw(n2_range), draw(n2_range)]
         else:
-            d, n = 3, [rng.choice((31, 63, 127)) for _ in range(3)]
+            d, n = 3, [draw(n3_range) for _ in range(3)]
         alpha = [rng.uniform(1.1, 1.9) for _ in range(d)]
         kappa = [rng.uniform(0.2, 1.0) for _ in range(d)]
         amp = rng.uniform(0.1, 1.0)
