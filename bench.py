@@ -398,6 +398,25 @@ def run_batched(args, stream, dev):
             "dtype": "f32 inner + f64 refinement", "launch": "one CUDA graph launch per step for all instances"}
 
 
+def served_precision(prob) -> int:
+    """Precision a served request asks for: the mixed form (FP32 inner solve, FP64 refinement) when
+    an FP32 matvec resolves the operator, i.e. eps_32 max_i eta_i ||s_i||_1 / e_min <= 0.05 with
+    eta_i = kappa_i dt / (2 h_i^alpha_i), ||s_i||_1 <= 2 s_0(alpha_i) and e >= 1 in the mix;
+    otherwise the double-float form (the FP32 error of eta T x, ~eps_32 eta ||s||_1 |x|, would
+    swamp the O(|x|) result that the cancelling Toeplitz sum leaves)."""
+    from paper_2404_10221_gb300 import tau
+
+    worst = 0.0
+    dt = prob.T / prob.M
+    for i in range(prob.d):
+        a = prob.alpha[i]
+        h = (prob.R[i] - prob.L[i]) / (prob.n[i] + 1)
+        eta = prob.kappa[i] * dt / (2.0 * h ** a)
+        s0 = math.gamma(a + 1.0) / math.gamma(a / 2.0 + 1.0) ** 2
+        worst = max(worst, eta * 2.0 * s0)
+    return tau.TAU_MIXED if 2.0 ** -23 * worst <= 0.05 else tau.TAU_DF64
+
+
 def run_serving(args, stream, dev):
     """Continuous batching: saturation throughput (all requests submitted at once) and latency
     under Poisson arrivals at half that throughput."""
@@ -408,7 +427,8 @@ def run_serving(args, stream, dev):
 
     wls = W.serving_mix(args.serve_requests, 20240416)
     tables = [wl.field_tables() for wl in wls]
-    descs = [tau.make_desc(wl.prob, precision=tau.TAU_MIXED) for wl in wls]
+    precs = [served_precision(wl.prob) for wl in wls]
+    descs = [tau.make_desc(wl.prob, precision=pr) for wl, pr in zip(wls, precs)]
     budget = 64 << 30
 
     def run(arrivals):
@@ -444,9 +464,12 @@ def run_serving(args, stream, dev):
                                   "p99_s": half.latency_p99_s, "completed": half.completed, "failed": half.failed},
             "plain_fp64_sequential_value": plain, "plain_sample_requests": args.plain_sample,
             "speedup_vs_plain_fp64": sat.throughput / plain,
-            "mix": "40% 1-D n ~ U[1023,4095]; 45% 2-D n ~ U[127,2047] per axis; 15% 3-D n ~ U[63,255] per axis; "
-                   "M ~ U[10,40]; any n (FFT, chirp and dense routes); mixed precision; "
-                   "latency = submit -> solution on the host"}
+            "mix": "40% 1-D n ~ U[1023,65535]; 45% 2-D n ~ U[127,2047] per axis; 15% 3-D n ~ U[63,255] per axis; "
+                   "M ~ U[10,40]; any n (FFT, chirp, dense and long-line routes); mixed precision where an "
+                   "FP32 matvec resolves the operator, double-float otherwise; "
+                   "latency = submit -> solution on the host",
+            "requests_mixed": sum(1 for pr in precs if pr == tau.TAU_MIXED),
+            "requests_double_float": sum(1 for pr in precs if pr == tau.TAU_DF64)}
 
 
 def aggregate_over_ranks(local_seconds: float, units_per_rank: float, world: int, device=None) -> tuple:

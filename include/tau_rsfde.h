@@ -77,9 +77,11 @@ typedef int tau_status;
                                  Hartley transform (dense, O(n_i) per element), B^{-1} by the DST.
                                  TAU_FP64 only; meant for comparisons at small n */
 
-#define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two, else chirp
-                                 for 128 <= n_i < 4096 (when one line fits in shared memory), else
-                                 dense */
+#define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two (<= 4096),
+                                 else chirp for 128 <= n_i < 4096 (when one line fits in shared
+                                 memory), else dense; d = 1: FFT for n+1 = 2^p <= 512, dense for
+                                 n < 128, long otherwise (one line in one CTA would leave the
+                                 other SMs idle) */
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
 #define TAU_ROUTE_DENSE 2     /* explicit n_i x n_i mode products (any n_i <= 8192) */
 #define TAU_ROUTE_CHIRP 3     /* any n_i < 4096: Toeplitz products through a power-of-two circulant
@@ -90,6 +92,10 @@ typedef int tau_status;
                                  elements) fits the chirp route up to n_i = 2048 and the dense
                                  route up to n_i = 6400; otherwise tau_create returns
                                  TAU_EUNSUPPORTED for a forced route */
+#define TAU_ROUTE_LONG 4      /* d = 1 only, any n (automatic from n = 128): the chirp route's
+                                 convolutions (length F = 2 K_T, K_T the power of two >= n+1) as
+                                 four-step FFTs over global memory, a few launches per operator
+                                 instead of one CTA per line; not with TAU_SPGM */
 
 typedef struct tau_problem tau_problem;
 
@@ -140,7 +146,7 @@ typedef struct {
   int max_iters_step;       /* largest per-step count so far */
   double last_relres;       /* |g_k| / ||r_0|| of the last step (preconditioned, Givens estimate) */
   double ebar, e_hat, e_check; /* Eqs. (bard), (dhat) */
-  int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT, _DENSE or _CHIRP) */
+  int route[3];             /* route chosen per dimension (TAU_ROUTE_FFT, _DENSE, _CHIRP or _LONG) */
   int graph;                /* 1 if steps run as CUDA-graph launches with device-side loop control */
   int64_t device_bytes;     /* device memory held by the problem */
   int64_t kernels_prologue; /* kernels of one step: prologue + iters * per_iter + epilogue */

@@ -23,7 +23,8 @@ __all__ = [
     "step_direct", "time_march", "l2_error", "OracleSolver", "fcd_apply_line",
     "gmres_paper_form", "theorem_c", "two_sided_gmres", "two_sided_structured", "beta_tensor",
     "apply_sine_diag", "numerical_range_bounds", "spectral_summary", "strang_circulant",
-    "circulant_dense", "strang_pc_eigs", "dense_Pc", "apply_Pc_inv", "spgm",
+    "circulant_dense", "strang_pc_eigs", "dense_Pc", "apply_Pc_inv", "spgm", "sine_rows",
+    "toeplitz_rows", "tau_eigs_q_at",
 ]
 
 
@@ -128,6 +129,32 @@ def tau_eigs_q(t: np.ndarray) -> np.ndarray:
         # angle pi j (i+1)/(N+1) with j (i+1) reduced modulo 2(N+1) (cos has period 2 pi)
         q += 2.0 * t[j] * np.cos(np.pi * ((j * i1) % (2 * (n + 1))) / (n + 1))
     return q
+
+
+def sine_rows(n: int, ks: np.ndarray) -> np.ndarray:
+    """Rows k (1-based, the entries of ks) of S of §3 (below Eq. (q)), for grids too large for
+    the whole matrix; j*k reduced modulo 2(N+1) as in sine_matrix."""
+    j = np.arange(1, n + 1, dtype=np.int64)
+    jk = np.outer(np.asarray(ks, dtype=np.int64), j) % (2 * (n + 1))
+    return math.sqrt(2.0 / (n + 1)) * np.sin(np.pi * jk / (n + 1))
+
+
+def toeplitz_rows(alpha: float, n: int, ks: np.ndarray) -> np.ndarray:
+    """Rows k (0-based, the entries of ks) of the Toeplitz S_{alpha_i} of Eq. (eq0): s_|k-j|."""
+    s = fcd_weights(alpha, n)
+    j = np.arange(n)
+    return s[np.abs(np.asarray(ks, dtype=np.int64)[:, None] - j[None, :])]
+
+
+def tau_eigs_q_at(t: np.ndarray, ks: np.ndarray) -> np.ndarray:
+    """q at the 1-based sine modes ks: q = t_0 + 2 sum_{j=1}^{N-1} t_j cos(pi j k/(N+1)), Eq. (q),
+    one mode at a time (O(N) each); j k reduced modulo 2(N+1)."""
+    n = len(t)
+    j = np.arange(1, n, dtype=np.int64)
+    out = np.empty(len(ks), dtype=np.float64)
+    for a, k in enumerate(np.asarray(ks, dtype=np.int64)):
+        out[a] = t[0] + 2.0 * np.dot(t[1:], np.cos(np.pi * ((j * k) % (2 * (n + 1))) / (n + 1)))
+    return out
 
 
 def beta_eigs(alpha: float, n: int) -> np.ndarray:

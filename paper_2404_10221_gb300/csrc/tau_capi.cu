@@ -85,6 +85,10 @@ struct tau_problem {
   df64x2 *chirp_df[3] = {nullptr, nullptr, nullptr}, *bhat_df[3] = {nullptr, nullptr, nullptr},
          *twM_df[3] = {nullptr, nullptr, nullptr};
   double2 *twK[3] = {nullptr, nullptr, nullptr}, *twK2[3] = {nullptr, nullptr, nullptr};
+  // LONG route (d = 1): four-step FFT tables per element type (work and ybuf shared by all three)
+  LongTab<double> lt64[3] = {};
+  LongTab<float> lt32[3] = {};
+  LongTab<df64> ltdf[3] = {};
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
   double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
@@ -250,6 +254,9 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
     D.K = p->KT[ax];
     D.M = p->MC[ax];
   }
+  if constexpr (std::is_same<T, double>::value) D.lng = &p->lt64[ax];
+  else if constexpr (std::is_same<T, df64>::value) D.lng = &p->ltdf[ax];
+  else D.lng = &p->lt32[ax];
   // shared memory per line: the line (N reals) plus the transform line (2K reals, FFT route) or a
   // second copy (N, dense route).  24 KB of lines per CTA lets 8 CTAs of 128 threads share an SM.
   size_t rs = (size_t)P.len;
@@ -286,6 +293,11 @@ using ChainIO = ChainT<double>;
 
 template <typename T>
 tau_status enq(const PassT<T>& P, cudaStream_t st) {
+  if (P.dim.route == ROUTE_LONG) {
+    tl_launches += long_launches(P) - 1;
+    KL(launch_long(P, *P.dim.lng, st));
+    return TAU_OK;
+  }
   KL(launch_pass(P, st));
   return TAU_OK;
 }
@@ -767,6 +779,10 @@ std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune_cache;
 template <typename T>
 tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   PassT<T> P = base_pass_t<T>(p, ax);   // heuristic tile (lpb_tuned not yet set for this axis)
+  if (P.dim.route == ROUTE_LONG) {        // no line tiles on the long-line route
+    p->lpb_tuned[prec_index<T>()][ax] = P.lpb;
+    return TAU_OK;
+  }
   const auto key = std::make_tuple(prec_index<T>(), P.dim.route, P.len, P.inner, P.nlines);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -858,6 +874,126 @@ tau_status sync_status(tau_problem* p) {
   return TAU_OK;
 }
 
+// LONG route tables of dimension i (d = 1): the four-step factorisation F = F1 x F2 of the
+// convolution length F = 2 K_T, the stage and four-step twiddles, the Toeplitz circulant spectrum
+// and the chirp-z kernel spectrum (both through the route's own forward transform, so they sit in
+// its output layout), the chirp w_m, the scratch, and q on the device (Eq. (q), O(n^2) work).
+tau_status setup_long(tau_problem* p, int i, const std::vector<double>& s) {
+  const int N = p->n[i];
+  int64_t kt = 2;
+  while (kt < (int64_t)N + 1) kt <<= 1;
+  const int F = (int)(2 * kt);
+  int lgF = 0;
+  while ((1 << lgF) < F) ++lgF;
+  const int F1 = 1 << ((lgF + 1) / 2), F2 = F / F1;
+  LongTab<double>& L = p->lt64[i];
+  L.n = N;
+  L.F = F;
+  L.F1 = F1;
+  L.F2 = F2;
+  L.cw = F2 < 2 ? F2 : 2;
+  {
+    int lpr = 4096 / F2;
+    const int par = F1 / 128 > 1 ? F1 / 128 : 1;   // keep about 128 row CTAs
+    if (lpr > par) lpr = par;
+    if (lpr < 1) lpr = 1;
+    L.lpr = lpr;
+  }
+  double2 *tw1 = nullptr, *tw2 = nullptr, *tw4 = nullptr, *lam = nullptr, *bh = nullptr, *w = nullptr;
+  TRY(dalloc_n(p, &tw1, (size_t)twp_size(F1)));
+  TRY(dalloc_n(p, &tw2, (size_t)twp_size(F2)));
+  TRY(dalloc_n(p, &tw4, (size_t)F));
+  TRY(dalloc_n(p, &lam, (size_t)F));
+  TRY(dalloc_n(p, &bh, (size_t)F));
+  KL(launch_twp(F1, tw1, p->st));
+  KL(launch_twp(F2, tw2, p->st));
+  KL(launch_long_tw4(F1, F2, tw4, p->st));
+  double2* work = nullptr;
+  double* ybuf = nullptr;
+  TRY(dalloc_n(p, &work, (size_t)F));             // 16 bytes per entry: any element type's complex
+  TRY(dalloc_n(p, &ybuf, 2 * (size_t)N));         // 16 bytes per entry: any element type
+  L.tw1 = tw1;
+  L.tw2 = tw2;
+  L.tw4 = tw4;
+  L.work = work;
+  L.ybuf = ybuf;
+  // chirp w_m = exp(i pi m^2/(2L)), m = 0..N (m^2 reduced mod 4L); kernel conj(w_|m|) at m mod F
+  const int64_t Lc = (int64_t)N + 1;
+  auto wph = [&](int64_t m) {
+    const int64_t r = (m * m) % (4 * Lc);
+    return make_double2(std::cos(M_PI * (double)r / (2.0 * (double)Lc)),
+                        std::sin(M_PI * (double)r / (2.0 * (double)Lc)));
+  };
+  std::vector<double2> wv((size_t)N + 1), host((size_t)F, make_double2(0.0, 0.0));
+  for (int m = 0; m <= N; ++m) wv[m] = wph(m);
+  TRY(upload(p, &w, wv.data(), wv.size()));
+  L.chirp = w;
+  // q's cosine table ct[t] = cos(pi t / L), t < 2L, and q's storage (tracked allocations first)
+  std::vector<double> ct(2 * (size_t)Lc);
+  for (int64_t t = 0; t < 2 * Lc; ++t) ct[t] = std::cos(M_PI * (double)t / (double)Lc);
+  double* dct = nullptr;
+  TRY(upload(p, &dct, ct.data(), ct.size()));
+  TRY(dalloc_n(p, &p->q[i], (size_t)N));
+  double2* src = nullptr;   // untracked staging buffer, freed before returning
+  CK(cudaMalloc(&src, (size_t)F * sizeof(double2)));
+  auto release = [&](tau_status st) {
+    cudaStreamSynchronize(p->st);
+    cudaFree(src);
+    src = nullptr;
+    return st;
+  };
+  // Toeplitz: c_0 = s_0, c_k = c_{F-k} = s_k (1 <= k < N); spectrum / F
+  host[0].x = s[0];
+  for (int k = 1; k < N; ++k) host[k].x = host[(size_t)F - k].x = s[k];
+  if (cudaMemcpy(src, host.data(), (size_t)F * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return release(fail(TAU_ECUDA, "long-route spectrum upload"));
+  if (launch_long_spectrum(L, src, lam, 1.0 / F, p->st) != cudaSuccess)
+    return release(fail(TAU_ECUDA, "long-route spectrum"));
+  // chirp kernel: spectrum * sqrt(2/L) / F
+  std::fill(host.begin(), host.end(), make_double2(0.0, 0.0));
+  for (int m = -(N - 1); m <= N - 1; ++m) {
+    const double2 v = wph(m < 0 ? -m : m);
+    host[(size_t)(((int64_t)m % F + F) % F)] = make_double2(v.x, -v.y);
+  }
+  if (cudaStreamSynchronize(p->st) != cudaSuccess ||
+      cudaMemcpy(src, host.data(), (size_t)F * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return release(fail(TAU_ECUDA, "long-route kernel upload"));
+  if (launch_long_spectrum(L, src, bh, std::sqrt(2.0 / (double)Lc) / F, p->st) != cudaSuccess)
+    return release(fail(TAU_ECUDA, "long-route kernel spectrum"));
+  L.lam = lam;
+  L.bhat = bh;
+  if (launch_q_direct(N, p->s[i], dct, p->q[i], p->st) != cudaSuccess) return release(fail(TAU_ECUDA, "q"));
+  return release(TAU_OK);
+}
+
+// The long-route tables of dimension i in another element type T (conv: double array -> T array
+// on the device); the scratch buffers are shared with the FP64 tables (16 bytes per entry).
+template <typename T, typename Conv>
+tau_status long_tables_as(tau_problem* p, int i, LongTab<T>& D, int cw, Conv conv) {
+  const LongTab<double>& L = p->lt64[i];
+  D.n = L.n;
+  D.F = L.F;
+  D.F1 = L.F1;
+  D.F2 = L.F2;
+  D.cw = L.F2 < cw ? L.F2 : cw;
+  D.lpr = L.lpr;
+  auto cvt = [&](const double2* src, const vec2<T>** dst, size_t cnt) -> tau_status {
+    T* f = nullptr;
+    TRY(conv(reinterpret_cast<const double*>(src), &f, 2 * cnt));
+    *dst = reinterpret_cast<const vec2<T>*>(f);
+    return TAU_OK;
+  };
+  TRY(cvt(L.tw1, &D.tw1, (size_t)twp_size(L.F1)));
+  TRY(cvt(L.tw2, &D.tw2, (size_t)twp_size(L.F2)));
+  TRY(cvt(L.tw4, &D.tw4, (size_t)L.F));
+  TRY(cvt(L.lam, &D.lam, (size_t)L.F));
+  TRY(cvt(L.bhat, &D.bhat, (size_t)L.F));
+  TRY(cvt(L.chirp, &D.chirp, (size_t)L.n + 1));
+  D.work = reinterpret_cast<vec2<T>*>(L.work);
+  D.ybuf = reinterpret_cast<T*>(L.ybuf);
+  return TAU_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -925,6 +1061,13 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     if (r == TAU_ROUTE_AUTO) {
       r = fft_ok ? TAU_ROUTE_FFT : (D.n[i] >= 128 && D.n[i] < KMAX ? TAU_ROUTE_CHIRP : TAU_ROUTE_DENSE);
       if (r == TAU_ROUTE_CHIRP && !fits(r)) r = TAU_ROUTE_DENSE;
+      // one line (d = 1): a CTA per line leaves the GPU idle; the four-step route spreads the
+      // transforms over the GPU and wins from n ~ 300 (measured; the FFT route keeps n + 1 <= 512)
+      if (D.d == 1 && D.method != TAU_SPGM && D.n[i] >= 128 && !(fft_ok && D.n[i] < 512)) r = TAU_ROUTE_LONG;
+    }
+    if (r == TAU_ROUTE_LONG && (D.d != 1 || D.method == TAU_SPGM)) {
+      delete p;
+      return fail(TAU_EUNSUPPORTED, "the long-line route serves d = 1 with the tau methods (dim %d)", i);
     }
     if (r == TAU_ROUTE_CHIRP && D.n[i] >= KMAX) {
       delete p;
@@ -939,16 +1082,19 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
       delete p;
       return fail(TAU_EUNSUPPORTED, "dense route limited to n <= 8192 (dim %d, n=%lld)", i, (long long)D.n[i]);
     }
-    if (r != TAU_ROUTE_FFT && r != TAU_ROUTE_DENSE && r != TAU_ROUTE_CHIRP) {
+    if (r != TAU_ROUTE_FFT && r != TAU_ROUTE_DENSE && r != TAU_ROUTE_CHIRP && r != TAU_ROUTE_LONG) {
       delete p;
       return fail(TAU_EINVAL, "route[%d]=%d", i, D.route[i]);
     }
-    if (!fits(r)) {
+    if (r != TAU_ROUTE_LONG && !fits(r)) {
       delete p;
       return fail(TAU_EUNSUPPORTED, "one line of dim %d (n=%lld) does not fit in shared memory on route %d", i,
                   (long long)D.n[i], r);
     }
-    p->route[i] = r == TAU_ROUTE_FFT ? ROUTE_FFT : (r == TAU_ROUTE_CHIRP ? ROUTE_CHIRP : ROUTE_DENSE);
+    p->route[i] = r == TAU_ROUTE_FFT     ? ROUTE_FFT
+                  : r == TAU_ROUTE_CHIRP ? ROUTE_CHIRP
+                  : r == TAU_ROUTE_LONG  ? ROUTE_LONG
+                                         : ROUTE_DENSE;
     if (p->route[i] == ROUTE_CHIRP) {
       p->KT[i] = (int)kt;
       p->MC[i] = (int)mc;
@@ -959,6 +1105,8 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     return s;
   };
   if (cudaError_t e = init_kernel_attributes(); e != cudaSuccess)
+    return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
+  if (cudaError_t e = init_long_attributes(); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
   if (cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
@@ -1114,7 +1262,8 @@ tau_status tau_setup(tau_problem* p) {
       TRY(upload(p, &p->sintab[i], st.data(), st.size()));
     }
     const bool chirp = p->route[i] == ROUTE_CHIRP;
-    if (p->route[i] != ROUTE_DENSE) {
+    const bool lng = p->route[i] == ROUTE_LONG;
+    if (p->route[i] == ROUTE_FFT || chirp) {
       // Toeplitz product: circulant embedding c of length 2KK (KK = K on the FFT route, the power
       // of two >= n+1 on the chirp route): c_0 = s_0, c_k = c_{2KK-k} = s_k (1 <= k < N), zeros
       // elsewhere.  On the FFT route its real spectrum at k = 1..N is also the eigenvalues q_k of
@@ -1146,7 +1295,8 @@ tau_status tau_setup(tau_problem* p) {
       if (!chirp)
         for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
     }
-    if (p->route[i] != ROUTE_FFT) {
+    if (lng) TRY(setup_long(p, i, s));
+    if (p->route[i] == ROUTE_DENSE || chirp) {
       // q_k = s_0 + 2 sum_j s_j cos(pi j k / K) (Eq. (q)) with a cosine table
       std::vector<double> ct(2 * (size_t)K);
       for (int t = 0; t < 2 * K; ++t) ct[t] = std::cos(M_PI * t / K);
@@ -1161,7 +1311,7 @@ tau_status tau_setup(tau_problem* p) {
         q[k - 1] = acc;
       }
     }
-    TRY(upload(p, &p->q[i], q.data(), q.size()));
+    if (!lng) TRY(upload(p, &p->q[i], q.data(), q.size()));
     if (chirp) {
       // chirp-z DST-I tables: w_m = exp(i pi m^2/(2L)), m = 0..N, L = N+1 (m^2 reduced mod 4L, the
       // period of the phase); kernel b_m = conj(w_|m|) for |m| < N placed at m mod MC; its FFT in
@@ -1224,7 +1374,7 @@ tau_status tau_setup(tau_problem* p) {
       const int N = p->n[i], K = N + 1;
       TRY(conv(p->s[i], &p->s_df[i], N));
       TRY(conv(p->sintab[i], &p->sintab_df[i], 2 * (size_t)K));
-      if (p->route[i] != ROUTE_DENSE) {
+      if (p->route[i] == ROUTE_FFT || p->route[i] == ROUTE_CHIRP) {
         const int KK = p->route[i] == ROUTE_CHIRP ? p->KT[i] : K;
         df64* f = nullptr;
         TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(KK / 2 + 1)));
@@ -1246,6 +1396,7 @@ tau_status tau_setup(tau_problem* p) {
         TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
         p->twM_df[i] = reinterpret_cast<df64x2*>(f);
       }
+      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->ltdf[i], 2, conv));
     }
     KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
   }
@@ -1259,7 +1410,7 @@ tau_status tau_setup(tau_problem* p) {
       const int N = p->n[i], K = N + 1;
       TRY(conv(p->s[i], &p->s32[i], N));
       TRY(conv(p->sintab[i], &p->sintab32[i], 2 * (size_t)K));
-      if (p->route[i] != ROUTE_DENSE) {
+      if (p->route[i] == ROUTE_FFT || p->route[i] == ROUTE_CHIRP) {
         const int KK = p->route[i] == ROUTE_CHIRP ? p->KT[i] : K;
         float* f = nullptr;
         TRY(conv(reinterpret_cast<const double*>(p->spec[i]), &f, 8 * (size_t)(KK / 2 + 1)));
@@ -1281,6 +1432,7 @@ tau_status tau_setup(tau_problem* p) {
         TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
         p->twM32[i] = reinterpret_cast<float2*>(f);
       }
+      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->lt32[i], 4, conv));
     }
     KL(launch_f64_to_f32(p->invmu, p->invmu32, p->n_tot, p->st));
     IRDev ir{};
@@ -1399,10 +1551,14 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->ebar = p->ebar;
   out->e_hat = p->ehat;
   out->e_check = p->echeck;
-  for (int i = 0; i < 3; ++i)
-    out->route[i] = i < p->d ? (p->route[i] == ROUTE_FFT ? TAU_ROUTE_FFT
-                                                         : (p->route[i] == ROUTE_CHIRP ? TAU_ROUTE_CHIRP : TAU_ROUTE_DENSE))
-                             : 0;
+  for (int i = 0; i < 3; ++i) {
+    const int r = i < p->d ? p->route[i] : 0;
+    out->route[i] = r == ROUTE_FFT     ? TAU_ROUTE_FFT
+                    : r == ROUTE_CHIRP ? TAU_ROUTE_CHIRP
+                    : r == ROUTE_LONG  ? TAU_ROUTE_LONG
+                    : r == ROUTE_DENSE ? TAU_ROUTE_DENSE
+                                       : 0;
+  }
   out->graph = p->graph_ok ? 1 : 0;
   for (int i = 0; i < 3; ++i) {
     out->lines_per_cta[i] = i < p->d ? base_pass_t<double>(p, i).lpb : 0;

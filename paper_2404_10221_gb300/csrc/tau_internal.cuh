@@ -27,8 +27,10 @@ __host__ __device__ inline int red_blocks(int64_t n) {
 
 // FFT: n + 1 = K a power of two.  CHIRP: any n; the Toeplitz product uses a power-of-two circulant
 // embedding of length 2K >= 2(n+1), the DST-I a chirp-z convolution of power-of-two length M >= 2n.
-// DENSE: explicit O(n) sums per output.
-enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2, ROUTE_CHIRP = 3 };
+// DENSE: explicit O(n) sums per output.  LONG (d = 1): lines longer than one CTA holds; the same
+// convolutions as CHIRP, through four-step FFTs in global memory (tau_long.cu).
+enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2, ROUTE_CHIRP = 3, ROUTE_LONG = 4 };
+
 
 // What the value computed by a matvec pass becomes at the last dimension.
 enum Finish : int {
@@ -105,6 +107,26 @@ template <> __device__ __forceinline__ df64 cvt<df64, df64>(df64 v) { return v; 
 template <> __device__ __forceinline__ double cvt<double, df64>(df64 v) { return to_d(v); }
 #endif
 
+// Device tables of the long-line route for one dimension, in the element type T.  Both
+// convolutions (Toeplitz product and chirp-z DST-I) have length F = 2 K_T (K_T the power of two
+// >= n + 1), computed as F = F1 x F2 four-step FFTs over the array work[r * F2 + c] (natural
+// index j = r F2 + c): F1-point DIFs down the columns, the twiddle tw4, F2-point DIFs along the
+// rows; the spectrum ends at work[p1 * F2 + p2] = X[k1 + F1 k2] with p = dif_pos(k, .).
+template <typename T>
+struct LongTab {
+  int n, F, F1, F2;
+  int cw;                 // columns per CTA of the column kernels
+  int lpr;                // rows per CTA of the row kernel
+  const vec2<T>* tw1;     // stage-packed twiddles of the F1-point FFT (twp_size(F1))
+  const vec2<T>* tw2;     // the same for F2
+  const vec2<T>* tw4;     // [p1 * F2 + j2] = exp(-2 pi i j2 k1 / F), p1 = dif_pos(k1, F1)
+  const vec2<T>* lam;     // Toeplitz circulant spectrum / F, in the spectrum layout
+  const vec2<T>* bhat;    // chirp kernel spectrum * sqrt(2/L) / F (L = n + 1), same layout
+  const vec2<T>* chirp;   // w_m = exp(i pi m^2 / (2L)), m = 0..n
+  vec2<T>* work;          // F complex (scratch shared by the precisions of one problem)
+  T* ybuf;                // n reals (scratch)
+};
+
 // Per-dimension data resident on the device, in the element type T of the pass (FP64 for the
 // plain path, FP32 for the inner solve of the mixed-precision form).
 template <typename T>
@@ -129,6 +151,7 @@ struct DimDataT {
   const vec2<T>* twM;    // stage-packed twiddles of the length-M FFT
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
   const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I
+  const LongTab<T>* lng;  // LONG route: host pointer to the dimension's tables (not read on the device)
 };
 using DimData = DimDataT<double>;
 
@@ -228,6 +251,20 @@ cudaError_t launch_chirp_spectrum(int M, const double2* b, double2* out, const d
                                   cudaStream_t st);
 // Fill a stage-packed twiddle table (twp_size(S) entries) on the device.
 cudaError_t launch_twp(int S, double2* twp, cudaStream_t st);
+
+// long-line route (tau_long.cu)
+cudaError_t init_long_attributes();
+// One line pass (the semantics of launch_pass for d = 1) as a sequence of four-step FFT launches.
+template <typename T> cudaError_t launch_long(const PassT<T>& p, const LongTab<T>& L, cudaStream_t st);
+// Kernels launch_long enqueues for the pass p.
+template <typename T> int long_launches(const PassT<T>& p);
+// Setup: tw4 of (F1, F2); the forward four-step FFT of src (F complex, natural order) scaled by
+// `scale` into dst (spectrum layout; work is overwritten); q_k = s_0 + 2 sum_j s_j cos(pi j k/(n+1))
+// with ct[t] = cos(pi t / (n+1)), t < 2(n+1).
+cudaError_t launch_long_tw4(int F1, int F2, double2* tw4, cudaStream_t st);
+cudaError_t launch_long_spectrum(const LongTab<double>& L, const double2* src, double2* dst, double scale,
+                                 cudaStream_t st);
+cudaError_t launch_q_direct(int n, const double* s, const double* ct, double* q, cudaStream_t st);
 
 // fields: e_m, Fdt_m for step m (read from g->m unless m_override >= 0)
 struct FieldDev {

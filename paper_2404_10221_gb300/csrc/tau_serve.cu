@@ -78,12 +78,20 @@ double now_s(const tau_server* s) {
 
 // Device bytes a request will hold (Krylov basis and work vectors), known before tau_create.
 int64_t estimate_bytes(const tau_problem_desc& d, int64_t n) {
+  // d = 1: the long-line route's tables and scratch (length F = 2 K_T, up to ~128 F bytes with
+  // the copies in the other element types and the setup's staging buffer)
+  int64_t lng = 0;
+  if (d.d == 1) {
+    int64_t kt = 2;
+    while (kt < n + 1) kt <<= 1;
+    lng = 128 * 2 * kt;
+  }
   if (d.precision == TAU_MIXED) {
     const int64_t k = d.inner_max_iter > 0 ? d.inner_max_iter : 30;
-    return (2 * k + 4) * n * 4 + 12 * n * 8 + (1 << 20);
+    return (2 * k + 4) * n * 4 + 12 * n * 8 + lng + (1 << 20);
   }
   // two-sided: two more vectors (the sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1})
-  return ((int64_t)d.max_iter + 11 + (d.method != TAU_OPGM ? 2 : 0)) * n * 8 + (1 << 20);
+  return ((int64_t)d.max_iter + 11 + (d.method != TAU_OPGM ? 2 : 0)) * n * 8 + lng + (1 << 20);
 }
 
 void finish(tau_server* s, const std::shared_ptr<Req>& r, tau_status st, const char* msg) {

@@ -38,6 +38,7 @@ TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
 TAU_ROUTE_CHIRP = 3
+TAU_ROUTE_LONG = 4
 
 
 class tau_problem_desc(C.Structure):

@@ -299,12 +299,12 @@ def random_positive(n: int, seed: int, lo: float = 0.5, hi: float = 2.0) -> np.n
 
 
 def serving_mix(count: int, seed: int = 20240416, M_range=(10, 40), precision_hint: str = "mixed",
-                n1_range=(1023, 4095), n2_range=(127, 2047), n3_range=(63, 255)) -> List[Workload]:
+                n1_range=(1023, 65535), n2_range=(127, 2047), n3_range=(63, 255)) -> List[Workload]:
     """Request mix of the served form: 40 % 1-D with n uniform on n1_range, 45 % 2-D with n uniform on
     n2_range per axis (uneven), 15 % 3-D with n uniform on n3_range per axis; M uniform in M_range;
     alpha_i ~ U(1.1,1.9), kappa_i ~ U(0.2,1), e = 1 + a prod sin(pi x_i)(1+t), a ~ U(0.1,1).
     Any integer n: lines whose n + 1 is a power of two take the FFT route, the others the chirp
-    route (n >= 128) or the dense one.  1-D lines are limited to n <= 4095 (one CTA per line)."""
+    route (n >= 128) or the dense one; 1-D lines with n >= 4096 the long-line route."""
     rng = SplitMix64(seed)
     out = []
     lo, hi = M_range

@@ -102,7 +102,8 @@ def problems():
         key = (d, tuple(n))
         if key not in cache:
             wl = _wl(d, n, max_iter=4)
-            cache[key] = (wl, _tau().Problem(wl))
+            # one-dimensional problems would take the long-line route automatically
+            cache[key] = (wl, _tau().Problem(wl, route=_chirp(1) if d == 1 else (0, 0, 0)))
         return cache[key]
 
     yield get
@@ -112,14 +113,19 @@ def problems():
 
 def test_auto_route_choice():
     tau = _tau()
-    cases = [((127,), tau.TAU_ROUTE_FFT), ((100,), tau.TAU_ROUTE_DENSE), ((128,), tau.TAU_ROUTE_CHIRP),
-             ((256,), tau.TAU_ROUTE_CHIRP), ((4094,), tau.TAU_ROUTE_CHIRP)]
+    # d = 1: FFT for n + 1 = 2^p <= 512, dense below 128, the long-line route otherwise
+    cases = [((127,), tau.TAU_ROUTE_FFT), ((511,), tau.TAU_ROUTE_FFT), ((100,), tau.TAU_ROUTE_DENSE),
+             ((128,), tau.TAU_ROUTE_LONG), ((1023,), tau.TAU_ROUTE_LONG), ((4094,), tau.TAU_ROUTE_LONG)]
     for n, want in cases:
         p = tau.Problem(_wl(1, n, max_iter=2))
         assert p.stats().route[0] == want, (n, p.stats().route[0])
         p.close()
+    # d >= 2: chirp for 128 <= n < 4096 with n + 1 not a power of two
+    p = tau.Problem(_wl(2, (128, 4094), max_iter=2))
+    assert p.stats().route[0] == tau.TAU_ROUTE_CHIRP and p.stats().route[1] == tau.TAU_ROUTE_CHIRP
+    p.close()
     # double-float lines of n > 2048 do not fit in shared memory on the chirp route: dense instead
-    p = tau.Problem(_wl(1, (3000,), max_iter=2), precision=tau.TAU_DF64)
+    p = tau.Problem(_wl(2, (3000, 5), max_iter=2), precision=tau.TAU_DF64)
     assert p.stats().route[0] == tau.TAU_ROUTE_DENSE
     p.close()
     with pytest.raises(tau.TauError) as ei:
@@ -172,7 +178,7 @@ def test_solve_parity(case):
     tau = _tau()
     d, n, M, x0 = case
     wl = _wl(d, n, M=M, x0_mode=x0)
-    p = tau.Problem(wl)
+    p = tau.Problem(wl, route=_chirp(1) if d == 1 else (0, 0, 0))
     assert all(p.stats().route[i] == tau.TAU_ROUTE_CHIRP for i in range(d) if n[i] >= 128)
     p.solve()
     u = p.solution().cpu().numpy()
@@ -208,7 +214,7 @@ def test_fp32_operators_parity(d, n):
     tau = _tau()
     wl = _wl(d, n, max_iter=4)
     pr = wl.prob
-    p = tau.Problem(wl, precision=tau.TAU_MIXED)
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, route=_chirp(1) if d == 1 else (0, 0, 0))
     t = wl.field_tables()
     ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
     x = W.random_vector(pr.n_tot, 43).astype(np.float32).astype(np.float64)

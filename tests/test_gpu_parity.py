@@ -85,7 +85,11 @@ def problems():
         key = (d, tuple(n))
         if key not in cache:
             wl = _wl(d, n, max_iter=4)
-            cache[key] = (wl, _tau().Problem(wl))
+            # one-dimensional lines of n >= 1023 would take the long-line route automatically; this
+            # file covers the one-CTA routes
+            fft = all(((m + 1) & m) == 0 for m in n)
+            route = (_tau().TAU_ROUTE_FFT, 0, 0) if d == 1 and fft else (0, 0, 0)
+            cache[key] = (wl, _tau().Problem(wl, route=route))
         return cache[key]
 
     yield get

@@ -85,3 +85,29 @@ def test_lemma_tauT(alpha, n):
 def test_toeplitz_S_spd():
     for alpha in [1.1, 1.5, 1.9]:
         assert np.linalg.eigvalsh(O.toeplitz_S(alpha, 25)).min() > 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 31, 100])
+def test_row_helpers_match_the_whole_matrices(n):
+    # sine_rows, toeplitz_rows and tau_eigs_q_at (the sampled forms used at sizes where the whole
+    # matrices do not fit) agree with sine_matrix, toeplitz_S and tau_eigs_q row by row.
+    ks1 = np.arange(1, n + 1)
+    assert np.array_equal(O.sine_rows(n, ks1), O.sine_matrix(n))
+    assert np.array_equal(O.toeplitz_rows(1.37, n, ks1 - 1), O.toeplitz_S(1.37, n))
+    t = O.fcd_weights(1.63, n)
+    assert np.allclose(O.tau_eigs_q_at(t, ks1), O.tau_eigs_q(t), rtol=1e-14, atol=1e-14)
+
+
+def test_row_helpers_closed_forms_at_large_n():
+    # Large-n special cases fixed by the mathematics: row k of S at the middle mode of an odd
+    # N + 1 = 2m alternates 0, +-sqrt(2/(N+1)) ... ; q of the tridiagonal t = (2, -1) is
+    # 2 - 2 cos(pi k/(N+1)) (the second-difference matrix, alpha = 2).
+    n = 65535
+    row = O.sine_rows(n, np.array([(n + 1) // 2]))[0]          # k = (N+1)/2: sin(pi j / 2)
+    j = np.arange(1, n + 1)
+    ref = math.sqrt(2.0 / (n + 1)) * np.where(j % 2 == 1, np.where(j % 4 == 1, 1.0, -1.0), 0.0)
+    assert np.allclose(row, ref, atol=1e-15)
+    t = np.zeros(n)
+    t[0], t[1] = 2.0, -1.0
+    ks = np.array([1, 17, 40000, n])
+    assert np.allclose(O.tau_eigs_q_at(t, ks), 2.0 - 2.0 * np.cos(np.pi * ks / (n + 1)), atol=1e-13)
