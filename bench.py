@@ -53,7 +53,12 @@ def parse():
                          "the NVTX range 'step' (ncu --nvtx --nvtx-include step/)")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="profiling driver: set up the workload (2 Krylov slots) and run this many "
-                         "preconditioned matvecs (4 line-pass launches each), then exit")
+                         "preconditioned matvecs (4 line-pass launches each on the 2-D FFT and chirp "
+                         "routes, 9 launches on the long-line route), then exit")
+    ap.add_argument("--matvec-n", type=int, default=1023,
+                    help="grid size per axis of --matvec-only (1023: FFT route; other n: chirp route in 2-D)")
+    ap.add_argument("--matvec-d", type=int, default=2, choices=[1, 2],
+                    help="dimension of --matvec-only (1: the 1-D workload, long-line route from n = 128)")
     ap.add_argument("--matvec-f32-3d", type=int, default=0,
                     help="profiling driver: the 3-D 255^3 workload in mixed precision (2 inner slots); run "
                          "this many FP32 A x (3 line passes) + M^{-1} r (5 line passes), then exit")
@@ -631,7 +636,9 @@ def run_matvec_only(args):
     from paper_2404_10221_gb300 import tau
     from paper_2404_10221_gb300 import workloads as W
 
-    wl = W.c2_2d()
+    # the 2-D workload at n per axis (1023: FFT route; other n: chirp route), or the 1-D workload
+    # (--matvec-d 1; long-line route from n = 128)
+    wl = W.c2_2d(n=args.matvec_n) if args.matvec_d == 2 else W.c1_1d(n=args.matvec_n)
     wl.prob.max_iter = 2
     p = tau.Problem(wl)
     x = torch.randn(wl.prob.n_tot, dtype=torch.float64, device="cuda")
@@ -644,8 +651,10 @@ def run_matvec_only(args):
         tau.tau_apply_MinvA(p.handle, 0, x, z)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    route = [int(r) for r in p.stats().route[:wl.prob.d]]
     p.close()
-    print(json.dumps({"matvec_only": args.matvec_only, "z_norm": float(torch.linalg.norm(z))}))
+    print(json.dumps({"matvec_only": args.matvec_only, "d": args.matvec_d, "n": args.matvec_n, "route": route,
+                      "z_norm": float(torch.linalg.norm(z))}))
     return 0
 
 

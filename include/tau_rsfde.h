@@ -85,11 +85,13 @@ typedef int tau_status;
 #define TAU_ROUTE_FFT 1       /* shared-memory FFT route (requires n_i+1 = 2^p, 2 <= n_i+1 <= 4096) */
 #define TAU_ROUTE_DENSE 2     /* explicit n_i x n_i mode products (any n_i <= 8192) */
 #define TAU_ROUTE_CHIRP 3     /* any n_i < 4096: Toeplitz products through a power-of-two circulant
-                                 embedding, DST-I through a chirp-z convolution of power-of-two
-                                 length >= 2 n_i (O(log n_i) per element).
+                                 embedding of length 2K (K the power of two >= n_i+1), DST-I of two
+                                 lines at once as one Bluestein DFT of length n_i+1 through a
+                                 convolution of power-of-two length >= 2 n_i (O(log n_i) per
+                                 element).
                                  Every route needs one line (the n_i values plus the route's work
                                  row) in at most 200 KB of shared memory: TAU_DF64 (16-byte
-                                 elements) fits the chirp route up to n_i = 2048 and the dense
+                                 elements) fits the chirp route up to n_i = 2047 and the dense
                                  route up to n_i = 6400; otherwise tau_create returns
                                  TAU_EUNSUPPORTED for a forced route */
 #define TAU_ROUTE_LONG 4      /* d = 1 only, any n (automatic from n = 128): the chirp route's

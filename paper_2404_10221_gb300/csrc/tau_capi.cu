@@ -76,7 +76,8 @@ struct tau_problem {
   int* iters = nullptr;
   double2* spec[3] = {nullptr, nullptr, nullptr};
   // CHIRP route: Toeplitz transform length KT (power of two >= n+1), DST convolution length MC
-  // (power of two >= 2n), the chirp w_m, the kernel spectrum and the length-MC twiddles
+  // (power of two >= 2n; Bluestein DFT of length n+1 for two lines at once), the chirp c_m, the
+  // kernel spectrum and the length-MC twiddles
   int KT[3] = {0, 0, 0}, MC[3] = {0, 0, 0};
   double2 *chirp[3] = {nullptr, nullptr, nullptr}, *bhat[3] = {nullptr, nullptr, nullptr},
           *twM[3] = {nullptr, nullptr, nullptr};
@@ -260,11 +261,12 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   // shared memory per line: the line (N reals) plus the transform line (2K reals, FFT route) or a
   // second copy (N, dense route).  24 KB of lines per CTA lets 8 CTAs of 128 threads share an SM.
   size_t rs = (size_t)P.len;
-  if (D.route == ROUTE_FFT) rs = 2 * (size_t)D.K;
-  if (D.route == ROUTE_CHIRP) rs = (((size_t)P.len + 1) & ~(size_t)1) + 2 * (size_t)D.M;
+  if (D.route == ROUTE_FFT || D.route == ROUTE_CHIRP) rs = 2 * (size_t)D.K;
   const size_t per_line = sizeof(T) * ((size_t)P.len + rs);
   int64_t lpb = (int64_t)(24576 / per_line);
   if (lpb < 1) lpb = 1;
+  // chirp route: two lines share one DST convolution; a single line pays for a pair's buffer anyway
+  if (D.route == ROUTE_CHIRP && lpb < 2) lpb = 2;
   if (lpb > 16) lpb = 16;
   const int64_t cap = ax == 0 ? P.nlines : inner;
   const int tuned = p->lpb_tuned[prec_index<T>()][ax];
@@ -891,11 +893,12 @@ tau_status setup_long(tau_problem* p, int i, const std::vector<double>& s) {
   L.F = F;
   L.F1 = F1;
   L.F2 = F2;
-  L.cw = F2 < 2 ? F2 : 2;
+  // one column per CTA and about F1/256 rows per CTA: at least 2 x 128 CTAs per launch where the
+  // transform allows (with 128 CTAs on 152 SMs the launches ran at ~6 % occupancy, latency-bound)
+  L.cw = 1;
   {
-    int lpr = 4096 / F2;
-    const int par = F1 / 128 > 1 ? F1 / 128 : 1;   // keep about 128 row CTAs
-    if (lpr > par) lpr = par;
+    int lpr = F1 / 256;
+    if (lpr > 4096 / F2) lpr = 4096 / F2;
     if (lpr < 1) lpr = 1;
     L.lpr = lpr;
   }
@@ -1053,9 +1056,10 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     const size_t nn = (size_t)D.n[i], npad = (nn + 1) & ~(size_t)1;
     size_t kt = 2, mc = 2;
     while (kt < nn + 1) kt <<= 1;
-    while (mc < 2 * nn) mc <<= 1;
+    while (mc < 2 * nn) mc <<= 1;   // chirp route: DST convolution length (2 kt, or kt for n = 2^p)
+    // (chirp: rows of 2K_T reals allocated in pairs, so one line takes two rows)
     auto fits = [&](int route) {
-      const size_t rs = route == TAU_ROUTE_FFT ? 2 * (nn + 1) : (route == TAU_ROUTE_CHIRP ? npad + 2 * mc : nn);
+      const size_t rs = route == TAU_ROUTE_FFT ? 2 * (nn + 1) : (route == TAU_ROUTE_CHIRP ? 4 * kt : nn);
       return esz * (npad + rs) <= 200 * 1024;
     };
     if (r == TAU_ROUTE_AUTO) {
@@ -1313,20 +1317,20 @@ tau_status tau_setup(tau_problem* p) {
     }
     if (!lng) TRY(upload(p, &p->q[i], q.data(), q.size()));
     if (chirp) {
-      // chirp-z DST-I tables: w_m = exp(i pi m^2/(2L)), m = 0..N, L = N+1 (m^2 reduced mod 4L, the
-      // period of the phase); kernel b_m = conj(w_|m|) for |m| < N placed at m mod MC; its FFT in
-      // fft_dif's order times sqrt(2/L)/MC
+      // chirp-z DST-I tables (two lines per Bluestein DFT of length L = N+1): c_m = exp(-i pi m^2/L),
+      // m = 0..N (m^2 reduced mod 2L, the period of the phase); kernel b_m = conj(c_|m|) for |m| <= N
+      // placed at m mod MC (MC = power of two >= 2N; b_N and b_{-N} coincide when MC = 2N, with one
+      // value); its FFT in fft_dif's order times sqrt(2/L)/(2 MC)
       const int MCi = p->MC[i];
       const int64_t L = N + 1;
-      auto wph = [&](int64_t m) {
-        const int64_t r = (m * m) % (4 * L);
-        return make_double2(std::cos(M_PI * (double)r / (2.0 * (double)L)),
-                            std::sin(M_PI * (double)r / (2.0 * (double)L)));
+      auto cph = [&](int64_t m) {
+        const int64_t r = (m * m) % (2 * L);
+        return make_double2(std::cos(M_PI * (double)r / (double)L), -std::sin(M_PI * (double)r / (double)L));
       };
       std::vector<double2> w(N + 1), bk(MCi, make_double2(0.0, 0.0));
-      for (int m = 0; m <= N; ++m) w[m] = wph(m);
-      for (int m = -(N - 1); m <= N - 1; ++m) {
-        const double2 v = wph(m < 0 ? -m : m);
+      for (int m = 0; m <= N; ++m) w[m] = cph(m);
+      for (int m = -N; m <= N; ++m) {
+        const double2 v = cph(m < 0 ? -m : m);
         bk[((m % MCi) + MCi) % MCi] = make_double2(v.x, -v.y);
       }
       TRY(upload(p, &p->chirp[i], w.data(), w.size()));
@@ -1335,7 +1339,7 @@ tau_status tau_setup(tau_problem* p) {
       double2* db = nullptr;
       TRY(upload(p, &db, bk.data(), bk.size()));
       TRY(dalloc_n(p, &p->bhat[i], (size_t)MCi));
-      KL(launch_chirp_spectrum(MCi, db, p->bhat[i], p->twM[i], std::sqrt(2.0 / (double)L) / MCi, p->st));
+      KL(launch_chirp_spectrum(MCi, db, p->bhat[i], p->twM[i], std::sqrt(2.0 / (double)L) / (2.0 * MCi), p->st));
     }
   }
   // ebar (Eqs. (bard), (dhat))
@@ -1396,7 +1400,7 @@ tau_status tau_setup(tau_problem* p) {
         TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
         p->twM_df[i] = reinterpret_cast<df64x2*>(f);
       }
-      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->ltdf[i], 2, conv));
+      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->ltdf[i], 1, conv));
     }
     KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
   }
@@ -1432,7 +1436,7 @@ tau_status tau_setup(tau_problem* p) {
         TRY(conv(reinterpret_cast<const double*>(p->twM[i]), &f, 2 * (size_t)twp_size(p->MC[i])));
         p->twM32[i] = reinterpret_cast<float2*>(f);
       }
-      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->lt32[i], 4, conv));
+      if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->lt32[i], 1, conv));
     }
     KL(launch_f64_to_f32(p->invmu, p->invmu32, p->n_tot, p->st));
     IRDev ir{};

@@ -26,7 +26,8 @@ __host__ __device__ inline int red_blocks(int64_t n) {
 }
 
 // FFT: n + 1 = K a power of two.  CHIRP: any n; the Toeplitz product uses a power-of-two circulant
-// embedding of length 2K >= 2(n+1), the DST-I a chirp-z convolution of power-of-two length M >= 2n.
+// embedding of length 2K >= 2(n+1), the DST-I (two lines at a time) a Bluestein DFT of length n+1
+// through a convolution of power-of-two length >= 2n.
 // DENSE: explicit O(n) sums per output.  LONG (d = 1): lines longer than one CTA holds; the same
 // convolutions as CHIRP, through four-step FFTs in global memory (tau_long.cu).
 enum Route : int { ROUTE_FFT = 1, ROUTE_DENSE = 2, ROUTE_CHIRP = 3, ROUTE_LONG = 4 };
@@ -142,12 +143,13 @@ struct DimDataT {
   const T* s;           // FCD weights s_0..s_{n-1}
   const T* sintab;      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: (1/2) sqrt(2/K) sin(pi t / K)
   const T* cas;         // Strang circulant method: cas(2 pi t / n) / sqrt(n), t = 0..n-1
-  // CHIRP route DST-I: y_k = Im(w_k z_k) sqrt(2/L), z = a * conj(w) (linear convolution, L = n+1),
-  // a_j = w_j x_j, w_m = exp(i pi m^2 / (2L)); M = convolution length (power of two >= 2n)
+  // CHIRP route DST-I: two lines share one DFT of length L = n+1 (the real-DFT form of the DST-I),
+  // taken by Bluestein's method with c_m = exp(-i pi m^2 / L); M = convolution length (power of two
+  // >= 2n: 2K, or K when n is a power of two)
   int M;
-  const vec2<T>* chirp;  // w_m, m = 0..n
-  const vec2<T>* bhat;   // FFT_M of conj(w_|m|) placed at m mod M, in the digit-reversed order fft_dif
-                         // leaves, times sqrt(2/L)/M
+  const vec2<T>* chirp;  // c_m, m = 0..n
+  const vec2<T>* bhat;   // FFT_M of conj(c_|m|) placed at m mod M, in the digit-reversed order fft_dif
+                         // leaves, times sqrt(2/L)/(2M)
   const vec2<T>* twM;    // stage-packed twiddles of the length-M FFT
   const vec2<T>* twK;   // FFT route: stage-packed twiddles of the length-K FFT, then W (see twp_size)
   const vec2<T>* twK2;  // FFT route: the same for the length-K/2 FFT of the DST-I

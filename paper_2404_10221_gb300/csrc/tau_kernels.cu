@@ -517,64 +517,114 @@ __device__ __forceinline__ float2 dst_packed_input(const float* row, int m, int 
   return make_float2(w[0], w[1]);
 }
 
-// Orthonormal DST-I of every line in place for any n (CHIRP route), by the chirp-z identity
-// jk = (j^2 + k^2 - (k-j)^2)/2:  sum_j x_j exp(i pi jk/L) = w_k sum_j (w_j x_j) conj(w_{k-j}),
-// w_m = exp(i pi m^2/(2L)), L = n + 1, so y_k = sqrt(2/L) Im(w_k z_k) with z the linear convolution
-// of a_j = w_j x_j (j = 1..n) and conj(w_m) (|m| < n), computed as a circular one of length M >= 2n:
-// forward FFT of a (upper half zero), pointwise product with bhat (the kernel's FFT in the same
-// digit-reversed order, scaled by sqrt(2/L)/M), inverse FFT (only [0, M/2) needed).  a_j sits at
-// position j-1 and z_k comes out at k-1, so both stay inside [0, M/2) even when M = 2n.  The line's
-// data occupy xs[l*xst + 0..n-1]; the complex work buffer follows them (xst = npad + 2M).
+// Chirp route DST-I of every line in place, two lines per convolution.  As on the FFT route the
+// DST-I of a line is a real DFT of length L = n + 1 of w_j = sin(pi j/L)(x_j + x_{L-j}) +
+// (x_j - x_{L-j})/2 (x_0 = x_L = 0): y_{2k} = -Im W_k, y_{2k+1} - y_{2k-1} = Re W_k, y_1 = Re W_0/2
+// (scaled by sqrt(2/L)).  Lines a, b of a pair share one complex DFT of v = w^a + i w^b, taken by
+// Bluestein's method: with c_m = exp(-i pi m^2/L), V_k = c_k sum_j (v_j c_j) conj(c_{k-j}) (v_0 = 0,
+// so the lags k - j span [-n, n-1]), a circular convolution of power-of-two length M >= 2n run as
+// forward DIF (upper half zero), product with the kernel's spectrum bhat (digit-reversed order of
+// the DIF, scaled by sqrt(2/L)/(2M)) and inverse DIT.  When M >= 2L, v_j sits at j and the inverse
+// computes its first half only; when M = 2n (n a power of two) v_j sits at j - 1, inside the half
+// the first DIF stage reads, and the inverse runs in full (z_0 lands at M - 1).  Then
+// W^a_k = V_k + conj V_{L-k}, W^b_k = -i (V_k - conj V_{L-k}) (V_L = V_0); the prefix sum gives
+// the odd outputs.
+// Layout: rows of xst = 2K reals (an even number of them: an odd last line pairs with a zero line);
+// the pair buffer of lines 2p, 2p+1 is their two rows (2K complex).  The lines are first copied to
+// scr (n reals per line), which also takes the recombined outputs before they return to the rows.
 template <typename T>
-__device__ void dst_chirp_lines(const PassT<T>& P, T* xs, int xst) {
+__device__ void dst_chirp_lines(const PassT<T>& P, T* xs, int xst, T* scr) {
   using V = vec2<T>;
-  const int N = P.len, lpb = P.lpb, M = P.dim.M;
+  const int N = P.len, lpb = P.lpb, M = P.dim.M, L = N + 1, K = P.dim.K;
   const int TH = blockDim.x, tid = threadIdx.x;
-  const int npad = (N + 1) & ~1, cs = xst >> 1, lgM = __ffs(M) - 1;
-  V* cb = reinterpret_cast<V*>(xs + npad);   // line l at cb + l*cs (complex)
-  const V* __restrict__ w = P.dim.chirp;
+  const int npair = (lpb + 1) >> 1;
+  const V* __restrict__ c = P.dim.chirp;
   const V* __restrict__ bh = P.dim.bhat;
-  const V z0 = mk<V>(from_f<T>(0.0f), from_f<T>(0.0f));
-  // position m holds a_{m+1} = w_{m+1} x_{m+1} for m < N; zero elsewhere in [0, M/2) (and in
-  // [M/2, M) when M <= 4, where the first DIF stage reads the whole line)
-  const int fill = M > 4 ? M >> 1 : M, lgf = __ffs(fill) - 1;
-  for (int b = tid; b < (lpb << lgf); b += TH) {
-    const int l = b >> lgf, m = b & (fill - 1);
-    V a = z0;
-    if (m < N) {
-      const T x = xs[l * xst + m];
-      const V wm = ldt(&w[m + 1]);
-      a = mk<V>(x * wm.x, x * wm.y);
-    }
-    cb[l * cs + m] = a;
+  const T* __restrict__ sn = P.dim.sintab;   // sin(pi t / L)
+  const T z0 = from_f<T>(0.0f), half = from_f<T>(0.5f);
+  V* cb = reinterpret_cast<V*>(xs);           // pair p at cb + p*xst (complex)
+  for (int b = tid; b < lpb * N; b += TH) {
+    const int l = b / N;
+    scr[b] = xs[l * xst + (b - l * N)];
   }
   __syncthreads();
-  fft_dif(cb, cs, lpb, M, P.dim.twM, M > 4);
-  for (int b = tid; b < (lpb << lgM); b += TH) {
-    const int l = b >> lgM, pos = b & (M - 1);
-    V* x = cb + l * cs + pos;
+  // v_j c_j at position j - sh for 1 <= j < L; zero elsewhere up to M/2 (the whole line when M <= 4,
+  // where the first DIF stage reads it)
+  const int sh = M < 2 * L ? 1 : 0;
+  const int fill = M > 4 ? M >> 1 : M, lgf = __ffs(fill) - 1;
+  for (int b = tid; b < (npair << lgf); b += TH) {
+    const int pr = b >> lgf, pos = b & (fill - 1), j = pos + sh;
+    V v = mk<V>(z0, z0);
+    if (j > 0 && j < L) {
+      const T s = sn[j];
+      T w[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int l = 2 * pr + r;
+        w[r] = z0;
+        if (l < lpb) {
+          const T xj = scr[l * N + j - 1], xk = scr[l * N + L - j - 1];
+          w[r] = tfma(s, xj + xk, half * (xj - xk));
+        }
+      }
+      v = cmul(mk<V>(w[0], w[1]), ldt(&c[j]));
+    }
+    cb[pr * xst + pos] = v;
+  }
+  __syncthreads();
+  const int lgM = __ffs(M) - 1;
+  fft_dif(cb, xst, npair, M, P.dim.twM, M > 4);
+  for (int b = tid; b < (npair << lgM); b += TH) {
+    const int pr = b >> lgM, pos = b & (M - 1);
+    V* x = cb + pr * xst + pos;
     *x = cmul(*x, ldt(&bh[pos]));
   }
   __syncthreads();
-  fft_dit<true>(cb, cs, lpb, M, P.dim.twM, M > 4);
-  for (int b = tid; b < lpb * N; b += TH) {
-    const int l = b / N, k = b - l * N + 1;
-    const V z = cb[l * cs + k - 1], wk = ldt(&w[k]);
-    xs[l * xst + k - 1] = tfma(wk.x, z.y, wk.y * z.x);   // Im(w_k z_k)
+  fft_dit<true>(cb, xst, npair, M, P.dim.twM, M > 4 && !sh);
+  // recombination, k = 0..N/2 (z_k at position (k - sh) mod M): Re W_k to scr[2k] (odd outputs, before the prefix sum), -Im W_k =
+  // y_{2k} to scr[2k-1]
+  const int nk = N / 2 + 1;
+  for (int b = tid; b < npair * nk; b += TH) {
+    const int pr = b / nk, k = b - pr * nk, km = k ? L - k : 0;
+    const V vk = cmul(ldt(&c[k]), cb[pr * xst + ((k - sh) & (M - 1))]);
+    const V vm = cmul(ldt(&c[km]), cb[pr * xst + ((km - sh) & (M - 1))]);
+    const V wa = mk<V>(vk.x + vm.x, vk.y - vm.y);
+    const V wb = mk<V>(vk.y + vm.y, vm.x - vk.x);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int l = 2 * pr + r;
+      if (l >= lpb) continue;
+      const V W = r ? wb : wa;
+      if (2 * k < N) scr[l * N + 2 * k] = W.x;
+      if (k >= 1) scr[l * N + 2 * k - 1] = -W.y;
+    }
   }
   __syncthreads();
+  // back to the rows, zero from n to K (the prefix sum runs over the K/2 even slots below K)
+  const int lgK = __ffs(K) - 1;
+  for (int b = tid; b < (lpb << lgK); b += TH) {
+    const int l = b >> lgK, j = b & (K - 1);
+    xs[l * xst + j] = j < N ? scr[l * N + j] : z0;
+  }
+  __syncthreads();
+  if constexpr (std::is_same<T, double>::value) {
+    prefix_segments(xs, xst, lpb, K >> 1);
+  } else {
+    prefix_warps(xs, xst, lpb, K >> 1);
+  }
 }
 
 // Orthonormal DST-I of every line in place: xs[l*xst + j] holds x_{j+1}; result y_{k} at
 // xs[l*xst + k-1].  FFT route: xst = 2K; the half-length complex FFT works in the line's upper
-// half [K, 2K), which holds no data (N < K).  Dense route: xst = N.
+// half [K, 2K), which holds no data (N < K).  Chirp route: xst = 2K (K the power of two >= n+1),
+// scr holds n reals per line.  Dense route: xst = N.
 template <typename T>
-__device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
+__device__ void dst_lines(const PassT<T>& P, T* xs, int xst, T* scr) {
   using V = vec2<T>;
   const int N = P.len, lpb = P.lpb;
   const int TH = blockDim.x, tid = threadIdx.x;
   if (P.dim.route == ROUTE_CHIRP) {
-    dst_chirp_lines(P, xs, xst);
+    dst_chirp_lines(P, xs, xst, scr);
     return;
   }
   if (P.dim.route == ROUTE_FFT) {
@@ -715,11 +765,12 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst) {
 // the line-pass kernel
 // ---------------------------------------------------------------------------
 // Shared memory: ra (lpb*N reals, rounded up to even) then rc (lpb lines of rs reals; rs = 2K on
-// the FFT route, whose transforms run in place in the padded line, rs = N on the dense route).
+// the FFT and chirp routes, whose transforms run in place in the padded line (the chirp route
+// allocates its rows in pairs), rs = N on the dense route).
 template <typename T>
 __device__ __forceinline__ int rc_stride(const PassT<T>& P) {
   if (P.dim.route == ROUTE_FFT) return 2 * P.dim.K;
-  if (P.dim.route == ROUTE_CHIRP) return ((P.len + 1) & ~1) + 2 * P.dim.M;   // data, then M complex
+  if (P.dim.route == ROUTE_CHIRP) return 2 * P.dim.K;   // K: the power of two >= n + 1
   return P.len;
 }
 
@@ -818,7 +869,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
   }
 
   if (P.post == POST_DST || P.post == POST_DST_MU_DST) {
-    dst_lines(P, rc, RS);
+    dst_lines(P, rc, RS, ra);
     if (P.post == POST_DST_MU_DST) {
       tile_load(tg, N, lpb, P.invmu, ra, N);
       __syncthreads();
@@ -828,7 +879,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
         rc[l * RS + j] *= ra[l * N + j];
       }
       __syncthreads();
-      dst_lines(P, rc, RS);
+      dst_lines(P, rc, RS, ra);
     }
   }
   tile_store(tg, N, lpb, rc, RS, out_a);
@@ -873,8 +924,12 @@ size_t pass_smem_bytes(const PassT<T>& p) {
   const size_t ra = ((size_t)p.lpb * p.len + 1) & ~(size_t)1;
   size_t rs = (size_t)p.len;
   if (p.dim.route == ROUTE_FFT) rs = 2 * (size_t)p.dim.K;
-  if (p.dim.route == ROUTE_CHIRP) rs = (((size_t)p.len + 1) & ~(size_t)1) + 2 * (size_t)p.dim.M;
-  return (ra + (size_t)p.lpb * rs) * sizeof(T);
+  size_t rows = (size_t)p.lpb;
+  if (p.dim.route == ROUTE_CHIRP) {   // rows in pairs: a pair's two rows are its DST buffer
+    rs = 2 * (size_t)p.dim.K;
+    rows = (rows + 1) & ~(size_t)1;
+  }
+  return (ra + rows * rs) * sizeof(T);
 }
 
 __global__ void k_spectrum(int K, const double* __restrict__ c, double* lam, const double2* __restrict__ twK);

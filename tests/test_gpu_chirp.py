@@ -124,7 +124,7 @@ def test_auto_route_choice():
     p = tau.Problem(_wl(2, (128, 4094), max_iter=2))
     assert p.stats().route[0] == tau.TAU_ROUTE_CHIRP and p.stats().route[1] == tau.TAU_ROUTE_CHIRP
     p.close()
-    # double-float lines of n > 2048 do not fit in shared memory on the chirp route: dense instead
+    # double-float lines of n > 2047 do not fit in shared memory on the chirp route: dense instead
     p = tau.Problem(_wl(2, (3000, 5), max_iter=2), precision=tau.TAU_DF64)
     assert p.stats().route[0] == tau.TAU_ROUTE_DENSE
     p.close()
