@@ -77,6 +77,10 @@ typedef int tau_status;
                                  Hartley transform (dense, O(n_i) per element), B^{-1} by the DST.
                                  TAU_FP64 only; meant for comparisons at small n */
 
+#define TAU_TC_AUTO 0
+#define TAU_TC_OFF 1
+#define TAU_TC_ON 2
+
 #define TAU_ROUTE_AUTO 0      /* per-dimension choice: FFT when n_i+1 is a power of two (<= 4096),
                                  else chirp for 128 <= n_i < 4096 (when one line fits in shared
                                  memory), else dense; d = 1: FFT for n+1 = 2^p <= 512, dense for
@@ -125,6 +129,12 @@ typedef struct {
                            sweep targets the reduction still needed, 0.3 refine_tol rho_0 / rho,
                            kept within [min(1e-6, inner_tol), inner_tol] */
   int method;           /* TAU_OPGM (0, default), TAU_TPGM or TAU_SPGM */
+  int tc;               /* TAU_MIXED only: the DST-I passes of the FP32 τ solve on dimensions with
+                           n_i <= 256 as tensor-core (tcgen05, TF32) mode products (relative error
+                           ~1e-3: the flexible inner GMRES takes the result as its preconditioner).
+                           TAU_TC_AUTO (0, default): tau_setup times the FP32 τ solve both ways and
+                           keeps the faster (cached per grid shape); TAU_TC_OFF (1): line passes;
+                           TAU_TC_ON (2): tensor cores wherever n_i <= 256 */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
@@ -161,6 +171,8 @@ typedef struct {
                                by the setup's autotuner (problems with >= 65536 unknowns, or
                                TAU_AUTOTUNE=1; TAU_AUTOTUNE=0 keeps the shared-memory heuristic) */
   int lines_per_cta_f32[3]; /* the same for the FP32 passes of a TAU_MIXED problem */
+  int tc_dims;              /* bit i set: the FP32 τ solve runs its DST-I along dimension i on the
+                               tensor cores (TAU_TC_ON, or TAU_TC_AUTO where it timed faster) */
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of

@@ -90,6 +90,10 @@ struct tau_problem {
   LongTab<double> lt64[3] = {};
   LongTab<float> lt32[3] = {};
   LongTab<df64> ltdf[3] = {};
+  // mixed form: tensor-core DST-I mode products of the FP32 τ solve (dimensions with n <= 256)
+  TcTab tc[3] = {};
+  bool tc_on[3] = {false, false, false};
+  int* tc_err = nullptr;
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
   double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
@@ -355,6 +359,14 @@ tau_status enq_minv_tail(tau_problem* p, cudaStream_t st, const ChainT<T>& io, i
     wire_in(P, io, rd);
     wire_out(P, io);
     rd = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (p->tc_on[ax]) {   // tensor-core mode products (DST, or DST·(1/mu)·DST as two of them)
+        const bool mu = post == POST_DST_MU_DST;
+        KL(launch_tc_dst(P, p->tc[ax], mu ? P.invmu : nullptr, false, st));
+        if (mu) KL(launch_tc_dst(P, p->tc[ax], nullptr, true, st));
+        return TAU_OK;
+      }
+    }
     return enq(P, st);
   };
   for (int ax = top; ax >= 1; --ax) TRY(dst_pass(ax, POST_DST));
@@ -870,6 +882,11 @@ tau_status check_ready(tau_problem* p) {
 
 tau_status sync_status(tau_problem* p) {
   CK(cudaStreamSynchronize(p->st));
+  if (p->tc_err) {
+    int e = 0;
+    CK(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return fail(TAU_ECUDA, "a tensor-core pass gave up waiting for its MMAs");
+  }
   GmresDev g;
   CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
   if (g.notconv) return fail(TAU_ENOTCONV, "a step reached max_iter=%d without meeting tol", p->desc.max_iter);
@@ -997,6 +1014,109 @@ tau_status long_tables_as(tau_problem* p, int i, LongTab<T>& D, int cw, Conv con
   return TAU_OK;
 }
 
+// Tensor-core DST tables of the mixed form (TAU_TC_AUTO): for every dimension with n <= 256 the
+// orthonormal DST-I matrix S[k][j] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1)) (j k reduced mod 2(n+1)),
+// rounded to TF32 (nearest, ties away: the rounding the kernel applies to its inputs), zero padded to
+// N = n rounded up to 16 rows and Kp = n rounded up to 32 columns.
+tau_status setup_tc(tau_problem* p) {
+  if (p->desc.tc == TAU_TC_OFF) return TAU_OK;
+  for (int i = 0; i < p->d; ++i) {
+    const int n = p->n[i];
+    if (n > 256) continue;
+    if (!p->tc_err) {
+      TRY(dalloc_n(p, &p->tc_err, 1));
+      CK(cudaMemsetAsync(p->tc_err, 0, sizeof(int), p->st));
+    }
+    TcTab& t = p->tc[i];
+    t.n = n;
+    // dimension 0 takes S as the A operand in tiles of 128 rows (accumulators 128 columns per tile);
+    // the others take it as the B operand (N a multiple of 16)
+    t.N = i == 0 ? (n + 127) & ~127 : (n + 15) & ~15;
+    t.Kp = (n + 31) & ~31;
+    t.nalloc = 32;
+    while (t.nalloc < t.N) t.nalloc <<= 1;
+    // stored per K-chunk of 32 columns in the kernel's shared-memory layout (core matrices of 8
+    // rows x 4 values: byte offset (k/8)*1024 + (j/4)*128 + (k%8)*16 + (j%4)*4 within the chunk)
+    std::vector<float> S((size_t)t.N * t.Kp, 0.0f);
+    const double sc = std::sqrt(2.0 / (double)(n + 1));
+    const int64_t L2 = 2 * ((int64_t)n + 1);
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j) {
+        const int64_t r = ((int64_t)(j + 1) * (k + 1)) % L2;
+        float v = (float)(sc * std::sin(M_PI * (double)r / (double)(n + 1)));
+        uint32_t b;
+        std::memcpy(&b, &v, 4);
+        b = (b + 0x1000u) & ~0x1FFFu;   // keep 10 mantissa bits, round to nearest (ties away)
+        std::memcpy(&v, &b, 4);
+        const int c = j >> 5, jj = j & 31;
+        const size_t off = (size_t)c * t.N * 32 + ((size_t)(k >> 3) * 1024 + (jj >> 2) * 128 + (k & 7) * 16 + (jj & 3) * 4) / 4;
+        S[off] = v;
+      }
+    float* dS = nullptr;
+    TRY(upload(p, &dS, S.data(), S.size()));
+    t.S = dS;
+    t.err = p->tc_err;
+    p->tc_on[i] = true;
+  }
+  return TAU_OK;
+}
+
+// TAU_TC_AUTO: time the FP32 τ solve with the tensor-core DST and with the line passes (CUDA events,
+// after a warm-up) and keep the faster; results are cached per grid shape.
+std::mutex g_tc_mu;
+std::map<std::tuple<int, int, int, int>, bool> g_tc_cache;
+
+tau_status choose_tc(tau_problem* p) {
+  if (p->desc.tc != TAU_TC_AUTO) return TAU_OK;
+  bool any = false;
+  for (int i = 0; i < p->d; ++i) any = any || p->tc_on[i];
+  if (!any) return TAU_OK;
+  const auto key = std::make_tuple(p->d, p->n[0], p->d > 1 ? p->n[1] : 0, p->d > 2 ? p->n[2] : 0);
+  bool use = false, cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    auto it = g_tc_cache.find(key);
+    if (it != g_tc_cache.end()) {
+      use = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    CK(cudaMemsetAsync(p->V32, 0, p->n_tot * sizeof(float), p->st));
+    ChainT<float> io;
+    io.x = p->V32;
+    io.out = p->Z32;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_minv = [&](float* ms) -> tau_status {
+      for (int r = 0; r < 2; ++r) TRY(enq_minv<float>(p, p->st, io));
+      CK(cudaEventRecord(e0, p->st));
+      for (int r = 0; r < 3; ++r) TRY(enq_minv<float>(p, p->st, io));
+      CK(cudaEventRecord(e1, p->st));
+      CK(cudaEventSynchronize(e1));
+      CK(cudaEventElapsedTime(ms, e0, e1));
+      return TAU_OK;
+    };
+    bool saved[3];
+    for (int i = 0; i < 3; ++i) saved[i] = p->tc_on[i];
+    float t_on = 0.0f, t_off = 0.0f;
+    tau_status st = time_minv(&t_on);
+    for (int i = 0; i < 3; ++i) p->tc_on[i] = false;
+    if (st == TAU_OK) st = time_minv(&t_off);
+    for (int i = 0; i < 3; ++i) p->tc_on[i] = saved[i];
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(st);
+    use = t_on < 0.97f * t_off;
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    g_tc_cache[key] = use;
+  }
+  if (!use)
+    for (int i = 0; i < 3; ++i) p->tc_on[i] = false;
+  return TAU_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1027,6 +1147,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     return fail(TAU_EINVAL, "precision %d", D.precision);
   if (D.method != TAU_OPGM && D.method != TAU_TPGM && D.method != TAU_SPGM)
     return fail(TAU_EINVAL, "method %d", D.method);
+  if (D.tc != TAU_TC_AUTO && D.tc != TAU_TC_OFF && D.tc != TAU_TC_ON) return fail(TAU_EINVAL, "tc %d", D.tc);
   if (D.method != TAU_OPGM && D.precision != TAU_FP64)
     return fail(TAU_EUNSUPPORTED, "the two-sided and Strang circulant methods run in TAU_FP64 only");
   if (D.precision == TAU_MIXED &&
@@ -1111,6 +1232,8 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (cudaError_t e = init_kernel_attributes(); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
   if (cudaError_t e = init_long_attributes(); e != cudaSuccess)
+    return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
+  if (cudaError_t e = init_tc_attributes(); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "kernel attributes: %s", cudaGetErrorString(e)));
   if (cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking); e != cudaSuccess)
     return cleanup(fail(TAU_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
@@ -1439,6 +1562,8 @@ tau_status tau_setup(tau_problem* p) {
       if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->lt32[i], 1, conv));
     }
     KL(launch_f64_to_f32(p->invmu, p->invmu32, p->n_tot, p->st));
+    TRY(setup_tc(p));
+    TRY(choose_tc(p));
     IRDev ir{};
     ir.tol = p->desc.refine_tol;
     ir.max_sweeps = p->desc.max_sweeps;
@@ -1567,6 +1692,9 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   for (int i = 0; i < 3; ++i) {
     out->lines_per_cta[i] = i < p->d ? base_pass_t<double>(p, i).lpb : 0;
     out->lines_per_cta_f32[i] = i < p->d && p->mixed ? base_pass_t<float>(p, i).lpb : 0;
+  out->tc_dims = 0;
+  for (int i = 0; i < p->d; ++i)
+    if (p->tc_on[i]) out->tc_dims |= 1 << i;
   }
   out->kernels_prologue = p->k_pro;
   out->kernels_per_iter = p->k_body;

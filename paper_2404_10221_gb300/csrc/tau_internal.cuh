@@ -254,6 +254,21 @@ cudaError_t launch_chirp_spectrum(int M, const double2* b, double2* out, const d
 // Fill a stage-packed twiddle table (twp_size(S) entries) on the device.
 cudaError_t launch_twp(int S, double2* twp, cudaStream_t st);
 
+// tensor-core DST-I mode product of the FP32 τ solve (tau_tc.cu), one dimension with n <= 256
+struct TcTab {
+  int n;          // line length
+  int N;          // rows of S: n rounded up to 128 on dimension 0, to 16 elsewhere
+  int Kp;         // n rounded up to 32 (shared-memory K chunks)
+  int nalloc;     // TMEM columns allocated (power of two >= max(32, N))
+  const float* S; // orthonormal DST-I matrix, TF32-rounded, zero padded to N x Kp, stored per K-chunk
+                  // of 32 columns in the kernel's shared-memory core-matrix layout
+  int* err;       // device flag: an mbarrier wait gave up
+};
+cudaError_t init_tc_attributes();
+// y = S x along p.ax for every line (from_out: x is p's output, in place); mul: optional diagonal
+// applied to the result
+cudaError_t launch_tc_dst(const PassT<float>& p, const TcTab& t, const float* mul, bool from_out, cudaStream_t st);
+
 // long-line route (tau_long.cu)
 cudaError_t init_long_attributes();
 // One line pass (the semantics of launch_pass for d = 1) as a sequence of four-step FFT launches.

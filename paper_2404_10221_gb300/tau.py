@@ -34,6 +34,9 @@ TAU_DF64 = 2
 TAU_OPGM = 0
 TAU_TPGM = 1
 TAU_SPGM = 2
+TAU_TC_AUTO = 0
+TAU_TC_OFF = 1
+TAU_TC_ON = 2
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
@@ -63,6 +66,7 @@ class tau_problem_desc(C.Structure):
         ("max_sweeps", C.c_int),
         ("inner_tol", C.c_double),
         ("method", C.c_int),
+        ("tc", C.c_int),
     ]
 
 
@@ -95,6 +99,7 @@ class tau_stats(C.Structure):
         ("total_sweeps", C.c_int64),
         ("lines_per_cta", C.c_int * 3),
         ("lines_per_cta_f32", C.c_int * 3),
+        ("tc_dims", C.c_int),
     ]
 
 
@@ -222,7 +227,8 @@ def _stream(stream=None) -> int:
 
 def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
               e_bounds: Optional[tuple] = None, refine_tol: float = 0.0, inner_max_iter: int = 0,
-              max_sweeps: int = 0, inner_tol: float = 0.0, method: int = TAU_OPGM) -> tau_problem_desc:
+              max_sweeps: int = 0, inner_tol: float = 0.0, method: int = TAU_OPGM,
+              tc: int = 0) -> tau_problem_desc:
     """tau_problem_desc from a workloads.Problem."""
     d = tau_problem_desc()
     d.d = prob.d
@@ -240,6 +246,7 @@ def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
     d.x0_mode = int(prob.x0_mode)
     d.precision = precision
     d.method = int(method)
+    d.tc = int(tc)
     if e_bounds is None:
         d.e_min = d.e_max = math.nan
     else:

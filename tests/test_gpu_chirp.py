@@ -214,7 +214,7 @@ def test_fp32_operators_parity(d, n):
     tau = _tau()
     wl = _wl(d, n, max_iter=4)
     pr = wl.prob
-    p = tau.Problem(wl, precision=tau.TAU_MIXED, route=_chirp(1) if d == 1 else (0, 0, 0))
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, route=_chirp(1) if d == 1 else (0, 0, 0), tc=tau.TAU_TC_OFF)
     t = wl.field_tables()
     ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
     x = W.random_vector(pr.n_tot, 43).astype(np.float32).astype(np.float64)

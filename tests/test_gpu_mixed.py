@@ -54,7 +54,8 @@ def test_fp32_operators_parity(d, n):
     tau = _tau()
     wl = _wl(d, n)
     pr = wl.prob
-    p = tau.Problem(wl, precision=tau.TAU_MIXED)
+    # the FP32 line passes (the tensor-core DST has its own bound, tests/test_gpu_tc.py)
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_OFF)
     t = wl.field_tables()
     ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
     x = W.random_vector(pr.n_tot, 31)
