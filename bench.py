@@ -59,6 +59,8 @@ def parse():
                     help="grid size per axis of --matvec-only (1023: FFT route; other n: chirp route in 2-D)")
     ap.add_argument("--matvec-d", type=int, default=2, choices=[1, 2],
                     help="dimension of --matvec-only (1: the 1-D workload, long-line route from n = 128)")
+    ap.add_argument("--tc", default="auto", choices=["auto", "on", "off"],
+                    help="tensor-core DST of the FP32 τ solve in --matvec-f32-3d (TAU_TC_AUTO/ON/OFF)")
     ap.add_argument("--matvec-f32-3d", type=int, default=0,
                     help="profiling driver: the 3-D 255^3 workload in mixed precision (2 inner slots); run "
                          "this many FP32 A x (3 line passes) + M^{-1} r (5 line passes), then exit")
@@ -234,13 +236,13 @@ def pass_flops_2d(n: int) -> float:
     return lines * sum(per_line.values())
 
 
-def measure_steps(wl, precision, warm, timed, stream, dev, method=0, route=(0, 0, 0)):
+def measure_steps(wl, precision, warm, timed, stream, dev, method=0, route=(0, 0, 0), tc=0):
     """Time `timed` steps (CUDA events per step, L2 flushed between steps) after `warm` steps."""
     import torch
 
     from paper_2404_10221_gb300 import tau
 
-    prob = tau.Problem(wl, precision=precision, route=route, stream=stream.cuda_stream, method=method)
+    prob = tau.Problem(wl, precision=precision, route=route, stream=stream.cuda_stream, method=method, tc=tc)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tau.tau_step(prob.handle, warm)
     tau.tau_sync(prob.handle, allow_notconv=True)
@@ -319,13 +321,21 @@ def run_forms(stream, dev):
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)
         rel = (torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)).item()
+        tc_extra = {}
+        if stmx.tc_dims:
+            # the same form with the FP32 τ solve on the line passes instead of the tensor cores
+            vlp, mslp, _, _, _ = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev, tc=tau.TAU_TC_OFF)
+            tc_extra = {"line_pass_tau_solve_value": vlp, "line_pass_tau_solve_ms_per_step": mslp,
+                        "tensor_core_over_line_pass": vmx / vlp}
         out[name] = {
             "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_compared": warm + timed,
             "mixed_value": vmx, "mixed_ms_per_step": msmx, "plain_fp64_value": v64, "plain_fp64_ms_per_step": ms64,
             "speedup_vs_plain_fp64": vmx / v64, "rel_err_vs_plain_fp64": rel,
             "mixed_inner_iters_per_step": float(np.mean(itmx)) if len(itmx) else None,
             "mixed_sweeps_total": int(stmx.total_sweeps), "plain_iters_per_step": float(np.mean(it64)),
-            "unit": UNIT, "dtype": "f32 inner (FFT tau solve, matvec, Arnoldi) + f64 residual/refinement",
+            "tc_dims": int(stmx.tc_dims), **tc_extra,
+            "unit": UNIT, "dtype": "f32 inner (tau solve: tensor-core TF32 DST on the dims in tc_dims, FP32 "
+                                   "line passes elsewhere; matvec and Arnoldi FP32) + f64 residual/refinement",
         }
     return out
 
@@ -691,7 +701,8 @@ def run_matvec_f32_3d(args):
     from paper_2404_10221_gb300 import workloads as W
 
     wl = W.c3_3d()
-    p = tau.Problem(wl, precision=tau.TAU_MIXED, inner_max_iter=2)
+    tc = {"auto": tau.TAU_TC_AUTO, "on": tau.TAU_TC_ON, "off": tau.TAU_TC_OFF}[args.tc]
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, inner_max_iter=2, tc=tc)
     x = torch.randn(wl.prob.n_tot, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
     torch.cuda.synchronize()
@@ -701,8 +712,9 @@ def run_matvec_f32_3d(args):
         tau.tau_apply_Minv_f32(p.handle, y, x)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
+    tc_dims = int(p.stats().tc_dims)
     p.close()
-    print(json.dumps({"matvec_f32_3d": args.matvec_f32_3d, "x_norm": float(torch.linalg.norm(x))}))
+    print(json.dumps({"matvec_f32_3d": args.matvec_f32_3d, "tc_dims": tc_dims, "x_norm": float(torch.linalg.norm(x))}))
     return 0
 
 
