@@ -132,9 +132,12 @@ typedef struct {
   int tc;               /* TAU_MIXED only: the DST-I passes of the FP32 τ solve on dimensions with
                            n_i <= 256 as tensor-core (tcgen05, TF32) mode products (relative error
                            ~1e-3: the flexible inner GMRES takes the result as its preconditioner).
-                           TAU_TC_AUTO (0, default): tau_setup times the FP32 τ solve both ways and
-                           keeps the faster (cached per grid shape); TAU_TC_OFF (1): line passes;
-                           TAU_TC_ON (2): tensor cores wherever n_i <= 256 */
+                           When every n_i <= 256 the FP32 matvec can also run its Toeplitz
+                           products on the tensor cores from split TF32 operands (FP32-level
+                           accuracy).  TAU_TC_AUTO (0, default): tau_setup times both operators
+                           both ways and keeps the faster of each (cached per grid shape);
+                           TAU_TC_OFF (1): line passes; TAU_TC_ON (2): tensor cores wherever
+                           n_i <= 256 */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
@@ -172,7 +175,8 @@ typedef struct {
                                TAU_AUTOTUNE=1; TAU_AUTOTUNE=0 keeps the shared-memory heuristic) */
   int lines_per_cta_f32[3]; /* the same for the FP32 passes of a TAU_MIXED problem */
   int tc_dims;              /* bit i set: the FP32 τ solve runs its DST-I along dimension i on the
-                               tensor cores (TAU_TC_ON, or TAU_TC_AUTO where it timed faster) */
+                               tensor cores (TAU_TC_ON, or TAU_TC_AUTO where it timed faster); bit 8
+                               set: the FP32 matvec runs as split-TF32 tensor-core passes */
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of

@@ -94,6 +94,10 @@ struct tau_problem {
   TcTab tc[3] = {};
   bool tc_on[3] = {false, false, false};
   int* tc_err = nullptr;
+  // mixed form: split-TF32 tensor-core Toeplitz matvec (every dimension n <= 256) and the second
+  // pair of FP32 channel buffers its passes alternate with
+  bool tcm = false;
+  float *A2 = nullptr, *C2 = nullptr;
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
   double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
@@ -380,6 +384,31 @@ template <typename T>
 tau_status enq_mv(tau_problem* p, cudaStream_t st, const ChainT<T>& io, double sgn, int finish, const T* src,
                   bool precond, const int* skip = nullptr) {
   const int d = p->d;
+  if constexpr (std::is_same<T, float>::value) {
+    if (p->tcm && finish == FIN_NONE && !precond) {
+      // split-TF32 tensor-core passes; the channels alternate between (A32, C32) and (A2, C2)
+      float* ba[2] = {p->A32, p->A2};
+      float* bc[2] = {p->C32, p->C2};
+      for (int ax = 0; ax < d; ++ax) {
+        PassT<float> P = base_pass_t<float>(p, ax);
+        P.skip = skip;
+        P.seta = sgn * p->eta[ax];
+        P.g = io.g;
+        P.e = e_of<float>(p);
+        const bool first = ax == 0, last = ax == d - 1;
+        const float* c_in = first ? io.x : bc[(ax - 1) & 1];
+        float* c_base = first ? io.in_base : nullptr;
+        const int c_sel = first ? io.in_sel : 0;
+        const float* a_in = first ? nullptr : ba[(ax - 1) & 1];
+        float* out_a = last ? io.out : ba[ax & 1];
+        float* out_base = last ? io.out_base : nullptr;
+        const int out_sel = last ? io.out_sel : 0;
+        float* out_c = last ? nullptr : bc[ax & 1];
+        KL(launch_tc_mv(P, p->tc[ax], c_in, c_base, c_sel, a_in, out_a, out_base, out_sel, out_c, first, last, st));
+      }
+      return TAU_OK;
+    }
+  }
   for (int ax = 0; ax < d; ++ax) {
     PassT<T> P = base_pass_t<T>(p, ax);
     P.skip = skip;
@@ -1057,6 +1086,43 @@ tau_status setup_tc(tau_problem* p) {
     t.S = dS;
     t.err = p->tc_err;
     p->tc_on[i] = true;
+    // the Toeplitz factor T[k][j] = s_|k-j| split as T_hi + T_lo (each rounded to TF32 from the
+    // FP64 weights), per K-chunk of 16 in the matvec kernel's layout
+    std::vector<double> sw(n);
+    CK(cudaMemcpy(sw.data(), p->s[i], n * sizeof(double), cudaMemcpyDeviceToHost));
+    t.Kp16 = (n + 15) & ~15;
+    std::vector<float> Th((size_t)t.N * t.Kp16, 0.0f), Tl((size_t)t.N * t.Kp16, 0.0f);
+    auto rna = [](float v) {
+      uint32_t b;
+      std::memcpy(&b, &v, 4);
+      b = (b + 0x1000u) & ~0x1FFFu;
+      std::memcpy(&v, &b, 4);
+      return v;
+    };
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j) {
+        const double w = sw[k > j ? k - j : j - k];
+        const float hi = rna((float)w), lo = rna((float)(w - (double)hi));
+        const int c = j >> 4, jj = j & 15;
+        const size_t off =
+            (size_t)c * t.N * 16 + ((size_t)(k >> 3) * 512 + (jj >> 2) * 128 + (k & 7) * 16 + (jj & 3) * 4) / 4;
+        Th[off] = hi;
+        Tl[off] = lo;
+      }
+    float *dh = nullptr, *dl = nullptr;
+    TRY(upload(p, &dh, Th.data(), Th.size()));
+    TRY(upload(p, &dl, Tl.data(), Tl.size()));
+    t.Thi = dh;
+    t.Tlo = dl;
+  }
+  bool all = true;
+  for (int i = 0; i < p->d; ++i) all = all && p->tc_on[i];
+  if (all) {
+    if (p->d == 3) {
+      TRY(dalloc_n(p, &p->A2, (size_t)p->n_tot));
+      TRY(dalloc_n(p, &p->C2, (size_t)p->n_tot));
+    }
+    p->tcm = true;
   }
   return TAU_OK;
 }
@@ -1114,6 +1180,48 @@ tau_status choose_tc(tau_problem* p) {
   }
   if (!use)
     for (int i = 0; i < 3; ++i) p->tc_on[i] = false;
+  if (p->tcm) {   // the split-TF32 matvec: its own measured choice
+    const auto kmv = std::make_tuple(-p->d, p->n[0], p->d > 1 ? p->n[1] : 0, p->d > 2 ? p->n[2] : 0);
+    bool use_mv = false, hit = false;
+    {
+      std::lock_guard<std::mutex> lk(g_tc_mu);
+      auto it = g_tc_cache.find(kmv);
+      if (it != g_tc_cache.end()) {
+        use_mv = it->second;
+        hit = true;
+      }
+    }
+    if (!hit) {
+      CK(cudaMemsetAsync(p->V32, 0, p->n_tot * sizeof(float), p->st));
+      ChainT<float> io;
+      io.x = p->V32;
+      io.out = p->Z32;
+      cudaEvent_t e0, e1;
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      auto time_mv = [&](float* ms) -> tau_status {
+        for (int r = 0; r < 2; ++r) TRY(enq_mv<float>(p, p->st, io, 1.0, FIN_NONE, nullptr, false));
+        CK(cudaEventRecord(e0, p->st));
+        for (int r = 0; r < 3; ++r) TRY(enq_mv<float>(p, p->st, io, 1.0, FIN_NONE, nullptr, false));
+        CK(cudaEventRecord(e1, p->st));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        return TAU_OK;
+      };
+      float t_on = 0.0f, t_off = 0.0f;
+      tau_status st = time_mv(&t_on);
+      p->tcm = false;
+      if (st == TAU_OK) st = time_mv(&t_off);
+      p->tcm = true;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      TRY(st);
+      use_mv = t_on < 0.97f * t_off;
+      std::lock_guard<std::mutex> lk(g_tc_mu);
+      g_tc_cache[kmv] = use_mv;
+    }
+    if (!use_mv) p->tcm = false;
+  }
   return TAU_OK;
 }
 
@@ -1695,6 +1803,7 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
   out->tc_dims = 0;
   for (int i = 0; i < p->d; ++i)
     if (p->tc_on[i]) out->tc_dims |= 1 << i;
+  if (p->tcm) out->tc_dims |= 1 << 8;
   }
   out->kernels_prologue = p->k_pro;
   out->kernels_per_iter = p->k_body;

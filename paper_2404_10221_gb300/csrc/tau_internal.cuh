@@ -263,11 +263,21 @@ struct TcTab {
   const float* S; // orthonormal DST-I matrix, TF32-rounded, zero padded to N x Kp, stored per K-chunk
                   // of 32 columns in the kernel's shared-memory core-matrix layout
   int* err;       // device flag: an mbarrier wait gave up
+  // split-TF32 Toeplitz matvec: T_ax (FCD weights) = T_hi + T_lo, zero padded to N x Kp16 (n rounded
+  // up to 16), stored per K-chunk of 16 columns in the core-matrix layout (512-byte row groups)
+  int Kp16;
+  const float* Thi;
+  const float* Tlo;
 };
 cudaError_t init_tc_attributes();
 // y = S x along p.ax for every line (from_out: x is p's output, in place); mul: optional diagonal
 // applied to the result
 cudaError_t launch_tc_dst(const PassT<float>& p, const TcTab& t, const float* mul, bool from_out, cudaStream_t st);
+// One matvec pass along p.ax with T c on the tensor cores (split TF32): a' = B a + seta T c,
+// c' = B c (not last); first: a = e∘x, c = x (c_in, optionally device-selected); last: a' to out
+cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_in, float* c_base, int c_sel,
+                         const float* a_in, float* out_a, float* out_base, int out_sel, float* out_c, bool first,
+                         bool last, cudaStream_t st);
 
 // long-line route (tau_long.cu)
 cudaError_t init_long_attributes();

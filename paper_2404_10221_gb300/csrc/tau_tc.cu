@@ -252,13 +252,285 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.nalloc));
 }
 
+// ---------------------------------------------------------------------------
+// Split-TF32 Toeplitz matvec pass of the FP32 inner solve (all dimensions n <= 256)
+// ---------------------------------------------------------------------------
+// One pass of the matvec chain along dimension ax, as in the line-pass kernel: with the channels
+// a (first pass: e∘x) and c (first pass: x),
+//     a' = B_ax a + seta T_ax c,      c' = B_ax c   (not on the last pass; the last stores a'),
+// B_ax the tridiagonal stencil (bd, bo) along the line and T_ax the Toeplitz matrix of the FCD
+// weights.  T c is a dense product on the tensor cores with FP32-level accuracy from split TF32
+// operands: c = c_hi + c_lo, T = T_hi + T_lo (each part TF32), T c ~ T_hi c_hi + T_hi c_lo + T_lo c_hi
+// (the dropped T_lo c_lo is ~2^-22 relative).  K-chunks of 16 (two MMA K-steps, three products
+// each), core-matrix layout with 512-byte row groups.  The stencil reads a and c (neighbours
+// included) from global memory in the epilogue, so the pass writes new channel buffers.
+constexpr int TM_KC = 16;
+
+struct TcMvArgs {
+  int n, ax, inner, N, Kp, nalloc;
+  int64_t nlines;
+  const float* Thi;      // per K-chunk of 16: N x 16 block of T_hi in the core-matrix layout
+  const float* Tlo;
+  const float* c_in;     // Toeplitz input (first pass: x)
+  float* c_base;
+  int c_sel;
+  const float* a_in;     // not first: channel a
+  const float* e;        // first pass: e
+  float* out_a;          // last: the result; else channel a'
+  float* out_base;
+  int out_sel;
+  float* out_c;          // not last: channel c'
+  int first, last;
+  float bd, bo, seta;
+  int64_t vstride;
+  const GmresDev* g;
+  const int* skip;
+  int* err;
+};
+
+__device__ __forceinline__ int cm16(int row, int k) {
+  return (row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
+  hi = to_tf32(v);
+  lo = to_tf32(v - hi);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  if ((a.g && a.g->done) || (a.skip && *a.skip)) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = a.N, n = a.n;
+  const bool flip = a.ax == 0;
+  const int MT = flip ? N >> 7 : 1;
+  const int xt = TC_M * TM_KC * 4, tt = N * TM_KC * 4;   // line tile, T tile (bytes)
+  const int stage = 2 * xt + 2 * tt;                     // x_hi, x_lo, T_hi, T_lo
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage + 16);
+  const int64_t L0 = (int64_t)blockIdx.x * TC_M;
+  const float* cin = a.c_sel ? a.c_base + (int64_t)(a.g->j + a.c_sel - 1) * a.vstride : a.c_in;
+  float* outa = a.out_sel ? a.out_base + (int64_t)(a.g->j + a.out_sel - 1) * a.vstride : a.out_a;
+  const int ln = tid & (TC_M - 1), hf = tid >> 7;
+  const int64_t L = L0 + ln;
+  const bool live = L < a.nlines;
+  int64_t base = 0, jstep = 1;
+  if (live && !flip) {
+    const int64_t sl = L / a.inner, b = L - sl * a.inner;
+    base = sl * n * a.inner + b;
+    jstep = a.inner;
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(a.nalloc));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const int nmma = flip ? TC_M : N;
+  const uint32_t idesc =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+  const int C = a.Kp / TM_KC;
+  bool ok = true;
+  for (int c = 0; c < C; ++c) {
+    const int s = c & 1;
+    unsigned char* sxh = sm + s * stage;
+    unsigned char* sxl = sxh + xt;
+    unsigned char* sth = sxl + xt;
+    unsigned char* stl = sth + tt;
+    if (c >= 2) {
+      ok = __syncthreads_and(bar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1) ? 1 : 0) != 0;
+      if (!ok) break;
+    }
+    const int j0 = c * TM_KC;
+    if (flip) {
+      // warp w stages lines 16w..16w+15: one instruction covers 8 lines x 4 consecutive j
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3), j = j0 + k;
+        const int64_t Lr = L0 + row;
+        const float v = (Lr < a.nlines && j < n) ? cin[Lr * n + j] : 0.0f;
+        float hi, lo;
+        split_tf32(v, hi, lo);
+        *reinterpret_cast<float*>(sxh + cm16(row, k)) = hi;
+        *reinterpret_cast<float*>(sxl + cm16(row, k)) = lo;
+      }
+    } else {
+      // half of this thread's line: 8 values as two 16-byte core-matrix rows, hi and lo
+      float v[TM_KC / 2];
+#pragma unroll
+      for (int jj = 0; jj < TM_KC / 2; ++jj) {
+        const int j = j0 + 8 * hf + jj;
+        v[jj] = (live && j < n) ? cin[base + (int64_t)j * jstep] : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float h[4], l[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) split_tf32(v[4 * q + r], h[r], l[r]);
+        *reinterpret_cast<float4*>(sxh + cm16(ln, 8 * hf + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(sxl + cm16(ln, 8 * hf + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+    }
+    {
+      const float4* srch = reinterpret_cast<const float4*>(a.Thi + (int64_t)c * N * TM_KC);
+      const float4* srcl = reinterpret_cast<const float4*>(a.Tlo + (int64_t)c * N * TM_KC);
+      float4* dh = reinterpret_cast<float4*>(sth);
+      float4* dl = reinterpret_cast<float4*>(stl);
+      for (int i = tid; i < N * TM_KC / 4; i += TC_THREADS) {
+        dh[i] = __ldg(&srch[i]);
+        dl[i] = __ldg(&srcl[i]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int q = 0; q < TM_KC / 8; ++q) {
+        for (int t = 0; t < MT; ++t) {
+          const uint32_t d = tmem + 128u * t;
+          const uint32_t xo = 256 * q, to = t * 8192 + 256 * q;
+          // T c ~ T_hi c_hi + T_hi c_lo + T_lo c_hi
+          const uint64_t xh = smem_desc(smem_u32(sxh) + xo, 128, 512), xl = smem_desc(smem_u32(sxl) + xo, 128, 512);
+          const uint64_t th = smem_desc(smem_u32(sth) + (flip ? to : xo), 128, 512);
+          const uint64_t tl = smem_desc(smem_u32(stl) + (flip ? to : xo), 128, 512);
+          const uint32_t acc0 = (c > 0 || q > 0) ? 1u : 0u;
+          if (flip) {
+            mma_tf32(d, th, xh, idesc, acc0);
+            mma_tf32(d, th, xl, idesc, 1u);
+            mma_tf32(d, tl, xh, idesc, 1u);
+          } else {
+            mma_tf32(d, xh, th, idesc, acc0);
+            mma_tf32(d, xl, th, idesc, 1u);
+            mma_tf32(d, xh, tl, idesc, 1u);
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&bars[s])));
+    }
+  }
+  if (ok) ok = __syncthreads_and(bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1) ? 1 : 0) != 0;
+  if (!ok) {
+    if (tid == 0) atomicExch(a.err, 1);
+    bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const float* __restrict__ av = a.first ? nullptr : a.a_in;
+    const float* __restrict__ ev = a.e;
+    const float bd = a.bd, bo = a.bo, seta = a.seta;
+    // the channels at index o (a = e∘x on the first pass, c = x there)
+    auto ach = [&](int64_t o) -> float { return a.first ? __ldg(&ev[o]) * cin[o] : __ldg(&av[o]); };
+    for (int t = 0; t < MT; ++t) {
+      const int ncol = flip ? TC_M : N;
+      for (int cc = 16 * hf; cc < ncol; cc += 32) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(128 * t + cc);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+          int64_t Lq;
+          int k;
+          int64_t o0, step;
+          if (flip) {
+            Lq = L0 + cc + q;
+            k = 128 * t + 32 * (warp & 3) + lane;
+            o0 = Lq * n;
+            step = 1;
+          } else {
+            Lq = L;
+            k = cc + q;
+            o0 = base;
+            step = jstep;
+          }
+          if (Lq >= a.nlines || k >= n || (!flip && !live)) continue;
+          const int64_t o = o0 + (int64_t)k * step;
+          const float tc = __uint_as_float(v[q]);
+          const float al = k > 0 ? ach(o - step) : 0.0f, ar = k + 1 < n ? ach(o + step) : 0.0f;
+          const float res = fmaf(seta, tc, fmaf(bd, ach(o), bo * (al + ar)));
+          if (a.last) {
+            outa[o] = res;
+          } else {
+            a.out_a[o] = res;
+            const float cl = k > 0 ? cin[o - step] : 0.0f, cr = k + 1 < n ? cin[o + step] : 0.0f;
+            a.out_c[o] = fmaf(bd, cin[o], bo * (cl + cr));
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.nalloc));
+}
+
+size_t tm_smem_bytes(int N) { return 2 * (size_t)(2 * TC_M * TM_KC * 4 + 2 * N * TM_KC * 4) + 64; }
+
+cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_in, float* c_base, int c_sel,
+                         const float* a_in, float* out_a, float* out_base, int out_sel, float* out_c, bool first,
+                         bool last, cudaStream_t st) {
+  TcMvArgs a{};
+  a.n = t.n;
+  a.ax = p.ax;
+  a.inner = (int)p.inner;
+  a.N = t.N;
+  a.Kp = t.Kp16;
+  a.nalloc = t.nalloc;
+  a.nlines = p.nlines;
+  a.Thi = t.Thi;
+  a.Tlo = t.Tlo;
+  a.c_in = c_in;
+  a.c_base = c_base;
+  a.c_sel = c_sel;
+  a.a_in = a_in;
+  a.e = p.e;
+  a.out_a = out_a;
+  a.out_base = out_base;
+  a.out_sel = out_sel;
+  a.out_c = out_c;
+  a.first = first;
+  a.last = last;
+  a.bd = p.dim.bdiag;
+  a.bo = p.dim.boff;
+  a.seta = (float)p.seta;
+  a.vstride = p.vstride;
+  a.g = p.g;
+  a.skip = p.skip;
+  a.err = t.err;
+  const unsigned grid = (unsigned)((p.nlines + TC_M - 1) / TC_M);
+  k_tc_mv<<<grid, TC_THREADS, tm_smem_bytes(t.N), st>>>(a);
+  return cudaGetLastError();
+}
+
 size_t tc_smem_bytes(int N) { return 2 * (size_t)(TC_M * TC_KC * 4 + N * TC_KC * 4) + 64; }
 
 cudaError_t init_tc_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_tc_mode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)tc_smem_bytes(256));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_tc_mode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(256));
+  e = cudaFuncSetAttribute(k_tc_mode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(256));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_tc_mv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tm_smem_bytes(256));
 }
 
 cudaError_t launch_tc_dst(const PassT<float>& p, const TcTab& t, const float* mul, bool from_out, cudaStream_t st) {

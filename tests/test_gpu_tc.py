@@ -142,16 +142,45 @@ def test_tc_and_line_pass_solves_agree_at_255_cubed_two_steps():
 
 def test_tc_dims_reported():
     tau = _tau()
-    for n, on_mask in (((63, 63, 63), 7), ((300, 129), 2), ((1000,), 0)):
+    # low bits: dimensions whose τ-solve DST runs on the tensor cores; bit 8: the split-TF32 matvec
+    # (every dimension n <= 256)
+    for n, on_mask, mv in (((63, 63, 63), 7, True), ((300, 129), 2, False), ((1000,), 0, False)):
         d = len(n)
         wl = _wl(d, n, M=2)
         wl.prob.max_iter = 4
         p = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_ON)
-        assert p.stats().tc_dims == on_mask, (n, p.stats().tc_dims)
+        st = p.stats().tc_dims
+        assert st & 0xFF == on_mask and bool(st & 0x100) == mv, (n, st)
         p.close()
         p = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_OFF)
         assert p.stats().tc_dims == 0
         p.close()
-        p = tau.Problem(wl, precision=tau.TAU_MIXED)   # automatic: measured choice, all or nothing
-        assert p.stats().tc_dims in (0, on_mask)
+        p = tau.Problem(wl, precision=tau.TAU_MIXED)   # automatic: measured choices
+        st = p.stats().tc_dims
+        assert st & 0xFF in (0, on_mask) and (mv or not st & 0x100)
         p.close()
+
+
+@pytest.mark.parametrize("d,n", [(1, (127,)), (1, (5,)), (2, (31, 63)), (2, (255, 255)), (2, (20, 9)),
+                                 (3, (15, 7, 31)), (3, (63, 63, 63))])
+def test_tc_split_matvec_f32(d, n):
+    """A x in FP32 with the Toeplitz products as split-TF32 tensor-core products: FP32-level
+    accuracy, the bound of the FP32 line passes (1e-5 relative against the oracle)."""
+    tau = _tau()
+    wl = _wl(d, n)
+    pr = wl.prob
+    pr.max_iter = 4
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_ON)
+    assert p.stats().tc_dims & 0x100
+    t = wl.field_tables()
+    x = W.random_vector(pr.n_tot, 62).astype(np.float32)
+    y = torch.empty(pr.n_tot, dtype=torch.float32, device="cuda")
+    for m in (0, 1):
+        tau.tau_apply_A_f32(p.handle, m, torch.from_numpy(x).to("cuda"), y)
+        torch.cuda.synchronize()
+        e = O.eval_field_interior(pr, t["e_tc"][m], t["e_sp"])
+        ref = O.apply_A(pr, e, x.astype(np.float64))
+        got = y.cpu().numpy().astype(np.float64)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-5, f"m={m}: {rel:.3e}"
+    p.close()
