@@ -434,8 +434,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
     const float* __restrict__ av = a.first ? nullptr : a.a_in;
     const float* __restrict__ ev = a.e;
     const float bd = a.bd, bo = a.bo, seta = a.seta;
+    const bool fst = a.first != 0, lst = a.last != 0;
     // the channels at index o (a = e∘x on the first pass, c = x there)
-    auto ach = [&](int64_t o) -> float { return a.first ? __ldg(&ev[o]) * cin[o] : __ldg(&av[o]); };
+    auto ach = [&](int64_t o) -> float { return fst ? __ldg(&ev[o]) * cin[o] : __ldg(&av[o]); };
     for (int t = 0; t < MT; ++t) {
       const int ncol = flip ? TC_M : N;
       for (int cc = 16 * hf; cc < ncol; cc += 32) {
@@ -447,33 +448,62 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll 4
-        for (int q = 0; q < 16; ++q) {
-          int64_t Lq;
-          int k;
-          int64_t o0, step;
-          if (flip) {
-            Lq = L0 + cc + q;
-            k = 128 * t + 32 * (warp & 3) + lane;
-            o0 = Lq * n;
-            step = 1;
-          } else {
-            Lq = L;
-            k = cc + q;
-            o0 = base;
-            step = jstep;
+        if (flip) {
+          // lane = k along line L0 + cc + q: each lane loads its own a_k, c_k; the neighbours come
+          // from the adjacent lanes (warp shuffles), the warp's edge lanes load the one beyond
+          const int k = 128 * t + 32 * (warp & 3) + lane;
+#pragma unroll 2
+          for (int q = 0; q < 16; ++q) {
+            const int64_t Lq = L0 + cc + q;
+            const bool lv = Lq < a.nlines, valid = lv && k < n;
+            const int64_t o = Lq * n + k;
+            const float ak = valid ? ach(o) : 0.0f;
+            const float ck = (!lst && valid) ? cin[o] : 0.0f;
+            float al = __shfl_up_sync(0xffffffffu, ak, 1), ar = __shfl_down_sync(0xffffffffu, ak, 1);
+            float cl = __shfl_up_sync(0xffffffffu, ck, 1), cr = __shfl_down_sync(0xffffffffu, ck, 1);
+            if (lane == 0) {
+              const bool ok0 = valid && k > 0;
+              al = ok0 ? ach(o - 1) : 0.0f;
+              cl = (!lst && ok0) ? cin[o - 1] : 0.0f;
+            }
+            if (lane == 31) {
+              const bool ok1 = valid && k + 1 < n;
+              ar = ok1 ? ach(o + 1) : 0.0f;
+              cr = (!lst && ok1) ? cin[o + 1] : 0.0f;
+            }
+            if (valid) {
+              const float res = fmaf(seta, __uint_as_float(v[q]), fmaf(bd, ak, bo * (al + ar)));
+              if (lst) {
+                outa[o] = res;
+              } else {
+                a.out_a[o] = res;
+                a.out_c[o] = fmaf(bd, ck, bo * (cl + cr));
+              }
+            }
           }
-          if (Lq >= a.nlines || k >= n || (!flip && !live)) continue;
-          const int64_t o = o0 + (int64_t)k * step;
-          const float tc = __uint_as_float(v[q]);
-          const float al = k > 0 ? ach(o - step) : 0.0f, ar = k + 1 < n ? ach(o + step) : 0.0f;
-          const float res = fmaf(seta, tc, fmaf(bd, ach(o), bo * (al + ar)));
-          if (a.last) {
-            outa[o] = res;
-          } else {
-            a.out_a[o] = res;
-            const float cl = k > 0 ? cin[o - step] : 0.0f, cr = k + 1 < n ? cin[o + step] : 0.0f;
-            a.out_c[o] = fmaf(bd, cin[o], bo * (cl + cr));
+        } else if (live) {
+          // lane = line, columns k = cc..cc+15: the channels' runs k = cc-1..cc+16 are loaded once
+          float ar[18], cr[18];
+#pragma unroll
+          for (int r = 0; r < 18; ++r) {
+            const int k = cc - 1 + r;
+            const bool in = k >= 0 && k < n;
+            const int64_t o = base + (int64_t)k * jstep;
+            ar[r] = in ? ach(o) : 0.0f;
+            cr[r] = (!lst && in) ? cin[o] : 0.0f;
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int k = cc + q;
+            if (k >= n) continue;
+            const int64_t o = base + (int64_t)k * jstep;
+            const float res = fmaf(seta, __uint_as_float(v[q]), fmaf(bd, ar[q + 1], bo * (ar[q] + ar[q + 2])));
+            if (lst) {
+              outa[o] = res;
+            } else {
+              a.out_a[o] = res;
+              a.out_c[o] = fmaf(bd, cr[q + 1], bo * (cr[q] + cr[q + 2]));
+            }
           }
         }
       }
