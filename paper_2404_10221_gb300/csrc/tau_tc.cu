@@ -126,6 +126,30 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
   const uint32_t idesc =
       (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
   const int C = a.Kp / TC_KC;
+  // the 16 line values this thread stages per chunk, loaded one chunk ahead (software pipeline:
+  // chunk c+1's loads are in flight during chunk c's copy of S, barrier and MMA issue)
+  //   dimension 0: warp w stages lines 16w..16w+15, one load instruction covering 8 lines x 4
+  //   consecutive j (8 sectors) whose shared-memory stores hit 32 distinct banks;
+  //   other dimensions: half of this thread's line, stored as four 16-byte core-matrix rows
+  float nv[16];
+  auto load_chunk = [&](int c) {
+    const int j0 = c * TC_KC;
+    if (flip) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3), j = j0 + k;
+        const int64_t Lr = L0 + row;
+        nv[i] = (Lr < a.nlines && j < n) ? x[Lr * n + j] : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = j0 + 16 * hf + jj;
+        nv[jj] = (live && j < n) ? x[base + (int64_t)j * jstep] : 0.0f;
+      }
+    }
+  };
+  load_chunk(0);
   bool ok = true;
   for (int c = 0; c < C; ++c) {
     const int s = c & 1;
@@ -137,32 +161,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
       ok = __syncthreads_and(bar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1) ? 1 : 0) != 0;
       if (!ok) break;
     }
-    const int j0 = c * TC_KC;
     if (flip) {
-      // warp w stages lines 16w..16w+15; one load instruction covers 8 lines x 4 consecutive j
-      // (8 sectors) and its shared-memory stores hit 32 distinct banks
-#pragma unroll 4
+#pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3), j = j0 + k;
-        const int64_t Lr = L0 + row;
-        const float v = (Lr < a.nlines && j < n) ? x[Lr * n + j] : 0.0f;
-        *reinterpret_cast<float*>(sx + cm_off(row, k)) = to_tf32(v);
+        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3);
+        *reinterpret_cast<float*>(sx + cm_off(row, k)) = to_tf32(nv[i]);
       }
     } else {
-      // half of this thread's line: 16 values, as four 16-byte rows of core matrices
-      float v[TC_KC / 2];
 #pragma unroll
-      for (int jj = 0; jj < TC_KC / 2; ++jj) {
-        const int j = j0 + 16 * hf + jj;
-        v[jj] = (live && j < n) ? x[base + (int64_t)j * jstep] : 0.0f;
-      }
-#pragma unroll
-      for (int q = 0; q < TC_KC / 8; ++q) {
-        const float4 w = make_float4(to_tf32(v[4 * q]), to_tf32(v[4 * q + 1]), to_tf32(v[4 * q + 2]),
-                                     to_tf32(v[4 * q + 3]));
+      for (int q = 0; q < 4; ++q) {
+        const float4 w = make_float4(to_tf32(nv[4 * q]), to_tf32(nv[4 * q + 1]), to_tf32(nv[4 * q + 2]),
+                                     to_tf32(nv[4 * q + 3]));
         *reinterpret_cast<float4*>(sx + cm_off(ln, 16 * hf + 4 * q)) = w;
       }
     }
+    if (c + 1 < C) load_chunk(c + 1);
     {   // the chunk's block of S, stored in the shared-memory layout: a straight 16-byte copy
       const float4* src = reinterpret_cast<const float4*>(a.S + (int64_t)c * N * TC_KC);
       float4* dst = reinterpret_cast<float4*>(ss);
@@ -345,6 +358,28 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
   const uint32_t idesc =
       (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
   const int C = a.Kp / TM_KC;
+  // the 8 values this thread stages per chunk, loaded one chunk ahead (dimension 0: warp w stages
+  // lines 16w..16w+15, 8 lines x 4 consecutive j per instruction; other dimensions: half of this
+  // thread's line as two 16-byte core-matrix rows, hi and lo)
+  float nv[8];
+  auto load_chunk = [&](int c) {
+    const int j0 = c * TM_KC;
+    if (flip) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3), j = j0 + k;
+        const int64_t Lr = L0 + row;
+        nv[i] = (Lr < a.nlines && j < n) ? cin[Lr * n + j] : 0.0f;
+      }
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = j0 + 8 * hf + jj;
+        nv[jj] = (live && j < n) ? cin[base + (int64_t)j * jstep] : 0.0f;
+      }
+    }
+  };
+  load_chunk(0);
   bool ok = true;
   for (int c = 0; c < C; ++c) {
     const int s = c & 1;
@@ -356,36 +391,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
       ok = __syncthreads_and(bar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1) ? 1 : 0) != 0;
       if (!ok) break;
     }
-    const int j0 = c * TM_KC;
     if (flip) {
-      // warp w stages lines 16w..16w+15: one instruction covers 8 lines x 4 consecutive j
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3), j = j0 + k;
-        const int64_t Lr = L0 + row;
-        const float v = (Lr < a.nlines && j < n) ? cin[Lr * n + j] : 0.0f;
+        const int row = 16 * warp + 8 * (i & 1) + (lane >> 2), k = 4 * (i >> 1) + (lane & 3);
         float hi, lo;
-        split_tf32(v, hi, lo);
+        split_tf32(nv[i], hi, lo);
         *reinterpret_cast<float*>(sxh + cm16(row, k)) = hi;
         *reinterpret_cast<float*>(sxl + cm16(row, k)) = lo;
       }
     } else {
-      // half of this thread's line: 8 values as two 16-byte core-matrix rows, hi and lo
-      float v[TM_KC / 2];
-#pragma unroll
-      for (int jj = 0; jj < TM_KC / 2; ++jj) {
-        const int j = j0 + 8 * hf + jj;
-        v[jj] = (live && j < n) ? cin[base + (int64_t)j * jstep] : 0.0f;
-      }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         float h[4], l[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) split_tf32(v[4 * q + r], h[r], l[r]);
+        for (int r = 0; r < 4; ++r) split_tf32(nv[4 * q + r], h[r], l[r]);
         *reinterpret_cast<float4*>(sxh + cm16(ln, 8 * hf + 4 * q)) = make_float4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<float4*>(sxl + cm16(ln, 8 * hf + 4 * q)) = make_float4(l[0], l[1], l[2], l[3]);
       }
     }
+    if (c + 1 < C) load_chunk(c + 1);
     {
       const float4* srch = reinterpret_cast<const float4*>(a.Thi + (int64_t)c * N * TM_KC);
       const float4* srcl = reinterpret_cast<const float4*>(a.Tlo + (int64_t)c * N * TM_KC);
