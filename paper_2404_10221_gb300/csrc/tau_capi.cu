@@ -98,6 +98,9 @@ struct tau_problem {
   // pair of FP32 channel buffers its passes alternate with
   bool tcm = false;
   float *A2 = nullptr, *C2 = nullptr;
+  // device flag: tmp holds the FP64 residual of the current solution (end of a mixed step), so the
+  // next right-hand side can be formed from it (tau_mixed.cu)
+  int* rres = nullptr;
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
   double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
@@ -585,11 +588,25 @@ tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle 
 // ---- mixed precision: prologue, refinement sweep (before / after the inner loop), inner
 //      FGMRES iteration, epilogue
 tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
+  // b = (B E - S) u + dt F.  After a step, tmp holds r = b_old - A_old u in FP64 and the flag is set:
+  // then b = B((E_old + E)∘u) + r - b_old + dt F (a stencil, tau_mixed.cu) and the line passes of
+  // the direct form skip themselves; otherwise (first step, a solution set by the caller) the
+  // line passes run and the stencil kernels return at once.
+  KL(launch_rres_save(p->rres, p->E, p->u, p->A, p->n_tot, st));
   TRY(enq_fields(p, st, -1));
   ChainIO rhs;
   rhs.x = p->u;
   rhs.out = p->b;
-  TRY(enq_mv<double>(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false));
+  TRY(enq_mv<double>(p, st, rhs, -1.0, FIN_ADD_F, p->Fdt, false, p->rres));
+  {
+    double bd[3] = {1.0, 1.0, 1.0}, bo[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < p->d; ++i) {
+      bd[i] = 1.0 - p->desc.alpha[i] / 12.0;
+      bo[i] = p->desc.alpha[i] / 24.0;
+    }
+    KL(launch_rres_rhs(p->rres, p->d, p->n, bd, bo, p->E, p->u, p->A, p->tmp, p->b, p->Fdt, p->n_tot, st));
+    tl_launches += 1;   // two kernels
+  }
   if (p->desc.x0_mode == TAU_X0_PREV)
     CK(cudaMemcpyAsync(p->X, p->u, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else
@@ -645,6 +662,7 @@ tau_status enq_mx_sweep_post(tau_problem* p, cudaStream_t st) {
 
 tau_status enq_mx_epilogue(tau_problem* p, cudaStream_t st) {
   CK(cudaMemcpyAsync(p->u, p->X, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  KL(launch_set_flag(p->rres, 1, st));   // tmp is the residual of this step's final iterate
   KL(launch_ir_finish(p->ir, p->g, p->iters, p->sweeps, st));
   return TAU_OK;
 }
@@ -1369,8 +1387,10 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
         (s = dalloc_n(p, &p->Hin, (size_t)(k + 1) * k)) ||
         (s = dalloc_n(p, &p->csin, k)) || (s = dalloc_n(p, &p->snin, k)) || (s = dalloc_n(p, &p->gvin, k + 1)) ||
         (s = dalloc_n(p, &p->h1in, k + 1)) || (s = dalloc_n(p, &p->h2in, k + 1)) || (s = dalloc_n(p, &p->yin, k + 1)) ||
-        (s = dalloc_n(p, &p->gin, 1)) || (s = dalloc_n(p, &p->ir, 1)) || (s = dalloc_n(p, &p->sweeps, (size_t)D.M)))
+        (s = dalloc_n(p, &p->gin, 1)) || (s = dalloc_n(p, &p->ir, 1)) || (s = dalloc_n(p, &p->sweeps, (size_t)D.M)) ||
+        (s = dalloc_n(p, &p->rres, 1)))
       return cleanup(s);
+    if (cudaMemset(p->rres, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(TAU_ECUDA, "memset"));
   }
   if (p->dfm && ((s = dalloc_n(p, &p->Edf, n)) || (s = dalloc_n(p, &p->Fdf, n)) ||
                  (s = dalloc_n(p, &p->invmu_df, n))))
@@ -1760,6 +1780,8 @@ tau_status tau_set_solution(tau_problem* p, const double* u, int is_device, int6
   if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
   // m lives in the device state read by the step graph
   CK(cudaMemcpyAsync(&p->g->m, &m, sizeof(int64_t), cudaMemcpyHostToDevice, p->st));
+  // the last residual no longer belongs to the solution: the next right-hand side takes the passes
+  if (p->rres) CK(cudaMemsetAsync(p->rres, 0, sizeof(int), p->st));
   CK(cudaStreamSynchronize(p->st));
   p->m_host = m;
   return TAU_OK;

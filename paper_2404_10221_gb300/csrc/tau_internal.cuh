@@ -279,6 +279,16 @@ cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_i
                          const float* a_in, float* out_a, float* out_base, int out_sel, float* out_c, bool first,
                          bool last, cudaStream_t st);
 
+// next right-hand side of the mixed form from the last residual (tau_mixed.cu); every kernel returns
+// at once when *flag == 0.  save: y = E∘u; rhs: y += E'∘u, b = B y + r - b + fdt (B the d-level
+// tridiagonal product with bd, bo per dimension); set_flag: *flag = v.
+cudaError_t launch_rres_save(const int* flag, const double* E, const double* u, double* y, int64_t n,
+                             cudaStream_t st);
+cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double* bd, const double* bo,
+                            const double* E, const double* u, double* y, const double* r, double* b,
+                            const double* fdt, int64_t n, cudaStream_t st);
+cudaError_t launch_set_flag(int* flag, int v, cudaStream_t st);
+
 // long-line route (tau_long.cu)
 cudaError_t init_long_attributes();
 // One line pass (the semantics of launch_pass for d = 1) as a sequence of four-step FFT launches.

@@ -124,3 +124,25 @@ def test_mixed_notconv_reported_when_sweeps_capped():
     st = p.solve(allow_notconv=True)
     assert st == tau.TAU_ENOTCONV
     p.close()
+
+
+def test_mixed_resume_matches_straight_run():
+    """From the second step on the mixed form forms each right-hand side from the previous step's
+    FP64 residual; a solution set by the caller (checkpoint resume) drops back to the line passes.
+    Both routes give the same march within the form's rounding."""
+    tau = _tau()
+    wl = _wl(3, (15, 7, 31), M=6)
+    a = tau.Problem(wl, precision=tau.TAU_MIXED)
+    a.solve()
+    ua = a.solution().cpu().numpy()
+    a.close()
+    b = tau.Problem(wl, precision=tau.TAU_MIXED)
+    b.step(3)
+    mid = b.solution().cpu().numpy()
+    b.close()
+    c = tau.Problem(wl, precision=tau.TAU_MIXED)
+    tau.tau_set_solution(c.handle, mid, False, 3)
+    c.step(3)
+    uc = c.solution().cpu().numpy()
+    c.close()
+    assert np.linalg.norm(uc - ua) <= 1e-10 * np.linalg.norm(ua)
