@@ -474,35 +474,49 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (flip) {
-          // lane = k along line L0 + cc + q: each lane loads its own a_k, c_k; the neighbours come
-          // from the adjacent lanes (warp shuffles), the warp's edge lanes load the one beyond
+          // lane = k along line L0 + cc + q: each lane loads its own a_k, c_k and the warp's edge
+          // lanes the value beyond (k-1 on lane 0, k+1 on lane 31), eight lines at a time with all
+          // loads issued before any use; the other neighbours come from the adjacent lanes
           const int k = 128 * t + 32 * (warp & 3) + lane;
-#pragma unroll 2
-          for (int q = 0; q < 16; ++q) {
-            const int64_t Lq = L0 + cc + q;
-            const bool lv = Lq < a.nlines, valid = lv && k < n;
-            const int64_t o = Lq * n + k;
-            const float ak = valid ? ach(o) : 0.0f;
-            const float ck = (!lst && valid) ? cin[o] : 0.0f;
-            float al = __shfl_up_sync(0xffffffffu, ak, 1), ar = __shfl_down_sync(0xffffffffu, ak, 1);
-            float cl = __shfl_up_sync(0xffffffffu, ck, 1), cr = __shfl_down_sync(0xffffffffu, ck, 1);
-            if (lane == 0) {
-              const bool ok0 = valid && k > 0;
-              al = ok0 ? ach(o - 1) : 0.0f;
-              cl = (!lst && ok0) ? cin[o - 1] : 0.0f;
+          const bool edge = lane == 0 || lane == 31;
+          const int de = lane == 0 ? -1 : 1;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float ak[8], ck[8], ae[8], ce[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int64_t Lq = L0 + cc + 8 * h + q;
+              const bool valid = Lq < a.nlines && k < n;
+              const int64_t o = Lq * n + k;
+              const bool ve = valid && edge && k + de >= 0 && k + de < n;
+              ak[q] = valid ? ach(o) : 0.0f;
+              ck[q] = (!lst && valid) ? cin[o] : 0.0f;
+              ae[q] = ve ? ach(o + de) : 0.0f;
+              ce[q] = (!lst && ve) ? cin[o + de] : 0.0f;
             }
-            if (lane == 31) {
-              const bool ok1 = valid && k + 1 < n;
-              ar = ok1 ? ach(o + 1) : 0.0f;
-              cr = (!lst && ok1) ? cin[o + 1] : 0.0f;
-            }
-            if (valid) {
-              const float res = fmaf(seta, __uint_as_float(v[q]), fmaf(bd, ak, bo * (al + ar)));
-              if (lst) {
-                outa[o] = res;
-              } else {
-                a.out_a[o] = res;
-                a.out_c[o] = fmaf(bd, ck, bo * (cl + cr));
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int64_t Lq = L0 + cc + 8 * h + q;
+              const bool valid = Lq < a.nlines && k < n;
+              const int64_t o = Lq * n + k;
+              float al = __shfl_up_sync(0xffffffffu, ak[q], 1), ar = __shfl_down_sync(0xffffffffu, ak[q], 1);
+              float cl = __shfl_up_sync(0xffffffffu, ck[q], 1), cr = __shfl_down_sync(0xffffffffu, ck[q], 1);
+              if (lane == 0) {
+                al = ae[q];
+                cl = ce[q];
+              }
+              if (lane == 31) {
+                ar = ae[q];
+                cr = ce[q];
+              }
+              if (valid) {
+                const float res = fmaf(seta, __uint_as_float(v[8 * h + q]), fmaf(bd, ak[q], bo * (al + ar)));
+                if (lst) {
+                  outa[o] = res;
+                } else {
+                  a.out_a[o] = res;
+                  a.out_c[o] = fmaf(bd, ck[q], bo * (cl + cr));
+                }
               }
             }
           }
