@@ -604,8 +604,8 @@ tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
       bd[i] = 1.0 - p->desc.alpha[i] / 12.0;
       bo[i] = p->desc.alpha[i] / 24.0;
     }
-    KL(launch_rres_rhs(p->rres, p->d, p->n, bd, bo, p->E, p->u, p->A, p->tmp, p->b, p->Fdt, p->n_tot, st));
-    tl_launches += 1;   // two kernels
+    KL(launch_rres_rhs(p->rres, p->d, p->n, bd, bo, p->E, p->u, p->A, p->C, p->tmp, p->b, p->Fdt, p->n_tot, st));
+    tl_launches += p->d;   // 1 + d kernels
   }
   if (p->desc.x0_mode == TAU_X0_PREV)
     CK(cudaMemcpyAsync(p->X, p->u, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -281,11 +281,12 @@ cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_i
 
 // next right-hand side of the mixed form from the last residual (tau_mixed.cu); every kernel returns
 // at once when *flag == 0.  save: y = E∘u; rhs: y += E'∘u, b = B y + r - b + fdt (B the d-level
-// tridiagonal product with bd, bo per dimension); set_flag: *flag = v.
+// tridiagonal product with bd, bo per dimension, applied one factor at a time through y2, which it
+// overwrites along with y); set_flag: *flag = v.
 cudaError_t launch_rres_save(const int* flag, const double* E, const double* u, double* y, int64_t n,
                              cudaStream_t st);
 cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double* bd, const double* bo,
-                            const double* E, const double* u, double* y, const double* r, double* b,
+                            const double* E, const double* u, double* y, double* y2, const double* r, double* b,
                             const double* fdt, int64_t n, cudaStream_t st);
 cudaError_t launch_set_flag(int* flag, int v, cudaStream_t st);
 

@@ -5,7 +5,8 @@
 // A_m x = B(E_m∘x) + S x, the right-hand side of step m+1,
 //     b' = (B E_{m+1} - S) x + dt F_{m+1},
 // equals B((E_m + E_{m+1})∘x) + r - b + dt F_{m+1}: one application of the tridiagonal product
-// B = ⊗ B_{alpha_i} (a 3^d-point stencil) in place of the three FP64 Toeplitz line passes.  A device
+// B = ⊗ B_{alpha_i} (d three-point passes, one per factor) in place of the three FP64 Toeplitz line
+// passes.  A device
 // flag says whether r belongs to the current solution (set at the end of every step, cleared when
 // the caller replaces the solution); the line passes of the usual right-hand side skip themselves
 // when it is set, these kernels return at once when it is not.
@@ -31,35 +32,23 @@ __global__ void k_rres_add(const int* __restrict__ flag, const double* __restric
     y[i] = fma(E[i], u[i], y[i]);
 }
 
-// b = B y + r - b + Fdt, B the d-level tridiagonal product (weights bd_i on the line, bo_i on the two
-// neighbours, zero outside the grid)
-__global__ void k_rres_rhs(const int* __restrict__ flag, int d, int n0, int n1, int n2, double bd0, double bo0,
-                           double bd1, double bo1, double bd2, double bo2, const double* __restrict__ y,
-                           const double* __restrict__ r, double* b, const double* __restrict__ fdt, int64_t n) {
+// One factor of B = B_{d-1} ⊗ ... ⊗ B_0 along the dimension with element stride `stride` and
+// length nk: dst = bd src + bo (src at the two neighbours along that dimension; zero outside).  The
+// last factor (fin) instead writes b = B y + r - b + Fdt.  Indices are unsigned 32-bit (n_tot <= 2^31,
+// so a grid-stride index stays below 2^32).
+__global__ void k_rres_line(const int* __restrict__ flag, const double* __restrict__ src, double* dst, unsigned n,
+                            unsigned stride, unsigned nk, double bd, double bo, int fin,
+                            const double* __restrict__ r, double* b, const double* __restrict__ fdt) {
   if (!*flag) return;
-  const int64_t s1 = n0, s2 = (int64_t)n0 * n1;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int i0 = (int)(i % n0);
-    const int64_t q = i / n0;
-    const int i1 = d > 1 ? (int)(q % n1) : 0;
-    const int i2 = d > 2 ? (int)(q / n1) : 0;
-    double acc = 0.0;
-    for (int o2 = (d > 2 ? -1 : 0); o2 <= (d > 2 ? 1 : 0); ++o2) {
-      const int j2 = i2 + o2;
-      if (j2 < 0 || (d > 2 && j2 >= n2)) continue;
-      const double w2 = d > 2 ? (o2 == 0 ? bd2 : bo2) : 1.0;
-      for (int o1 = (d > 1 ? -1 : 0); o1 <= (d > 1 ? 1 : 0); ++o1) {
-        const int j1 = i1 + o1;
-        if (j1 < 0 || (d > 1 && j1 >= n1)) continue;
-        const double w21 = w2 * (d > 1 ? (o1 == 0 ? bd1 : bo1) : 1.0);
-        const int64_t row = (int64_t)o2 * s2 + (int64_t)o1 * s1;
-        double line = bd0 * y[i + row];
-        if (i0 > 0) line = fma(bo0, y[i + row - 1], line);
-        if (i0 + 1 < n0) line = fma(bo0, y[i + row + 1], line);
-        acc = fma(w21, line, acc);
-      }
-    }
-    b[i] = acc + r[i] - b[i] + fdt[i];
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned ik = (i / stride) % nk;
+    double v = bd * src[i];
+    if (ik > 0) v = fma(bo, src[i - stride], v);
+    if (ik + 1 < nk) v = fma(bo, src[i + stride], v);
+    if (fin)
+      b[i] = v + r[i] - b[i] + fdt[i];
+    else
+      dst[i] = v;
   }
 }
 
@@ -77,15 +66,24 @@ cudaError_t launch_rres_save(const int* flag, const double* E, const double* u, 
 }
 
 cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double* bd, const double* bo,
-                            const double* E, const double* u, double* y, const double* r, double* b,
+                            const double* E, const double* u, double* y, double* y2, const double* r, double* b,
                             const double* fdt, int64_t n, cudaStream_t st) {
   k_rres_add<<<mx_blocks(n), MX_THREADS, 0, st>>>(flag, E, u, y, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_rres_rhs<<<mx_blocks(n), MX_THREADS, 0, st>>>(flag, d, nn[0], d > 1 ? nn[1] : 1, d > 2 ? nn[2] : 1, bd[0],
-                                                    bo[0], d > 1 ? bd[1] : 1.0, d > 1 ? bo[1] : 0.0,
-                                                    d > 2 ? bd[2] : 1.0, d > 2 ? bo[2] : 0.0, y, r, b, fdt, n);
-  return cudaGetLastError();
+  // B one dimension at a time, y -> y2 -> y -> ..., the last factor combining into b
+  double* bufs[2] = {y, y2};
+  int64_t stride = 1;
+  for (int ax = 0; ax < d; ++ax) {
+    const int fin = ax == d - 1;
+    k_rres_line<<<mx_blocks(n), MX_THREADS, 0, st>>>(flag, bufs[ax & 1], bufs[(ax + 1) & 1], (unsigned)n,
+                                                       (unsigned)stride, (unsigned)nn[ax], bd[ax], bo[ax], fin, r, b,
+                                                       fdt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    stride *= nn[ax];
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_set_flag(int* flag, int v, cudaStream_t st) {
