@@ -195,10 +195,10 @@ class ClockSampler:
 # 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
 # kernel sources that capture measured (sha256 below), else the bench reports null.
 TRAFFIC_CAPTURE = {
-    "bytes_per_matvec": 16917248 + 768 + 16963072 + 768 + 16903680 + 0 + 8493568 + 0,
+    "bytes_per_matvec": 16916480 + 512 + 16963840 + 1280 + 16904192 + 0 + 8493312 + 0,
     "sha256": {
         "paper_2404_10221_gb300/csrc/tau_kernels.cu": "a94d0eb3d679a7db564bc1a87b6c868419eb242bd9d756b449ab16f61bd08daa",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "569aa13fa65bcc7b8e119dc26986205bb7ba494567ae9baa460390a5dd1b6b54",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "6873be8fcee38a12bcdaac1c1b138fc94673da13d44fafec12a8bb6b4c86acad",
         "paper_2404_10221_gb300/csrc/tau_fft.cuh": "ccccc8cd138b0e0753a8603a34e7f4230828c94aa4bd560053e4eddc1469012a",
     },
 }

@@ -259,6 +259,12 @@ tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_c
  * roofline of the FP64-bound kernels; runs a bounded kernel for a few milliseconds). */
 tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s);
 
+/* Self-test of the bounded waits of the tensor-core kernels: one CTA waits on an mbarrier that
+ * nothing arrives at, with a limit of 1e5 polls, and *gave_up (host int) is set to 1 when the wait
+ * ran out and the kernel returned as it must (0 would mean a wait that could not time out).  Runs
+ * on `stream` (NULL = default) and synchronizes it.  Errors: TAU_EINVAL (NULL gave_up), TAU_ECUDA. */
+tau_status tau_selftest_bounded_wait(void* stream, int* gave_up);
+
 /* ---- batching: many independent problems advanced by one graph launch per step.
  *
  * tau_batch_create groups `count` problems that have completed tau_setup, share the CUDA device,

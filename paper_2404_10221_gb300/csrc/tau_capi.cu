@@ -2036,6 +2036,20 @@ tau_status tau_apply_Minv_f32(tau_problem* p, const float* r, float* z) {
   return enq_minv<float>(p, p->st, io);
 }
 
+tau_status tau_selftest_bounded_wait(void* stream, int* gave_up) {
+  if (!gave_up) return fail(TAU_EINVAL, "NULL output");
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(d, 0xff, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_wait_selftest(100000, d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gave_up, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(TAU_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+  return TAU_OK;
+}
+
 tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_check) {
   TRY(check_ready(p));
   if (ebar) *ebar = p->ebar;

@@ -270,6 +270,9 @@ struct TcTab {
   const float* Tlo;
 };
 cudaError_t init_tc_attributes();
+// one CTA waits (bounded, `polls` polls) on an mbarrier nothing arrives at; *gave_up = 1 when the
+// wait gave up as it must
+cudaError_t launch_wait_selftest(int polls, int* gave_up, cudaStream_t st);
 // y = S x along p.ax for every line (from_out: x is p's output, in place); mul: optional diagonal
 // applied to the result
 cudaError_t launch_tc_dst(const PassT<float>& p, const TcTab& t, const float* mul, bool from_out, cudaStream_t st);

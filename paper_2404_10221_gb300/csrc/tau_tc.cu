@@ -63,8 +63,8 @@ __device__ __forceinline__ float to_tf32(float v) {
 }
 
 // bounded wait for the completion of the phase with the given parity
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < TC_WAIT; ++it) {
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int limit = TC_WAIT) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -588,6 +588,21 @@ cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_i
   a.err = t.err;
   const unsigned grid = (unsigned)((p.nlines + TC_M - 1) / TC_M);
   k_tc_mv<<<grid, TC_THREADS, tm_smem_bytes(t.N), st>>>(a);
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded wait: one CTA waits on an mbarrier that nothing arrives at; the wait must
+// give up after `polls` polls and report it (no fault, no hang).
+__global__ void k_wait_selftest(int polls, int* gave_up) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+  __syncthreads();
+  const bool ok = __syncthreads_and(bar_wait(smem_u32(&bar), 0, polls) ? 1 : 0) != 0;
+  if (threadIdx.x == 0) *gave_up = ok ? 0 : 1;
+}
+
+cudaError_t launch_wait_selftest(int polls, int* gave_up, cudaStream_t st) {
+  k_wait_selftest<<<1, 64, 0, st>>>(polls, gave_up);
   return cudaGetLastError();
 }
 

@@ -175,6 +175,7 @@ def lib():
             "tau_toeplitz_mode": [P, C.c_int, P, P],
             "tau_get_ebar": [P, D, D, D],
             "tau_measure_fp64_peak": [P, D],
+            "tau_selftest_bounded_wait": [P, C.POINTER(C.c_int)],
             "tau_apply_A_noalloc": [C.POINTER(tau_problem_desc), P, P, P, P],
             "tau_apply_A_f32": [P, C.c_int64, P, P],
             "tau_batch_create": [C.POINTER(P), C.c_int, P, C.POINTER(P)],
@@ -375,6 +376,13 @@ def tau_measure_fp64_peak(stream=None) -> float:
     v = C.c_double()
     _check(lib().tau_measure_fp64_peak(C.c_void_p(_stream(stream)), C.byref(v)))
     return v.value
+
+
+def tau_selftest_bounded_wait(stream=None) -> bool:
+    """True when a device wait on an mbarrier that nothing arrives at gave up as it must."""
+    v = C.c_int(-1)
+    _check(lib().tau_selftest_bounded_wait(C.c_void_p(_stream(stream)), C.byref(v)))
+    return v.value == 1
 
 
 def tau_apply_A_noalloc(desc: tau_problem_desc, e, x, y, stream=None):

@@ -184,3 +184,12 @@ def test_tc_split_matvec_f32(d, n):
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert rel <= 1e-5, f"m={m}: {rel:.3e}"
     p.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The tensor-core kernels wait on mbarriers with a poll limit.  A wait on a barrier that
+    nothing arrives at must end with the error status, not hang, and the CUDA context must stay
+    usable: a tensor-core M^-1 product right after it still meets its bound."""
+    tau = _tau()
+    assert tau.tau_selftest_bounded_wait() is True
+    test_tc_minv_f32(2, (31, 63))
