@@ -474,49 +474,49 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (flip) {
-          // lane = k along line L0 + cc + q: each lane loads its own a_k, c_k and the warp's edge
-          // lanes the value beyond (k-1 on lane 0, k+1 on lane 31), eight lines at a time with all
-          // loads issued before any use; the other neighbours come from the adjacent lanes
-          const int k = 128 * t + 32 * (warp & 3) + lane;
-          const bool edge = lane == 0 || lane == 31;
-          const int de = lane == 0 ? -1 : 1;
+          // lane = k along the 16 lines L0 + cc + q: each lane loads its own a_k, c_k of all 16 lines
+          // before any use; the neighbours come from the adjacent lanes, and the two beyond the
+          // warp's 32 columns (k-1 for lane 0, k+1 for lane 31) from one halo load per channel, lane q
+          // holding line q's left value and lane 16 + q its right one
+          const int kb = 128 * t + 32 * (warp & 3), k = kb + lane;
+          const int hk = lane < 16 ? kb - 1 : kb + 32;
+          const int64_t Lh = L0 + cc + (lane & 15);
+          const bool vh = Lh < a.nlines && hk >= 0 && hk < n;
+          const float ha = vh ? ach(Lh * n + hk) : 0.0f;
+          const float hc = (!lst && vh) ? cin[Lh * n + hk] : 0.0f;
+          float ak[16], ck[16];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float ak[8], ck[8], ae[8], ce[8];
+          for (int q = 0; q < 16; ++q) {
+            const int64_t Lq = L0 + cc + q;
+            const bool valid = Lq < a.nlines && k < n;
+            const int64_t o = Lq * n + k;
+            ak[q] = valid ? ach(o) : 0.0f;
+            ck[q] = (!lst && valid) ? cin[o] : 0.0f;
+          }
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int64_t Lq = L0 + cc + 8 * h + q;
-              const bool valid = Lq < a.nlines && k < n;
-              const int64_t o = Lq * n + k;
-              const bool ve = valid && edge && k + de >= 0 && k + de < n;
-              ak[q] = valid ? ach(o) : 0.0f;
-              ck[q] = (!lst && valid) ? cin[o] : 0.0f;
-              ae[q] = ve ? ach(o + de) : 0.0f;
-              ce[q] = (!lst && ve) ? cin[o + de] : 0.0f;
+          for (int q = 0; q < 16; ++q) {
+            const int64_t Lq = L0 + cc + q;
+            const bool valid = Lq < a.nlines && k < n;
+            const int64_t o = Lq * n + k;
+            float al = __shfl_up_sync(0xffffffffu, ak[q], 1), ar = __shfl_down_sync(0xffffffffu, ak[q], 1);
+            float cl = __shfl_up_sync(0xffffffffu, ck[q], 1), cr = __shfl_down_sync(0xffffffffu, ck[q], 1);
+            const int src = lane == 0 ? q : 16 + q;
+            const float hav = __shfl_sync(0xffffffffu, ha, src), hcv = __shfl_sync(0xffffffffu, hc, src);
+            if (lane == 0) {
+              al = hav;
+              cl = hcv;
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int64_t Lq = L0 + cc + 8 * h + q;
-              const bool valid = Lq < a.nlines && k < n;
-              const int64_t o = Lq * n + k;
-              float al = __shfl_up_sync(0xffffffffu, ak[q], 1), ar = __shfl_down_sync(0xffffffffu, ak[q], 1);
-              float cl = __shfl_up_sync(0xffffffffu, ck[q], 1), cr = __shfl_down_sync(0xffffffffu, ck[q], 1);
-              if (lane == 0) {
-                al = ae[q];
-                cl = ce[q];
-              }
-              if (lane == 31) {
-                ar = ae[q];
-                cr = ce[q];
-              }
-              if (valid) {
-                const float res = fmaf(seta, __uint_as_float(v[8 * h + q]), fmaf(bd, ak[q], bo * (al + ar)));
-                if (lst) {
-                  outa[o] = res;
-                } else {
-                  a.out_a[o] = res;
-                  a.out_c[o] = fmaf(bd, ck[q], bo * (cl + cr));
-                }
+            if (lane == 31) {
+              ar = hav;
+              cr = hcv;
+            }
+            if (valid) {
+              const float res = fmaf(seta, __uint_as_float(v[q]), fmaf(bd, ak[q], bo * (al + ar)));
+              if (lst) {
+                outa[o] = res;
+              } else {
+                a.out_a[o] = res;
+                a.out_c[o] = fmaf(bd, ck[q], bo * (cl + cr));
               }
             }
           }

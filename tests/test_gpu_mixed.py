@@ -2,7 +2,7 @@
 
 FP32 operators are compared with the FP64 oracle at single-precision tolerances; whole solves
 must agree with the FP64 oracle (and with the plain FP64 GPU path) to a relative 2-norm of 1e-8,
-the benchmark spec's bound for the precision form.
+the accuracy bar the precision form is held to.
 """
 
 import numpy as np
