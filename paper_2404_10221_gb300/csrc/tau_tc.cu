@@ -77,6 +77,25 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int limi
   return false;
 }
 
+// Bulk asynchronous copy (TMA engine, untiled) of `bytes` from global to shared memory, completing
+// on the mbarrier `bar`; both addresses 16-byte aligned, bytes a multiple of 16.  The caller has
+// announced the bytes on the barrier with expect_tx.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bars_init(uint64_t* bars, int count) {
+  for (int i = 0; i < count; ++i)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[i])), "r"(1));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
 template <bool MUL>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -89,8 +108,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
   const bool flip = a.ax == 0;
   const int MT = flip ? N >> 7 : 1;
   const int stage = TC_M * TC_KC * 4 + N * TC_KC * 4;   // line tile, then the S tile
+  // bars[0..1]: MMAs of the stage done; bars[2..3]: the stage's S block landed
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage + 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage + 32);
   const int64_t L0 = (int64_t)blockIdx.x * TC_M;
   const float* x = a.in_sel ? a.in_base + (int64_t)(a.g->j + a.in_sel - 1) * a.vstride : a.in;
   float* y = a.out_sel ? a.out_base + (int64_t)(a.g->j + a.out_sel - 1) * a.vstride : a.out;
@@ -106,10 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
     base = sl * n * a.inner + b;
     jstep = a.inner;
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
-  }
+  if (tid == 0) bars_init(bars, 4);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(a.nalloc));
@@ -151,6 +168,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
   };
   load_chunk(0);
   bool ok = true;
+  int pend = -1;   // chunk whose S copy is in flight and not yet seen complete
+  int lastc = -1;  // last chunk whose MMAs were committed
   for (int c = 0; c < C; ++c) {
     const int s = c & 1;
     unsigned char* sx = sm + s * stage;          // 128 lines x 32
@@ -161,6 +180,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
       ok = __syncthreads_and(bar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1) ? 1 : 0) != 0;
       if (!ok) break;
     }
+    // the chunk's block of S is stored in the shared-memory layout: one bulk copy (N*128 bytes from
+    // a 16-byte aligned offset into a 1 KB aligned stage), in flight while the lines are staged
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)(N * TC_KC * 4);
+      bar_expect_tx(smem_u32(&bars[2 + s]), bytes);
+      bulk_g2s(smem_u32(ss), a.S + (int64_t)c * N * TC_KC, bytes, smem_u32(&bars[2 + s]));
+    }
+    pend = c;
     if (flip) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -176,13 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
       }
     }
     if (c + 1 < C) load_chunk(c + 1);
-    {   // the chunk's block of S, stored in the shared-memory layout: a straight 16-byte copy
-      const float4* src = reinterpret_cast<const float4*>(a.S + (int64_t)c * N * TC_KC);
-      float4* dst = reinterpret_cast<float4*>(ss);
-      for (int i = tid; i < N * TC_KC / 4; i += TC_THREADS) dst[i] = __ldg(&src[i]);
-    }
+    // the lines' stores made visible to the tensor cores, and the S block landed
     asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
+    ok = __syncthreads_and(bar_wait(smem_u32(&bars[2 + s]), (c >> 1) & 1) ? 1 : 0) != 0;
+    if (!ok) break;
+    pend = -1;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       for (int q = 0; q < TC_KC / 8; ++q) {
@@ -202,13 +227,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&bars[s])));
     }
+    lastc = c;
   }
   // the last commit tracks every MMA of the CTA
-  if (ok) ok = __syncthreads_and(bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1) ? 1 : 0) != 0;
+  if (ok) ok = __syncthreads_and(bar_wait(smem_u32(&bars[lastc & 1]), (lastc >> 1) & 1) ? 1 : 0) != 0;
   if (!ok) {
     if (tid == 0) atomicExch(a.err, 1);
-    // give the MMAs in flight a further bounded wait before the accumulators are released
-    bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1);
+    // give the copy and the MMAs in flight a further bounded wait before the shared memory and the
+    // accumulators are released
+    if (pend >= 0) bar_wait(smem_u32(&bars[2 + (pend & 1)]), (pend >> 1) & 1);
+    if (lastc >= 0) bar_wait(smem_u32(&bars[lastc & 1]), (lastc >> 1) & 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
@@ -326,8 +354,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
   const int MT = flip ? N >> 7 : 1;
   const int xt = TC_M * TM_KC * 4, tt = N * TM_KC * 4;   // line tile, T tile (bytes)
   const int stage = 2 * xt + 2 * tt;                     // x_hi, x_lo, T_hi, T_lo
+  // bars[0..1]: MMAs of the stage done; bars[2..3]: the stage's T_hi, T_lo blocks landed
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * stage);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage + 16);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 2 * stage + 32);
   const int64_t L0 = (int64_t)blockIdx.x * TC_M;
   const float* cin = a.c_sel ? a.c_base + (int64_t)(a.g->j + a.c_sel - 1) * a.vstride : a.c_in;
   float* outa = a.out_sel ? a.out_base + (int64_t)(a.g->j + a.out_sel - 1) * a.vstride : a.out_a;
@@ -340,10 +369,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
     base = sl * n * a.inner + b;
     jstep = a.inner;
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
-  }
+  if (tid == 0) bars_init(bars, 4);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(a.nalloc));
@@ -381,6 +407,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
   };
   load_chunk(0);
   bool ok = true;
+  int pend = -1;   // chunk whose T copies are in flight and not yet seen complete
+  int lastc = -1;  // last chunk whose MMAs were committed
   for (int c = 0; c < C; ++c) {
     const int s = c & 1;
     unsigned char* sxh = sm + s * stage;
@@ -391,6 +419,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
       ok = __syncthreads_and(bar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1) ? 1 : 0) != 0;
       if (!ok) break;
     }
+    // the chunk's T_hi and T_lo blocks (N*64 bytes each, 16-byte aligned offsets, stored in the
+    // shared-memory layout): two bulk copies on one barrier, in flight while the lines are staged
+    if (tid == 0) {
+      const uint32_t bytes = (uint32_t)tt;
+      bar_expect_tx(smem_u32(&bars[2 + s]), 2 * bytes);
+      bulk_g2s(smem_u32(sth), a.Thi + (int64_t)c * N * TM_KC, bytes, smem_u32(&bars[2 + s]));
+      bulk_g2s(smem_u32(stl), a.Tlo + (int64_t)c * N * TM_KC, bytes, smem_u32(&bars[2 + s]));
+    }
+    pend = c;
     if (flip) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -411,18 +448,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
       }
     }
     if (c + 1 < C) load_chunk(c + 1);
-    {
-      const float4* srch = reinterpret_cast<const float4*>(a.Thi + (int64_t)c * N * TM_KC);
-      const float4* srcl = reinterpret_cast<const float4*>(a.Tlo + (int64_t)c * N * TM_KC);
-      float4* dh = reinterpret_cast<float4*>(sth);
-      float4* dl = reinterpret_cast<float4*>(stl);
-      for (int i = tid; i < N * TM_KC / 4; i += TC_THREADS) {
-        dh[i] = __ldg(&srch[i]);
-        dl[i] = __ldg(&srcl[i]);
-      }
-    }
     asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
+    ok = __syncthreads_and(bar_wait(smem_u32(&bars[2 + s]), (c >> 1) & 1) ? 1 : 0) != 0;
+    if (!ok) break;
+    pend = -1;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       for (int q = 0; q < TM_KC / 8; ++q) {
@@ -448,11 +477,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&bars[s])));
     }
+    lastc = c;
   }
-  if (ok) ok = __syncthreads_and(bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1) ? 1 : 0) != 0;
+  if (ok) ok = __syncthreads_and(bar_wait(smem_u32(&bars[lastc & 1]), (lastc >> 1) & 1) ? 1 : 0) != 0;
   if (!ok) {
     if (tid == 0) atomicExch(a.err, 1);
-    bar_wait(smem_u32(&bars[(C - 1) & 1]), ((C - 1) >> 1) & 1);
+    if (pend >= 0) bar_wait(smem_u32(&bars[2 + (pend & 1)]), (pend >> 1) & 1);
+    if (lastc >= 0) bar_wait(smem_u32(&bars[lastc & 1]), (lastc >> 1) & 1);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
