@@ -413,22 +413,12 @@ def run_batched(args, stream, dev):
 
 
 def served_precision(prob) -> int:
-    """Precision a served request asks for: the mixed form (FP32 inner solve, FP64 refinement) when
-    an FP32 matvec resolves the operator, i.e. eps_32 max_i eta_i ||s_i||_1 / e_min <= 0.05 with
-    eta_i = kappa_i dt / (2 h_i^alpha_i), ||s_i||_1 <= 2 s_0(alpha_i) and e >= 1 in the mix;
-    otherwise the double-float form (the FP32 error of eta T x, ~eps_32 eta ||s||_1 |x|, would
-    swamp the O(|x|) result that the cancelling Toeplitz sum leaves)."""
+    """Precision a served request asks for: the library's host-side policy (tau_choose_precision:
+    the mixed form when an FP32 matvec resolves the operator, else double-float), with e_min = 1,
+    a lower bound of every field e in the mix."""
     from paper_2404_10221_gb300 import tau
 
-    worst = 0.0
-    dt = prob.T / prob.M
-    for i in range(prob.d):
-        a = prob.alpha[i]
-        h = (prob.R[i] - prob.L[i]) / (prob.n[i] + 1)
-        eta = prob.kappa[i] * dt / (2.0 * h ** a)
-        s0 = math.gamma(a + 1.0) / math.gamma(a / 2.0 + 1.0) ** 2
-        worst = max(worst, eta * 2.0 * s0)
-    return tau.TAU_MIXED if 2.0 ** -23 * worst <= 0.05 else tau.TAU_DF64
+    return tau.tau_choose_precision(tau.make_desc(prob, e_bounds=(1.0, 1.0)))
 
 
 def run_serving(args, stream, dev):

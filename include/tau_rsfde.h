@@ -259,6 +259,17 @@ tau_status tau_get_ebar(tau_problem* p, double* ebar, double* e_hat, double* e_c
  * roofline of the FP64-bound kernels; runs a bounded kernel for a few milliseconds). */
 tau_status tau_measure_fp64_peak(void* stream, double* flops_per_s);
 
+/* Host only (no CUDA call; usable without a GPU): the faster precision form that still resolves
+ * this problem's operator.  TAU_MIXED when an FP32 matvec resolves it,
+ *     2^-23 max_i eta_i 2 s_0(alpha_i) / e_min <= 0.05,
+ * eta_i = kappa_i dt / (2 h_i^alpha_i) (Eq. (tls)), s_0(alpha) = Gamma(alpha+1)/Gamma(alpha/2+1)^2 the
+ * diagonal fractional weight and 2 s_0 a bound of the weights' 1-norm (Eq. (As1)); otherwise
+ * TAU_DF64: the FP32 rounding error of eta_i T x (about eps_32 eta_i ||s||_1 |x|) would swamp the
+ * O(e |x|) value that the cancelling Toeplitz sum leaves, and the inner solve could not converge.
+ * Reads d, n, L, R, alpha, kappa, T, M and e_min (a positive number, not NaN; a lower bound of e
+ * over the grid and all t_{m+1/2}).  Errors: TAU_EINVAL. */
+tau_status tau_choose_precision(const tau_problem_desc* desc, int* precision);
+
 /* Self-test of the bounded waits of the tensor-core kernels: one CTA waits on an mbarrier that
  * nothing arrives at, with a limit of 1e5 polls, and *gave_up (host int) is set to 1 when the wait
  * ran out and the kernel returned as it must (0 would mean a wait that could not time out).  Runs

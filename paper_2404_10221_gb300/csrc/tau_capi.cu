@@ -2036,6 +2036,30 @@ tau_status tau_apply_Minv_f32(tau_problem* p, const float* r, float* z) {
   return enq_minv<float>(p, p->st, io);
 }
 
+tau_status tau_choose_precision(const tau_problem_desc* desc, int* precision) {
+  if (!desc || !precision) return fail(TAU_EINVAL, "desc/precision is NULL");
+  const tau_problem_desc& D = *desc;
+  if (D.d < 1 || D.d > 3) return fail(TAU_EINVAL, "d=%d outside 1..3", D.d);
+  if (!(D.T > 0) || D.M < 1) return fail(TAU_EINVAL, "T must be > 0 and M >= 1");
+  if (!(D.e_min > 0) || !std::isfinite(D.e_min)) return fail(TAU_EINVAL, "e_min must be a positive number");
+  const double dt = D.T / (double)D.M;
+  double worst = 0.0;
+  for (int i = 0; i < D.d; ++i) {
+    if (D.n[i] < 1) return fail(TAU_EINVAL, "n[%d] < 1", i);
+    if (!(D.alpha[i] > 1.0 && D.alpha[i] < 2.0)) return fail(TAU_EINVAL, "alpha[%d]=%g not in (1,2)", i, D.alpha[i]);
+    if (!(D.kappa[i] >= 0.0)) return fail(TAU_EINVAL, "kappa[%d]=%g < 0", i, D.kappa[i]);
+    if (!(D.R[i] > D.L[i])) return fail(TAU_EINVAL, "R[%d] <= L[%d]", i, i);
+    const double a = D.alpha[i], h = (D.R[i] - D.L[i]) / (double)(D.n[i] + 1);
+    const double eta = D.kappa[i] * dt / (2.0 * std::pow(h, a));
+    // s_0 = Gamma(a+1) / Gamma(a/2+1)^2, the diagonal FCD weight; ||s||_1 <= 2 s_0
+    const double g = std::tgamma(a / 2.0 + 1.0);
+    const double s0 = std::tgamma(a + 1.0) / (g * g);
+    worst = std::max(worst, eta * 2.0 * s0 / D.e_min);
+  }
+  *precision = std::ldexp(worst, -23) <= 0.05 ? TAU_MIXED : TAU_DF64;
+  return TAU_OK;
+}
+
 tau_status tau_selftest_bounded_wait(void* stream, int* gave_up) {
   if (!gave_up) return fail(TAU_EINVAL, "NULL output");
   cudaStream_t st = (cudaStream_t)stream;

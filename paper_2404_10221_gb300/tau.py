@@ -176,6 +176,7 @@ def lib():
             "tau_get_ebar": [P, D, D, D],
             "tau_measure_fp64_peak": [P, D],
             "tau_selftest_bounded_wait": [P, C.POINTER(C.c_int)],
+            "tau_choose_precision": [C.POINTER(tau_problem_desc), C.POINTER(C.c_int)],
             "tau_apply_A_noalloc": [C.POINTER(tau_problem_desc), P, P, P, P],
             "tau_apply_A_f32": [P, C.c_int64, P, P],
             "tau_batch_create": [C.POINTER(P), C.c_int, P, C.POINTER(P)],
@@ -375,6 +376,13 @@ def tau_get_ebar(h: int):
 def tau_measure_fp64_peak(stream=None) -> float:
     v = C.c_double()
     _check(lib().tau_measure_fp64_peak(C.c_void_p(_stream(stream)), C.byref(v)))
+    return v.value
+
+
+def tau_choose_precision(desc: tau_problem_desc) -> int:
+    """TAU_MIXED or TAU_DF64 for this problem (host only; desc.e_min must be set)."""
+    v = C.c_int(-1)
+    _check(lib().tau_choose_precision(C.byref(desc), C.byref(v)))
     return v.value
 
 

@@ -127,3 +127,29 @@ def test_make_desc_marshals_problem():
     assert d.d == 3 and list(d.n) == [15, 15, 15] and d.M == 7
     assert list(d.alpha) == [1.2, 1.5, 1.9]
     assert math.isnan(d.e_min) and math.isnan(d.e_max)
+
+
+def test_choose_precision_policy(lib):
+    """tau_choose_precision runs on the host (no GPU).  Its verdicts agree with what the GPU solves
+    showed: the FP32 inner solve of the mixed form converges on the 1-D workload at n = 5000
+    (policy value 0.022) and on the 1023^2 and 255^3 workloads, and cannot resolve the operator of
+    the 1-D workload at n = 65535 (eta ~ 3e6, value 1.05), where the double-float form is needed."""
+    from paper_2404_10221_gb300 import tau
+    from paper_2404_10221_gb300 import workloads as W
+    cases = [(W.c1_1d(n=5000, M=3), tau.TAU_MIXED), (W.c1_1d(n=65535, M=3), tau.TAU_DF64),
+             (W.c2_2d(), tau.TAU_MIXED), (W.c3_3d(), tau.TAU_MIXED), (W.c1_1d(), tau.TAU_MIXED)]
+    for wl, want in cases:
+        d = tau.make_desc(wl.prob, e_bounds=(1.0, 3.0))
+        assert tau.tau_choose_precision(d) == want, wl.prob.n
+    # the boundary moves with e_min: a 25x larger e_min brings n = 65535 under the bound
+    d = tau.make_desc(W.c1_1d(n=65535, M=3).prob, e_bounds=(25.0, 30.0))
+    assert tau.tau_choose_precision(d) == tau.TAU_MIXED
+    # e_min unset (NaN) or not positive, or a bad order: argument errors, no GPU touched
+    for bounds in (None, (0.0, 1.0), (-1.0, 1.0)):
+        d = tau.make_desc(W.c1_1d(n=127).prob, e_bounds=bounds)
+        with pytest.raises(tau.TauError):
+            tau.tau_choose_precision(d)
+    d = tau.make_desc(W.c1_1d(n=127).prob, e_bounds=(1.0, 2.0))
+    d.alpha[0] = 2.0
+    with pytest.raises(tau.TauError):
+        tau.tau_choose_precision(d)
