@@ -4,6 +4,7 @@
 #include "tau_rsfde.h"
 #include "tau_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <map>
