@@ -728,7 +728,7 @@ tau_status build_graph_inner(tau_problem* p, cudaGraph_t G) {
     p->k_pro = tl_launches;
     cudaGraphConditionalHandle h;
     cudaGraphNode_t w;
-    cudaGraph_t body;
+    cudaGraph_t body = nullptr;
     TRY(make_handle(G, &h));
     TRY(add_while(G, leaves, &h, &w, &body));
     TRY(capture_into(p, body, none, [&](cudaStream_t s) { return enq_body(p, s, h, 1); }, tmp));
@@ -741,7 +741,7 @@ tau_status build_graph_inner(tau_problem* p, cudaGraph_t G) {
   p->k_pro = tl_launches;
   cudaGraphConditionalHandle ho, hi;
   cudaGraphNode_t wo, wi;
-  cudaGraph_t bo, bi;
+  cudaGraph_t bo = nullptr, bi = nullptr;
   TRY(make_handle(G, &ho));
   TRY(add_while(G, leaves, &ho, &wo, &bo));
   TRY(make_handle(bo, &hi));

@@ -117,7 +117,7 @@ void finish(tau_server* s, const std::shared_ptr<Req>& r, tau_status st, const c
 }
 
 // Create, fill and set up the request's problem on its own stream (worker thread).
-tau_status admit(tau_server* s, const std::shared_ptr<Req>& r) {
+tau_status admit(const std::shared_ptr<Req>& r) {
   if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
     return TAU_ECUDA;
@@ -194,7 +194,7 @@ void worker_loop(tau_server* s) {
         r->state = TAU_REQ_RUNNING;
         r->t_admit = now_s(s);
       }
-      tau_status st = admit(s, r);
+      tau_status st = admit(r);
       std::lock_guard<std::mutex> lk(s->mu);
       if (st != TAU_OK) {
         finish(s, r, st, tau_last_error());
