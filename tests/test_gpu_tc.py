@@ -74,8 +74,8 @@ def emulated_minv(pr, ebar, r, tc_dims):
     return X.reshape(-1)
 
 
-SHAPES = [(1, (127,)), (1, (100,)), (1, (5,)), (2, (31, 63)), (2, (20, 9)), (2, (255, 255)),
-          (2, (300, 129)), (3, (15, 7, 31)), (3, (63, 63, 63))]
+SHAPES = [(1, (127,)), (1, (100,)), (1, (5,)), (1, (256,)), (2, (31, 63)), (2, (20, 9)), (2, (255, 255)),
+          (2, (300, 129)), (2, (129, 17)), (3, (15, 7, 31)), (3, (63, 63, 63)), (3, (2, 3, 5))]
 
 
 @pytest.mark.parametrize("d,n", SHAPES)
@@ -161,8 +161,9 @@ def test_tc_dims_reported():
         p.close()
 
 
-@pytest.mark.parametrize("d,n", [(1, (127,)), (1, (5,)), (2, (31, 63)), (2, (255, 255)), (2, (20, 9)),
-                                 (3, (15, 7, 31)), (3, (63, 63, 63))])
+@pytest.mark.parametrize("d,n", [(1, (127,)), (1, (5,)), (1, (256,)), (2, (31, 63)), (2, (255, 255)),
+                                 (2, (20, 9)), (2, (129, 17)), (3, (15, 7, 31)), (3, (63, 63, 63)),
+                                 (3, (2, 3, 5))])
 def test_tc_split_matvec_f32(d, n):
     """A x in FP32 with the Toeplitz products as split-TF32 tensor-core products: FP32-level
     accuracy, the bound of the FP32 line passes (1e-5 relative against the oracle)."""
