@@ -4,7 +4,7 @@
 Workload: the 2-D RSFDE on (0,1)^2 with n = 1023 per dimension (1,046,529
 unknowns), alpha = (1.4, 1.8), kappa = (1, 0.5), e = 2 + sin(pi x) cos(pi y)(1+t),
 T = 1, M = 100 Crank–Nicolson steps, manufactured u = e^{-t} x^2(1-x)^2 y^2(1-y)^2,
-plain FP64, GMRES tol 1e-12 (synthetic inputs).
+plain FP64, GMRES tol 1e-12 (synthetic, seeded inputs from paper_2404_10221_gb300.workloads).
 
 One bench step = one Crank–Nicolson step (right-hand side + a complete
 τ-preconditioned GMRES solve + solution update) on the full grid.
@@ -190,8 +190,9 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of the four line-pass launches of one preconditioned matvec on the
-# 1023^2 grid, from the ncu capture summarised in profiles/k_pass_2d1023_full.md; valid only for the
-# kernel sources that capture measured (sha256 below), else the bench reports null.
+# 1023^2 grid, from an ncu capture (--set full, -k regex:k_pass -c 4) of `bench.py --matvec-only 3`;
+# valid only for the kernel sources that capture measured (sha256 below), else the bench reports
+# null.
 TRAFFIC_CAPTURE = {
     "bytes_per_matvec": 16916480 + 512 + 16963840 + 1280 + 16904192 + 0 + 8493312 + 0,
     "sha256": {
