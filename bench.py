@@ -580,15 +580,16 @@ def run_native(args):
         host_in = torch.empty(n_tot, dtype=torch.float64).pin_memory()
         host_out = torch.empty(n_tot, dtype=torch.float64).pin_memory()
         tau.tau_get_solution(h2, host_in.numpy(), False)
-        Ke = min(K, 5)
-        for i in range(min(Wm, 1)):
+        # the same steps as the device-timed run: Wm untimed, then K timed
+        Ke = K
+        for i in range(Wm):
             tau.tau_set_solution(h2, host_in.numpy(), False, i)
             tau.tau_step(h2, 1)
             tau.tau_get_solution(h2, host_out.numpy(), False)
             host_in.copy_(host_out)
         barrier()
         t0 = time.perf_counter()
-        m0 = min(Wm, 1)
+        m0 = Wm
         for i in range(Ke):
             tau.tau_set_solution(h2, host_in.numpy(), False, m0 + i)
             tau.tau_step(h2, 1)
