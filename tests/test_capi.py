@@ -97,6 +97,33 @@ def test_invalid_desc_rejected_before_any_device_call(lib):
     d.max_iter = 0
     with pytest.raises(tau.TauError):
         tau.tau_create(d, 0)
+    # empty or oversized grids, a degenerate time grid or domain, unknown selectors
+    def edits():
+        yield "n[0] = 0", lambda d: d.n.__setitem__(0, 0)
+        yield "n[1] = 2^20 + 1", lambda d: d.n.__setitem__(1, (1 << 20) + 1)
+        yield "n_tot > 2^31", lambda d: (setattr(d, "d", 3), d.n.__setitem__(0, 2048), d.n.__setitem__(1, 2048),
+                                         d.n.__setitem__(2, 2048))
+        yield "T = 0", lambda d: setattr(d, "T", 0.0)
+        yield "M = 0", lambda d: setattr(d, "M", 0)
+        yield "R <= L", lambda d: d.R.__setitem__(0, d.L[0])
+        yield "all kappa 0", lambda d: (d.kappa.__setitem__(0, 0.0), d.kappa.__setitem__(1, 0.0))
+        yield "tol = 0", lambda d: setattr(d, "tol", 0.0)
+        yield "x0_mode", lambda d: setattr(d, "x0_mode", 3)
+        yield "precision", lambda d: setattr(d, "precision", 7)
+        yield "method", lambda d: setattr(d, "method", 9)
+        yield "tc", lambda d: setattr(d, "tc", 5)
+    for what, edit in edits():
+        d = tau.make_desc(wl.prob)
+        edit(d)
+        with pytest.raises(tau.TauError) as ei:
+            tau.tau_create(d, 0)
+        assert ei.value.status == tau.TAU_EINVAL, what
+    # the two-sided and Strang circulant methods run in FP64 only
+    for method in (tau.TAU_TPGM, tau.TAU_SPGM):
+        d = tau.make_desc(wl.prob, precision=tau.TAU_MIXED, method=method)
+        with pytest.raises(tau.TauError) as ei:
+            tau.tau_create(d, 0)
+        assert ei.value.status == tau.TAU_EUNSUPPORTED
     d = tau.make_desc(wl.prob, route=(1, 0, 0))
     d.n[0] = 6                       # FFT route needs n+1 = 2^p
     with pytest.raises(tau.TauError) as ei:
