@@ -933,7 +933,7 @@ tau_status sync_status(tau_problem* p) {
   if (p->tc_err) {
     int e = 0;
     CK(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) return fail(TAU_ECUDA, "a tensor-core pass gave up waiting for its MMAs");
+    if (e) return fail(TAU_ETIMEOUT, "a tensor-core pass gave up waiting on an mbarrier (its copies or MMAs)");
   }
   GmresDev g;
   CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
