@@ -6,7 +6,9 @@
 // one tcgen05.mma.kind::tf32 per 8 values of j (M = 128, N columns of fp32 accumulators in tensor
 // memory), the operands staged in shared memory in the 8-row x 16-byte core-matrix layout
 // (K-major, no swizzle: LBO = 128 B between core matrices along K, SBO = 1 KB between 8-row
-// groups), two K-chunks of 32 in flight.  Inputs are rounded to TF32 (10-bit mantissa) on the way
+// groups), two K-chunks of 32 in flight.  Each chunk's block of S is stored at setup in exactly
+// that layout and staged by one bulk asynchronous copy (TMA engine) that completes on the stage's
+// mbarrier; the lines go through registers.  Inputs are rounded to TF32 (10-bit mantissa) on the way
 // into shared memory, S once at setup, so the product carries a relative error of order 1e-3: the
 // flexible GMRES of the mixed form takes the result as its (variable) preconditioner, so this
 // changes its iteration count, not the solution it converges to.  The epilogue reads the
@@ -303,7 +305,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mode(const TcArgs a) {
 // weights.  T c is a dense product on the tensor cores with FP32-level accuracy from split TF32
 // operands: c = c_hi + c_lo, T = T_hi + T_lo (each part TF32), T c ~ T_hi c_hi + T_hi c_lo + T_lo c_hi
 // (the dropped T_lo c_lo is ~2^-22 relative).  K-chunks of 16 (two MMA K-steps, three products
-// each), core-matrix layout with 512-byte row groups.  The stencil reads a and c (neighbours
+// each), core-matrix layout with 512-byte row groups; the chunk's T_hi and T_lo blocks arrive by
+// two bulk asynchronous copies on the stage's mbarrier.  The stencil reads a and c (neighbours
 // included) from global memory in the epilogue, so the pass writes new channel buffers.
 constexpr int TM_KC = 16;
 
