@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--profile-step", default="", choices=["", "2d_1023_fp64", "3d_255_mixed"],
+    ap.add_argument("--profile-step", default="", choices=["", "2d_1023_fp64", "3d_255_mixed", "2d_1023_mixed"],
                     help="profiling driver: set up the workload, run one step, then one more step inside "
                          "the NVTX range 'step' (ncu --nvtx --nvtx-include step/)")
     ap.add_argument("--matvec-only", type=int, default=0,
@@ -667,6 +667,8 @@ def run_profile_step(args):
 
     if args.profile_step == "2d_1023_fp64":
         wl, prec = W.c2_2d(), tau.TAU_FP64
+    elif args.profile_step == "2d_1023_mixed":
+        wl, prec = W.c2_2d(), tau.TAU_MIXED
     else:
         wl, prec = W.c3_3d(), tau.TAU_MIXED
     p = tau.Problem(wl, precision=prec)

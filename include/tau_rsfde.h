@@ -153,6 +153,28 @@ typedef struct {
   const double* space[3];
 } tau_field;
 
+/* Fields as device arrays, for e and f of any form (not only separable expansions): the
+ * problem statement (§1, Eq. (RSFDE)) allows any positive e(x,t) and any source f(x,t), and each
+ * Crank–Nicolson step (Eq. (tls)) needs them only at t_{m+1/2} on the grid.
+ *   e:   e(x_J, t_{m+1/2}) at the interior nodes (x_1 fastest), step m at e + m * e_step;
+ *        e_step = n_tot (M slabs of n_tot doubles) or 0 (e does not depend on t: one slab).
+ *   f:   f(x, t_{m+1/2}) on the padded grid prod_i (n_i + 2) (boundary nodes included, x_1
+ *        fastest), step m at f + m * f_step; f_step = prod(n_i + 2) or 0.  NULL: f = 0.
+ *        The library forms F = interior restriction of (⊗_l 𝓗_{alpha_l}) f (Eq. (2.2), Appendix A).
+ *   psi: u^{(0)} = psi(x_J) at the interior nodes (n_tot doubles); NULL: psi = 0.
+ * All three are device pointers of the problem's device, owned by the caller, who keeps them
+ * alive and their contents as given until tau_destroy: the library keeps the pointers (no copy)
+ * and reads e and f of step m, on the problem's stream, when that step runs (so a caller may
+ * write a step's slab on that stream any time before the step is enqueued); tau_setup reads all
+ * of e (the ebar scan, unless desc bounds are given) and psi. */
+typedef struct {
+  const double* e;
+  int64_t e_step;
+  const double* f;
+  int64_t f_step;
+  const double* psi;
+} tau_field_device;
+
 /* Per-problem statistics (host copy). */
 typedef struct {
   int64_t steps_done;       /* m: number of completed steps */
@@ -177,6 +199,19 @@ typedef struct {
   int tc_dims;              /* bit i set: the FP32 τ solve runs its DST-I along dimension i on the
                                tensor cores (TAU_TC_ON, or TAU_TC_AUTO where it timed faster); bit 8
                                set: the FP32 matvec runs as split-TF32 tensor-core passes */
+  int route_source[3];      /* how route[i] was chosen: 0 by the rule of TAU_ROUTE_AUTO (or forced),
+                               1 measured by this tau_setup (d >= 2, TAU_ROUTE_AUTO, tuning on: the
+                               FFT or chirp route against the dense route, FP64 passes timed), 2 from
+                               an earlier measurement on this device and shape (in memory, or the
+                               autotune file: $TAU_TUNE_CACHE, default
+                               $XDG_CACHE_HOME/tau_rsfde/autotune.txt or ~/.cache/tau_rsfde/...;
+                               "off" disables the file) */
+  double route_ms[3];       /* measured device time of the chosen route's representative passes (one
+                               matvec pass and one DST pass along dimension i, ms); 0 if not measured */
+  double route_alt_ms[3];   /* the same for the fastest rejected candidate; 0 if none */
+  int resid_precision;      /* TAU_MIXED: precision of the outer residual b - A x (TAU_FP64, or
+                               TAU_DF64 where its rounding floor 2^-48 * 8 * max_i eta_i 2 s_0(alpha_i)
+                               / ebar is at most refine_tol / 2); otherwise desc.precision */
 } tau_stats;
 
 /* Create a problem: validates desc, allocates device state (Krylov basis of
@@ -188,6 +223,11 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
  * at t_{m+1/2} on the padded grid) and psi (u^{(0)} = psi(G)) to the device.
  * Requires e->n_times == f->n_times == M and psi->n_times == 1.  Synchronous. */
 tau_status tau_set_fields(tau_problem* p, const tau_field* e, const tau_field* f, const tau_field* psi);
+
+/* The device-array form of tau_set_fields (tau_field_device above); either call sets the fields
+ * once.  Errors: TAU_EINVAL (NULL e, a step that is neither 0 nor the slab size), TAU_ESTATE
+ * (fields already set).  Enqueues nothing. */
+tau_status tau_set_fields_device(tau_problem* p, const tau_field_device* fields);
 
 /* One-time setup (Remark after Theorem GMRES: the preconditioner does not depend on the step):
  * FCD weights (§2), Toeplitz spectra, tau eigenvalues q (Eq. (q)), beta (Lemma Heig), 1/mu,
@@ -276,6 +316,13 @@ tau_status tau_choose_precision(const tau_problem_desc* desc, int* precision);
  * on `stream` (NULL = default) and synchronizes it.  Errors: TAU_EINVAL (NULL gave_up), TAU_ECUDA. */
 tau_status tau_selftest_bounded_wait(void* stream, int* gave_up);
 
+/* Test hook of the error path of the bounded device waits: sets, on the problem's stream, the
+ * device flag that a tensor-core kernel sets when one of its mbarrier waits runs out.  The next
+ * tau_sync / tau_solve / tau_batch_sync of the problem returns TAU_ETIMEOUT and clears the flag
+ * (an expired wait is reported once); the syncs after that return to normal.  No device wait is
+ * made to run out.  Errors: TAU_EINVAL (NULL), TAU_ECUDA. */
+tau_status tau_inject_wait_timeout(tau_problem* p);
+
 /* ---- batching: many independent problems advanced by one graph launch per step.
  *
  * tau_batch_create groups `count` problems that have completed tau_setup, share the CUDA device,
@@ -346,8 +393,10 @@ tau_status tau_server_destroy(tau_server* s);
 /* ---- allocation-free entry point (the paper has no counterpart).
  *
  * y = A x = B_alpha (e ∘ x) + S_alpha x for the grid and coefficients of `desc` (d, n, L, R, alpha,
- * kappa, T, M give h_i, dt and eta_i; the other fields are ignored), without a tau_problem and
- * without allocating device memory.  For callers that cannot call cudaMalloc: code living inside
+ * kappa, T, M give h_i, dt and eta_i; route[i] must be TAU_ROUTE_AUTO; the other fields are
+ * ignored), without a tau_problem and without allocating device memory.  The entry point picks
+ * its own route per dimension: the FFT route when n_i + 1 is a power of two, dense O(n_i) sums
+ * otherwise (a forced route returns TAU_EINVAL).  For callers that cannot call cudaMalloc: code living inside
  * a host application whose memory pool owns the device, plugins that must not change the
  * device's memory footprint, and latency-critical loops where an allocation (which may
  * synchronise the device) is not acceptable.

@@ -653,23 +653,49 @@ class OracleSolver:
 
     def __init__(self, prob, tables: dict, ebar: Optional[float] = None, sided: int = 1):
         """sided 1: one-sided (OPGM, Eq. (one-sided)); 2: two-sided (TPGM, Eq. (Pls));
-        3: the Strang circulant comparison method (SPGM, Table 1)."""
+        3: the Strang circulant comparison method (SPGM, Table 1).
+
+        tables: separable tables (e_tc, e_sp, f_tc, f_sp, psi_tc, psi_sp), or the fields as grid
+        arrays of any form (§1 allows any positive e and any f): "e_dense" of shape (M, n_tot) or
+        (n_tot,) for an e that does not depend on t, "f_dense" of shape (M, prod(n_i + 2)) or
+        (prod(n_i + 2),) on the padded grid (x_1 fastest) or None for f = 0, and "psi_dense" of
+        shape (n_tot,) or None for psi = 0; every value taken at t_{m+1/2} (reading R5)."""
         self.prob = prob
         self.sided = sided
         self.t = tables
+        self.dense = "e_dense" in tables
         if ebar is None:
-            ebar = ebar_from_tables(prob, tables["e_tc"], tables["e_sp"])[0]
+            if self.dense:
+                ev = np.asarray(tables["e_dense"])
+                ebar = 0.5 * (float(ev.max()) + float(ev.min()))   # Eqs. (bard), (dhat) over all values
+            else:
+                ebar = ebar_from_tables(prob, tables["e_tc"], tables["e_sp"])[0]
         self.ebar = ebar
         self.toeps = _per_dim(prob, toeplitz_S)
         self.mu = mu_tensor(prob, ebar)
-        self.u = eval_field_interior(prob, tables["psi_tc"][0], tables["psi_sp"])
+        if self.dense:
+            psi = tables.get("psi_dense")
+            self.u = np.zeros(prob.n_tot) if psi is None else np.array(psi, dtype=np.float64)
+        else:
+            self.u = eval_field_interior(prob, tables["psi_tc"][0], tables["psi_sp"])
         self.m = 0
         self.iters: List[int] = []
 
     def e_at(self, m):
+        if self.dense:
+            ev = np.asarray(self.t["e_dense"], dtype=np.float64)
+            return ev[m] if ev.ndim == 2 else ev
         return eval_field_interior(self.prob, self.t["e_tc"][m], self.t["e_sp"])
 
     def F_at(self, m):
+        if self.dense:
+            fv = self.t.get("f_dense")
+            if fv is None:
+                return np.zeros(self.prob.n_tot)
+            fv = np.asarray(fv, dtype=np.float64)
+            fm = fv[m] if fv.ndim == 2 else fv
+            shape = tuple(self.prob.n[i] + 2 for i in reversed(range(self.prob.d)))
+            return rhs_F(self.prob, fm.reshape(shape))
         return rhs_F(self.prob, eval_field(self.prob, self.t["f_tc"][m], self.t["f_sp"]))
 
     def step(self, direct: bool = False) -> GmresResult | None:

@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <sys/stat.h>
+
 using namespace tau;
 
 namespace {
@@ -105,6 +107,9 @@ struct tau_problem {
   double *s[3] = {nullptr, nullptr, nullptr}, *sintab[3] = {nullptr, nullptr, nullptr};
   double *beta[3] = {nullptr, nullptr, nullptr}, *q[3] = {nullptr, nullptr, nullptr};
   double *e_tc = nullptr, *f_tc = nullptr, *psi_tc = nullptr;
+  // fields given as caller-owned device arrays (tau_set_fields_device)
+  const double *e_dev = nullptr, *f_dev = nullptr, *psi_dev = nullptr;
+  int64_t e_step = 0, f_step = 0;
   double *e_sp[3] = {nullptr, nullptr, nullptr}, *f_hsp[3] = {nullptr, nullptr, nullptr},
          *psi_sp[3] = {nullptr, nullptr, nullptr};
   int re = 0, rf = 0, rp = 0;
@@ -127,11 +132,17 @@ struct tau_problem {
          *twK2_32[3] = {nullptr, nullptr, nullptr};
   float *s32[3] = {nullptr, nullptr, nullptr}, *sintab32[3] = {nullptr, nullptr, nullptr};
   int64_t k_ir_pre = 0, k_ir_post = 0;         // kernels of one refinement sweep around the inner loop
+  int route_src[3] = {0, 0, 0};                 // 0 rule or forced, 1 measured, 2 recorded measurement
+  double route_ms[3] = {0, 0, 0}, route_alt_ms[3] = {0, 0, 0};
   int lpb_tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // lines per CTA chosen by the autotuner
                                                           // (FP64, FP32, double-float)
   // double-float precision (TAU_DF64): solver vectors live in the FP64 buffers above as df64 pairs
   bool dfm = false;
   df64 *Edf = nullptr, *Fdf = nullptr, *invmu_df = nullptr;
+  // mixed form: the outer residual b - A x as double-float line passes (X and tmp then hold df64
+  // pairs, b is copied to bdf), chosen at setup where its rounding floor is below refine_tol
+  bool res_df = false;
+  df64* bdf = nullptr;
   // two-sided method (TAU_TPGM): sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1}
   int tpgm = 0;
   double *pmh = nullptr, *pmhb = nullptr;
@@ -191,6 +202,15 @@ FieldDev field_dev(const tau_problem* p) {
   f.e_tc = p->e_tc;
   f.f_tc = p->f_tc;
   f.dt = p->dt;
+  f.e_dev = p->e_dev;
+  f.e_step = p->e_step;
+  f.f_dev = p->f_dev;
+  f.f_step = p->f_step;
+  for (int i = 0; i < 3; ++i) {
+    const double a = i < p->d ? p->desc.alpha[i] : 0.0;
+    f.hw[i][0] = a / 24.0;
+    f.hw[i][1] = 1.0 - a / 12.0;
+  }
   return f;
 }
 
@@ -479,6 +499,7 @@ tau_status enq_fields(tau_problem* p, cudaStream_t st, int64_t m_override) {
     KL(launch_d_to_df(p->E, p->Edf, p->n_tot, st));
     KL(launch_d_to_df(p->Fdt, p->Fdf, p->n_tot, st));
   }
+  if (p->res_df) KL(launch_d_to_df(p->E, p->Edf, p->n_tot, st));
   if (p->mixed) KL(launch_f64_to_f32(p->E, p->E32, p->n_tot, st));
   return TAU_OK;
 }
@@ -587,9 +608,10 @@ tau_status enq_body(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle 
 }
 
 // ---- mixed precision: prologue, refinement sweep (before / after the inner loop), inner
-//      FGMRES iteration, epilogue
+//      FGMRES iteration, epilogue.  The refinement iterate X and the residual in tmp are FP64, or
+//      double-float pairs in the same buffers when the residual runs on the FP32 pipes (res_df).
 tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
-  // b = (B E - S) u + dt F.  After a step, tmp holds r = b_old - A_old u in FP64 and the flag is set:
+  // b = (B E - S) u + dt F.  After a step, tmp holds r = b_old - A_old u and the flag is set:
   // then b = B((E_old + E)∘u) + r - b_old + dt F (a stencil, tau_mixed.cu) and the line passes of
   // the direct form skip themselves; otherwise (first step, a solution set by the caller) the
   // line passes run and the stencil kernels return at once.
@@ -605,28 +627,47 @@ tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
       bd[i] = 1.0 - p->desc.alpha[i] / 12.0;
       bo[i] = p->desc.alpha[i] / 24.0;
     }
-    KL(launch_rres_rhs(p->rres, p->d, p->n, bd, bo, p->E, p->u, p->A, p->C, p->tmp, p->b, p->Fdt, p->n_tot, st));
+    KL(launch_rres_rhs(p->rres, p->d, p->n, bd, bo, p->E, p->u, p->A, p->C, p->tmp, p->res_df ? 1 : 0, p->b,
+                       p->Fdt, p->n_tot, st));
     tl_launches += p->d;   // 1 + d kernels
   }
-  if (p->desc.x0_mode == TAU_X0_PREV)
+  if (p->res_df) {
+    KL(launch_d_to_df(p->b, p->bdf, p->n_tot, st));
+    if (p->desc.x0_mode == TAU_X0_PREV) KL(launch_d_to_df(p->u, as<df64>(p->X), p->n_tot, st));
+    else CK(cudaMemsetAsync(p->X, 0, p->n_tot * sizeof(double), st));
+  } else if (p->desc.x0_mode == TAU_X0_PREV) {
     CK(cudaMemcpyAsync(p->X, p->u, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  else
+  } else {
     CK(cudaMemsetAsync(p->X, 0, p->n_tot * sizeof(double), st));
+  }
   KL(launch_ir_init(p->ir, st));
   return TAU_OK;
 }
 
 tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandle h,
                             cudaGraphConditionalHandle h_in, int use_cond) {
-  // r = b - A x in FP64; on the first sweep of a zero initial guess r = b and the passes are skipped
-  KL(launch_ir_first_resid(p->ir, p->b, p->tmp, p->n_tot, p->desc.x0_mode == TAU_X0_ZERO, st));
+  // r = b - A x (FP64, or double-float); on the first sweep of a zero initial guess r = b and the
+  // passes are skipped (the copy is bitwise, so it serves both storage types)
+  const bool zero = p->desc.x0_mode == TAU_X0_ZERO;
+  if (p->res_df) {
+    KL(launch_ir_first_resid(p->ir, reinterpret_cast<const double*>(p->bdf), p->tmp, p->n_tot, zero, st));
+    ChainT<df64> r;
+    r.x = as<df64>(p->X);
+    r.out = as<df64>(p->tmp);
+    TRY(enq_mv<df64>(p, st, r, 1.0, FIN_RESID, p->bdf, false, &p->ir->skip_resid));
+    KL(launch_norm_partial<df64>(as<df64>(p->tmp), p->n_tot, p->g, p->pnorm, st));
+    KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, st));
+    KL(launch_scale_to_f32<df64>(as<df64>(p->tmp), p->V32, p->n_tot, p->ir, st));
+    return TAU_OK;
+  }
+  KL(launch_ir_first_resid(p->ir, p->b, p->tmp, p->n_tot, zero, st));
   ChainIO r;
   r.x = p->X;
   r.out = p->tmp;
   TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false, &p->ir->skip_resid));
   KL(launch_norm_partial(p->tmp, p->n_tot, p->g, p->pnorm, st));
   KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, st));
-  KL(launch_scale_to_f32(p->tmp, p->V32, p->n_tot, p->ir, st));
+  KL(launch_scale_to_f32<double>(p->tmp, p->V32, p->n_tot, p->ir, st));
   return TAU_OK;
 }
 
@@ -657,12 +698,14 @@ tau_status enq_mx_inner(tau_problem* p, cudaStream_t st, cudaGraphConditionalHan
 
 tau_status enq_mx_sweep_post(tau_problem* p, cudaStream_t st) {
   KL(launch_backsolve(p->gin, p->Hin, p->gvin, p->kin + 1, p->yin, st));
-  KL(launch_update_x(p->X, p->Z32, p->yin, p->n_tot, p->gin, p->ir, st));
+  if (p->res_df) KL(launch_update_x<df64>(as<df64>(p->X), p->Z32, p->yin, p->n_tot, p->gin, p->ir, st));
+  else KL(launch_update_x<double>(p->X, p->Z32, p->yin, p->n_tot, p->gin, p->ir, st));
   return TAU_OK;
 }
 
 tau_status enq_mx_epilogue(tau_problem* p, cudaStream_t st) {
-  CK(cudaMemcpyAsync(p->u, p->X, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (p->res_df) KL(launch_df_to_d(as<df64>(p->X), p->u, p->n_tot, st));
+  else CK(cudaMemcpyAsync(p->u, p->X, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
   KL(launch_set_flag(p->rres, 1, st));   // tmp is the residual of this step's final iterate
   KL(launch_ir_finish(p->ir, p->g, p->iters, p->sweeps, st));
   return TAU_OK;
@@ -835,6 +878,111 @@ tau_status fields_for(tau_problem* p, int64_t m) {
 
 // ---- tile autotuner: lines per CTA for each dimension and element type.  Candidates are timed
 // on the real matvec pass (channels a, c in place) with CUDA events; results are cached per shape.
+// ---- persistent record of the autotuner's decisions (lines per CTA, route, tensor cores), keyed
+// by device and shape.  It lives in memory for the process and, unless TAU_TUNE_CACHE is "off",
+// "0" or empty, in a text file: $TAU_TUNE_CACHE, else $XDG_CACHE_HOME/tau_rsfde/autotune.txt, else
+// $HOME/.cache/tau_rsfde/autotune.txt.  The file's first line names the library build; a file
+// written by another build is discarded (its kernels may have changed), so a rebuilt library
+// measures again.  Lines are "key<TAB>value"; a later line overrides an earlier one.
+struct TuneStore {
+  std::mutex mu;
+  bool loaded = false, fresh = true;   // fresh: the file must be (re)written with a header first
+  std::string path;
+  std::map<std::string, std::string> kv;
+};
+TuneStore g_store;
+
+std::string tune_header() { return std::string("# tau_rsfde autotune ") + __DATE__ + " " + __TIME__; }
+
+std::string tune_path() {
+  const char* e = std::getenv("TAU_TUNE_CACHE");
+  if (e) return (!e[0] || !strcmp(e, "off") || !strcmp(e, "0")) ? std::string() : std::string(e);
+  const char* x = std::getenv("XDG_CACHE_HOME");
+  std::string base;
+  if (x && x[0]) {
+    base = x;
+  } else {
+    const char* h = std::getenv("HOME");
+    if (!h || !h[0]) return std::string();
+    base = std::string(h) + "/.cache";
+  }
+  return base + "/tau_rsfde/autotune.txt";
+}
+
+void tune_load_locked() {
+  if (g_store.loaded) return;
+  g_store.loaded = true;
+  g_store.path = tune_path();
+  if (g_store.path.empty()) return;
+  FILE* f = fopen(g_store.path.c_str(), "r");
+  if (!f) return;
+  char line[1024];
+  const std::string hdr = tune_header();
+  if (fgets(line, sizeof(line), f) && std::string(line).rfind(hdr, 0) == 0) {
+    g_store.fresh = false;
+    while (fgets(line, sizeof(line), f)) {
+      std::string s(line);
+      while (!s.empty() && (s.back() == '\n' || s.back() == '\r')) s.pop_back();
+      const size_t t = s.find('\t');
+      if (t != std::string::npos) g_store.kv[s.substr(0, t)] = s.substr(t + 1);
+    }
+  }
+  fclose(f);
+}
+
+bool tune_get(const std::string& key, std::string* val) {
+  std::lock_guard<std::mutex> lk(g_store.mu);
+  tune_load_locked();
+  auto it = g_store.kv.find(key);
+  if (it == g_store.kv.end()) return false;
+  *val = it->second;
+  return true;
+}
+
+// Record a decision; the file write is best effort (a read-only cache location only costs a
+// measurement in the next process).
+void tune_put(const std::string& key, const std::string& val) {
+  std::lock_guard<std::mutex> lk(g_store.mu);
+  tune_load_locked();
+  g_store.kv[key] = val;
+  if (g_store.path.empty()) return;
+  if (g_store.fresh) {
+    for (size_t s = 1; (s = g_store.path.find('/', s)) != std::string::npos; ++s)
+      mkdir(g_store.path.substr(0, s).c_str(), 0755);
+    FILE* f = fopen(g_store.path.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "%s\n", tune_header().c_str());
+    for (const auto& e : g_store.kv) fprintf(f, "%s\t%s\n", e.first.c_str(), e.second.c_str());
+    fclose(f);
+    g_store.fresh = false;
+    return;
+  }
+  FILE* f = fopen(g_store.path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s\t%s\n", key.c_str(), val.c_str());
+  fclose(f);
+}
+
+// Device part of every key: name and SM count of the current device.
+std::string dev_key() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string s = pr.name;
+  for (char& ch : s)
+    if (ch == ' ' || ch == '\t' || ch == '|') ch = '_';
+  return s + "/" + std::to_string(pr.multiProcessorCount);
+}
+
+std::string join_key(std::initializer_list<long long> v) {
+  std::string s;
+  for (long long x : v) s += "|" + std::to_string(x);
+  return s;
+}
+
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int64_t, int64_t>, int> g_tune_cache;
 
@@ -846,11 +994,21 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
     return TAU_OK;
   }
   const auto key = std::make_tuple(prec_index<T>(), P.dim.route, P.len, P.inner, P.nlines);
+  const std::string skey = "lpb|" + dev_key() + join_key({prec_index<T>(), P.dim.route, P.len, P.inner, P.nlines});
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       p->lpb_tuned[prec_index<T>()][ax] = it->second;
+      return TAU_OK;
+    }
+  }
+  {
+    std::string v;
+    if (tune_get(skey, &v) && atoi(v.c_str()) > 0) {
+      p->lpb_tuned[prec_index<T>()][ax] = atoi(v.c_str());
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = atoi(v.c_str());
       return TAU_OK;
     }
   }
@@ -902,6 +1060,7 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->lpb_tuned[prec_index<T>()][ax] = best_lpb;
+  tune_put(skey, std::to_string(best_lpb));
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = best_lpb;
   return TAU_OK;
@@ -911,7 +1070,7 @@ tau_status autotune(tau_problem* p) {
   CK(cudaMemsetAsync(p->A, 0, p->n_tot * sizeof(double), p->st));
   CK(cudaMemsetAsync(p->C, 0, p->n_tot * sizeof(double), p->st));
   for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<double>(p, ax, p->A, p->C));
-  if (p->dfm)
+  if (p->dfm || p->res_df)
     for (int ax = 0; ax < p->d; ++ax) TRY(tune_dim<df64>(p, ax, as<df64>(p->A), as<df64>(p->C)));
   if (p->mixed) {
     CK(cudaMemsetAsync(p->A32, 0, p->n_tot * sizeof(float), p->st));
@@ -931,9 +1090,14 @@ tau_status check_ready(tau_problem* p) {
 tau_status sync_status(tau_problem* p) {
   CK(cudaStreamSynchronize(p->st));
   if (p->tc_err) {
+    // an expired wait is reported once: the flag is cleared with the report, so later syncs see
+    // only waits that expire after it (the results of the work in flight at the time are not valid)
     int e = 0;
     CK(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) return fail(TAU_ETIMEOUT, "a tensor-core pass gave up waiting on an mbarrier (its copies or MMAs)");
+    if (e) {
+      CK(cudaMemset(p->tc_err, 0, sizeof(int)));
+      return fail(TAU_ETIMEOUT, "a tensor-core pass gave up waiting on an mbarrier (its copies or MMAs)");
+    }
   }
   GmresDev g;
   CK(cudaMemcpy(&g, p->g, sizeof(GmresDev), cudaMemcpyDeviceToHost));
@@ -1157,6 +1321,8 @@ tau_status choose_tc(tau_problem* p) {
   for (int i = 0; i < p->d; ++i) any = any || p->tc_on[i];
   if (!any) return TAU_OK;
   const auto key = std::make_tuple(p->d, p->n[0], p->d > 1 ? p->n[1] : 0, p->d > 2 ? p->n[2] : 0);
+  const std::string shape = dev_key() + join_key({p->d, p->n[0], p->d > 1 ? p->n[1] : 0, p->d > 2 ? p->n[2] : 0,
+                                                  p->route[0], p->route[1], p->route[2]});
   bool use = false, cached = false;
   {
     std::lock_guard<std::mutex> lk(g_tc_mu);
@@ -1164,6 +1330,15 @@ tau_status choose_tc(tau_problem* p) {
     if (it != g_tc_cache.end()) {
       use = it->second;
       cached = true;
+    }
+  }
+  if (!cached) {
+    std::string v;
+    if (tune_get("tc|" + shape, &v)) {
+      use = v == "1";
+      cached = true;
+      std::lock_guard<std::mutex> lk(g_tc_mu);
+      g_tc_cache[key] = use;
     }
   }
   if (!cached) {
@@ -1194,6 +1369,7 @@ tau_status choose_tc(tau_problem* p) {
     cudaEventDestroy(e1);
     TRY(st);
     use = t_on < 0.97f * t_off;
+    tune_put("tc|" + shape, use ? "1" : "0");
     std::lock_guard<std::mutex> lk(g_tc_mu);
     g_tc_cache[key] = use;
   }
@@ -1208,6 +1384,15 @@ tau_status choose_tc(tau_problem* p) {
       if (it != g_tc_cache.end()) {
         use_mv = it->second;
         hit = true;
+      }
+    }
+    if (!hit) {
+      std::string v;
+      if (tune_get("tcmv|" + shape, &v)) {
+        use_mv = v == "1";
+        hit = true;
+        std::lock_guard<std::mutex> lk(g_tc_mu);
+        g_tc_cache[kmv] = use_mv;
       }
     }
     if (!hit) {
@@ -1236,11 +1421,231 @@ tau_status choose_tc(tau_problem* p) {
       cudaEventDestroy(e1);
       TRY(st);
       use_mv = t_on < 0.97f * t_off;
+      tune_put("tcmv|" + shape, use_mv ? "1" : "0");
       std::lock_guard<std::mutex> lk(g_tc_mu);
       g_tc_cache[kmv] = use_mv;
     }
     if (!use_mv) p->tcm = false;
   }
+  return TAU_OK;
+}
+
+// Per-dimension tables of the line passes on dimension i for its current route p->route[i]: the
+// DST weights, the Toeplitz circulant spectrum and twiddles (FFT and chirp routes), the chirp-z
+// DST-I tables (chirp route), the long-line route's four-step tables; and the τ eigenvalues q of
+// Eq. (q) (uploaded to p->q[i]; on the long-line route computed on the device).
+tau_status route_tables(tau_problem* p, int i, const std::vector<double>& s) {
+  const int N = p->n[i], K = N + 1;
+  std::vector<double> q(N);
+  {
+    // dense route: sin(pi t / K), t = 0..2K-1; FFT route: the half-length DST's input weights
+    // with the orthonormal scale folded in, (1/2) sqrt(2/K) sin(pi t / K), t = 0..K-1
+    std::vector<double> st(2 * (size_t)K);
+    const double hs = p->route[i] == ROUTE_FFT ? 0.5 * std::sqrt(2.0 / K) : 1.0;
+    for (int t = 0; t < 2 * K; ++t) st[t] = hs * std::sin(M_PI * t / K);
+    TRY(upload(p, &p->sintab[i], st.data(), st.size()));
+  }
+  const bool chirp = p->route[i] == ROUTE_CHIRP;
+  const bool lng = p->route[i] == ROUTE_LONG;
+  if (p->route[i] == ROUTE_FFT || chirp) {
+    // Toeplitz product: circulant embedding c of length 2KK (KK = K on the FFT route, the power
+    // of two >= n+1 on the chirp route): c_0 = s_0, c_k = c_{2KK-k} = s_k (1 <= k < N), zeros
+    // elsewhere.  On the FFT route its real spectrum at k = 1..N is also the eigenvalues q_k of
+    // tau(S) (Eq. (q)).
+    const int KK = chirp ? p->KT[i] : K;
+    TRY(dalloc_n(p, &p->twK[i], (size_t)twp_size(KK)));
+    KL(launch_twp(KK, p->twK[i], p->st));
+    if (!chirp) {
+      TRY(dalloc_n(p, &p->twK2[i], (size_t)twp_size(K / 2)));
+      KL(launch_twp(K / 2, p->twK2[i], p->st));
+    }
+    std::vector<double> c(2 * (size_t)KK, 0.0);
+    c[0] = s[0];
+    for (int k = 1; k < N; ++k) c[k] = c[2 * KK - k] = s[k];
+    double *dc = nullptr, *dl = nullptr;
+    TRY(upload(p, &dc, c.data(), c.size()));
+    TRY(dalloc_n(p, &dl, (size_t)KK + 1));
+    KL(launch_spectrum(KK, dc, dl, p->twK[i], p->st));
+    std::vector<double> lam(KK + 1);
+    CK(cudaMemcpyAsync(lam.data(), dl, (KK + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    std::vector<double2> spec(4 * (size_t)(KK / 2 + 1));
+    for (int k = 0; k <= KK / 2; ++k) {
+      double abcd[8];
+      toep_pack_coeffs(lam[k], lam[KK - k], std::cos(M_PI * k / KK), -std::sin(M_PI * k / KK), KK, abcd);
+      for (int r = 0; r < 4; ++r) spec[4 * (size_t)k + r] = make_double2(abcd[2 * r], abcd[2 * r + 1]);
+    }
+    TRY(upload(p, &p->spec[i], spec.data(), spec.size()));
+    if (!chirp)
+      for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
+  }
+  if (lng) TRY(setup_long(p, i, s));
+  if (p->route[i] == ROUTE_DENSE || chirp) {
+    // q_k = s_0 + 2 sum_j s_j cos(pi j k / K) (Eq. (q)) with a cosine table
+    std::vector<double> ct(2 * (size_t)K);
+    for (int t = 0; t < 2 * K; ++t) ct[t] = std::cos(M_PI * t / K);
+    for (int k = 1; k <= N; ++k) {
+      double acc = s[0];
+      int64_t ph = 0;
+      for (int j = 1; j < N; ++j) {
+        ph += k;
+        if (ph >= 2 * K) ph -= 2 * K;
+        acc += 2.0 * s[j] * ct[ph];
+      }
+      q[k - 1] = acc;
+    }
+  }
+  if (!lng) TRY(upload(p, &p->q[i], q.data(), q.size()));
+  if (chirp) {
+    // chirp-z DST-I tables (two lines per Bluestein DFT of length L = N+1): c_m = exp(-i pi m^2/L),
+    // m = 0..N (m^2 reduced mod 2L, the period of the phase); kernel b_m = conj(c_|m|) for |m| <= N
+    // placed at m mod MC (MC = power of two >= 2N; b_N and b_{-N} coincide when MC = 2N, with one
+    // value); its FFT in fft_dif's order times sqrt(2/L)/(2 MC)
+    const int MCi = p->MC[i];
+    const int64_t L = N + 1;
+    auto cph = [&](int64_t m) {
+      const int64_t r = (m * m) % (2 * L);
+      return make_double2(std::cos(M_PI * (double)r / (double)L), -std::sin(M_PI * (double)r / (double)L));
+    };
+    std::vector<double2> w(N + 1), bk(MCi, make_double2(0.0, 0.0));
+    for (int m = 0; m <= N; ++m) w[m] = cph(m);
+    for (int m = -N; m <= N; ++m) {
+      const double2 v = cph(m < 0 ? -m : m);
+      bk[((m % MCi) + MCi) % MCi] = make_double2(v.x, -v.y);
+    }
+    TRY(upload(p, &p->chirp[i], w.data(), w.size()));
+    TRY(dalloc_n(p, &p->twM[i], (size_t)twp_size(MCi)));
+    KL(launch_twp(MCi, p->twM[i], p->st));
+    double2* db = nullptr;
+    TRY(upload(p, &db, bk.data(), bk.size()));
+    TRY(dalloc_n(p, &p->bhat[i], (size_t)MCi));
+    KL(launch_chirp_spectrum(MCi, db, p->bhat[i], p->twM[i], std::sqrt(2.0 / (double)L) / (2.0 * MCi), p->st));
+  }
+  return TAU_OK;
+}
+
+// Whether one line of n values fits the line-pass kernel's 200 KB of shared memory on a route,
+// for elements of esz bytes: the line plus its transform row (2K on the FFT route, 2 rows of 2 K_T
+// on the chirp route, a second copy on the dense route).
+bool route_fits(int64_t n, int route, size_t esz) {
+  const size_t nn = (size_t)n, npad = (nn + 1) & ~(size_t)1;
+  size_t kt = 2;
+  while (kt < nn + 1) kt <<= 1;
+  const size_t rs = route == ROUTE_FFT ? 2 * (nn + 1) : (route == ROUTE_CHIRP ? 4 * kt : nn);
+  return esz * (npad + rs) <= 200 * 1024;
+}
+
+void set_route(tau_problem* p, int i, int r) {
+  p->route[i] = r;
+  if (r == ROUTE_CHIRP) {
+    int64_t kt = 2, mc = 2;
+    while (kt < (int64_t)p->n[i] + 1) kt <<= 1;
+    while (mc < 2 * (int64_t)p->n[i]) mc <<= 1;
+    p->KT[i] = (int)kt;
+    p->MC[i] = (int)mc;
+  }
+}
+
+// Routes the measured choice considers for dimension i: only for TAU_ROUTE_AUTO in d >= 2 with the
+// τ methods (1-D lines keep the long-line rule; the Strang method's Hartley passes are dense).  The
+// FFT route where n + 1 is a power of two, else the chirp route, against the dense route.
+std::vector<int> route_candidates(const tau_problem* p, int i) {
+  std::vector<int> c;
+  if (p->desc.route[i] != TAU_ROUTE_AUTO || p->d == 1 || p->spgm) return c;
+  const int64_t n = p->n[i], K = n + 1;
+  const size_t esz = p->dfm ? 16 : 8;
+  if (is_pow2(K) && K >= 2 && K <= KMAX) c.push_back(ROUTE_FFT);
+  else if (n < KMAX && route_fits(n, ROUTE_CHIRP, esz)) c.push_back(ROUTE_CHIRP);
+  if (n <= 8192 && route_fits(n, ROUTE_DENSE, esz)) c.push_back(ROUTE_DENSE);
+  return c;
+}
+
+// Device time of the FP64 line passes along dimension i on its current route: its lines per CTA
+// chosen first (tune_dim), then one matvec pass and one DST pass, the unit tune_dim times too,
+// five times after a warm-up (CUDA events; milliseconds per repetition).
+tau_status time_route(tau_problem* p, int i, double* ms) {
+  p->lpb_tuned[0][i] = 0;
+  TRY(tune_dim<double>(p, i, p->A, p->C));
+  PassT<double> P = base_pass_t<double>(p, i);
+  P.seta = 1.0;
+  P.mv = 1;
+  P.in_a = P.out_a = p->A;
+  P.in_c = P.out_c = p->C;
+  PassT<double> Q = base_pass_t<double>(p, i);
+  Q.post = POST_DST;
+  Q.in_a = Q.out_a = p->C;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = launch_pass(P, p->st);
+  if (e == cudaSuccess) e = launch_pass(Q, p->st);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, p->st);
+  for (int r = 0; r < 5 && e == cudaSuccess; ++r) {
+    e = launch_pass(P, p->st);
+    if (e == cudaSuccess) e = launch_pass(Q, p->st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, p->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(TAU_ECUDA, "route timing: %s", cudaGetErrorString(e));
+  *ms = t / 5.0;
+  return TAU_OK;
+}
+
+// The measured route choice of dimension i (the GEMM-or-FFT decision of the FP64 passes: dense
+// O(n) mode products against the FFT or chirp-z transforms): every candidate's tables are built and
+// its passes timed, the fastest is kept (its tables built last), and the decision is recorded per
+// device and shape.  Without tuning, or with one candidate, the rule of tau_create stands.
+tau_status choose_route(tau_problem* p, int i, const std::vector<double>& s, bool tune) {
+  const std::vector<int> cands = tune ? route_candidates(p, i) : std::vector<int>();
+  if (cands.size() < 2) return route_tables(p, i, s);
+  int64_t inner = 1;
+  for (int l = 0; l < i; ++l) inner *= p->n[l];
+  const std::string key = "route|" + dev_key() + join_key({p->dfm ? 2 : 0, i, p->n[i], inner, p->n_tot / p->n[i]});
+  std::string v;
+  if (tune_get(key, &v)) {
+    int r = 0;
+    double ms = 0.0, alt = 0.0;
+    if (sscanf(v.c_str(), "%d %lf %lf", &r, &ms, &alt) == 3 &&
+        std::find(cands.begin(), cands.end(), r) != cands.end()) {
+      set_route(p, i, r);
+      p->route_src[i] = 2;
+      p->route_ms[i] = ms;
+      p->route_alt_ms[i] = alt;
+      return route_tables(p, i, s);
+    }
+  }
+  CK(cudaMemsetAsync(p->A, 0, p->n_tot * sizeof(double), p->st));
+  CK(cudaMemsetAsync(p->C, 0, p->n_tot * sizeof(double), p->st));
+  double best = 0.0, alt = 0.0;
+  int best_r = -1;
+  for (int r : cands) {
+    set_route(p, i, r);
+    TRY(route_tables(p, i, s));
+    double ms = 0.0;
+    TRY(time_route(p, i, &ms));
+    if (best_r < 0 || ms < best) {
+      if (best_r >= 0) alt = best;
+      best = ms;
+      best_r = r;
+    } else if (alt == 0.0 || ms < alt) {
+      alt = ms;
+    }
+  }
+  if (p->route[i] != best_r) {
+    set_route(p, i, best_r);
+    TRY(route_tables(p, i, s));
+  }
+  p->lpb_tuned[0][i] = 0;   // set again by autotune (from the cache tune_dim filled)
+  p->route_src[i] = 1;
+  p->route_ms[i] = best;
+  p->route_alt_ms[i] = alt;
+  char buf[96];
+  snprintf(buf, sizeof(buf), "%d %.6g %.6g", best_r, best, alt);
+  tune_put(key, buf);
   return TAU_OK;
 }
 
@@ -1392,6 +1797,8 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
         (s = dalloc_n(p, &p->rres, 1)))
       return cleanup(s);
     if (cudaMemset(p->rres, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(TAU_ECUDA, "memset"));
+    // double-float copies of e and b for the residual passes (used when tau_setup picks them)
+    if ((s = dalloc_n(p, &p->Edf, n)) || (s = dalloc_n(p, &p->bdf, n))) return cleanup(s);
   }
   if (p->dfm && ((s = dalloc_n(p, &p->Edf, n)) || (s = dalloc_n(p, &p->Fdf, n)) ||
                  (s = dalloc_n(p, &p->invmu_df, n))))
@@ -1408,6 +1815,8 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
       (s = dalloc_n(p, &p->escan, 2 * RED_BLOCKS)) || (s = dalloc_n(p, &p->g, 1)) ||
       (s = dalloc_n(p, &p->iters, (size_t)D.M)))
     return cleanup(s);
+  if ((s = dalloc_n(p, &p->tc_err, 1))) return cleanup(s);
+  if (cudaMemset(p->tc_err, 0, sizeof(int)) != cudaSuccess) return cleanup(fail(TAU_ECUDA, "memset"));
   if (cudaMallocHost(&p->h_done, sizeof(int)) != cudaSuccess) {
     p->h_done = nullptr;
     return cleanup(fail(TAU_ENOMEM, "cudaMallocHost"));
@@ -1455,11 +1864,35 @@ tau_status tau_set_fields(tau_problem* p, const tau_field* e, const tau_field* f
   return TAU_OK;
 }
 
+tau_status tau_set_fields_device(tau_problem* p, const tau_field_device* fd) {
+  if (!p || !fd) return fail(TAU_EINVAL, "NULL argument");
+  if (p->fields_set) return fail(TAU_ESTATE, "fields already set");
+  if (!fd->e) return fail(TAU_EINVAL, "e is NULL (a coefficient field is required)");
+  int64_t n_pad = 1;
+  for (int i = 0; i < p->d; ++i) n_pad *= (int64_t)p->n[i] + 2;
+  if (fd->e_step != 0 && fd->e_step != p->n_tot)
+    return fail(TAU_EINVAL, "e_step=%lld must be 0 or n_tot=%lld", (long long)fd->e_step, (long long)p->n_tot);
+  if (fd->f && fd->f_step != 0 && fd->f_step != n_pad)
+    return fail(TAU_EINVAL, "f_step=%lld must be 0 or prod(n_i+2)=%lld", (long long)fd->f_step, (long long)n_pad);
+  p->e_dev = fd->e;
+  p->e_step = fd->e_step;
+  p->f_dev = fd->f;
+  p->f_step = fd->f ? fd->f_step : 0;
+  p->psi_dev = fd->psi;
+  p->re = p->rf = p->rp = 0;
+  p->fields_set = true;
+  return TAU_OK;
+}
+
 tau_status tau_setup(tau_problem* p) {
   if (!p) return fail(TAU_EINVAL, "problem is NULL");
-  if (!p->fields_set) return fail(TAU_ESTATE, "tau_set_fields has not run");
+  if (!p->fields_set) return fail(TAU_ESTATE, "neither tau_set_fields nor tau_set_fields_device has run");
   if (p->setup_done) return fail(TAU_ESTATE, "tau_setup already ran");
   const int d = p->d;
+  // measured choices (routes, lines per CTA, tensor cores) for problems of >= 65536 unknowns, or
+  // as TAU_AUTOTUNE says (1: always, 0: never; the rules of tau_create and the heuristics stand)
+  const char* tn = std::getenv("TAU_AUTOTUNE");
+  const bool tune = tn ? tn[0] == '1' : p->n_tot >= (1 << 16);
   for (int i = 0; i < d; ++i) {
     const int N = p->n[i], K = N + 1;
     const double a = p->desc.alpha[i];
@@ -1508,91 +1941,7 @@ tau_status tau_setup(tau_problem* p) {
       TRY(upload(p, &p->ss[i], ls.data(), ls.size()));
       TRY(upload(p, &p->cas[i], ct.data(), ct.size()));
     }
-    std::vector<double> q(N);
-    {
-      // dense route: sin(pi t / K), t = 0..2K-1; FFT route: the half-length DST's input weights
-      // with the orthonormal scale folded in, (1/2) sqrt(2/K) sin(pi t / K), t = 0..K-1
-      std::vector<double> st(2 * (size_t)K);
-      const double hs = p->route[i] == ROUTE_FFT ? 0.5 * std::sqrt(2.0 / K) : 1.0;
-      for (int t = 0; t < 2 * K; ++t) st[t] = hs * std::sin(M_PI * t / K);
-      TRY(upload(p, &p->sintab[i], st.data(), st.size()));
-    }
-    const bool chirp = p->route[i] == ROUTE_CHIRP;
-    const bool lng = p->route[i] == ROUTE_LONG;
-    if (p->route[i] == ROUTE_FFT || chirp) {
-      // Toeplitz product: circulant embedding c of length 2KK (KK = K on the FFT route, the power
-      // of two >= n+1 on the chirp route): c_0 = s_0, c_k = c_{2KK-k} = s_k (1 <= k < N), zeros
-      // elsewhere.  On the FFT route its real spectrum at k = 1..N is also the eigenvalues q_k of
-      // tau(S) (Eq. (q)).
-      const int KK = chirp ? p->KT[i] : K;
-      TRY(dalloc_n(p, &p->twK[i], (size_t)twp_size(KK)));
-      KL(launch_twp(KK, p->twK[i], p->st));
-      if (!chirp) {
-        TRY(dalloc_n(p, &p->twK2[i], (size_t)twp_size(K / 2)));
-        KL(launch_twp(K / 2, p->twK2[i], p->st));
-      }
-      std::vector<double> c(2 * (size_t)KK, 0.0);
-      c[0] = s[0];
-      for (int k = 1; k < N; ++k) c[k] = c[2 * KK - k] = s[k];
-      double *dc = nullptr, *dl = nullptr;
-      TRY(upload(p, &dc, c.data(), c.size()));
-      TRY(dalloc_n(p, &dl, (size_t)KK + 1));
-      KL(launch_spectrum(KK, dc, dl, p->twK[i], p->st));
-      std::vector<double> lam(KK + 1);
-      CK(cudaMemcpyAsync(lam.data(), dl, (KK + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->st));
-      CK(cudaStreamSynchronize(p->st));
-      std::vector<double2> spec(4 * (size_t)(KK / 2 + 1));
-      for (int k = 0; k <= KK / 2; ++k) {
-        double abcd[8];
-        toep_pack_coeffs(lam[k], lam[KK - k], std::cos(M_PI * k / KK), -std::sin(M_PI * k / KK), KK, abcd);
-        for (int r = 0; r < 4; ++r) spec[4 * (size_t)k + r] = make_double2(abcd[2 * r], abcd[2 * r + 1]);
-      }
-      TRY(upload(p, &p->spec[i], spec.data(), spec.size()));
-      if (!chirp)
-        for (int k = 1; k <= N; ++k) q[k - 1] = lam[k];
-    }
-    if (lng) TRY(setup_long(p, i, s));
-    if (p->route[i] == ROUTE_DENSE || chirp) {
-      // q_k = s_0 + 2 sum_j s_j cos(pi j k / K) (Eq. (q)) with a cosine table
-      std::vector<double> ct(2 * (size_t)K);
-      for (int t = 0; t < 2 * K; ++t) ct[t] = std::cos(M_PI * t / K);
-      for (int k = 1; k <= N; ++k) {
-        double acc = s[0];
-        int64_t ph = 0;
-        for (int j = 1; j < N; ++j) {
-          ph += k;
-          if (ph >= 2 * K) ph -= 2 * K;
-          acc += 2.0 * s[j] * ct[ph];
-        }
-        q[k - 1] = acc;
-      }
-    }
-    if (!lng) TRY(upload(p, &p->q[i], q.data(), q.size()));
-    if (chirp) {
-      // chirp-z DST-I tables (two lines per Bluestein DFT of length L = N+1): c_m = exp(-i pi m^2/L),
-      // m = 0..N (m^2 reduced mod 2L, the period of the phase); kernel b_m = conj(c_|m|) for |m| <= N
-      // placed at m mod MC (MC = power of two >= 2N; b_N and b_{-N} coincide when MC = 2N, with one
-      // value); its FFT in fft_dif's order times sqrt(2/L)/(2 MC)
-      const int MCi = p->MC[i];
-      const int64_t L = N + 1;
-      auto cph = [&](int64_t m) {
-        const int64_t r = (m * m) % (2 * L);
-        return make_double2(std::cos(M_PI * (double)r / (double)L), -std::sin(M_PI * (double)r / (double)L));
-      };
-      std::vector<double2> w(N + 1), bk(MCi, make_double2(0.0, 0.0));
-      for (int m = 0; m <= N; ++m) w[m] = cph(m);
-      for (int m = -N; m <= N; ++m) {
-        const double2 v = cph(m < 0 ? -m : m);
-        bk[((m % MCi) + MCi) % MCi] = make_double2(v.x, -v.y);
-      }
-      TRY(upload(p, &p->chirp[i], w.data(), w.size()));
-      TRY(dalloc_n(p, &p->twM[i], (size_t)twp_size(MCi)));
-      KL(launch_twp(MCi, p->twM[i], p->st));
-      double2* db = nullptr;
-      TRY(upload(p, &db, bk.data(), bk.size()));
-      TRY(dalloc_n(p, &p->bhat[i], (size_t)MCi));
-      KL(launch_chirp_spectrum(MCi, db, p->bhat[i], p->twM[i], std::sqrt(2.0 / (double)L) / (2.0 * MCi), p->st));
-    }
+    TRY(choose_route(p, i, s, tune));
   }
   // ebar (Eqs. (bard), (dhat))
   if (std::isnan(p->desc.e_min) || std::isnan(p->desc.e_max)) {
@@ -1618,9 +1967,28 @@ tau_status tau_setup(tau_problem* p) {
   if (p->tpgm) KL(launch_tpgm_diag(d, p->n, p->n_tot, p->ebar, p->beta, p->q, p->eta, p->pmh, p->pmhb, p->st));
   if (p->spgm)
     KL(launch_spgm_diag(d, p->n, p->n_tot, p->ebar, p->sb, p->ss, p->eta, p->beta, p->pcinv, p->binv, p->st));
-  KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->dfm ? p->tmp : p->u, p->st));
+  if (p->e_dev) {
+    double* u0 = p->dfm ? p->tmp : p->u;
+    if (p->psi_dev) CK(cudaMemcpyAsync(u0, p->psi_dev, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, p->st));
+    else CK(cudaMemsetAsync(u0, 0, p->n_tot * sizeof(double), p->st));
+  } else {
+    KL(launch_psi(d, p->n, p->n_tot, p->rp, p->psi_tc, p->psi_sp, p->dfm ? p->tmp : p->u, p->st));
+  }
   if (p->dfm) KL(launch_d_to_df(p->tmp, as<df64>(p->u), p->n_tot, p->st));
-  if (p->dfm) {
+  if (p->mixed) {
+    // The mixed form's outer residual b - A x runs as double-float line passes when their rounding
+    // floor stays below half the refinement tolerance.  The cancelling Toeplitz sums of A x carry
+    // an absolute error of about eps_df * (a few) * max_i eta_i ||s^{(i)}||_1 |x| (eps_df = 2^-48,
+    // ||s||_1 <= 2 s_0, Eq. (As1)), against ||b|| ~ ebar |x|: floor = 2^-48 * 8 * max_i eta_i 2 s_0 / ebar.
+    // Otherwise (large eta: long lines at alpha near 2) the residual stays FP64.
+    double worst = 0.0;
+    for (int i = 0; i < d; ++i) {
+      const double a = p->desc.alpha[i], g = std::tgamma(a / 2.0 + 1.0);
+      worst = std::max(worst, p->eta[i] * 2.0 * std::tgamma(a + 1.0) / (g * g));
+    }
+    p->res_df = std::ldexp(8.0 * worst / p->ebar, -48) <= 0.5 * p->desc.refine_tol;
+  }
+  if (p->dfm || p->res_df) {
     auto conv = [&](const double* src, df64** dst, size_t cnt) -> tau_status {
       TRY(dalloc_n(p, dst, cnt));
       KL(launch_d_to_df(src, *dst, (int64_t)cnt, p->st));
@@ -1654,7 +2022,7 @@ tau_status tau_setup(tau_problem* p) {
       }
       if (p->route[i] == ROUTE_LONG) TRY(long_tables_as(p, i, p->ltdf[i], 1, conv));
     }
-    KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
+    if (p->dfm) KL(launch_d_to_df(p->invmu, p->invmu_df, p->n_tot, p->st));
   }
   if (p->mixed) {
     auto conv = [&](const double* src, float** dst, size_t cnt) -> tau_status {
@@ -1714,8 +2082,6 @@ tau_status tau_setup(tau_problem* p) {
   CK(cudaMemcpyAsync(p->g, &g, sizeof(g), cudaMemcpyHostToDevice, p->st));
   CK(cudaStreamSynchronize(p->st));
   p->m_host = 0;
-  const char* tn = std::getenv("TAU_AUTOTUNE");
-  const bool tune = tn ? tn[0] == '1' : p->n_tot >= (1 << 16);
   if (tune) TRY(autotune(p));
   p->setup_done = true;
   const char* nog = std::getenv("TAU_NO_GRAPH");
@@ -1828,6 +2194,12 @@ tau_status tau_get_stats(tau_problem* p, tau_stats* out) {
     if (p->tc_on[i]) out->tc_dims |= 1 << i;
   if (p->tcm) out->tc_dims |= 1 << 8;
   }
+  for (int i = 0; i < p->d; ++i) {
+    out->route_source[i] = p->route_src[i];
+    out->route_ms[i] = p->route_ms[i];
+    out->route_alt_ms[i] = p->route_alt_ms[i];
+  }
+  out->resid_precision = p->mixed ? (p->res_df ? TAU_DF64 : TAU_FP64) : p->desc.precision;
   out->kernels_prologue = p->k_pro;
   out->kernels_per_iter = p->k_body;
   out->kernels_epilogue = p->k_epi;
@@ -2072,6 +2444,12 @@ tau_status tau_selftest_bounded_wait(void* stream, int* gave_up) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(d);
   if (e != cudaSuccess) return fail(TAU_ECUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+  return TAU_OK;
+}
+
+tau_status tau_inject_wait_timeout(tau_problem* p) {
+  if (!p) return fail(TAU_EINVAL, "problem is NULL");
+  CK(cudaMemsetAsync(p->tc_err, 0xff, sizeof(int), p->st));
   return TAU_OK;
 }
 

@@ -289,8 +289,8 @@ cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_i
 cudaError_t launch_rres_save(const int* flag, const double* E, const double* u, double* y, int64_t n,
                              cudaStream_t st);
 cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double* bd, const double* bo,
-                            const double* E, const double* u, double* y, double* y2, const double* r, double* b,
-                            const double* fdt, int64_t n, cudaStream_t st);
+                            const double* E, const double* u, double* y, double* y2, const double* r, int r_df,
+                            double* b, const double* fdt, int64_t n, cudaStream_t st);
 cudaError_t launch_set_flag(int* flag, int v, cudaStream_t st);
 
 // long-line route (tau_long.cu)
@@ -318,6 +318,14 @@ struct FieldDev {
   const double* f_tc;         // [M x rf]
   const double* f_hsp[3];     // [rf x n_i]: 𝓗-stencilled f space tables (interior)
   double dt;
+  // dense form (tau_set_fields_device; the tables above are unused when e_dev is set): e at the
+  // interior nodes, step m at e_dev + m * e_step; f on the padded grid prod (n_i + 2), step m at
+  // f_dev + m * f_step (NULL: f = 0); a step of 0 means the field does not depend on t
+  const double* e_dev;
+  int64_t e_step;
+  const double* f_dev;
+  int64_t f_step;
+  double hw[3][2];            // 𝓗_{alpha_i} stencil weights: (alpha_i/24, 1 - alpha_i/12)
 };
 cudaError_t launch_fields(const FieldDev& f, const GmresDev* g, int64_t m_override, double* e_out,
                           double* fdt_out, cudaStream_t st);
@@ -389,6 +397,8 @@ struct IRDev {
   double tol;        // ||b - A x|| <= tol ||b - A x_0||
   double rho0, rho, last_rel;
   double inner_tol;  // inner FGMRES target of the first sweep (later sweeps: k_ir_control)
+  double rho_prev;   // residual norm before the last correction
+  double itol_prev;  // inner target of the last sweep
 };
 cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
 cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);
@@ -398,8 +408,12 @@ cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t
 cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm, int64_t n,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
                               cudaStream_t st);
-cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st);
-cudaError_t launch_update_x(double* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
+// v = r / rho in FP32 from the residual stored as S (double, or double-float)
+template <typename S>
+cudaError_t launch_scale_to_f32(const S* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st);
+// x += rho sum_i y_i Z_i (the sum in FP64) with x stored as X (double, or double-float)
+template <typename X>
+cudaError_t launch_update_x(X* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
                             cudaStream_t st);
 cudaError_t launch_ir_finish(const IRDev* ir, GmresDev* g, int* iters_log, int* sweeps_log, cudaStream_t st);
 cudaError_t launch_backsolve(GmresDev* g, const double* H, const double* gv, int ldH, double* y, cudaStream_t st);

@@ -1061,9 +1061,40 @@ __device__ __forceinline__ void unflatten(int64_t idx, int d, const int* n, int*
   }
 }
 
+// F = interior restriction of (⊗_l 𝓗_{alpha_l}) f at interior node j, from f on the padded grid
+// (Eq. (2.2) applied to the source; Appendix A's 1-D and 2-D forms): the 3^d-point tensor stencil
+// with per-dimension weights (alpha/24, 1 - alpha/12, alpha/24), summed one dimension at a time.
+__device__ __forceinline__ double fields_hstencil(const FieldDev& F, const double* f, const int* j) {
+  const int64_t p0 = F.n[0] + 2, p1 = F.n[1] + 2;
+  double acc2 = 0.0;
+  for (int o2 = 0; o2 < (F.d > 2 ? 3 : 1); ++o2) {
+    double acc1 = 0.0;
+    for (int o1 = 0; o1 < (F.d > 1 ? 3 : 1); ++o1) {
+      const int64_t i1 = F.d > 1 ? j[1] + o1 : 0, i2 = F.d > 2 ? j[2] + o2 : 0;
+      const double* row = f + (i2 * p1 + i1) * p0 + j[0];
+      const double v = F.hw[0][0] * (row[0] + row[2]) + F.hw[0][1] * row[1];
+      acc1 += (F.d > 1 ? (o1 == 1 ? F.hw[1][1] : F.hw[1][0]) : 1.0) * v;
+    }
+    acc2 += (F.d > 2 ? (o2 == 1 ? F.hw[2][1] : F.hw[2][0]) : 1.0) * acc1;
+  }
+  return acc2;
+}
+
 __global__ void k_fields(const FieldDev F, const GmresDev* __restrict__ g, int64_t m_override, double* e_out,
                          double* fdt_out) {
   const int64_t m = m_override >= 0 ? m_override : g->m;
+  if (F.e_dev) {
+    const double* em = F.e_dev + m * F.e_step;
+    const double* fm = F.f_dev ? F.f_dev + m * F.f_step : nullptr;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      int j[3] = {0, 0, 0};
+      unflatten(idx, F.d, F.n, j);
+      if (e_out) e_out[idx] = em[idx];
+      if (fdt_out) fdt_out[idx] = fm ? F.dt * fields_hstencil(F, fm, j) : 0.0;
+    }
+    return;
+  }
   const double* etc = F.e_tc + m * F.re;
   const double* ftc = F.f_tc + m * F.rf;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
@@ -1140,10 +1171,17 @@ cudaError_t launch_psi(int d, const int* n, int64_t n_tot, int rank, const doubl
 __global__ void k_escan(const FieldDev F, int64_t M, double* partial) {
   __shared__ double smax[256], smin[256];
   double hi = -INFINITY, lo = INFINITY;
-  const int64_t total = F.n_tot * M;
+  // dense form: every stored value (one slab when e does not depend on t)
+  const int64_t total = F.n_tot * (F.e_dev && F.e_step == 0 ? 1 : M);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = t / F.n_tot;
     const int64_t idx = t - m * F.n_tot;
+    if (F.e_dev) {
+      const double ev = F.e_dev[m * F.e_step + idx];
+      hi = fmax(hi, ev);
+      lo = fmin(lo, ev);
+      continue;
+    }
     int j[3] = {0, 0, 0};
     unflatten(idx, F.d, F.n, j);
     const double* etc = F.e_tc + m * F.re;
@@ -1715,6 +1753,8 @@ __global__ void k_ir_init(IRDev* ir) {
     ir->skip_resid = 0;
     ir->rho0 = 0.0;
     ir->rho = 0.0;
+    ir->rho_prev = 0.0;
+    ir->itol_prev = ir->inner_tol;
   }
 }
 
@@ -1765,16 +1805,24 @@ __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const doub
     }
     return;
   }
-  ir->sweep += 1;
-  // Inner target: the first sweep solves to inner_tol; a later one asks only for the reduction
-  // still needed, with a factor 0.3 of margin, rho0 tol / rho, kept within [1e-6, inner_tol]
-  // (an FP32 solve cannot resolve much below 1e-6 of its right-hand side).
+  // Inner target.  The first sweep solves to inner_tol.  A later one asks for the reduction still
+  // needed, with a factor 0.3 of margin, need = 0.3 rho0 tol / rho, within [1e-6, 0.5] (an FP32
+  // solve cannot resolve much below 1e-6 of its right-hand side).  It never asks for much less than
+  // the floor the last sweep ran into: when the last correction reduced the residual by a factor
+  // red well above its inner target (the FP32 operator's own error then limits every sweep), a
+  // tighter inner solve costs iterations and buys nothing, so the target is at least red / 2.
   double itol = ir->inner_tol;
-  if (ir->sweep > 1) {
+  if (ir->sweep > 0) {
     const double need = 0.3 * ir->tol * ir->rho0 / rho;
-    itol = need < itol ? need : itol;
-    if (itol < 1e-6) itol = 1e-6 < ir->inner_tol ? 1e-6 : ir->inner_tol;
+    const double red = ir->rho_prev > 0.0 ? rho / ir->rho_prev : 0.0;
+    const double floor_hit = red > 2.0 * ir->itol_prev ? 0.5 * red : 0.0;
+    itol = need > floor_hit ? need : floor_hit;
+    if (itol < 1e-6) itol = 1e-6;
+    if (itol > 0.5) itol = 0.5;
   }
+  ir->sweep += 1;
+  ir->rho_prev = rho;
+  ir->itol_prev = itol;
   gin->tol = itol;
   gin->j = 0;
   gin->k = 0;
@@ -1796,45 +1844,60 @@ cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const dou
 }
 
 // v_0 = (float)(r / rho)
-__global__ void k_scale_to_f32(const double* __restrict__ r, float* v, int64_t n, const IRDev* __restrict__ ir) {
+template <typename S>
+__global__ void k_scale_to_f32(const S* __restrict__ r, float* v, int64_t n, const IRDev* __restrict__ ir) {
   if (ir->done) return;
   __shared__ double sinv;   // one FP64 division per block
   if (threadIdx.x == 0) sinv = 1.0 / ir->rho;
   __syncthreads();
   const double inv = sinv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = (float)(r[i] * inv);
+    v[i] = (float)(to_d(r[i]) * inv);
 }
 
-cudaError_t launch_scale_to_f32(const double* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st) {
-  k_scale_to_f32<<<red_blocks(n), RED_THREADS, 0, st>>>(r, v, n, ir);
+template <typename S>
+cudaError_t launch_scale_to_f32(const S* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st) {
+  k_scale_to_f32<S><<<red_blocks(n), RED_THREADS, 0, st>>>(r, v, n, ir);
   return cudaGetLastError();
 }
+template cudaError_t launch_scale_to_f32<double>(const double*, float*, int64_t, const IRDev*, cudaStream_t);
+template cudaError_t launch_scale_to_f32<df64>(const df64*, float*, int64_t, const IRDev*, cudaStream_t);
 
-// x += rho * sum_{i<k} y_i Z_i: the correction is summed over the FP32 preconditioned directions in
-// FP32 (it needs only the inner solve's accuracy, and the Z_i are FP32 already) and added to x in
-// FP64, so FP64 work is one addition per element.
-__global__ void k_update_x(double* x, const float* __restrict__ Z, const double* __restrict__ y, int64_t n,
+// x += rho * sum_{i<k} y_i Z_i over the FP32 preconditioned directions Z_i.  The sum runs in FP64:
+// the Z_i are exact FP32 vectors, and rounding the correction itself to FP32 would add an error of
+// eps_32 |d| whose image under A (not smooth, so A does not cancel on it) is a sizeable part of
+// the next residual.  x is FP64 or double-float (X = df64; the addition then on the FP32 pipes).
+template <typename X> __device__ __forceinline__ void add_to(X& x, double d);
+template <> __device__ __forceinline__ void add_to<double>(double& x, double d) { x += d; }
+template <> __device__ __forceinline__ void add_to<df64>(df64& x, double d) { x = x + from_d<df64>(d); }
+
+template <typename X>
+__global__ void k_update_x(X* x, const float* __restrict__ Z, const double* __restrict__ y, int64_t n,
                            const GmresDev* __restrict__ gin, IRDev* ir) {
-  __shared__ float ys[MAX_ITER_CAP];
+  __shared__ double ys[MAX_ITER_CAP];
   if (ir->done) return;
   const int k = gin->k;
   const double rho = ir->rho;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = (float)(rho * y[i]);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * y[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) ir->inner_total += k;
   __syncthreads();
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
-    float d = 0.0f;
-    for (int i = 0; i < k; ++i) d = fmaf(ys[i], Z[(int64_t)i * n + idx], d);
-    x[idx] += (double)d;
+    double d = 0.0;
+    for (int i = 0; i < k; ++i) d = fma(ys[i], (double)Z[(int64_t)i * n + idx], d);
+    add_to(x[idx], d);
   }
 }
 
-cudaError_t launch_update_x(double* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
+template <typename X>
+cudaError_t launch_update_x(X* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
                             cudaStream_t st) {
-  k_update_x<<<red_blocks(n), RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
+  k_update_x<X><<<red_blocks(n), RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
   return cudaGetLastError();
 }
+template cudaError_t launch_update_x<double>(double*, const float*, const double*, int64_t, const GmresDev*, IRDev*,
+                                             cudaStream_t);
+template cudaError_t launch_update_x<df64>(df64*, const float*, const double*, int64_t, const GmresDev*, IRDev*,
+                                           cudaStream_t);
 
 __global__ void k_ir_finish(const IRDev* __restrict__ ir, GmresDev* g, int* iters_log, int* sweeps_log) {
   if (threadIdx.x != 0) return;

@@ -34,11 +34,11 @@ __global__ void k_rres_add(const int* __restrict__ flag, const double* __restric
 
 // One factor of B = B_{d-1} ⊗ ... ⊗ B_0 along the dimension with element stride `stride` and
 // length nk: dst = bd src + bo (src at the two neighbours along that dimension; zero outside).  The
-// last factor (fin) instead writes b = B y + r - b + Fdt.  Indices are unsigned 32-bit (n_tot <= 2^31,
-// so a grid-stride index stays below 2^32).
+// last factor (fin) instead writes b = B y + r - b + Fdt, r stored in FP64 or (r_df) as double-float
+// pairs.  Indices are unsigned 32-bit (n_tot <= 2^31, so a grid-stride index stays below 2^32).
 __global__ void k_rres_line(const int* __restrict__ flag, const double* __restrict__ src, double* dst, unsigned n,
                             unsigned stride, unsigned nk, double bd, double bo, int fin,
-                            const double* __restrict__ r, double* b, const double* __restrict__ fdt) {
+                            const double* __restrict__ r, int r_df, double* b, const double* __restrict__ fdt) {
   if (!*flag) return;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const unsigned ik = (i / stride) % nk;
@@ -46,7 +46,7 @@ __global__ void k_rres_line(const int* __restrict__ flag, const double* __restri
     if (ik > 0) v = fma(bo, src[i - stride], v);
     if (ik + 1 < nk) v = fma(bo, src[i + stride], v);
     if (fin)
-      b[i] = v + r[i] - b[i] + fdt[i];
+      b[i] = v + (r_df ? to_d(reinterpret_cast<const df64*>(r)[i]) : r[i]) - b[i] + fdt[i];
     else
       dst[i] = v;
   }
@@ -66,8 +66,8 @@ cudaError_t launch_rres_save(const int* flag, const double* E, const double* u, 
 }
 
 cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double* bd, const double* bo,
-                            const double* E, const double* u, double* y, double* y2, const double* r, double* b,
-                            const double* fdt, int64_t n, cudaStream_t st) {
+                            const double* E, const double* u, double* y, double* y2, const double* r, int r_df,
+                            double* b, const double* fdt, int64_t n, cudaStream_t st) {
   k_rres_add<<<mx_blocks(n), MX_THREADS, 0, st>>>(flag, E, u, y, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -77,8 +77,8 @@ cudaError_t launch_rres_rhs(const int* flag, int d, const int* nn, const double*
   for (int ax = 0; ax < d; ++ax) {
     const int fin = ax == d - 1;
     k_rres_line<<<mx_blocks(n), MX_THREADS, 0, st>>>(flag, bufs[ax & 1], bufs[(ax + 1) & 1], (unsigned)n,
-                                                       (unsigned)stride, (unsigned)nn[ax], bd[ax], bo[ax], fin, r, b,
-                                                       fdt);
+                                                       (unsigned)stride, (unsigned)nn[ax], bd[ax], bo[ax], fin, r, r_df,
+                                                       b, fdt);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     stride *= nn[ax];

@@ -100,6 +100,12 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     }
     if (!(D.alpha[i] > 1.0 && D.alpha[i] < 2.0) || !(D.kappa[i] >= 0.0) || !(D.R[i] > D.L[i]))
       return na_fail(TAU_EINVAL, "tau_apply_A_noalloc: alpha must lie in (1,2), kappa >= 0, R > L");
+    // the route is this entry point's own (FFT when n_i + 1 is a power of two, else dense sums):
+    // a forced route would silently not be honoured, so it is refused
+    if (D.route[i] != TAU_ROUTE_AUTO) {
+      snprintf(buf, sizeof(buf), "tau_apply_A_noalloc: route[%d]=%d; only TAU_ROUTE_AUTO is accepted", i, D.route[i]);
+      return na_fail(TAU_EINVAL, buf);
+    }
     n_tot *= D.n[i];
   }
   if (n_tot > NA_MAX_UNKNOWNS) {

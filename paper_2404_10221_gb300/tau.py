@@ -79,6 +79,16 @@ class tau_field(C.Structure):
     ]
 
 
+class tau_field_device(C.Structure):
+    _fields_ = [
+        ("e", C.c_void_p),
+        ("e_step", C.c_int64),
+        ("f", C.c_void_p),
+        ("f_step", C.c_int64),
+        ("psi", C.c_void_p),
+    ]
+
+
 class tau_stats(C.Structure):
     _fields_ = [
         ("steps_done", C.c_int64),
@@ -100,6 +110,10 @@ class tau_stats(C.Structure):
         ("lines_per_cta", C.c_int * 3),
         ("lines_per_cta_f32", C.c_int * 3),
         ("tc_dims", C.c_int),
+        ("route_source", C.c_int * 3),
+        ("route_ms", C.c_double * 3),
+        ("route_alt_ms", C.c_double * 3),
+        ("resid_precision", C.c_int),
     ]
 
 
@@ -158,6 +172,7 @@ def lib():
         sigs = {
             "tau_create": [C.POINTER(tau_problem_desc), P, C.POINTER(P)],
             "tau_set_fields": [P, C.POINTER(tau_field), C.POINTER(tau_field), C.POINTER(tau_field)],
+            "tau_set_fields_device": [P, C.POINTER(tau_field_device)],
             "tau_setup": [P],
             "tau_step": [P, C.c_int64],
             "tau_solve": [P],
@@ -176,6 +191,7 @@ def lib():
             "tau_get_ebar": [P, D, D, D],
             "tau_measure_fp64_peak": [P, D],
             "tau_selftest_bounded_wait": [P, C.POINTER(C.c_int)],
+            "tau_inject_wait_timeout": [P],
             "tau_choose_precision": [C.POINTER(tau_problem_desc), C.POINTER(C.c_int)],
             "tau_apply_A_noalloc": [C.POINTER(tau_problem_desc), P, P, P, P],
             "tau_apply_A_f32": [P, C.c_int64, P, P],
@@ -290,6 +306,20 @@ def tau_set_fields(h: int, tables: dict):
     _check(lib().tau_set_fields(C.c_void_p(h), C.byref(e.f), C.byref(f.f), C.byref(p.f)))
 
 
+def tau_set_fields_device(h: int, e, f=None, psi=None, e_step: Optional[int] = None,
+                          f_step: Optional[int] = None):
+    """Fields as caller-owned CUDA float64 tensors: e of M x n_tot (or n_tot: not time dependent),
+    f of M x prod(n_i + 2) on the padded grid (or one slab, or None: f = 0), psi of n_tot (or None).
+    The tensors must stay alive and unchanged until the problem is destroyed."""
+    fd = tau_field_device()
+    fd.e = _ptr(e)
+    fd.e_step = int(e_step) if e_step is not None else (e.shape[-1] if e.dim() == 2 else 0)
+    fd.f = _ptr(f) if f is not None else None
+    fd.f_step = int(f_step) if f_step is not None else (f.shape[-1] if f is not None and f.dim() == 2 else 0)
+    fd.psi = _ptr(psi) if psi is not None else None
+    _check(lib().tau_set_fields_device(C.c_void_p(h), C.byref(fd)))
+
+
 def tau_setup(h: int):
     _check(lib().tau_setup(C.c_void_p(h)))
 
@@ -391,6 +421,10 @@ def tau_selftest_bounded_wait(stream=None) -> bool:
     v = C.c_int(-1)
     _check(lib().tau_selftest_bounded_wait(C.c_void_p(_stream(stream)), C.byref(v)))
     return v.value == 1
+
+
+def tau_inject_wait_timeout(h: int):
+    _check(lib().tau_inject_wait_timeout(C.c_void_p(h)))
 
 
 def tau_apply_A_noalloc(desc: tau_problem_desc, e, x, y, stream=None):

@@ -328,3 +328,35 @@ def serving_mix(count: int, seed: int = 20240416, M_range=(10, 40), precision_hi
         e_terms = [(_const(1.0), [_one] * d), (lambda t, a=amp: a * (1.0 + t), [_sinpi] * d)]
         out.append(manufactured(f"req{d}d", prob, e_terms, 2, 2, 1.0))
     return out
+
+
+def dense_fields(prob: Problem, time_dependent_e: bool = True, with_f: bool = True) -> dict:
+    """Fields that are not separable expansions, sampled on the grid (for the device-array field
+    form of the boundary): e = 1 + (x_1 x_2 ... x_d) exp(-t x_1) (positive), f = sin(pi x_1 x_2 ...)
+    (1 + t) + x_1^2 cos(pi t (x_2 + ... )), psi = prod x_i (1 - x_i) exp(x_1 x_d), each at
+    t_{m+1/2}; x_1 fastest.  Returns e_dense (M, n_tot) or (n_tot,), f_dense (M, prod(n_i+2)) or
+    None, psi_dense (n_tot,)."""
+    d = prob.d
+    pad = [prob.grid(i) for i in range(d)]
+
+    def mesh(axes):
+        # arrays of shape (n_d, ..., n_1): index i of the list is dimension i + 1
+        grids = np.meshgrid(*reversed(axes), indexing="ij")
+        return list(reversed(grids))
+
+    xi = mesh([g[1:-1] for g in pad])
+    xp = mesh(pad)
+    prod_i = np.prod(np.stack(xi), axis=0)
+    prod_p = np.prod(np.stack(xp), axis=0)
+    rest_p = sum(xp[1:]) if d > 1 else np.zeros_like(xp[0])
+    ts = prob.half_times()
+    if time_dependent_e:
+        e = np.stack([(1.0 + prod_i * np.exp(-t * xi[0])).reshape(-1) for t in ts])
+    else:
+        e = (1.0 + prod_i * np.exp(-0.5 * xi[0])).reshape(-1)
+    f = None
+    if with_f:
+        f = np.stack([(np.sin(np.pi * prod_p) * (1.0 + t) + xp[0] ** 2 * np.cos(np.pi * t * rest_p)).reshape(-1)
+                      for t in ts])
+    psi = np.prod(np.stack([x * (1.0 - x) for x in xi]), axis=0) * np.exp(xi[0] * xi[-1])
+    return {"e_dense": e, "f_dense": f, "psi_dense": psi.reshape(-1)}

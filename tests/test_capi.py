@@ -49,12 +49,13 @@ def test_struct_layout_matches_c_compiler(tmp_path):
     checks = {
         "tau_problem_desc": ["d", "n", "L", "R", "alpha", "kappa", "T", "M", "tol", "max_iter", "x0_mode",
                              "precision", "route", "e_min", "e_max", "refine_tol", "inner_max_iter",
-                             "max_sweeps", "inner_tol"],
+                             "max_sweeps", "inner_tol", "method", "tc"],
         "tau_field": ["rank", "n_times", "time_coef", "space"],
         "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
                       "e_hat", "e_check", "route", "graph", "device_bytes", "kernels_prologue",
                       "kernels_per_iter", "kernels_epilogue", "kernels_total", "total_sweeps", "lines_per_cta",
-                      "lines_per_cta_f32"],
+                      "lines_per_cta_f32", "tc_dims", "route_source", "route_ms", "route_alt_ms",
+                      "resid_precision"],
         "tau_request_info": ["id", "state", "status", "t_submit", "t_admit", "t_finish", "unknowns", "steps",
                              "gmres_iters", "device_bytes"],
         "tau_server_stats": ["completed", "failed", "queued", "active", "device_bytes_in_use", "latency_p50_s",
@@ -180,3 +181,18 @@ def test_choose_precision_policy(lib):
     d.alpha[0] = 2.0
     with pytest.raises(tau.TauError):
         tau.tau_choose_precision(d)
+
+
+def test_noalloc_refuses_a_forced_route_before_any_device_call(lib):
+    """tau_apply_A_noalloc picks its own route (FFT for n_i + 1 = 2^p, else dense sums); a caller
+    that forces one gets TAU_EINVAL instead of a silently different route.  The check runs before
+    any CUDA call, so non-null placeholder pointers suffice here."""
+    import ctypes as C
+    from paper_2404_10221_gb300 import tau, workloads
+    wl = workloads.c2_2d(n=63, M=2)
+    for route in (tau.TAU_ROUTE_FFT, tau.TAU_ROUTE_DENSE, tau.TAU_ROUTE_CHIRP, tau.TAU_ROUTE_LONG):
+        d = tau.make_desc(wl.prob, route=(0, route, 0))
+        fake = C.c_void_p(16)
+        st = lib.tau_apply_A_noalloc(C.byref(d), fake, fake, fake, None)
+        assert st == tau.TAU_EINVAL, route
+        assert b"TAU_ROUTE_AUTO" in lib.tau_last_error()

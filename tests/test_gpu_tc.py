@@ -194,3 +194,25 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     tau = _tau()
     assert tau.tau_selftest_bounded_wait() is True
     test_tc_minv_f32(2, (31, 63))
+
+
+def test_expired_wait_is_reported_once_by_sync():
+    """The error path of an expired wait: the device flag that a tensor-core kernel sets when a
+    bounded wait runs out (set here through the test hook; no wait is made to run out) makes the
+    next sync return TAU_ETIMEOUT; the report clears it, so the sync after that is clean and the
+    problem keeps working (a solve after it meets the form's bar against the oracle)."""
+    tau = _tau()
+    wl = _wl(2, (31, 15), M=2)
+    p = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_ON)
+    assert tau.tau_sync(p.handle) == tau.TAU_OK
+    tau.tau_inject_wait_timeout(p.handle)
+    with pytest.raises(tau.TauError) as ei:
+        tau.tau_sync(p.handle)
+    assert ei.value.status == tau.TAU_ETIMEOUT
+    assert tau.tau_sync(p.handle) == tau.TAU_OK
+    p.solve()
+    u = p.solution().cpu().numpy()
+    p.close()
+    ref = O.OracleSolver(wl.prob, wl.field_tables())
+    ref.run()
+    assert np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u) <= 1e-8
