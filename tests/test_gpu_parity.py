@@ -199,9 +199,10 @@ def test_solve_parity_paper_example1_iterations():
     assert np.all(np.abs(its - np.array(ref.iters)) <= 1)
 
 
-def test_full_size_2d_operators_and_two_steps():
+def test_full_size_2d_operators_and_five_steps():
     """The 2-D workload at its full size (1023^2 unknowns, M = 100): operators in full and the
-    first two time steps against the oracle."""
+    first five time steps against the oracle, for the plain FP64 path (1e-10, iterations +-1) and
+    for the mixed-precision form (1e-8)."""
     tau = _tau()
     wl = W.c2_2d()
     pr = wl.prob
@@ -218,15 +219,37 @@ def test_full_size_2d_operators_and_two_steps():
     tau.tau_apply_Minv(p.handle, xd, y)
     torch.cuda.synchronize()
     _cmp(y, O.apply_Minv(pr, ebar, x), minv_rtol(pr, ebar))
-    p.step(2)
+    p.step(5)
     u = p.solution().cpu().numpy()
-    its = p.iters()[:2]
+    its = p.iters()[:5]
     p.close()
+    q = tau.Problem(wl, precision=tau.TAU_MIXED)
+    q.step(5)
+    umx = q.solution().cpu().numpy()
+    q.close()
     ref = O.OracleSolver(pr, t)
-    ref.run(steps=2)
+    ref.run(steps=5)
     rel = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
     assert rel <= SOLVE_RTOL, rel
     assert np.all(np.abs(its - np.array(ref.iters)) <= 1), (its, ref.iters)
+    rel_mx = np.linalg.norm(umx - ref.u) / np.linalg.norm(ref.u)
+    assert rel_mx <= 1e-8, rel_mx
+
+
+def test_full_size_3d_mixed_step_against_oracle():
+    """The 3-D workload at its full size (255^3 = 16.6M unknowns) in the mixed-precision form with
+    its measured tensor-core choices: one Crank-Nicolson step against the oracle's structured tier
+    (the form's bar, 1e-8)."""
+    tau = _tau()
+    wl = W.c3_3d()
+    q = tau.Problem(wl, precision=tau.TAU_MIXED)
+    q.step(1)
+    u = q.solution().cpu().numpy()
+    q.close()
+    ref = O.OracleSolver(wl.prob, wl.field_tables())
+    ref.run(steps=1)
+    rel = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    assert rel <= 1e-8, rel
 
 
 def test_full_size_3d_operators():
