@@ -364,7 +364,11 @@ def plain_sequential_throughput(wls, stream, dev):
 
 def run_batched(args, stream, dev):
     """512 independent 2-D instances (uneven n from {63,127,255,511}, random alpha, kappa, e), M = 20,
-    mixed precision, one graph launch per step for all instances."""
+    mixed precision, one graph launch per step for all instances.  The batch groups the instances
+    (every kernel of the step one launch over all instances of a group); the same batch with grouping
+    off (one graph branch per instance) is timed beside it.  The plain FP64 baseline is size-matched:
+    one instance of every (n_x, n_y) shape that occurs is timed alone, and the whole batch's plain
+    time is the sum over its instances of their shape's time."""
     import numpy as np
     import torch
 
@@ -373,23 +377,38 @@ def run_batched(args, stream, dev):
 
     rng = W.SplitMix64(10221)
     wls = [W.random_2d(rng, sizes=(63, 127, 255, 511), M=20) for _ in range(args.batch_count)]
-    t0 = time.perf_counter()
-    probs = [tau.Problem(wl, precision=tau.TAU_MIXED, stream=stream.cuda_stream) for wl in wls]
-    b = tau.tau_batch_create([p.handle for p in probs], stream.cuda_stream)
-    t_setup = time.perf_counter() - t0
     M = 20
     warm = 2
-    tau.tau_batch_step(b, warm)
-    tau.tau_batch_sync(b, allow_notconv=True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    tau.tau_batch_step(b, M - warm)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    tau.tau_batch_sync(b, allow_notconv=True)
-    tau.tau_batch_destroy(b)
+
+    def timed_batch(grouped):
+        old = os.environ.get("TAU_BATCH_GROUPS")
+        os.environ["TAU_BATCH_GROUPS"] = "1" if grouped else "0"
+        try:
+            t0 = time.perf_counter()
+            probs = [tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_OFF, stream=stream.cuda_stream)
+                     for wl in wls]
+            b = tau.tau_batch_create([p.handle for p in probs], stream.cuda_stream)
+            t_setup = time.perf_counter() - t0
+        finally:
+            if old is None:
+                os.environ.pop("TAU_BATCH_GROUPS")
+            else:
+                os.environ["TAU_BATCH_GROUPS"] = old
+        info = tau.tau_batch_get_info(b)
+        tau.tau_batch_step(b, warm)
+        tau.tau_batch_sync(b, allow_notconv=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tau.tau_batch_step(b, M - warm)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tau.tau_batch_sync(b, allow_notconv=True)
+        tau.tau_batch_destroy(b)
+        return probs, info, ms, t_setup
+
+    probs, info, ms, t_setup = timed_batch(True)
     n_tot = sum(wl.prob.n_tot for wl in wls)
     value = n_tot * (M - warm) / (ms * 1e-3)
     # accuracy: a sample of instances against the plain FP64 path
@@ -399,18 +418,52 @@ def run_batched(args, stream, dev):
         tau.tau_step(ref.handle, M)
         ur = ref.solution()
         um = probs[i].solution()
+        stream.synchronize()   # the solution copies are enqueued on the problems' stream
         errs.append((torch.linalg.norm(um - ur) / torch.linalg.norm(ur)).item())
         ref.close()
-    kernels = sum(int(tau.tau_get_stats(p.handle).kernels_total) for p in probs)
+    kernels_alone = sum(int(tau.tau_get_stats(p.handle).kernels_total) for p in probs)
+    its = np.array([tau.tau_get_iters(p.handle, M) for p in probs])
     for p in probs:
         p.close()
-    plain = plain_sequential_throughput(wls[:args.plain_sample], stream, dev)
+    probs_b, info_b, ms_b, _ = timed_batch(False)
+    for p in probs_b:
+        p.close()
+    plain, shapes = plain_size_matched(wls, M, stream, dev)
     return {"instances": len(wls), "unknowns_total": n_tot, "steps_timed": M - warm, "value": value,
             "ms_per_step": ms / (M - warm), "setup_s": t_setup, "unit": UNIT,
             "max_rel_err_vs_plain_fp64": max(errs), "plain_fp64_sequential_value": plain,
-            "plain_sample_instances": args.plain_sample, "speedup_vs_plain_fp64": value / plain,
-            "kernels_launched_all_steps": kernels,
-            "dtype": "f32 inner + f64 refinement", "launch": "one CUDA graph launch per step for all instances"}
+            "plain_baseline": f"size-matched: {shapes} shapes timed alone (plain FP64, 1 warm-up + 3 timed steps each), "
+                              "weighted by their counts in the batch",
+            "speedup_vs_plain_fp64": value / plain,
+            "groups": int(info.groups), "grouped_instances": int(info.grouped_problems),
+            "grouped_launches_per_inner_iter": int(info.launches_per_inner_iter),
+            "grouped_launches_per_sweep": int(info.launches_per_sweep),
+            "grouped_launches_prologue_epilogue": int(info.launches_prologue_epilogue),
+            "inner_iters_per_step_max": int(its[:, warm:].max()),
+            "kernels_if_launched_per_instance_all_steps": kernels_alone,
+            "ungrouped_value": n_tot * (M - warm) / (ms_b * 1e-3), "ungrouped_ms_per_step": ms_b / (M - warm),
+            "grouped_over_ungrouped": ms_b / ms,
+            "dtype": "f32 inner + f64 or double-float refinement",
+            "launch": "one CUDA graph launch per step; every kernel of the step one launch over all instances of a group"}
+
+
+def plain_size_matched(wls, M, stream, dev):
+    """Plain FP64 unknowns*steps/s of solving every instance alone, one after another, estimated
+    from one instance per (n_x, n_y) shape: 1 warm-up and 3 timed steps (CUDA events), the batch's
+    total plain time = sum over instances of their shape's time per step times the steps."""
+    from paper_2404_10221_gb300 import tau
+
+    rep = {}
+    for wl in wls:
+        rep.setdefault(tuple(wl.prob.n[:wl.prob.d]), wl)
+    per_step = {}
+    for key, wl in rep.items():
+        _, ms, _, _, _ = measure_steps(wl, tau.TAU_FP64, 1, 3, stream, dev)
+        per_step[key] = ms
+    steps = M - 2
+    tot_ms = sum(per_step[tuple(wl.prob.n[:wl.prob.d])] for wl in wls) * steps
+    n_tot = sum(wl.prob.n_tot for wl in wls)
+    return n_tot * steps / (tot_ms * 1e-3), len(rep)
 
 
 def served_precision(prob) -> int:

@@ -336,6 +336,23 @@ tau_status tau_inject_wait_timeout(tau_problem* p);
  * TAU_EUNSUPPORTED (graph construction failed), TAU_ENOMEM. */
 typedef struct tau_batch tau_batch;
 tau_status tau_batch_create(tau_problem* const* problems, int count, void* stream, tau_batch** out);
+/* Grouped execution.  Mixed-precision problems on the line-pass routes (TAU_MIXED with the tensor
+ * cores off, no long-line dimension) that share d, the residual precision chosen by tau_setup and
+ * x0_mode form a group: the group's branch of the graph is the mixed step with every kernel one
+ * launch over all of its problems (each CTA works for one problem, from a table of their argument
+ * blocks), its loops running while any problem still iterates and problems that finished skipping
+ * their work.  The number of kernels per step then no longer grows with the number of problems.  A
+ * problem's arithmetic is unchanged (same kernels, tiles and reduction order as alone).  Other
+ * problems get a branch each.  TAU_BATCH_GROUPS=0 in the environment turns grouping off. */
+typedef struct {
+  int groups;                         /* groups formed */
+  int grouped_problems;               /* problems in them */
+  int branches;                       /* independent branches of the graph (groups + single problems) */
+  int64_t launches_prologue_epilogue; /* grouped launches per step outside the loops (sum over groups) */
+  int64_t launches_per_sweep;         /* grouped launches per refinement sweep around the inner loop */
+  int64_t launches_per_inner_iter;    /* grouped launches per inner FGMRES iteration */
+} tau_batch_info;
+tau_status tau_batch_get_info(tau_batch* b, tau_batch_info* info);
 /* Advance every problem of the batch by `count` steps (asynchronous; one graph launch per step). */
 tau_status tau_batch_step(tau_batch* b, int64_t count);
 /* Wait for the batch's work; TAU_ENOTCONV if some problem's step hit its iteration cap. */

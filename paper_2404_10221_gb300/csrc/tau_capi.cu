@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,9 @@ struct tau_problem {
   // pairs, b is copied to bdf), chosen at setup where its rounding floor is below refine_tol
   bool res_df = false;
   df64* bdf = nullptr;
+  // grouped batch: the group's loop-condition aggregators ([0] refinement control, [1] Givens);
+  // set while the batch graph is recorded (use_cond 2), NULL otherwise
+  GroupCtl* gctl = nullptr;
   // two-sided method (TAU_TPGM): sine-basis diagonals of P^{-1/2} and P^{-1/2} B^{-1}
   int tpgm = 0;
   double *pmh = nullptr, *pmhb = nullptr;
@@ -574,7 +578,7 @@ tau_status enq_body_t(tau_problem* p, cudaStream_t st, cudaGraphConditionalHandl
   T* V = as<T>(p->V);
   KL(launch_dots<T>(V, p->n_tot, p->g, p->pdots, ld, p->h1, st));
   KL(launch_update_dots<T>(V, p->n_tot, p->g, p->h1, p->pdots, ld, p->h2, st));
-  const GivensArgs ga{p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->desc.max_iter + 1, use_cond, h};
+  const GivensArgs ga{p->H, p->cs, p->sn, p->gv, p->h1, p->h2, p->desc.max_iter + 1, use_cond, h, nullptr};
   KL(launch_update_norm_givens<T>(V, p->n_tot, p->g, p->h2, p->pnorm, ga, st));
   KL(launch_scale_next<T>(V, p->n_tot, p->g, st));
   return TAU_OK;
@@ -631,14 +635,14 @@ tau_status enq_mx_prologue(tau_problem* p, cudaStream_t st) {
                        p->Fdt, p->n_tot, st));
     tl_launches += p->d;   // 1 + d kernels
   }
+  // (copies as kernels, so that a batch can record and group them; a zero double-float pair is
+  // two zero floats, the bits of a zero double)
   if (p->res_df) {
     KL(launch_d_to_df(p->b, p->bdf, p->n_tot, st));
     if (p->desc.x0_mode == TAU_X0_PREV) KL(launch_d_to_df(p->u, as<df64>(p->X), p->n_tot, st));
-    else CK(cudaMemsetAsync(p->X, 0, p->n_tot * sizeof(double), st));
-  } else if (p->desc.x0_mode == TAU_X0_PREV) {
-    CK(cudaMemcpyAsync(p->X, p->u, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else KL(launch_copy(p->X, nullptr, p->n_tot, st));
   } else {
-    CK(cudaMemsetAsync(p->X, 0, p->n_tot * sizeof(double), st));
+    KL(launch_copy(p->X, p->desc.x0_mode == TAU_X0_PREV ? p->u : nullptr, p->n_tot, st));
   }
   KL(launch_ir_init(p->ir, st));
   return TAU_OK;
@@ -656,7 +660,7 @@ tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditiona
     r.out = as<df64>(p->tmp);
     TRY(enq_mv<df64>(p, st, r, 1.0, FIN_RESID, p->bdf, false, &p->ir->skip_resid));
     KL(launch_norm_partial<df64>(as<df64>(p->tmp), p->n_tot, p->g, p->pnorm, st));
-    KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, st));
+    KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, p->gctl, st));
     KL(launch_scale_to_f32<df64>(as<df64>(p->tmp), p->V32, p->n_tot, p->ir, st));
     return TAU_OK;
   }
@@ -666,7 +670,7 @@ tau_status enq_mx_sweep_pre(tau_problem* p, cudaStream_t st, cudaGraphConditiona
   r.out = p->tmp;
   TRY(enq_mv<double>(p, st, r, 1.0, FIN_RESID, p->b, false, &p->ir->skip_resid));
   KL(launch_norm_partial(p->tmp, p->n_tot, p->g, p->pnorm, st));
-  KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, st));
+  KL(launch_ir_control(p->ir, p->gin, p->gvin, p->pnorm, p->n_tot, h, h_in, use_cond, p->gctl, st));
   KL(launch_scale_to_f32<double>(p->tmp, p->V32, p->n_tot, p->ir, st));
   return TAU_OK;
 }
@@ -690,7 +694,8 @@ tau_status enq_mx_inner(tau_problem* p, cudaStream_t st, cudaGraphConditionalHan
   const int ld = RED_BLOCKS;
   KL(launch_dots<float>(p->V32, p->n_tot, p->gin, p->pdots, ld, p->h1in, st));
   KL(launch_update_dots<float>(p->V32, p->n_tot, p->gin, p->h1in, p->pdots, ld, p->h2in, st));
-  const GivensArgs ga{p->Hin, p->csin, p->snin, p->gvin, p->h1in, p->h2in, p->kin + 1, use_cond, h};
+  const GivensArgs ga{p->Hin, p->csin, p->snin, p->gvin, p->h1in, p->h2in, p->kin + 1, use_cond, h,
+                      p->gctl ? p->gctl + 1 : nullptr};
   KL(launch_update_norm_givens<float>(p->V32, p->n_tot, p->gin, p->h2in, p->pnorm, ga, st));
   KL(launch_scale_next<float>(p->V32, p->n_tot, p->gin, st));
   return TAU_OK;
@@ -705,7 +710,7 @@ tau_status enq_mx_sweep_post(tau_problem* p, cudaStream_t st) {
 
 tau_status enq_mx_epilogue(tau_problem* p, cudaStream_t st) {
   if (p->res_df) KL(launch_df_to_d(as<df64>(p->X), p->u, p->n_tot, st));
-  else CK(cudaMemcpyAsync(p->u, p->X, p->n_tot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else KL(launch_copy(p->u, p->X, p->n_tot, st));
   KL(launch_set_flag(p->rres, 1, st));   // tmp is the residual of this step's final iterate
   KL(launch_ir_finish(p->ir, p->g, p->iters, p->sweeps, st));
   return TAU_OK;
@@ -2314,7 +2319,133 @@ struct tau_batch {
   std::vector<tau_problem*> probs;
   cudaStream_t st = nullptr;
   cudaGraphExec_t exec = nullptr;
+  std::vector<void*> dmem;   // grouped launches: argument tables, block ranges, loop aggregators
+  tau_batch_info info{};
 };
+
+namespace {
+
+// One grouped launch: the grouped kernel of a body over the problems of a group, their argument
+// blocks (device) and block ranges start[0..n] (device).
+struct Merged {
+  const void* fn;
+  unsigned grid, block;
+  size_t smem;
+  void* dargs;
+  int* dstart;
+  int n;
+};
+
+// Grouping applies to the mixed-precision form on the line-pass routes: every problem of a group
+// then enqueues the same sequence of kernels (same d, residual precision and initial guess), which
+// is what lets their launches merge position by position.
+bool groupable(const tau_problem* p) {
+  if (!p->mixed || p->tcm || p->spgm || p->tpgm) return false;
+  for (int i = 0; i < p->d; ++i)
+    if (p->tc_on[i] || p->route[i] == ROUTE_LONG) return false;
+  return true;
+}
+
+// Record `fn` for every problem of the group (nothing is launched) and merge the records position
+// by position into grouped launches whose tables are uploaded now (no capture is active).
+tau_status record_merge(tau_batch* b, const std::vector<tau_problem*>& ps,
+                        const std::function<tau_status(tau_problem*)>& fn, std::vector<Merged>& out) {
+  std::vector<std::vector<LaunchRec>> R(ps.size());
+  for (size_t i = 0; i < ps.size(); ++i) {
+    tl_rec = &R[i];
+    const tau_status s = fn(ps[i]);
+    tl_rec = nullptr;
+    if (s != TAU_OK) return s;
+  }
+  const size_t L = R[0].size();
+  for (size_t i = 1; i < ps.size(); ++i)
+    if (R[i].size() != L) return fail(TAU_EUNSUPPORTED, "grouped batch: problems enqueue different kernel sequences");
+  const int n = (int)ps.size();
+  for (size_t k = 0; k < L; ++k) {
+    const LaunchRec& r0 = R[0][k];
+    const size_t asz = r0.args.size();
+    std::vector<unsigned char> args(asz * n);
+    std::vector<int> start(n + 1, 0);
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+      const LaunchRec& r = R[i][k];
+      if (r.fn != r0.fn || r.block != r0.block || r.args.size() != asz)
+        return fail(TAU_EUNSUPPORTED, "grouped batch: launch %zu differs between problems", k);
+      memcpy(args.data() + asz * i, r.args.data(), asz);
+      start[i + 1] = start[i] + (int)r.grid;
+      smem = std::max(smem, r.smem);
+    }
+    const size_t off = (asz * n + 15) & ~(size_t)15;
+    void* d = nullptr;
+    CK(cudaMalloc(&d, off + sizeof(int) * (n + 1)));
+    b->dmem.push_back(d);
+    CK(cudaMemcpy(d, args.data(), asz * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(static_cast<char*>(d) + off, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    out.push_back(Merged{r0.fn, (unsigned)start[n], r0.block, smem, d,
+                         reinterpret_cast<int*>(static_cast<char*>(d) + off), n});
+  }
+  return TAU_OK;
+}
+
+tau_status launch_merged(const std::vector<Merged>& v, cudaStream_t s) {
+  for (const Merged& m : v) {
+    if (m.grid == 0) continue;
+    void* dargs = m.dargs;
+    int* dstart = m.dstart;
+    int nn = m.n;
+    void* kargs[] = {&dargs, &dstart, &nn};
+    CK(cudaLaunchKernel(m.fn, dim3(m.grid), dim3(m.block), kargs, m.smem, s));
+  }
+  return TAU_OK;
+}
+
+// One branch of the batch graph for a group: the mixed step's graph (prologue -> WHILE(refinement
+// control -> WHILE(FGMRES iteration) -> correction) -> epilogue) with every kernel a grouped launch
+// over the group's problems.  Each loop runs while any problem of the group still iterates; a
+// problem that finished skips its work in the remaining iterations.
+tau_status build_group_inner(tau_batch* b, const std::vector<tau_problem*>& ps, cudaGraph_t G) {
+  tau_problem* p0 = ps[0];
+  GroupCtl* gc = nullptr;
+  CK(cudaMalloc(&gc, 2 * sizeof(GroupCtl)));
+  b->dmem.push_back(gc);
+  const GroupCtl init[2] = {{0u, 0, (int)ps.size(), 0}, {0u, 0, (int)ps.size(), 0}};
+  CK(cudaMemcpy(gc, init, sizeof(init), cudaMemcpyHostToDevice));
+  for (tau_problem* p : ps) p->gctl = gc;
+  auto done = [&](tau_status s) {
+    for (tau_problem* p : ps) p->gctl = nullptr;
+    return s;
+  };
+  std::vector<Merged> pro, pre, inner, post, epi;
+  std::vector<cudaGraphNode_t> none, leaves, preL, tmp;
+  tau_status s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_prologue(p, p->cap); }, pro);
+  if (s == TAU_OK) s = capture_into(p0, G, none, [&](cudaStream_t st) { return launch_merged(pro, st); }, leaves);
+  cudaGraphConditionalHandle ho = 0, hi = 0;
+  cudaGraphNode_t wo = nullptr, wi = nullptr;
+  cudaGraph_t bo = nullptr, bi = nullptr;
+  if (s == TAU_OK) s = make_handle(G, &ho);
+  if (s == TAU_OK) s = add_while(G, leaves, &ho, &wo, &bo);
+  if (s == TAU_OK) s = make_handle(bo, &hi);
+  if (s == TAU_OK)
+    s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_sweep_pre(p, p->cap, ho, hi, 2); }, pre);
+  if (s == TAU_OK) s = capture_into(p0, bo, none, [&](cudaStream_t st) { return launch_merged(pre, st); }, preL);
+  if (s == TAU_OK) s = add_while(bo, preL, &hi, &wi, &bi);
+  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_inner(p, p->cap, hi, 2); }, inner);
+  if (s == TAU_OK) s = capture_into(p0, bi, none, [&](cudaStream_t st) { return launch_merged(inner, st); }, tmp);
+  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_sweep_post(p, p->cap); }, post);
+  if (s == TAU_OK) s = capture_into(p0, bo, {wi}, [&](cudaStream_t st) { return launch_merged(post, st); }, tmp);
+  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_epilogue(p, p->cap); }, epi);
+  if (s == TAU_OK) s = capture_into(p0, G, {wo}, [&](cudaStream_t st) { return launch_merged(epi, st); }, tmp);
+  if (s == TAU_OK) {
+    b->info.groups += 1;
+    b->info.grouped_problems += (int)ps.size();
+    b->info.launches_prologue_epilogue += (int64_t)(pro.size() + epi.size());
+    b->info.launches_per_sweep += (int64_t)(pre.size() + post.size());
+    b->info.launches_per_inner_iter += (int64_t)inner.size();
+  }
+  return done(s);
+}
+
+}  // namespace
 
 tau_status tau_batch_create(tau_problem* const* problems, int count, void* stream, tau_batch** out) {
   if (!problems || !out || count < 1) return fail(TAU_EINVAL, "tau_batch_create: bad arguments");
@@ -2336,8 +2467,28 @@ tau_status tau_batch_create(tau_problem* const* problems, int count, void* strea
     delete b;
     return fail(TAU_ECUDA, "cudaGraphCreate");
   }
+  // groups of mixed-precision problems with the same kernel sequence (TAU_BATCH_GROUPS=0: none)
+  const char* ge = std::getenv("TAU_BATCH_GROUPS");
+  const bool grouping = !(ge && ge[0] == '0');
+  std::map<std::tuple<int, int, int>, std::vector<tau_problem*>> groups;
+  std::vector<tau_problem*> single;
+  for (tau_problem* p : b->probs) {
+    if (grouping && groupable(p)) groups[std::make_tuple(p->d, p->res_df ? 1 : 0, p->desc.x0_mode)].push_back(p);
+    else single.push_back(p);
+  }
   tau_status st = TAU_OK;
-  for (int i = 0; i < count && st == TAU_OK; ++i) st = build_graph_inner(b->probs[i], G);
+  for (auto& kv : groups) {
+    if (kv.second.size() < 2) {
+      single.push_back(kv.second[0]);
+      continue;
+    }
+    if (st == TAU_OK) st = build_group_inner(b, kv.second, G);
+  }
+  for (size_t i = 0; i < single.size() && st == TAU_OK; ++i) {
+    st = build_graph_inner(single[i], G);
+    b->info.branches += 1;
+  }
+  b->info.branches += b->info.groups;
   if (st == TAU_OK) {
     cudaError_t e = cudaGraphInstantiate(&b->exec, G, 0);
     if (e != cudaSuccess) {
@@ -2347,10 +2498,17 @@ tau_status tau_batch_create(tau_problem* const* problems, int count, void* strea
   }
   cudaGraphDestroy(G);
   if (st != TAU_OK) {
+    for (void* d : b->dmem) cudaFree(d);
     delete b;
     return st;
   }
   *out = b;
+  return TAU_OK;
+}
+
+tau_status tau_batch_get_info(tau_batch* b, tau_batch_info* info) {
+  if (!b || !info) return fail(TAU_EINVAL, "NULL argument");
+  *info = b->info;
   return TAU_OK;
 }
 
@@ -2383,6 +2541,7 @@ tau_status tau_batch_destroy(tau_batch* b) {
   if (!b) return TAU_OK;
   cudaStreamSynchronize(b->st);
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (void* d : b->dmem) cudaFree(d);
   delete b;
   return TAU_OK;
 }

@@ -5,7 +5,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace tau {
+
+// Virtual block of a kernel body (tau_group.cuh): (blockIdx.x, gridDim.x) in a plain launch; the
+// block's index and count within its problem's range in a grouped launch.
+struct VB {
+  int bid, nb;
+};
+
+// Aggregation of one device-controlled loop condition over the n problems of a group.
+struct GroupCtl {
+  unsigned int ticket;
+  int any;
+  int n;
+  int pad;
+};
+
+// A recorded launch: the grouped kernel of the body, its argument bytes, grid, block, shared memory.
+struct LaunchRec {
+  const void* fn;
+  std::vector<unsigned char> args;
+  unsigned grid, block;
+  size_t smem;
+  int kthreads;
+};
+// When set, the launch functions of the mixed-precision step record instead of launching.
+extern thread_local std::vector<LaunchRec>* tl_rec;
 
 // Largest half-length complex FFT size K = n + 1 of the FFT route.
 constexpr int KMAX = 4096;
@@ -367,8 +394,9 @@ struct GivensArgs {
   const double* h1;
   const double* h2;
   int ldH;
-  int use_cond;
+  int use_cond;        // 0 none, 1 this problem's handle, 2 a group's (gc)
   cudaGraphConditionalHandle cond;
+  GroupCtl* gc;
 };
 template <typename S>
 cudaError_t launch_update_norm_givens(S* V, int64_t n, GmresDev* g, const double* h2, double* partial_norm,
@@ -407,7 +435,9 @@ cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st);
 cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st);
 cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm, int64_t n,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
-                              cudaStream_t st);
+                              GroupCtl* gc, cudaStream_t st);
+// dst = src (src non-null) or dst = 0, n doubles (a kernel, so it can be recorded and grouped)
+cudaError_t launch_copy(double* dst, const double* src, int64_t n, cudaStream_t st);
 // v = r / rho in FP32 from the residual stored as S (double, or double-float)
 template <typename S>
 cudaError_t launch_scale_to_f32(const S* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st);

@@ -18,12 +18,15 @@
 // explicit O(n_i) sums per output.
 #include "tau_internal.cuh"
 #include "tau_fft.cuh"
+#include "tau_group.cuh"
 
 #include <math.h>
 
 #include <type_traits>
 
 namespace tau {
+
+thread_local std::vector<LaunchRec>* tl_rec = nullptr;
 
 constexpr int PASS_THREADS = 128;
 
@@ -782,7 +785,7 @@ template <> struct PassOcc<float> { static constexpr int ctas = 10; };
 template <> struct PassOcc<df64> { static constexpr int ctas = 6; };
 
 template <typename T>
-__global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const PassT<T> P) {
+__device__ __forceinline__ void pass_run(const PassT<T>& P, VB vb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = P.len, lpb = P.lpb;
   const int RS = rc_stride(P);
@@ -791,7 +794,7 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
   T* rc = ra + ((lpb * N + 1) & ~1);
   if (P.g && P.g->done) return;
   if (P.skip && *P.skip) return;
-  const TileGeo tg = tile_geo(P, blockIdx.x);
+  const TileGeo tg = tile_geo(P, vb.bid);
   const int TH = blockDim.x, tid = threadIdx.x;
   // element loops run over lpb lines of 2^lgnp >= N slots (shift and mask, no division)
   const int lgnp = lg_pad(N), NP = 1 << lgnp, NTP = lpb << lgnp;
@@ -885,6 +888,19 @@ __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const P
   tile_store(tg, N, lpb, rc, RS, out_a);
 }
 
+template <typename T>
+struct PassBody {
+  using Args = PassT<T>;
+  static constexpr int kThreads = PASS_THREADS;
+  static constexpr int kCtas = PassOcc<T>::ctas;
+  static __device__ __forceinline__ void run(const PassT<T>& P, VB vb) { pass_run<T>(P, vb); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const PassT<T> P) {
+  pass_run<T>(P, VB{(int)blockIdx.x, (int)gridDim.x});
+}
+
 // Hartley passes of the Strang circulant method (POST_HT, POST_HT_D_HT): a kernel of their own, so
 // the dense Hartley loop does not weigh on the register allocation of the line-pass kernel.
 template <typename T>
@@ -945,6 +961,12 @@ cudaError_t init_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ht_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBody<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBody<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBody<df64>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_chirp_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -952,8 +974,12 @@ cudaError_t init_kernel_attributes() {
 
 template <typename T>
 cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
-  if (p.ntiles <= 0) return cudaSuccess;
   const size_t smem = pass_smem_bytes(p);
+  if (tl_rec) {
+    if (p.post == POST_HT || p.post == POST_HT_D_HT) return cudaErrorNotSupported;   // not grouped
+    return record_launch<PassBody<T>>(p, p.ntiles > 0 ? (unsigned)p.ntiles : 0u, PASS_THREADS, smem);
+  }
+  if (p.ntiles <= 0) return cudaSuccess;
   if (p.post == POST_HT || p.post == POST_HT_D_HT) {
     if constexpr (std::is_same<T, double>::value) {
       k_ht_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
@@ -1080,14 +1106,24 @@ __device__ __forceinline__ double fields_hstencil(const FieldDev& F, const doubl
   return acc2;
 }
 
-__global__ void k_fields(const FieldDev F, const GmresDev* __restrict__ g, int64_t m_override, double* e_out,
-                         double* fdt_out) {
-  const int64_t m = m_override >= 0 ? m_override : g->m;
+struct FieldsArgs {
+  FieldDev F;
+  const GmresDev* g;
+  int64_t m_override;
+  double* e_out;
+  double* fdt_out;
+};
+
+__device__ __forceinline__ void fields_run(const FieldsArgs& A, VB vb) {
+  const FieldDev& F = A.F;
+  double* e_out = A.e_out;
+  double* fdt_out = A.fdt_out;
+  const int64_t m = A.m_override >= 0 ? A.m_override : A.g->m;
   if (F.e_dev) {
     const double* em = F.e_dev + m * F.e_step;
     const double* fm = F.f_dev ? F.f_dev + m * F.f_step : nullptr;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
+         idx += (int64_t)vb.nb * blockDim.x) {
       int j[3] = {0, 0, 0};
       unflatten(idx, F.d, F.n, j);
       if (e_out) e_out[idx] = em[idx];
@@ -1097,8 +1133,8 @@ __global__ void k_fields(const FieldDev F, const GmresDev* __restrict__ g, int64
   }
   const double* etc = F.e_tc + m * F.re;
   const double* ftc = F.f_tc + m * F.rf;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
-       idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
+       idx += (int64_t)vb.nb * blockDim.x) {
     int j[3] = {0, 0, 0};
     unflatten(idx, F.d, F.n, j);
     double ev = 0.0;
@@ -1118,11 +1154,21 @@ __global__ void k_fields(const FieldDev F, const GmresDev* __restrict__ g, int64
   }
 }
 
+struct FieldsBody {
+  using Args = FieldsArgs;
+  static constexpr int kThreads = 256, kCtas = 1;
+  static __device__ __forceinline__ void run(const FieldsArgs& a, VB vb) { fields_run(a, vb); }
+};
+
+__global__ void k_fields(const FieldsArgs A) { fields_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
 cudaError_t launch_fields(const FieldDev& f, const GmresDev* g, int64_t m_override, double* e_out, double* fdt_out,
                           cudaStream_t st) {
   int64_t blocks = (f.n_tot + 255) / 256;
   if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
-  k_fields<<<(unsigned)blocks, 256, 0, st>>>(f, g, m_override, e_out, fdt_out);
+  const FieldsArgs a{f, g, m_override, e_out, fdt_out};
+  if (tl_rec) return record_launch<FieldsBody>(a, (unsigned)blocks, 256, 0);
+  k_fields<<<(unsigned)blocks, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1386,13 +1432,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // the block that draws the last one sees all partials and finishes the reduction.  The counter is
 // the problem's own (GmresDev.tickets), so concurrent problems never share it; the last block
 // resets it for the next launch.
-__device__ __forceinline__ bool last_block(unsigned int* tickets) {
+__device__ __forceinline__ bool last_block(unsigned int* tickets, VB vb) {
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int t = atomicAdd(tickets, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)vb.nb - 1u);
     if (s_last) *tickets = 0u;
   }
   __syncthreads();
@@ -1401,11 +1447,11 @@ __device__ __forceinline__ bool last_block(unsigned int* tickets) {
 
 // h[i] = sum_b partial[i * ld + b], i = 0..jj, by one block (a warp per i); the partials come from
 // other SMs, so they are read through L2.
-__device__ void reduce_partials(const double* partial, int ld, int jj, double* h) {
+__device__ void reduce_partials(const double* partial, int ld, int jj, double* h, VB vb) {
   const int warp = threadIdx.x >> 5, ln = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i <= jj; i += nw) {
     double s = 0.0;
-    for (int b = ln; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[(int64_t)i * ld + b]);
+    for (int b = ln; b < vb.nb; b += 32) s += __ldcg(&partial[(int64_t)i * ld + b]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (ln == 0) h[i] = s;
   }
@@ -1415,8 +1461,23 @@ __device__ void reduce_partials(const double* partial, int ld, int jj, double* h
 // the last block sums them into h.  Per-element products and per-thread sums in the storage type
 // S; block and grid sums in FP64.
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, int64_t n, GmresDev* g,
-                                                      double* partial, int ld, double* h) {
+struct DotsArgs {
+  const S* V;
+  int64_t n;
+  GmresDev* g;
+  double* partial;
+  double* h;
+  int ld;
+  int pad;
+};
+
+template <typename S>
+__device__ __forceinline__ void dots_run(const DotsArgs<S>& A, VB vb) {
+  const S* __restrict__ V = A.V;
+  const int64_t n = A.n;
+  GmresDev* g = A.g;
+  double* partial = A.partial;
+  const int ld = A.ld;
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   if (g->done) return;
   const int jj = g->j;
@@ -1426,7 +1487,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, i
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
       const S wv = w[idx];
 #pragma unroll
       for (int r = 0; r < DOT_CHUNK; ++r)
@@ -1436,16 +1497,30 @@ __global__ void __launch_bounds__(RED_THREADS) k_dots(const S* __restrict__ V, i
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
         const double s = block_sum(to_d(acc[r]), sh);
-        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + vb.bid] = s;
       }
     }
   }
-  if (last_block(&g->tickets)) reduce_partials(partial, ld, jj, h);
+  if (last_block(&g->tickets, vb)) reduce_partials(partial, ld, jj, A.h, vb);
+}
+
+template <typename S>
+struct DotsBody {
+  using Args = DotsArgs<S>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { dots_run<S>(a, vb); }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_dots(const DotsArgs<S> A) {
+  dots_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
 template <typename S>
 cudaError_t launch_dots(const S* V, int64_t n, GmresDev* g, double* partial, int ld, double* h, cudaStream_t st) {
-  k_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, partial, ld, h);
+  const DotsArgs<S> a{V, n, g, partial, h, ld, 0};
+  if (tl_rec) return record_launch<DotsBody<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_dots<double>(const double*, int64_t, GmresDev*, double*, int, double*, cudaStream_t);
@@ -1488,10 +1563,10 @@ __device__ void givens_column(GmresDev* g, const GivensArgs& a, double nsq) {
     g->done = 1;
     g->k = j + 1;
     if (!conv && !brk) g->notconv = 1;
-    if (a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    report_cond(a.use_cond, a.gc, false, a.cond, a.cond, false);
   } else {
     g->j = j + 1;
-    if (a.use_cond) cudaGraphSetConditional(a.cond, 1);
+    report_cond(a.use_cond, a.gc, true, a.cond, a.cond, false);
   }
 }
 
@@ -1499,14 +1574,34 @@ __device__ void givens_column(GmresDev* g, const GivensArgs& a, double nsq) {
 // V_i (CGS2 second pass) finished into h_out by the last block, or, with norm_only = true, ||w||^2
 // finished by the last block, which then runs the Givens step.
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, GmresDev* g,
-                                                             const double* __restrict__ h, double* partial, int ld,
-                                                             double* h_out, int norm_only, const GivensArgs ga) {
+struct UpdArgs {
+  S* V;
+  int64_t n;
+  GmresDev* g;
+  const double* h;
+  double* partial;
+  double* h_out;
+  int ld;
+  int norm_only;
+  GivensArgs ga;
+};
+
+template <typename S>
+__device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
+  S* V = A.V;
+  const int64_t n = A.n;
+  GmresDev* g = A.g;
+  const double* __restrict__ h = A.h;
+  double* partial = A.partial;
+  const int ld = A.ld;
+  const int norm_only = A.norm_only;
+  const GivensArgs& ga = A.ga;
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
   __shared__ S hs[MAX_ITER_CAP + 1];
   if (g->done) {
-    // a finished step: the loop body still runs once after the prologue found r_0 = 0
-    if (norm_only && ga.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(ga.cond, 0);
+    // a finished step (the loop body still runs once after the prologue found r_0 = 0), or, in a
+    // grouped launch, a problem that finished before the others: it reports "stop" once
+    if (norm_only && vb.bid == 0 && threadIdx.x == 0) report_cond(ga.use_cond, ga.gc, false, ga.cond, ga.cond, false);
     return;
   }
   const int jj = g->j;
@@ -1514,7 +1609,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, Gm
   for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = from_d<S>(h[i]);
   __syncthreads();
   S nacc = from_f<S>(0.0f);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
     S wv = w[idx];
     for (int i = 0; i <= jj; ++i) wv = tfma(-hs[i], V[(int64_t)i * n + idx], wv);
     w[idx] = wv;
@@ -1522,10 +1617,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, Gm
   }
   if (norm_only) {
     const double s = block_sum(to_d(nacc), sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
-    if (last_block(&g->tickets)) {
+    if (threadIdx.x == 0) partial[vb.bid] = s;
+    if (last_block(&g->tickets, vb)) {
       double t = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&partial[b]);
+      for (int b = threadIdx.x; b < vb.nb; b += blockDim.x) t += __ldcg(&partial[b]);
       t = block_sum(t, sh);
       if (threadIdx.x == 0) givens_column(g, ga, t);
     }
@@ -1538,7 +1633,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, Gm
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
       const S wv = w[idx];
 #pragma unroll
       for (int r = 0; r < DOT_CHUNK; ++r)
@@ -1548,24 +1643,39 @@ __global__ void __launch_bounds__(RED_THREADS) k_update_dots(S* V, int64_t n, Gm
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
         const double s = block_sum(to_d(acc[r]), sh);
-        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + blockIdx.x] = s;
+        if (threadIdx.x == 0) partial[(int64_t)(i0 + r) * ld + vb.bid] = s;
       }
     }
   }
-  if (last_block(&g->tickets)) reduce_partials(partial, ld, jj, h_out);
+  if (last_block(&g->tickets, vb)) reduce_partials(partial, ld, jj, A.h_out, vb);
+}
+
+template <typename S>
+struct UpdBody {
+  using Args = UpdArgs<S>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { update_dots_run<S>(a, vb); }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_update_dots(const UpdArgs<S> A) {
+  update_dots_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
 template <typename S>
 cudaError_t launch_update_dots(S* V, int64_t n, GmresDev* g, const double* h, double* partial, int ld,
                                double* h_out, cudaStream_t st) {
-  GivensArgs none{};
-  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, h, partial, ld, h_out, 0, none);
+  const UpdArgs<S> a{V, n, g, h, partial, h_out, ld, 0, GivensArgs{}};
+  if (tl_rec) return record_launch<UpdBody<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template <typename S>
 cudaError_t launch_update_norm_givens(S* V, int64_t n, GmresDev* g, const double* h2, double* partial_norm,
                                       const GivensArgs& ga, cudaStream_t st) {
-  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g, h2, partial_norm, 0, nullptr, 1, ga);
+  const UpdArgs<S> a{V, n, g, h2, partial_norm, nullptr, 0, 1, ga};
+  if (tl_rec) return record_launch<UpdBody<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_update_dots<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 #define TAU_CGS_INST(S)                                                                                          \
@@ -1581,21 +1691,41 @@ TAU_CGS_INST(df64)
 // V_{j} <- w / ||w|| where w sits in the slot of V_j (after the Givens step advanced j). When the
 // column closed the iteration (done), nothing is scaled.
 template <typename S>
-__global__ void k_scale_next(S* V, int64_t n, const GmresDev* __restrict__ g) {
+struct ScaleNextArgs {
+  S* V;
+  int64_t n;
+  const GmresDev* g;
+};
+
+template <typename S>
+__device__ __forceinline__ void scale_next_run(const ScaleNextArgs<S>& A, VB vb) {
+  const GmresDev* __restrict__ g = A.g;
   if (g->done) return;
   const int j = g->j;
   __shared__ double sinv;   // one FP64 division per block
   if (threadIdx.x == 0) sinv = 1.0 / g->hnorm;
   __syncthreads();
   const S inv = from_d<S>(sinv);
-  S* v = V + (int64_t)j * n;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+  S* v = A.V + (int64_t)j * A.n;
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < A.n; idx += (int64_t)vb.nb * blockDim.x)
     v[idx] *= inv;
 }
 
 template <typename S>
+struct ScaleNextBody {
+  using Args = ScaleNextArgs<S>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { scale_next_run<S>(a, vb); }
+};
+
+template <typename S>
+__global__ void k_scale_next(const ScaleNextArgs<S> A) { scale_next_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
+template <typename S>
 cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st) {
-  k_scale_next<S><<<red_blocks(n), RED_THREADS, 0, st>>>(V, n, g);
+  const ScaleNextArgs<S> a{V, n, g};
+  if (tl_rec) return record_launch<ScaleNextBody<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_scale_next<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_scale_next<double>(double*, int64_t, const GmresDev*, cudaStream_t);
@@ -1603,19 +1733,41 @@ template cudaError_t launch_scale_next<float>(float*, int64_t, const GmresDev*, 
 template cudaError_t launch_scale_next<df64>(df64*, int64_t, const GmresDev*, cudaStream_t);
 
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const S* __restrict__ w, int64_t n, double* partial) {
+struct NormArgs {
+  const S* w;
+  int64_t n;
+  double* partial;
+};
+
+template <typename S>
+__device__ __forceinline__ void norm_partial_run(const NormArgs<S>& A, VB vb) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
+  const S* __restrict__ w = A.w;
   S acc = from_f<S>(0.0f);
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < A.n; idx += (int64_t)vb.nb * blockDim.x)
     acc = tfma(w[idx], w[idx], acc);
   const double s = block_sum(to_d(acc), sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (threadIdx.x == 0) A.partial[vb.bid] = s;
+}
+
+template <typename S>
+struct NormBody {
+  using Args = NormArgs<S>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { norm_partial_run<S>(a, vb); }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(RED_THREADS) k_norm_partial(const NormArgs<S> A) {
+  norm_partial_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
 template <typename S>
 cudaError_t launch_norm_partial(const S* w, int64_t n, const GmresDev* g, double* partial, cudaStream_t st) {
   (void)g;
-  k_norm_partial<S><<<red_blocks(n), RED_THREADS, 0, st>>>(w, n, partial);
+  const NormArgs<S> a{w, n, partial};
+  if (tl_rec) return record_launch<NormBody<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_norm_partial<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_norm_partial<double>(const double*, int64_t, const GmresDev*, double*, cudaStream_t);
@@ -1660,9 +1812,24 @@ template cudaError_t launch_init_beta<double>(GmresDev*, const double*, double*,
 template cudaError_t launch_init_beta<df64>(GmresDev*, const double*, double*, df64*, int64_t, cudaStream_t);
 
 // y = R^{-1} g (upper triangular k x k in H after the rotations), then u = x0 + V_k y.
-__global__ void k_backsolve(GmresDev* g, const double* __restrict__ H, const double* __restrict__ gv, int ldH,
-                            double* y, int* iters_log) {
+struct BacksolveArgs {
+  GmresDev* g;
+  const double* H;
+  const double* gv;
+  double* y;
+  int* iters_log;
+  int ldH;
+  int pad;
+};
+
+__device__ __forceinline__ void backsolve_run(const BacksolveArgs& A, VB) {
   if (threadIdx.x != 0) return;
+  GmresDev* g = A.g;
+  const double* __restrict__ H = A.H;
+  const double* __restrict__ gv = A.gv;
+  double* y = A.y;
+  const int ldH = A.ldH;
+  int* iters_log = A.iters_log;
   const int k = g->k;
   for (int i = k - 1; i >= 0; --i) {
     double acc = gv[i];
@@ -1671,6 +1838,14 @@ __global__ void k_backsolve(GmresDev* g, const double* __restrict__ H, const dou
   }
   if (iters_log) iters_log[g->m] = k;
 }
+
+struct BacksolveBody {
+  using Args = BacksolveArgs;
+  static constexpr int kThreads = 32, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { backsolve_run(a, vb); }
+};
+
+__global__ void k_backsolve(const BacksolveArgs A) { backsolve_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
 
 template <typename S>
 __global__ void k_update_solution(const GmresDev* __restrict__ g, const double* __restrict__ y,
@@ -1693,7 +1868,7 @@ __global__ void k_advance(GmresDev* g) {
 template <typename S>
 cudaError_t launch_backsolve_update(GmresDev* g, const double* H, const double* gv, int ldH, double* y, const S* V,
                                     int64_t n, S* u, int x0_prev, int* iters_log, cudaStream_t st) {
-  k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, iters_log);
+  k_backsolve<<<1, 32, 0, st>>>(BacksolveArgs{g, H, gv, y, iters_log, ldH, 0});
   k_update_solution<S><<<red_blocks(n), RED_THREADS, 0, st>>>(g, y, V, n, u, x0_prev);
   k_advance<<<1, 32, 0, st>>>(g);
   return cudaGetLastError();
@@ -1703,49 +1878,97 @@ template cudaError_t launch_backsolve_update<double>(GmresDev*, const double*, c
 template cudaError_t launch_backsolve_update<df64>(GmresDev*, const double*, const double*, int, double*, const df64*,
                                                    int64_t, df64*, int, int*, cudaStream_t);
 
-// double <-> double-float conversion of whole vectors (setup, per-step fields, API boundary)
-__global__ void k_d_to_df(const double* __restrict__ a, df64* b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = from_d<df64>(a[i]);
-}
-__global__ void k_df_to_d(const df64* __restrict__ a, double* b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = to_d(a[i]);
+// Element-wise conversion or copy of whole vectors (setup, per-step fields, API boundary): b = f(a).
+template <typename S, typename D>
+struct CvtArgs {
+  const S* a;   // NULL (copy only): b = 0
+  D* b;
+  int64_t n;
+};
+
+template <typename S, typename D> __device__ __forceinline__ D cvt_elem(S v);
+template <> __device__ __forceinline__ df64 cvt_elem<double, df64>(double v) { return from_d<df64>(v); }
+template <> __device__ __forceinline__ double cvt_elem<df64, double>(df64 v) { return to_d(v); }
+template <> __device__ __forceinline__ float cvt_elem<double, float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double cvt_elem<double, double>(double v) { return v; }
+
+template <typename S, typename D>
+__device__ __forceinline__ void cvt_run(const CvtArgs<S, D>& A, VB vb) {
+  for (int64_t i = vb.bid * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)vb.nb * blockDim.x)
+    A.b[i] = A.a ? cvt_elem<S, D>(A.a[i]) : D{};
 }
 
-cudaError_t launch_d_to_df(const double* a, df64* b, int64_t n, cudaStream_t st) {
+template <typename S, typename D>
+struct CvtBody {
+  using Args = CvtArgs<S, D>;
+  static constexpr int kThreads = 256, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { cvt_run<S, D>(a, vb); }
+};
+
+__global__ void k_d_to_df(const CvtArgs<double, df64> A) { cvt_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_df_to_d(const CvtArgs<df64, double> A) { cvt_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_f64_to_f32(const CvtArgs<double, float> A) { cvt_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_copy(const CvtArgs<double, double> A) { cvt_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
+static unsigned cvt_blocks(int64_t n) {
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
   if (blocks < 1) blocks = 1;
-  k_d_to_df<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  return (unsigned)blocks;
+}
+
+cudaError_t launch_d_to_df(const double* a, df64* b, int64_t n, cudaStream_t st) {
+  const CvtArgs<double, df64> c{a, b, n};
+  if (tl_rec) return record_launch<CvtBody<double, df64>>(c, cvt_blocks(n), 256, 0);
+  k_d_to_df<<<cvt_blocks(n), 256, 0, st>>>(c);
   return cudaGetLastError();
 }
 
 cudaError_t launch_df_to_d(const df64* a, double* b, int64_t n, cudaStream_t st) {
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
-  if (blocks < 1) blocks = 1;
-  k_df_to_d<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  const CvtArgs<df64, double> c{a, b, n};
+  if (tl_rec) return record_launch<CvtBody<df64, double>>(c, cvt_blocks(n), 256, 0);
+  k_df_to_d<<<cvt_blocks(n), 256, 0, st>>>(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(double* dst, const double* src, int64_t n, cudaStream_t st) {
+  const CvtArgs<double, double> c{src, dst, n};
+  if (tl_rec) return record_launch<CvtBody<double, double>>(c, cvt_blocks(n), 256, 0);
+  k_copy<<<cvt_blocks(n), 256, 0, st>>>(c);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // mixed precision: FP64 iterative refinement around an FP32 flexible GMRES
 // ---------------------------------------------------------------------------
-__global__ void k_f64_to_f32(const double* __restrict__ a, float* b, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-
 cudaError_t launch_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
-  int64_t blocks = (n + 255) / 256;
-  if (blocks > 4 * 152 * 8) blocks = 4 * 152 * 8;
-  if (blocks < 1) blocks = 1;
-  k_f64_to_f32<<<(unsigned)blocks, 256, 0, st>>>(a, b, n);
+  const CvtArgs<double, float> c{a, b, n};
+  if (tl_rec) return record_launch<CvtBody<double, float>>(c, cvt_blocks(n), 256, 0);
+  k_f64_to_f32<<<cvt_blocks(n), 256, 0, st>>>(c);
   return cudaGetLastError();
 }
 
-__global__ void k_ir_init(IRDev* ir) {
+struct IRArgs {
+  IRDev* ir;
+  GmresDev* g;          // outer state (ir_finish)
+  GmresDev* gin;        // inner FGMRES state (ir_control)
+  double* gv_in;
+  const double* pnorm;  // ir_control: per-block partial sums of ||r||^2 (nblk of them)
+  const double* b;      // first_resid: r = b (bitwise: FP64 or double-float)
+  double* r;
+  int* iters_log;
+  int* sweeps_log;
+  GroupCtl* gc;
+  int64_t n;
+  int nblk;
+  int x0_zero;
+  int use_cond;
+  int pad;
+  cudaGraphConditionalHandle cond, cond_in;
+};
+
+__device__ __forceinline__ void ir_init_run(const IRArgs& A, VB) {
+  IRDev* ir = A.ir;
   if (threadIdx.x == 0) {
     ir->sweep = 0;
     ir->done = 0;
@@ -1758,35 +1981,33 @@ __global__ void k_ir_init(IRDev* ir) {
   }
 }
 
-cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st) {
-  k_ir_init<<<1, 32, 0, st>>>(ir);
-  return cudaGetLastError();
-}
-
-__global__ void k_ir_first_resid(IRDev* ir, const double* __restrict__ b, double* r, int64_t n, int x0_zero) {
-  const bool first = x0_zero && ir->sweep == 0 && !ir->done;
+// r = b on the first sweep of a zero initial guess (the residual passes then skip themselves); a
+// problem that already converged (a grouped launch runs on while others refine) skips them too.
+__device__ __forceinline__ void ir_first_resid_run(const IRArgs& A, VB vb) {
+  IRDev* ir = A.ir;
+  const bool first = A.x0_zero && ir->sweep == 0 && !ir->done;
   if (first) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-      r[i] = b[i];
+    for (int64_t i = vb.bid * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)vb.nb * blockDim.x)
+      A.r[i] = A.b[i];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) ir->skip_resid = first ? 1 : 0;
+  if (vb.bid == 0 && threadIdx.x == 0) ir->skip_resid = (first || ir->done) ? 1 : 0;
 }
 
-cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st) {
-  k_ir_first_resid<<<red_blocks(n), RED_THREADS, 0, st>>>(ir, b, r, n, x0_zero);
-  return cudaGetLastError();
-}
-
-// rho = ||b - A x|| (FP64); stop when rho <= tol rho_0 or after max_sweeps corrections; otherwise
+// rho = ||b - A x||; stop when rho <= tol rho_0 or after max_sweeps corrections; otherwise
 // start the inner flexible GMRES on v_0 = (b - A x)/rho (beta = 1).
 // In the step graph the inner WHILE node lives in the outer loop's body; a handle's default value
 // is applied only when the whole graph is launched, so this kernel sets the inner condition for
 // every sweep (cond_in) as well as the outer one (cond).
-__global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* __restrict__ pnorm, int nblk,
-                             cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond) {
+__device__ __forceinline__ void ir_control_run(const IRArgs& A, VB) {
   __shared__ double sh[RED_THREADS];   // block_sum staging (blocks of RED_THREADS threads)
+  IRDev* ir = A.ir;
+  GmresDev* gin = A.gin;
+  if (ir->done) {   // converged earlier: only possible in a grouped launch
+    if (threadIdx.x == 0) report_cond(A.use_cond, A.gc, false, A.cond, A.cond_in, true);
+    return;
+  }
   double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += pnorm[b];
+  for (int b = threadIdx.x; b < A.nblk; b += blockDim.x) s += A.pnorm[b];
   s = block_sum(s, sh);
   if (threadIdx.x != 0) return;
   const double rho = sqrt(s);
@@ -1799,10 +2020,7 @@ __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const doub
     ir->done = 1;
     if (!conv) ir->notconv = 1;
     gin->done = 1;
-    if (use_cond) {
-      cudaGraphSetConditional(cond, 0);
-      cudaGraphSetConditional(cond_in, 0);
-    }
+    report_cond(A.use_cond, A.gc, false, A.cond, A.cond_in, true);
     return;
   }
   // Inner target.  The first sweep solves to inner_tol.  A later one asks for the reduction still
@@ -1829,35 +2047,119 @@ __global__ void k_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const doub
   gin->done = 0;
   gin->beta = 1.0;
   gin->hnorm = 1.0;
-  gv_in[0] = 1.0;
-  if (use_cond) {
-    cudaGraphSetConditional(cond, 1);
-    cudaGraphSetConditional(cond_in, 1);
-  }
+  A.gv_in[0] = 1.0;
+  report_cond(A.use_cond, A.gc, true, A.cond, A.cond_in, true);
+}
+
+__device__ __forceinline__ void ir_finish_run(const IRArgs& A, VB) {
+  if (threadIdx.x != 0) return;
+  const IRDev* ir = A.ir;
+  GmresDev* g = A.g;
+  if (A.iters_log) A.iters_log[g->m] = ir->inner_total;
+  if (A.sweeps_log) A.sweeps_log[g->m] = ir->sweep;
+  if (ir->notconv) g->notconv = 1;
+  g->relres = ir->last_rel;
+  g->m += 1;
+}
+
+struct IRInitBody {
+  using Args = IRArgs;
+  static constexpr int kThreads = 32, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { ir_init_run(a, vb); }
+};
+struct IRFirstBody {
+  using Args = IRArgs;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { ir_first_resid_run(a, vb); }
+};
+struct IRControlBody {
+  using Args = IRArgs;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { ir_control_run(a, vb); }
+};
+struct IRFinishBody {
+  using Args = IRArgs;
+  static constexpr int kThreads = 32, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { ir_finish_run(a, vb); }
+};
+
+__global__ void k_ir_init(const IRArgs A) { ir_init_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_ir_first_resid(const IRArgs A) { ir_first_resid_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_ir_control(const IRArgs A) { ir_control_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void k_ir_finish(const IRArgs A) { ir_finish_run(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
+cudaError_t launch_ir_init(IRDev* ir, cudaStream_t st) {
+  IRArgs a{};
+  a.ir = ir;
+  if (tl_rec) return record_launch<IRInitBody>(a, 1, 32, 0);
+  k_ir_init<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_first_resid(IRDev* ir, const double* b, double* r, int64_t n, int x0_zero, cudaStream_t st) {
+  IRArgs a{};
+  a.ir = ir;
+  a.b = b;
+  a.r = r;
+  a.n = n;
+  a.x0_zero = x0_zero;
+  if (tl_rec) return record_launch<IRFirstBody>(a, red_blocks(n), RED_THREADS, 0);
+  k_ir_first_resid<<<red_blocks(n), RED_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ir_control(IRDev* ir, GmresDev* gin, double* gv_in, const double* pnorm, int64_t n,
                               cudaGraphConditionalHandle cond, cudaGraphConditionalHandle cond_in, int use_cond,
-                              cudaStream_t st) {
-  k_ir_control<<<1, 256, 0, st>>>(ir, gin, gv_in, pnorm, red_blocks(n), cond, cond_in, use_cond);
+                              GroupCtl* gc, cudaStream_t st) {
+  IRArgs a{};
+  a.ir = ir;
+  a.gin = gin;
+  a.gv_in = gv_in;
+  a.pnorm = pnorm;
+  a.nblk = red_blocks(n);   // partials of launch_norm_partial(n)
+  a.cond = cond;
+  a.cond_in = cond_in;
+  a.use_cond = use_cond;
+  a.gc = gc;
+  if (tl_rec) return record_launch<IRControlBody>(a, 1, RED_THREADS, 0);
+  k_ir_control<<<1, RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-// v_0 = (float)(r / rho)
 template <typename S>
-__global__ void k_scale_to_f32(const S* __restrict__ r, float* v, int64_t n, const IRDev* __restrict__ ir) {
-  if (ir->done) return;
+struct ScaleF32Args {
+  const S* r;
+  float* v;
+  int64_t n;
+  const IRDev* ir;
+};
+
+template <typename S>
+__device__ __forceinline__ void scale_to_f32_run(const ScaleF32Args<S>& A, VB vb) {
+  if (A.ir->done) return;
   __shared__ double sinv;   // one FP64 division per block
-  if (threadIdx.x == 0) sinv = 1.0 / ir->rho;
+  if (threadIdx.x == 0) sinv = 1.0 / A.ir->rho;
   __syncthreads();
   const double inv = sinv;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[i] = (float)(to_d(r[i]) * inv);
+  for (int64_t i = vb.bid * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)vb.nb * blockDim.x)
+    A.v[i] = (float)(to_d(A.r[i]) * inv);
 }
 
 template <typename S>
+struct ScaleF32Body {
+  using Args = ScaleF32Args<S>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { scale_to_f32_run<S>(a, vb); }
+};
+
+template <typename S>
+__global__ void k_scale_to_f32(const ScaleF32Args<S> A) { scale_to_f32_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
+template <typename S>
 cudaError_t launch_scale_to_f32(const S* r, float* v, int64_t n, const IRDev* ir, cudaStream_t st) {
-  k_scale_to_f32<S><<<red_blocks(n), RED_THREADS, 0, st>>>(r, v, n, ir);
+  const ScaleF32Args<S> a{r, v, n, ir};
+  if (tl_rec) return record_launch<ScaleF32Body<S>>(a, red_blocks(n), RED_THREADS, 0);
+  k_scale_to_f32<S><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_scale_to_f32<double>(const double*, float*, int64_t, const IRDev*, cudaStream_t);
@@ -1872,26 +2174,49 @@ template <> __device__ __forceinline__ void add_to<double>(double& x, double d) 
 template <> __device__ __forceinline__ void add_to<df64>(df64& x, double d) { x = x + from_d<df64>(d); }
 
 template <typename X>
-__global__ void k_update_x(X* x, const float* __restrict__ Z, const double* __restrict__ y, int64_t n,
-                           const GmresDev* __restrict__ gin, IRDev* ir) {
+struct UpdXArgs {
+  X* x;
+  const float* Z;
+  const double* y;
+  int64_t n;
+  const GmresDev* gin;
+  IRDev* ir;
+};
+
+template <typename X>
+__device__ __forceinline__ void update_x_run(const UpdXArgs<X>& A, VB vb) {
   __shared__ double ys[MAX_ITER_CAP];
+  IRDev* ir = A.ir;
   if (ir->done) return;
-  const int k = gin->k;
+  const int k = A.gin->k;
   const double rho = ir->rho;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * y[i];
-  if (blockIdx.x == 0 && threadIdx.x == 0) ir->inner_total += k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * A.y[i];
+  if (vb.bid == 0 && threadIdx.x == 0) ir->inner_total += k;
   __syncthreads();
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n = A.n;
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
     double d = 0.0;
-    for (int i = 0; i < k; ++i) d = fma(ys[i], (double)Z[(int64_t)i * n + idx], d);
-    add_to(x[idx], d);
+    for (int i = 0; i < k; ++i) d = fma(ys[i], (double)A.Z[(int64_t)i * n + idx], d);
+    add_to(A.x[idx], d);
   }
 }
 
 template <typename X>
+struct UpdXBody {
+  using Args = UpdXArgs<X>;
+  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static __device__ __forceinline__ void run(const Args& a, VB vb) { update_x_run<X>(a, vb); }
+};
+
+template <typename X>
+__global__ void k_update_x(const UpdXArgs<X> A) { update_x_run<X>(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+
+template <typename X>
 cudaError_t launch_update_x(X* x, const float* Z, const double* y, int64_t n, const GmresDev* gin, IRDev* ir,
                             cudaStream_t st) {
-  k_update_x<X><<<red_blocks(n), RED_THREADS, 0, st>>>(x, Z, y, n, gin, ir);
+  const UpdXArgs<X> a{x, Z, y, n, gin, ir};
+  if (tl_rec) return record_launch<UpdXBody<X>>(a, red_blocks(n), RED_THREADS, 0);
+  k_update_x<X><<<red_blocks(n), RED_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 template cudaError_t launch_update_x<double>(double*, const float*, const double*, int64_t, const GmresDev*, IRDev*,
@@ -1899,22 +2224,21 @@ template cudaError_t launch_update_x<double>(double*, const float*, const double
 template cudaError_t launch_update_x<df64>(df64*, const float*, const double*, int64_t, const GmresDev*, IRDev*,
                                            cudaStream_t);
 
-__global__ void k_ir_finish(const IRDev* __restrict__ ir, GmresDev* g, int* iters_log, int* sweeps_log) {
-  if (threadIdx.x != 0) return;
-  if (iters_log) iters_log[g->m] = ir->inner_total;
-  if (sweeps_log) sweeps_log[g->m] = ir->sweep;
-  if (ir->notconv) g->notconv = 1;
-  g->relres = ir->last_rel;
-  g->m += 1;
-}
-
 cudaError_t launch_ir_finish(const IRDev* ir, GmresDev* g, int* iters_log, int* sweeps_log, cudaStream_t st) {
-  k_ir_finish<<<1, 32, 0, st>>>(ir, g, iters_log, sweeps_log);
+  IRArgs a{};
+  a.ir = const_cast<IRDev*>(ir);
+  a.g = g;
+  a.iters_log = iters_log;
+  a.sweeps_log = sweeps_log;
+  if (tl_rec) return record_launch<IRFinishBody>(a, 1, 32, 0);
+  k_ir_finish<<<1, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_backsolve(GmresDev* g, const double* H, const double* gv, int ldH, double* y, cudaStream_t st) {
-  k_backsolve<<<1, 32, 0, st>>>(g, H, gv, ldH, y, nullptr);
+  const BacksolveArgs a{g, H, gv, y, nullptr, ldH, 0};
+  if (tl_rec) return record_launch<BacksolveBody>(a, 1, 32, 0);
+  k_backsolve<<<1, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -117,6 +117,17 @@ class tau_stats(C.Structure):
     ]
 
 
+class tau_batch_info(C.Structure):
+    _fields_ = [
+        ("groups", C.c_int),
+        ("grouped_problems", C.c_int),
+        ("branches", C.c_int),
+        ("launches_prologue_epilogue", C.c_int64),
+        ("launches_per_sweep", C.c_int64),
+        ("launches_per_inner_iter", C.c_int64),
+    ]
+
+
 TAU_REQ_QUEUED, TAU_REQ_RUNNING, TAU_REQ_DONE, TAU_REQ_FAILED = 0, 1, 2, 3
 
 
@@ -199,6 +210,7 @@ def lib():
             "tau_batch_step": [P, C.c_int64],
             "tau_batch_sync": [P],
             "tau_batch_destroy": [P],
+            "tau_batch_get_info": [P, C.POINTER(tau_batch_info)],
             "tau_server_create": [C.c_int64, C.c_int, C.c_int, C.POINTER(P)],
             "tau_server_submit": [P, C.POINTER(tau_problem_desc), C.POINTER(tau_field), C.POINTER(tau_field),
                                   C.POINTER(tau_field), C.POINTER(C.c_int64)],
@@ -446,6 +458,12 @@ def tau_batch_step(b: int, count: int = 1):
 
 def tau_batch_sync(b: int, allow_notconv: bool = False):
     return _check(lib().tau_batch_sync(C.c_void_p(b)), (TAU_ENOTCONV,) if allow_notconv else ())
+
+
+def tau_batch_get_info(b: int) -> tau_batch_info:
+    info = tau_batch_info()
+    _check(lib().tau_batch_get_info(C.c_void_p(b), C.byref(info)))
+    return info
 
 
 def tau_batch_destroy(b: int):
