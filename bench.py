@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision/batched/served form measurements")
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5],
+                    help="Poisson arrival rates of the served form, as fractions of its saturation throughput")
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--profile-step", default="", choices=["", "2d_1023_fp64", "3d_255_mixed", "2d_1023_mixed"],
@@ -262,6 +264,56 @@ def measure_steps(wl, precision, warm, timed, stream, dev, method=0, route=(0, 0
     return wl.prob.n_tot * timed / (ms * 1e-3), ms / timed, u, st, its
 
 
+def measured_peaks():
+    """HBM GB/s and dense bf16 TFLOP/s (burst) measured on the GB300s (MEASURED_PEAKS.json,
+    written by the harness), else the recipe's fallback; TF32 is the bf16 figure times the nominal
+    ratio 1.1 / 2.25."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    hbm, bf16, kind = 6800.0, 1900.0, "fallback"
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        hbm, bf16, kind = float(m["hbm_gbs"]), float(m["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        pass
+    return {"hbm_gbs": hbm, "bf16_tflops": bf16, "tf32_tflops": bf16 * 1.1 / 2.25, "kind": kind}
+
+
+def mixed_step_roofline(prob, ms_step, inner_iters, sweeps, tc_dims, resid_bytes):
+    """Roofline of one step of the mixed form against HBM and, where the tensor cores run, the TF32
+    tensor pipe.  Algorithmic bytes per unknown (streaming minimum of each operation, the element
+    size of the form): inner FGMRES iteration j (FP32): matvec 12 (x, e in; y out), tau solve 8,
+    CGS2 16 (j + 1) (the basis read twice), norm and scale 8; per refinement sweep: residual
+    resid_bytes (x, e, b in; r out in the residual's element size), FP32 scaling 12, correction
+    4 k + 16 (k directions, x read and written); next right-hand side from the residual 48.
+    Tensor-pipe FLOPs per element: 2 n_i per DST-I mode product on a tensor-core dimension (two per
+    tau solve), 3 x 2 n_i per split-TF32 Toeplitz product when the matvec runs there."""
+    peaks = measured_peaks()
+    d, N = prob.d, prob.n_tot
+    sweeps = max(1, int(round(sweeps)))
+    k = inner_iters / sweeps
+    cgs = 16.0 * sweeps * (k * (k + 1) / 2.0)
+    per_unknown = inner_iters * (12 + 8 + 8) + cgs + sweeps * (resid_bytes + 12 + 4 * k + 16) + 48
+    bytes_step = per_unknown * N
+    t = ms_step * 1e-3
+    hbm = bytes_step / t / 1e9
+    out = {"bound": "hbm", "bytes_per_step": bytes_step, "achieved_gbs": hbm, "peak_gbs": peaks["hbm_gbs"],
+           "frac_hbm": hbm / peaks["hbm_gbs"], "peak_kind": peaks["kind"],
+           "model": "algorithmic bytes per unknown: inner iteration j 28 + 16(j+1) (FP32), per sweep "
+                    "residual + 12 + 4k + 16, right-hand side 48"}
+    tc_flops = 0.0
+    for i in range(d):
+        if tc_dims & (1 << i):
+            tc_flops += 2 * 2.0 * prob.n[i]
+        if tc_dims & (1 << 8):
+            tc_flops += 3 * 2.0 * prob.n[i]
+    if tc_flops:
+        tf = tc_flops * N * inner_iters / t / 1e12
+        out.update({"tensor_flops_per_step": tc_flops * N * inner_iters, "achieved_tf32_tflops": tf,
+                    "peak_tf32_tflops": peaks["tf32_tflops"], "frac_tensor": tf / peaks["tf32_tflops"]})
+    return out
+
+
 def run_forms(stream, dev):
     """Mixed-precision form against the plain FP64 path: the 3-D 255^3 workload (its own config)
     and the 2-D benchmark workload."""
@@ -316,7 +368,34 @@ def run_forms(stream, dev):
         "rel_diff_vs_dense_route": (torch.linalg.norm(uc - ud) / torch.linalg.norm(ud)).item(),
         "chirp_iters_per_step": float(np.mean(itc)), "dense_iters_per_step": float(np.mean(itd)),
         "steps_compared": 5, "unit": UNIT, "dtype": "f64"}
-    for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 2), ("2d_1023_mixed", W.c2_2d(), 2, 3)]:
+    # the 1-D workload (127 unknowns, M = 32): latency-bound, timed as whole solves (device time of
+    # 32 steps from u^(0), CUDA events; 3 untimed solves, then 20)
+    wl = W.c1_1d()
+    p = tau.Problem(wl, stream=stream.cuda_stream)
+    u0 = np.empty(wl.prob.n_tot)
+    tau.tau_get_solution(p.handle, u0, False)
+    lat = []
+    for r in range(23):
+        tau.tau_set_solution(p.handle, u0, False, 0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tau.tau_step(p.handle, wl.prob.M)
+        b.record(stream)
+        b.synchronize()
+        if r >= 3:
+            lat.append(a.elapsed_time(b))
+    its1 = tau.tau_get_iters(p.handle, wl.prob.M)
+    p.close()
+    lat = np.sort(np.array(lat))
+    out["1d_127_latency"] = {
+        "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_per_solve": wl.prob.M, "solves_timed": len(lat),
+        "solve_ms_p50": float(np.percentile(lat, 50)), "solve_ms_p99": float(np.percentile(lat, 99)),
+        "step_ms_p50": float(np.percentile(lat, 50)) / wl.prob.M,
+        "value": wl.prob.n_tot * wl.prob.M / (float(np.percentile(lat, 50)) * 1e-3),
+        "gmres_iters_per_step": float(np.mean(its1)), "unit": UNIT, "dtype": "f64",
+        "timing": "device time of one 32-step solve from u^(0) (one graph launch per step), CUDA events"}
+    for name, wl, warm, timed in [("3d_255_mixed", W.c3_3d(), 2, 5), ("2d_1023_mixed", W.c2_2d(), 2, 5)]:
         v64, ms64, u64, st64, it64 = measure_steps(wl, tau.TAU_FP64, warm, timed, stream, dev)
         vmx, msmx, umx, stmx, itmx = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev)
         rel = (torch.linalg.norm(umx - u64) / torch.linalg.norm(u64)).item()
@@ -326,8 +405,13 @@ def run_forms(stream, dev):
             vlp, mslp, _, _, _ = measure_steps(wl, tau.TAU_MIXED, warm, timed, stream, dev, tc=tau.TAU_TC_OFF)
             tc_extra = {"line_pass_tau_solve_value": vlp, "line_pass_tau_solve_ms_per_step": mslp,
                         "tensor_core_over_line_pass": vmx / vlp}
+        its_step = float(np.mean(itmx)) if len(itmx) else 0.0
+        sweeps_step = float(stmx.total_sweeps) / max(1, int(stmx.steps_done))
+        resid_bytes = 32   # x, e, b read and r written, 8-byte elements (FP64 or double-float)
         out[name] = {
             "workload": wl.name, "unknowns": wl.prob.n_tot, "steps_compared": warm + timed,
+            "roofline": mixed_step_roofline(wl.prob, msmx, its_step, sweeps_step, int(stmx.tc_dims), resid_bytes),
+            "resid_precision": "double-float" if int(stmx.resid_precision) == tau.TAU_DF64 else "f64",
             "mixed_value": vmx, "mixed_ms_per_step": msmx, "plain_fp64_value": v64, "plain_fp64_ms_per_step": ms64,
             "speedup_vs_plain_fp64": vmx / v64, "rel_err_vs_plain_fp64": rel,
             "mixed_inner_iters_per_step": float(np.mean(itmx)) if len(itmx) else None,
@@ -337,29 +421,6 @@ def run_forms(stream, dev):
                                    "line passes elsewhere; matvec and Arnoldi FP32) + f64 residual/refinement",
         }
     return out
-
-
-def plain_sequential_throughput(wls, stream, dev):
-    """unknowns*steps/s of solving the given problems one after another with the plain FP64 path
-    (each alone, steps of every problem, host waits excluded by CUDA events)."""
-    import torch
-
-    from paper_2404_10221_gb300 import tau
-
-    ms = 0.0
-    work = 0.0
-    for wl in wls:
-        p = tau.Problem(wl, stream=stream.cuda_stream)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        tau.tau_step(p.handle, wl.prob.M)
-        b.record(stream)
-        b.synchronize()
-        ms += a.elapsed_time(b)
-        work += wl.prob.n_tot * wl.prob.M
-        p.close()
-    return work / (ms * 1e-3)
 
 
 def run_batched(args, stream, dev):
@@ -476,14 +537,17 @@ def served_precision(prob) -> int:
 
 
 def run_serving(args, stream, dev):
-    """Continuous batching: saturation throughput (all requests submitted at once) and latency
-    under Poisson arrivals at half that throughput."""
+    """Continuous batching on the serving mix (1-D/2-D/3-D requests, M ~ U[10, 200]): saturation
+    throughput (all requests submitted at once), then Poisson arrivals at fractions of it, with
+    p50/p99 latency (submit -> solution on the host) at each rate.  The plain FP64 baseline is
+    size-matched: every request's plain per-step time (1 warm-up and 2 timed steps alone) times its
+    step count, summed."""
     import random
 
     from paper_2404_10221_gb300 import tau
     from paper_2404_10221_gb300 import workloads as W
 
-    wls = W.serving_mix(args.serve_requests, 20240416)
+    wls = W.serving_mix(args.serve_requests, 20240416, M_range=(10, 200))
     tables = [wl.field_tables() for wl in wls]
     precs = [served_precision(wl.prob) for wl in wls]
     descs = [tau.make_desc(wl.prob, precision=pr) for wl, pr in zip(wls, precs)]
@@ -499,33 +563,49 @@ def run_serving(args, stream, dev):
                 time.sleep(wait)
             ids.append(tau.tau_server_submit(s, d, tb))
         for i in ids:
-            tau.tau_server_wait(s, i, 600.0)
+            tau.tau_server_wait(s, i, 1800.0)
         summ = tau.tau_server_summary(s)
         tau.tau_server_destroy(s)
         return summ
 
+    def line(summ, rate=None):
+        out = {"throughput": summ.throughput, "p50_s": summ.latency_p50_s, "p99_s": summ.latency_p99_s,
+               "mean_s": summ.latency_mean_s, "completed": summ.completed, "failed": summ.failed,
+               "shared_launches": summ.group_launches, "group_rebuilds": summ.group_rebuilds,
+               "request_steps_in_shared_launches": summ.group_request_steps}
+        if rate is not None:
+            out["rate_req_per_s"] = rate
+        return out
+
     sat = run([0.0] * len(wls))
     work = sum(wl.prob.n_tot * wl.prob.M for wl in wls)
-    rate = 0.5 * sat.throughput / (work / len(wls))        # requests per second at half saturation
-    rnd = random.Random(20240416)
-    t = 0.0
-    arr = []
-    for _ in wls:
-        t += rnd.expovariate(rate)
-        arr.append(t)
-    half = run(arr)
-    plain = plain_sequential_throughput(wls[:args.plain_sample], stream, dev)
+    sat_rate = sat.throughput / (work / len(wls))        # requests per second at saturation
+    rates = {}
+    for frac in args.serve_rates:
+        rnd = random.Random(20240416 + int(1000 * frac))
+        t = 0.0
+        arr = []
+        for _ in wls:
+            t += rnd.expovariate(frac * sat_rate)
+            arr.append(t)
+        rates[f"{frac:g}x_saturation"] = line(run(arr), frac * sat_rate)
+    plain_ms = 0.0
+    for wl in wls:
+        _, ms, _, _, _ = measure_steps(wl, tau.TAU_FP64, 1, 2, stream, dev)
+        plain_ms += ms * wl.prob.M
+    plain = work / (plain_ms * 1e-3)
     return {"requests": len(wls), "unknowns_steps_total": work, "unit": UNIT,
-            "saturation": {"throughput": sat.throughput, "p50_s": sat.latency_p50_s, "p99_s": sat.latency_p99_s,
-                           "completed": sat.completed, "failed": sat.failed},
-            "poisson_half_rate": {"rate_req_per_s": rate, "throughput": half.throughput, "p50_s": half.latency_p50_s,
-                                  "p99_s": half.latency_p99_s, "completed": half.completed, "failed": half.failed},
-            "plain_fp64_sequential_value": plain, "plain_sample_requests": args.plain_sample,
+            "saturation": line(sat, sat_rate), "poisson": rates,
+            "plain_fp64_sequential_value": plain,
+            "plain_baseline": "size-matched: every request's plain FP64 per-step time (1 warm-up + 2 timed steps "
+                              "alone) times its step count",
             "speedup_vs_plain_fp64": sat.throughput / plain,
             "mix": "40% 1-D n ~ U[1023,65535]; 45% 2-D n ~ U[127,2047] per axis; 15% 3-D n ~ U[63,255] per axis; "
-                   "M ~ U[10,40]; any n (FFT, chirp, dense and long-line routes); mixed precision where an "
+                   "M ~ U[10,200]; any n (FFT, chirp, dense and long-line routes); mixed precision where an "
                    "FP32 matvec resolves the operator, double-float otherwise; "
                    "latency = submit -> solution on the host",
+            "stream_cap": f"{len(wls)} requests per rate point (the configuration's 10,000-request stream is "
+                          "capped so the run ends within minutes)",
             "requests_mixed": sum(1 for pr in precs if pr == tau.TAU_MIXED),
             "requests_double_float": sum(1 for pr in precs if pr == tau.TAU_DF64)}
 

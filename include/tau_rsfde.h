@@ -96,12 +96,19 @@ typedef int tau_status;
                                  Every route needs one line (the n_i values plus the route's work
                                  row) in at most 200 KB of shared memory: TAU_DF64 (16-byte
                                  elements) fits the chirp route up to n_i = 2047 and the dense
-                                 route up to n_i = 6400; otherwise tau_create returns
+                                 route up to n_i = 4266; otherwise tau_create returns
                                  TAU_EUNSUPPORTED for a forced route */
 #define TAU_ROUTE_LONG 4      /* d = 1 only, any n (automatic from n = 128): the chirp route's
                                  convolutions (length F = 2 K_T, K_T the power of two >= n+1) as
                                  four-step FFTs over global memory, a few launches per operator
                                  instead of one CTA per line; not with TAU_SPGM */
+
+#define TAU_TUNE_AUTO 0       /* measure new choices (and reuse recorded ones) for problems of >= 65536
+                                 unknowns; TAU_AUTOTUNE=1/0 in the environment forces it on/off */
+#define TAU_TUNE_ON 1         /* measure new choices, reuse recorded ones */
+#define TAU_TUNE_OFF 2        /* the rules and heuristics only */
+#define TAU_TUNE_RECORDED 3   /* recorded choices where present (this process, or the autotune file),
+                                 the rules otherwise; nothing is measured (setup stays short) */
 
 typedef struct tau_problem tau_problem;
 
@@ -138,6 +145,9 @@ typedef struct {
                            both ways and keeps the faster of each (cached per grid shape);
                            TAU_TC_OFF (1): line passes; TAU_TC_ON (2): tensor cores wherever
                            n_i <= 256 */
+  int autotune;         /* TAU_TUNE_AUTO (0, default), TAU_TUNE_ON, TAU_TUNE_OFF or TAU_TUNE_RECORDED:
+                           whether tau_setup times the route of each dimension (d >= 2), the lines
+                           per CTA of the line passes and (TAU_TC_AUTO) the tensor-core choice */
 } tau_problem_desc;
 
 /* A field g(x,t) = sum_{r<rank} c_r(t) prod_i phi_{r,i}(x_i) given as tables (host memory,
@@ -366,9 +376,18 @@ tau_status tau_batch_destroy(tau_batch* b);
  * queue.  The worker admits queued requests while the estimated device memory of the admitted
  * ones stays within `device_bytes_budget` and fewer than `max_active` are admitted; each admitted
  * request gets its own stream and a tau_problem whose Krylov basis and solution stay on the
- * device until its last step.  The worker keeps every admitted request's stream fed with
- * `steps_per_launch` steps at a time, so requests that arrive while others run are admitted as
- * memory frees up and their kernels overlap on the GPU.  A finished request's solution u^(M) is
+ * device until its last step.  Admitted TAU_MIXED requests run their inner solve on the line
+ * passes (the server sets tc = TAU_TC_OFF) and, unless the request asks for TAU_TUNE_ON or _OFF,
+ * take the recorded autotuning choices only (TAU_TUNE_RECORDED: admission measures nothing).
+ * Requests of at most 2^20 unknowns of the same kind (d, the residual precision tau_setup chose,
+ * x0_mode; no long-line dimension) batch their iterations together: one step graph
+ * whose kernels are each one launch over all of them (the grouped execution of tau_batch), rebuilt
+ * whenever the set changes, every launch advancing each member by one step.  Larger requests fill
+ * the GPU by themselves and step on their own streams, as do the others.  TAU_BATCH_GROUPS=0 in the
+ * environment at tau_server_create turns the shared launches off.  The worker issues `steps_per_launch` steps at a time (a group: at most the
+ * steps its nearest-to-finish member has left), so requests that arrive while others run are
+ * admitted as memory frees up and join the next group or overlap on the GPU.  A request's result is
+ * the same alone and in the mix (its arithmetic does not depend on the group).  A finished request's solution u^(M) is
  * copied to host memory and its device memory returns to the budget.  A request whose estimate
  * exceeds the whole budget fails at once with TAU_ENOMEM.  All host waits are bounded.
  * Times are seconds since tau_server_create. */
@@ -392,6 +411,9 @@ typedef struct {
   double unknowns_steps;          /* sum of n_tot * M over completed requests */
   double span_s;                  /* first submit -> last completion */
   double throughput;              /* unknowns_steps / span_s */
+  int64_t group_launches;         /* step-graph launches shared by a group of requests */
+  int64_t group_rebuilds;         /* group graphs built (the set of requests changed) */
+  int64_t group_request_steps;    /* request steps taken inside shared launches */
 } tau_server_stats;
 tau_status tau_server_create(int64_t device_bytes_budget, int max_active, int steps_per_launch, tau_server** out);
 tau_status tau_server_submit(tau_server* s, const tau_problem_desc* desc, const tau_field* e, const tau_field* f,

@@ -133,6 +133,8 @@ struct tau_problem {
          *twK2_32[3] = {nullptr, nullptr, nullptr};
   float *s32[3] = {nullptr, nullptr, nullptr}, *sintab32[3] = {nullptr, nullptr, nullptr};
   int64_t k_ir_pre = 0, k_ir_post = 0;         // kernels of one refinement sweep around the inner loop
+  // autotuning of this problem's setup: measure new choices, and/or take recorded ones
+  bool tune_measure = false, tune_records = false;
   int route_src[3] = {0, 0, 0};                 // 0 rule or forced, 1 measured, 2 recorded measurement
   double route_ms[3] = {0, 0, 0}, route_alt_ms[3] = {0, 0, 0};
   int lpb_tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // lines per CTA chosen by the autotuner
@@ -296,7 +298,7 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   else D.lng = &p->lt32[ax];
   // shared memory per line: the line (N reals) plus the transform line (2K reals, FFT route) or a
   // second copy (N, dense route).  24 KB of lines per CTA lets 8 CTAs of 128 threads share an SM.
-  size_t rs = (size_t)P.len;
+  size_t rs = 2 * (size_t)P.len;   // dense route: the line and its outputs
   if (D.route == ROUTE_FFT || D.route == ROUTE_CHIRP) rs = 2 * (size_t)D.K;
   const size_t per_line = sizeof(T) * ((size_t)P.len + rs);
   int64_t lpb = (int64_t)(24576 / per_line);
@@ -1017,6 +1019,7 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
       return TAU_OK;
     }
   }
+  if (!p->tune_measure) return TAU_OK;   // recorded choices only: the heuristic stands
   // representative work: one matvec pass (channels a, c in place) and one DST pass (on c)
   P.seta = 1.0;
   P.in_a = chA;
@@ -1346,6 +1349,7 @@ tau_status choose_tc(tau_problem* p) {
       g_tc_cache[key] = use;
     }
   }
+  if (!cached && !p->tune_measure) return TAU_OK;   // no record and no measurement: tensor cores where n <= 256
   if (!cached) {
     CK(cudaMemsetAsync(p->V32, 0, p->n_tot * sizeof(float), p->st));
     ChainT<float> io;
@@ -1400,6 +1404,7 @@ tau_status choose_tc(tau_problem* p) {
         g_tc_cache[kmv] = use_mv;
       }
     }
+    if (!hit && !p->tune_measure) hit = use_mv = true;   // no record and no measurement: keep it
     if (!hit) {
       CK(cudaMemsetAsync(p->V32, 0, p->n_tot * sizeof(float), p->st));
       ChainT<float> io;
@@ -1531,12 +1536,12 @@ tau_status route_tables(tau_problem* p, int i, const std::vector<double>& s) {
 
 // Whether one line of n values fits the line-pass kernel's 200 KB of shared memory on a route,
 // for elements of esz bytes: the line plus its transform row (2K on the FFT route, 2 rows of 2 K_T
-// on the chirp route, a second copy on the dense route).
+// on the chirp route, the line and its outputs on the dense route).
 bool route_fits(int64_t n, int route, size_t esz) {
   const size_t nn = (size_t)n, npad = (nn + 1) & ~(size_t)1;
   size_t kt = 2;
   while (kt < nn + 1) kt <<= 1;
-  const size_t rs = route == ROUTE_FFT ? 2 * (nn + 1) : (route == ROUTE_CHIRP ? 4 * kt : nn);
+  const size_t rs = route == ROUTE_FFT ? 2 * (nn + 1) : (route == ROUTE_CHIRP ? 4 * kt : 2 * nn);
   return esz * (npad + rs) <= 200 * 1024;
 }
 
@@ -1611,7 +1616,7 @@ tau_status choose_route(tau_problem* p, int i, const std::vector<double>& s, boo
   for (int l = 0; l < i; ++l) inner *= p->n[l];
   const std::string key = "route|" + dev_key() + join_key({p->dfm ? 2 : 0, i, p->n[i], inner, p->n_tot / p->n[i]});
   std::string v;
-  if (tune_get(key, &v)) {
+  if (p->tune_records && tune_get(key, &v)) {
     int r = 0;
     double ms = 0.0, alt = 0.0;
     if (sscanf(v.c_str(), "%d %lf %lf", &r, &ms, &alt) == 3 &&
@@ -1623,6 +1628,7 @@ tau_status choose_route(tau_problem* p, int i, const std::vector<double>& s, boo
       return route_tables(p, i, s);
     }
   }
+  if (!p->tune_measure) return route_tables(p, i, s);   // no record: the rule stands
   CK(cudaMemsetAsync(p->A, 0, p->n_tot * sizeof(double), p->st));
   CK(cudaMemsetAsync(p->C, 0, p->n_tot * sizeof(double), p->st));
   double best = 0.0, alt = 0.0;
@@ -1685,6 +1691,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
   if (D.method != TAU_OPGM && D.method != TAU_TPGM && D.method != TAU_SPGM)
     return fail(TAU_EINVAL, "method %d", D.method);
   if (D.tc != TAU_TC_AUTO && D.tc != TAU_TC_OFF && D.tc != TAU_TC_ON) return fail(TAU_EINVAL, "tc %d", D.tc);
+  if (D.autotune < TAU_TUNE_AUTO || D.autotune > TAU_TUNE_RECORDED) return fail(TAU_EINVAL, "autotune %d", D.autotune);
   if (D.method != TAU_OPGM && D.precision != TAU_FP64)
     return fail(TAU_EUNSUPPORTED, "the two-sided and Strang circulant methods run in TAU_FP64 only");
   if (D.precision == TAU_MIXED &&
@@ -1709,7 +1716,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     const bool fft_ok = is_pow2(K) && K >= 2 && K <= KMAX;
     // shared memory one line of the pass kernel needs on each route (the kernel's dynamic limit is
     // 200 KB): the line plus its transform row (2K on the FFT route, the data then 2 MC reals of
-    // chirp-z work on the chirp route, a second copy on the dense route)
+    // chirp-z work on the chirp route, the line and its outputs on the dense route)
     const size_t esz = D.precision == TAU_DF64 ? 16 : 8;
     const size_t nn = (size_t)D.n[i], npad = (nn + 1) & ~(size_t)1;
     size_t kt = 2, mc = 2;
@@ -1717,7 +1724,7 @@ tau_status tau_create(const tau_problem_desc* desc, void* stream, tau_problem** 
     while (mc < 2 * nn) mc <<= 1;   // chirp route: DST convolution length (2 kt, or kt for n = 2^p)
     // (chirp: rows of 2K_T reals allocated in pairs, so one line takes two rows)
     auto fits = [&](int route) {
-      const size_t rs = route == TAU_ROUTE_FFT ? 2 * (nn + 1) : (route == TAU_ROUTE_CHIRP ? 4 * kt : nn);
+      const size_t rs = route == TAU_ROUTE_FFT ? 2 * (nn + 1) : (route == TAU_ROUTE_CHIRP ? 4 * kt : 2 * nn);
       return esz * (npad + rs) <= 200 * 1024;
     };
     if (r == TAU_ROUTE_AUTO) {
@@ -1896,8 +1903,14 @@ tau_status tau_setup(tau_problem* p) {
   const int d = p->d;
   // measured choices (routes, lines per CTA, tensor cores) for problems of >= 65536 unknowns, or
   // as TAU_AUTOTUNE says (1: always, 0: never; the rules of tau_create and the heuristics stand)
-  const char* tn = std::getenv("TAU_AUTOTUNE");
-  const bool tune = tn ? tn[0] == '1' : p->n_tot >= (1 << 16);
+  if (p->desc.autotune == TAU_TUNE_AUTO) {
+    const char* tn = std::getenv("TAU_AUTOTUNE");
+    p->tune_measure = p->tune_records = tn ? tn[0] == '1' : p->n_tot >= (1 << 16);
+  } else {
+    p->tune_measure = p->desc.autotune == TAU_TUNE_ON;
+    p->tune_records = p->desc.autotune == TAU_TUNE_ON || p->desc.autotune == TAU_TUNE_RECORDED;
+  }
+  const bool tune = p->tune_measure || p->tune_records;
   for (int i = 0; i < d; ++i) {
     const int N = p->n[i], K = N + 1;
     const double a = p->desc.alpha[i];
@@ -2336,19 +2349,37 @@ struct Merged {
   int n;
 };
 
+// Argument tables of a group's launches: staged on the host while the launches are recorded, with
+// their device addresses handed out in advance (dev + offset), and uploaded in one copy when the
+// graph is complete.  A dry run (dev == NULL) only measures the size.
+struct Arena {
+  std::vector<unsigned char> host;
+  char* dev = nullptr;
+  size_t take(size_t bytes) {
+    const size_t off = (host.size() + 15) & ~(size_t)15;
+    host.resize(off + bytes);
+    return off;
+  }
+  void* at(size_t off) const { return dev ? dev + off : nullptr; }
+};
+
 // Grouping applies to the mixed-precision form on the line-pass routes: every problem of a group
 // then enqueues the same sequence of kernels (same d, residual precision and initial guess), which
 // is what lets their launches merge position by position.
 bool groupable(const tau_problem* p) {
-  if (!p->mixed || p->tcm || p->spgm || p->tpgm) return false;
+  if (!p->mixed || p->tcm || p->spgm || p->tpgm || !p->setup_done) return false;
   for (int i = 0; i < p->d; ++i)
     if (p->tc_on[i] || p->route[i] == ROUTE_LONG) return false;
   return true;
 }
 
+std::tuple<int, int, int> group_key(const tau_problem* p) {
+  return std::make_tuple(p->d, p->res_df ? 1 : 0, p->desc.x0_mode);
+}
+
 // Record `fn` for every problem of the group (nothing is launched) and merge the records position
-// by position into grouped launches whose tables are uploaded now (no capture is active).
-tau_status record_merge(tau_batch* b, const std::vector<tau_problem*>& ps,
+// by position into grouped launches whose tables go to the arena.
+tau_status record_merge(Arena& ar, const std::vector<tau_problem*>& ps,
                         const std::function<tau_status(tau_problem*)>& fn, std::vector<Merged>& out) {
   std::vector<std::vector<LaunchRec>> R(ps.size());
   for (size_t i = 0; i < ps.size(); ++i) {
@@ -2359,30 +2390,24 @@ tau_status record_merge(tau_batch* b, const std::vector<tau_problem*>& ps,
   }
   const size_t L = R[0].size();
   for (size_t i = 1; i < ps.size(); ++i)
-    if (R[i].size() != L) return fail(TAU_EUNSUPPORTED, "grouped batch: problems enqueue different kernel sequences");
+    if (R[i].size() != L) return fail(TAU_EUNSUPPORTED, "grouped launches: problems enqueue different kernel sequences");
   const int n = (int)ps.size();
   for (size_t k = 0; k < L; ++k) {
     const LaunchRec& r0 = R[0][k];
     const size_t asz = r0.args.size();
-    std::vector<unsigned char> args(asz * n);
-    std::vector<int> start(n + 1, 0);
+    const size_t oa = ar.take(asz * n), os = ar.take(sizeof(int) * (n + 1));
+    int* start = reinterpret_cast<int*>(ar.host.data() + os);
+    start[0] = 0;
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
       const LaunchRec& r = R[i][k];
       if (r.fn != r0.fn || r.block != r0.block || r.args.size() != asz)
-        return fail(TAU_EUNSUPPORTED, "grouped batch: launch %zu differs between problems", k);
-      memcpy(args.data() + asz * i, r.args.data(), asz);
+        return fail(TAU_EUNSUPPORTED, "grouped launches: launch %zu differs between problems", k);
+      memcpy(ar.host.data() + oa + asz * i, r.args.data(), asz);
       start[i + 1] = start[i] + (int)r.grid;
       smem = std::max(smem, r.smem);
     }
-    const size_t off = (asz * n + 15) & ~(size_t)15;
-    void* d = nullptr;
-    CK(cudaMalloc(&d, off + sizeof(int) * (n + 1)));
-    b->dmem.push_back(d);
-    CK(cudaMemcpy(d, args.data(), asz * n, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(static_cast<char*>(d) + off, start.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-    out.push_back(Merged{r0.fn, (unsigned)start[n], r0.block, smem, d,
-                         reinterpret_cast<int*>(static_cast<char*>(d) + off), n});
+    out.push_back(Merged{r0.fn, (unsigned)start[n], r0.block, smem, ar.at(oa), static_cast<int*>(ar.at(os)), n});
   }
   return TAU_OK;
 }
@@ -2399,50 +2424,89 @@ tau_status launch_merged(const std::vector<Merged>& v, cudaStream_t s) {
   return TAU_OK;
 }
 
-// One branch of the batch graph for a group: the mixed step's graph (prologue -> WHILE(refinement
-// control -> WHILE(FGMRES iteration) -> correction) -> epilogue) with every kernel a grouped launch
-// over the group's problems.  Each loop runs while any problem of the group still iterates; a
-// problem that finished skips its work in the remaining iterations.
-tau_status build_group_inner(tau_batch* b, const std::vector<tau_problem*>& ps, cudaGraph_t G) {
+// The graph of one step for a group: the mixed step (prologue -> WHILE(refinement control ->
+// WHILE(FGMRES iteration) -> correction) -> epilogue) with every kernel a grouped launch over the
+// group's problems.  Each loop runs while any problem of the group still iterates; a problem that
+// finished skips its work in the remaining iterations.  The problems may stand at different steps
+// (each reads its own m on the device).  With ar.dev == NULL nothing is captured (dry run).
+struct GroupCounts {
+  int64_t pro_epi = 0, sweep = 0, inner = 0;
+};
+
+tau_status build_group_inner(Arena& ar, const std::vector<tau_problem*>& ps, cudaGraph_t G, GroupCounts* cnt) {
   tau_problem* p0 = ps[0];
-  GroupCtl* gc = nullptr;
-  CK(cudaMalloc(&gc, 2 * sizeof(GroupCtl)));
-  b->dmem.push_back(gc);
-  const GroupCtl init[2] = {{0u, 0, (int)ps.size(), 0}, {0u, 0, (int)ps.size(), 0}};
-  CK(cudaMemcpy(gc, init, sizeof(init), cudaMemcpyHostToDevice));
-  for (tau_problem* p : ps) p->gctl = gc;
+  const bool dry = ar.dev == nullptr;
+  // the group's loop-condition aggregators, at the start of the arena
+  const size_t ogc = ar.take(2 * sizeof(GroupCtl));
+  GroupCtl* gc_host = reinterpret_cast<GroupCtl*>(ar.host.data() + ogc);
+  for (int k = 0; k < 2; ++k) gc_host[k] = GroupCtl{0u, 0, (int)ps.size(), 0};
+  for (tau_problem* p : ps) p->gctl = static_cast<GroupCtl*>(ar.at(ogc));
   auto done = [&](tau_status s) {
     for (tau_problem* p : ps) p->gctl = nullptr;
     return s;
   };
   std::vector<Merged> pro, pre, inner, post, epi;
   std::vector<cudaGraphNode_t> none, leaves, preL, tmp;
-  tau_status s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_prologue(p, p->cap); }, pro);
-  if (s == TAU_OK) s = capture_into(p0, G, none, [&](cudaStream_t st) { return launch_merged(pro, st); }, leaves);
   cudaGraphConditionalHandle ho = 0, hi = 0;
   cudaGraphNode_t wo = nullptr, wi = nullptr;
   cudaGraph_t bo = nullptr, bi = nullptr;
-  if (s == TAU_OK) s = make_handle(G, &ho);
-  if (s == TAU_OK) s = add_while(G, leaves, &ho, &wo, &bo);
-  if (s == TAU_OK) s = make_handle(bo, &hi);
+  tau_status s = record_merge(ar, ps, [&](tau_problem* p) { return enq_mx_prologue(p, p->cap); }, pro);
+  if (s == TAU_OK && !dry)
+    s = capture_into(p0, G, none, [&](cudaStream_t st) { return launch_merged(pro, st); }, leaves);
+  if (s == TAU_OK && !dry) s = make_handle(G, &ho);
+  if (s == TAU_OK && !dry) s = add_while(G, leaves, &ho, &wo, &bo);
+  if (s == TAU_OK && !dry) s = make_handle(bo, &hi);
   if (s == TAU_OK)
-    s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_sweep_pre(p, p->cap, ho, hi, 2); }, pre);
-  if (s == TAU_OK) s = capture_into(p0, bo, none, [&](cudaStream_t st) { return launch_merged(pre, st); }, preL);
-  if (s == TAU_OK) s = add_while(bo, preL, &hi, &wi, &bi);
-  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_inner(p, p->cap, hi, 2); }, inner);
-  if (s == TAU_OK) s = capture_into(p0, bi, none, [&](cudaStream_t st) { return launch_merged(inner, st); }, tmp);
-  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_sweep_post(p, p->cap); }, post);
-  if (s == TAU_OK) s = capture_into(p0, bo, {wi}, [&](cudaStream_t st) { return launch_merged(post, st); }, tmp);
-  if (s == TAU_OK) s = record_merge(b, ps, [&](tau_problem* p) { return enq_mx_epilogue(p, p->cap); }, epi);
-  if (s == TAU_OK) s = capture_into(p0, G, {wo}, [&](cudaStream_t st) { return launch_merged(epi, st); }, tmp);
-  if (s == TAU_OK) {
-    b->info.groups += 1;
-    b->info.grouped_problems += (int)ps.size();
-    b->info.launches_prologue_epilogue += (int64_t)(pro.size() + epi.size());
-    b->info.launches_per_sweep += (int64_t)(pre.size() + post.size());
-    b->info.launches_per_inner_iter += (int64_t)inner.size();
+    s = record_merge(ar, ps, [&](tau_problem* p) { return enq_mx_sweep_pre(p, p->cap, ho, hi, 2); }, pre);
+  if (s == TAU_OK && !dry)
+    s = capture_into(p0, bo, none, [&](cudaStream_t st) { return launch_merged(pre, st); }, preL);
+  if (s == TAU_OK && !dry) s = add_while(bo, preL, &hi, &wi, &bi);
+  if (s == TAU_OK) s = record_merge(ar, ps, [&](tau_problem* p) { return enq_mx_inner(p, p->cap, hi, 2); }, inner);
+  if (s == TAU_OK && !dry)
+    s = capture_into(p0, bi, none, [&](cudaStream_t st) { return launch_merged(inner, st); }, tmp);
+  if (s == TAU_OK) s = record_merge(ar, ps, [&](tau_problem* p) { return enq_mx_sweep_post(p, p->cap); }, post);
+  if (s == TAU_OK && !dry)
+    s = capture_into(p0, bo, {wi}, [&](cudaStream_t st) { return launch_merged(post, st); }, tmp);
+  if (s == TAU_OK) s = record_merge(ar, ps, [&](tau_problem* p) { return enq_mx_epilogue(p, p->cap); }, epi);
+  if (s == TAU_OK && !dry)
+    s = capture_into(p0, G, {wo}, [&](cudaStream_t st) { return launch_merged(epi, st); }, tmp);
+  if (s == TAU_OK && cnt) {
+    cnt->pro_epi = (int64_t)(pro.size() + epi.size());
+    cnt->sweep = (int64_t)(pre.size() + post.size());
+    cnt->inner = (int64_t)inner.size();
   }
   return done(s);
+}
+
+// Build a group's branch into G: a dry run sizes the argument tables, one allocation holds them
+// (returned in *dev, owned by the caller; with pool_cap non-null, *dev is a buffer of *pool_cap
+// bytes to reuse when large enough, otherwise it is replaced by a larger one), the real run records
+// and captures, one copy uploads.
+tau_status add_group_branch(const std::vector<tau_problem*>& ps, cudaGraph_t G, void** dev, GroupCounts* cnt,
+                            size_t* pool_cap = nullptr) {
+  Arena dry;
+  TRY(build_group_inner(dry, ps, G, nullptr));
+  Arena ar;
+  const size_t need = dry.host.size() + 16;
+  if (pool_cap && *dev && *pool_cap >= need) {
+    ar.dev = static_cast<char*>(*dev);
+  } else {
+    if (pool_cap && *dev) {
+      cudaFree(*dev);   // waits for the device: only when the tables outgrow the buffer
+      *dev = nullptr;
+      *pool_cap = 0;
+    }
+    const size_t cap = pool_cap ? need + need / 2 : need;
+    *dev = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void**>(&ar.dev), cap));
+    if (pool_cap) *pool_cap = cap;
+  }
+  *dev = ar.dev;
+  ar.host.reserve(dry.host.size());
+  TRY(build_group_inner(ar, ps, G, cnt));
+  if (ar.host.size() > dry.host.size()) return fail(TAU_EUNSUPPORTED, "grouped launches: table size changed");
+  CK(cudaMemcpy(ar.dev, ar.host.data(), ar.host.size(), cudaMemcpyHostToDevice));
+  return TAU_OK;
 }
 
 }  // namespace
@@ -2473,7 +2537,7 @@ tau_status tau_batch_create(tau_problem* const* problems, int count, void* strea
   std::map<std::tuple<int, int, int>, std::vector<tau_problem*>> groups;
   std::vector<tau_problem*> single;
   for (tau_problem* p : b->probs) {
-    if (grouping && groupable(p)) groups[std::make_tuple(p->d, p->res_df ? 1 : 0, p->desc.x0_mode)].push_back(p);
+    if (grouping && groupable(p)) groups[group_key(p)].push_back(p);
     else single.push_back(p);
   }
   tau_status st = TAU_OK;
@@ -2482,7 +2546,18 @@ tau_status tau_batch_create(tau_problem* const* problems, int count, void* strea
       single.push_back(kv.second[0]);
       continue;
     }
-    if (st == TAU_OK) st = build_group_inner(b, kv.second, G);
+    if (st != TAU_OK) continue;
+    void* dev = nullptr;   // owned by the batch
+    GroupCounts cnt;
+    st = add_group_branch(kv.second, G, &dev, &cnt);
+    if (dev) b->dmem.push_back(dev);
+    if (st == TAU_OK) {
+      b->info.groups += 1;
+      b->info.grouped_problems += (int)kv.second.size();
+      b->info.launches_prologue_epilogue += cnt.pro_epi;
+      b->info.launches_per_sweep += cnt.sweep;
+      b->info.launches_per_inner_iter += cnt.inner;
+    }
   }
   for (size_t i = 0; i < single.size() && st == TAU_OK; ++i) {
     st = build_graph_inner(single[i], G);
@@ -2505,6 +2580,74 @@ tau_status tau_batch_create(tau_problem* const* problems, int count, void* strea
   *out = b;
   return TAU_OK;
 }
+
+}  // extern "C"
+
+// ---- grouped steps for the serving loop (tau_serve.cu): problems that may stand at different
+// steps, each advanced by one step per launch of the group's graph
+namespace tau {
+
+struct GroupExec {
+  std::vector<tau_problem*> ps;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// Groupable problems and the key of their group (-1: not groupable).
+int64_t problem_group_key(const tau_problem* p) {
+  if (!groupable(p)) return -1;
+  const auto k = group_key(p);
+  return (int64_t)std::get<0>(k) * 16 + std::get<1>(k) * 4 + std::get<2>(k);
+}
+
+// pool/pool_cap: the caller's argument-table buffer, reused (or replaced by a larger one); the
+// caller keeps it past group_exec_destroy and frees it once no launch of the group can run.
+tau_status group_exec_create(tau_problem* const* ps, int n, GroupExec** out, void** pool, size_t* pool_cap) {
+  *out = nullptr;
+  GroupExec* g = new (std::nothrow) GroupExec();
+  if (!g) return fail(TAU_ENOMEM, "host allocation");
+  g->ps.assign(ps, ps + n);
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) {
+    delete g;
+    return fail(TAU_ECUDA, "cudaGraphCreate");
+  }
+  GroupCounts cnt;
+  tau_status st = add_group_branch(g->ps, G, pool, &cnt, pool_cap);
+  if (st == TAU_OK && cudaGraphInstantiate(&g->exec, G, 0) != cudaSuccess) {
+    cudaGetLastError();
+    st = fail(TAU_EUNSUPPORTED, "group graph instantiation");
+  }
+  cudaGraphDestroy(G);
+  if (st != TAU_OK) {
+    delete g;
+    return st;
+  }
+  *out = g;
+  return TAU_OK;
+}
+
+tau_status group_exec_launch(GroupExec* g, int64_t count, cudaStream_t st) {
+  for (tau_problem* p : g->ps)
+    if (p->m_host + count > p->desc.M) return fail(TAU_EINVAL, "group step past a member's last step");
+  for (int64_t c = 0; c < count; ++c) CK(cudaGraphLaunch(g->exec, st));
+  for (tau_problem* p : g->ps) {
+    p->m_host += count;
+    p->fields_m = -1;
+  }
+  return TAU_OK;
+}
+
+// The group's graph is freed (launches already enqueued still run); the argument tables stay
+// with the caller.
+void group_exec_destroy(GroupExec* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+}
+
+}  // namespace tau
+
+extern "C" {
 
 tau_status tau_batch_get_info(tau_batch* b, tau_batch_info* info) {
   if (!b || !info) return fail(TAU_EINVAL, "NULL argument");

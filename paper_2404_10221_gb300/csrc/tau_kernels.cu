@@ -284,6 +284,17 @@ __device__ __forceinline__ T stencil_B(const T* row, int j, int N, T bd, T bo) {
 // ---------------------------------------------------------------------------
 // per-line transforms on shared memory
 // ---------------------------------------------------------------------------
+// Dense-route transforms read the whole line for every output: they write their outputs to the
+// second half of each row (row stride 2N) and this copies them back over the input after a barrier.
+template <typename T>
+__device__ __forceinline__ void dense_copy_back(T* xs, int xst, int lpb, int N) {
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < lpb * N; idx += blockDim.x) {
+    const int l = idx / N;
+    xs[l * xst + idx - l * N] = xs[l * xst + N + idx - l * N];
+  }
+  __syncthreads();
+}
 // Toeplitz product T x in place for every line: x_j at xs[l*xst + j].  FFT route: xst = 2K and
 // the line's 2K reals are the packed complex sequence z_j = (y_2j, y_2j+1) of the zero-padded
 // y (y_t = x_t for t < N, 0 otherwise), so packing is only y_N = 0 (the upper half is zero by
@@ -321,36 +332,19 @@ __device__ void toeplitz_lines(const PassT<T>& P, T* xs, int xst) {
       fft_dit<true>(cb, cs, lpb, K, P.dim.twK, true);
     }
   } else {
+    // dense: (T x)_a = sum_b s_|a-b| x_b.  Every output reads the whole line, so the outputs go to
+    // the second half of the row (xst = 2N) and are copied back once all of them are computed.
     const T* __restrict__ s = P.dim.s;
-    T acc[8];
     const T z0 = from_f<T>(0.0f);
-    // dense: (T x)_a = sum_b s_|a-b| x_b; each thread accumulates its outputs in registers first
-    // and writes them after a barrier (in place).
     const int tot = lpb * N;
-    for (int base = 0; base < tot; base += 8 * TH) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * TH + tid;
-        acc[r] = z0;
-        if (idx < tot) {
-          const int l = idx / N, a = idx - l * N;
-          const T* row = xs + l * xst;
-          T sacc = z0;
-          for (int bb = 0; bb < N; ++bb) sacc = tfma(s[abs(a - bb)], row[bb], sacc);
-          acc[r] = sacc;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * TH + tid;
-        if (idx < tot) {
-          const int l = idx / N;
-          xs[l * xst + idx - l * N] = acc[r];
-        }
-      }
-      __syncthreads();
+    for (int idx = tid; idx < tot; idx += TH) {
+      const int l = idx / N, a = idx - l * N;
+      const T* row = xs + l * xst;
+      T sacc = z0;
+      for (int bb = 0; bb < N; ++bb) sacc = tfma(s[abs(a - bb)], row[bb], sacc);
+      xs[l * xst + N + a] = sacc;
     }
+    dense_copy_back(xs, xst, lpb, N);
   }
 }
 
@@ -363,37 +357,20 @@ __device__ void hartley_lines(const PassT<T>& P, T* xs, int xst) {
   const int TH = blockDim.x, tid = threadIdx.x;
   const T* __restrict__ ct = P.dim.cas;
   const T z0 = from_f<T>(0.0f);
-  T acc[8];
   const int tot = lpb * N;
-  for (int base = 0; base < tot; base += 8 * TH) {
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int idx = base + r * TH + tid;
-      acc[r] = z0;
-      if (idx < tot) {
-        const int l = idx / N, k = idx - l * N;
-        const T* row = xs + l * xst;
-        T sacc = z0;
-        int ph = 0;  // (j * k) mod N
-        for (int j = 0; j < N; ++j) {
-          sacc = tfma(ct[ph], row[j], sacc);
-          ph += k;
-          if (ph >= N) ph -= N;
-        }
-        acc[r] = sacc;
-      }
+  for (int idx = tid; idx < tot; idx += TH) {
+    const int l = idx / N, k = idx - l * N;
+    const T* row = xs + l * xst;
+    T sacc = z0;
+    int ph = 0;  // (j * k) mod N
+    for (int j = 0; j < N; ++j) {
+      sacc = tfma(ct[ph], row[j], sacc);
+      ph += k;
+      if (ph >= N) ph -= N;
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int idx = base + r * TH + tid;
-      if (idx < tot) {
-        const int l = idx / N;
-        xs[l * xst + idx - l * N] = acc[r];
-      }
-    }
-    __syncthreads();
+    xs[l * xst + N + k] = sacc;
   }
+  dense_copy_back(xs, xst, lpb, N);
 }
 
 // Prefix sums over the even slots of each line of the DST recombination:
@@ -730,37 +707,20 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst, T* scr) {
     const T* __restrict__ st = P.dim.sintab;
     const T sc = P.dim.dsc;   // sqrt(2/K), precomputed per dimension
     const T z0 = from_f<T>(0.0f);
-    T acc[8];
     const int tot = lpb * N;
-    for (int base = 0; base < tot; base += 8 * TH) {
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * TH + tid;
-        acc[r] = z0;
-        if (idx < tot) {
-          const int l = idx / N, k = idx - l * N + 1;
-          const T* row = xs + l * xst;
-          T sacc = z0;
-          int ph = k;  // (j * k) mod 2K for j = 1
-          for (int j = 1; j <= N; ++j) {
-            sacc = tfma(st[ph], row[j - 1], sacc);
-            ph += k;
-            if (ph >= 2 * K) ph -= 2 * K;
-          }
-          acc[r] = sc * sacc;
-        }
+    for (int idx = tid; idx < tot; idx += TH) {
+      const int l = idx / N, k = idx - l * N + 1;
+      const T* row = xs + l * xst;
+      T sacc = z0;
+      int ph = k;  // (j * k) mod 2K for j = 1
+      for (int j = 1; j <= N; ++j) {
+        sacc = tfma(st[ph], row[j - 1], sacc);
+        ph += k;
+        if (ph >= 2 * K) ph -= 2 * K;
       }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int idx = base + r * TH + tid;
-        if (idx < tot) {
-          const int l = idx / N;
-          xs[l * xst + idx - l * N] = acc[r];
-        }
-      }
-      __syncthreads();
+      xs[l * xst + N + k - 1] = sc * sacc;
     }
+    dense_copy_back(xs, xst, lpb, N);
   }
 }
 
@@ -769,12 +729,12 @@ __device__ void dst_lines(const PassT<T>& P, T* xs, int xst, T* scr) {
 // ---------------------------------------------------------------------------
 // Shared memory: ra (lpb*N reals, rounded up to even) then rc (lpb lines of rs reals; rs = 2K on
 // the FFT and chirp routes, whose transforms run in place in the padded line (the chirp route
-// allocates its rows in pairs), rs = N on the dense route).
+// allocates its rows in pairs), rs = 2N on the dense route: the line, then its outputs).
 template <typename T>
 __device__ __forceinline__ int rc_stride(const PassT<T>& P) {
   if (P.dim.route == ROUTE_FFT) return 2 * P.dim.K;
   if (P.dim.route == ROUTE_CHIRP) return 2 * P.dim.K;   // K: the power of two >= n + 1
-  return P.len;
+  return 2 * P.len;   // dense: the line, then its outputs (dense_copy_back)
 }
 
 // Resident CTAs of 128 threads per SM the register budget allows: 7 for FP64 (72 registers; a
@@ -938,7 +898,7 @@ __global__ void __launch_bounds__(PASS_THREADS) k_ht_pass(const PassT<T> P) {
 template <typename T>
 size_t pass_smem_bytes(const PassT<T>& p) {
   const size_t ra = ((size_t)p.lpb * p.len + 1) & ~(size_t)1;
-  size_t rs = (size_t)p.len;
+  size_t rs = 2 * (size_t)p.len;   // dense: the line and its outputs
   if (p.dim.route == ROUTE_FFT) rs = 2 * (size_t)p.dim.K;
   size_t rows = (size_t)p.lpb;
   if (p.dim.route == ROUTE_CHIRP) {   // rows in pairs: a pair's two rows are its DST buffer
@@ -2026,14 +1986,17 @@ __device__ __forceinline__ void ir_control_run(const IRArgs& A, VB) {
   // Inner target.  The first sweep solves to inner_tol.  A later one asks for the reduction still
   // needed, with a factor 0.3 of margin, need = 0.3 rho0 tol / rho, within [1e-6, 0.5] (an FP32
   // solve cannot resolve much below 1e-6 of its right-hand side).  It never asks for much less than
-  // the floor the last sweep ran into: when the last correction reduced the residual by a factor
-  // red well above its inner target (the FP32 operator's own error then limits every sweep), a
-  // tighter inner solve costs iterations and buys nothing, so the target is at least red / 2.
+  // the floor the last sweep ran into: when the last inner solve met its target but the correction
+  // reduced the residual by a factor red well above that target (the FP32 operator's own error
+  // then limits every sweep), a tighter inner solve costs iterations and buys nothing, so the
+  // target is at least red / 2.  (An inner solve stopped by its iteration cap says nothing about
+  // that floor.)
   double itol = ir->inner_tol;
   if (ir->sweep > 0) {
     const double need = 0.3 * ir->tol * ir->rho0 / rho;
     const double red = ir->rho_prev > 0.0 ? rho / ir->rho_prev : 0.0;
-    const double floor_hit = red > 2.0 * ir->itol_prev ? 0.5 * red : 0.0;
+    const bool met = gin->relres <= 1.0001 * ir->itol_prev;
+    const double floor_hit = met && red > 2.0 * ir->itol_prev ? 0.5 * red : 0.0;
     itol = need > floor_hit ? need : floor_hit;
     if (itol < 1e-6) itol = 1e-6;
     if (itol > 0.5) itol = 0.5;

@@ -181,7 +181,7 @@ extern "C" tau_status tau_apply_A_noalloc(const tau_problem_desc* desc, const do
     P.inner = inner;
     P.nlines = n_tot / P.len;
     P.dim = dims[ax];
-    const size_t per_line = 8 * ((size_t)P.len + (P.dim.route == ROUTE_FFT ? 2 * (size_t)P.dim.K : (size_t)P.len));
+    const size_t per_line = 8 * ((size_t)P.len + (P.dim.route == ROUTE_FFT ? 2 * (size_t)P.dim.K : 2 * (size_t)P.len));
     int64_t lpb = (int64_t)(24576 / per_line);
     if (lpb < 1) lpb = 1;
     if (lpb > 16) lpb = 16;

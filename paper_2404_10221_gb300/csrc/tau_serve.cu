@@ -4,10 +4,15 @@
 // budget and the active-slot limit admit them; an admitted request gets its own stream and a
 // tau_problem whose Krylov basis and solution stay on the device until its last step.  Every
 // pass of the loop harvests finished requests (memory returns to the budget), admits waiting ones,
-// and enqueues the next steps of every admitted request whose previous launch has completed, so
-// requests that arrive while others run join the mix and their kernels overlap on the GPU.
-// Host-side waits are bounded (condition variable with a timeout); the device is never polled in a
-// spin loop.
+// and enqueues the next steps of the admitted requests.  Admitted mixed-precision requests of the
+// same kind (d, residual precision, initial guess; line-pass routes, which the server selects for
+// them) share their steps: one graph whose every kernel is a single launch over all of them
+// (tau_batch's grouped execution), rebuilt when the set changes, each launch advancing every
+// member by one step whatever step it stands at.  Other requests step on their own streams.
+// Requests that arrive while others run join the next group or overlap on the GPU.  A request's
+// last enqueued work is marked by its event, on whichever stream it ran, and every stream waits
+// for a request's event before stepping it.  Host-side waits are bounded (condition variable with
+// a timeout); the device is never polled in a spin loop.
 #include "tau_rsfde.h"
 #include "tau_internal.cuh"
 
@@ -16,8 +21,10 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -25,9 +32,32 @@
 #include <unordered_map>
 #include <vector>
 
+namespace tau {
+struct GroupExec;
+int64_t problem_group_key(const tau_problem* p);
+tau_status group_exec_create(tau_problem* const* ps, int n, GroupExec** out, void** pool, size_t* pool_cap);
+tau_status group_exec_launch(GroupExec* g, int64_t count, cudaStream_t st);
+void group_exec_destroy(GroupExec* g);
+}  // namespace tau
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// A group of admitted requests stepping together, its stream, and the event of its last launch.
+struct Group {
+  tau::GroupExec* ge = nullptr;
+  std::vector<int64_t> ids;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  void* tables = nullptr;   // argument tables of the group's launches, reused across rebuilds
+  size_t tables_cap = 0;
+};
+
+// Requests up to this many unknowns share launches: below it a request's own kernels leave much of
+// the GPU idle (launch- and latency-bound); above it they fill the GPU by themselves.
+constexpr int64_t GROUP_MAX_UNKNOWNS = (int64_t)1 << 20;
 
 struct Req {
   int64_t id = 0;
@@ -68,6 +98,9 @@ struct tau_server {
   Clock::time_point t0;
   std::atomic<bool> stop{false};
   std::thread worker;
+  std::map<int64_t, Group> groups;   // by group key (worker thread only)
+  bool grouping = true;              // TAU_BATCH_GROUPS=0 at creation: every request steps alone
+  int64_t group_launches = 0, group_rebuilds = 0, group_steps = 0;
 };
 
 namespace {
@@ -116,8 +149,13 @@ void finish(tau_server* s, const std::shared_ptr<Req>& r, tau_status st, const c
   }
 }
 
-// Create, fill and set up the request's problem on its own stream (worker thread).
+// Create, fill and set up the request's problem on its own stream (worker thread).  Mixed-precision
+// requests run their inner solve on the line passes (TAU_TC_OFF), whose kernels can be grouped.
 tau_status admit(const std::shared_ptr<Req>& r) {
+  if (r->desc.precision == TAU_MIXED) r->desc.tc = TAU_TC_OFF;
+  // admission runs on the worker thread, between the launches that keep the GPU busy: no timing
+  // runs unless the request asks for them; recorded choices still apply
+  if (r->desc.autotune == TAU_TUNE_AUTO) r->desc.autotune = TAU_TUNE_RECORDED;
   if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
     return TAU_ECUDA;
@@ -206,24 +244,90 @@ void worker_loop(tau_server* s) {
       }
       progress = true;
     }
-    // 3. keep every admitted request's stream fed with steps
+    // 3. steps: groups of mixed requests share launches; the others step on their own streams
     {
       std::lock_guard<std::mutex> lk(s->mu);
       act = s->active;
     }
+    std::map<int64_t, std::vector<std::shared_ptr<Req>>> members;
+    std::vector<std::shared_ptr<Req>> alone;
     for (auto& r : act) {
       if (r->launched >= r->desc.M) continue;
+      const int64_t key = s->grouping && r->n_tot <= GROUP_MAX_UNKNOWNS ? tau::problem_group_key(r->p) : -1;
+      if (key >= 0) members[key].push_back(r);
+      else alone.push_back(r);
+    }
+    for (auto& kv : members)
+      if (kv.second.size() < 2) {
+        alone.push_back(kv.second[0]);
+        kv.second.clear();
+      }
+    auto fail_req = [&](const std::shared_ptr<Req>& r, tau_status st) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, r, st, tau_last_error());
+      s->used -= r->bytes_est;
+      s->failed++;
+      s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+      s->cv.notify_all();
+    };
+    for (auto& kv : s->groups) {   // groups whose launches completed
+      Group& G = kv.second;
+      if (G.busy && cudaEventQuery(G.ev) == cudaSuccess) G.busy = false;
+    }
+    for (auto& kv : members) {
+      auto& mem = kv.second;
+      if (mem.empty()) continue;
+      Group& G = s->groups[kv.first];
+      if (G.busy) continue;   // its last launch is still running
+      std::vector<int64_t> ids;
+      for (auto& r : mem) ids.push_back(r->id);
+      if (ids != G.ids || !G.ge) {   // the set changed: a new graph for the new set
+        tau::group_exec_destroy(G.ge);
+        G.ge = nullptr;
+        G.ids.clear();
+        if (!G.st && (cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking) != cudaSuccess ||
+                      cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming) != cudaSuccess)) {
+          for (auto& r : mem) fail_req(r, TAU_ECUDA);
+          continue;
+        }
+        std::vector<tau_problem*> ps;
+        for (auto& r : mem) ps.push_back(r->p);
+        const tau_status st = tau::group_exec_create(ps.data(), (int)ps.size(), &G.ge, &G.tables, &G.tables_cap);
+        if (st != TAU_OK) {   // step them alone instead
+          for (auto& r : mem) alone.push_back(r);
+          continue;
+        }
+        G.ids = ids;
+        s->group_rebuilds++;
+      }
+      int64_t c = s->chunk;
+      for (auto& r : mem) c = std::min<int64_t>(c, r->desc.M - r->launched);
+      cudaError_t e = cudaSuccess;
+      for (auto& r : mem)
+        if (e == cudaSuccess && r->launched > 0) e = cudaStreamWaitEvent(G.st, r->ev, 0);
+      tau_status st = e == cudaSuccess ? tau::group_exec_launch(G.ge, c, G.st) : TAU_ECUDA;
+      for (auto& r : mem)
+        if (st == TAU_OK && cudaEventRecord(r->ev, G.st) != cudaSuccess) st = TAU_ECUDA;
+      if (st == TAU_OK && cudaEventRecord(G.ev, G.st) != cudaSuccess) st = TAU_ECUDA;
+      if (st != TAU_OK) {
+        for (auto& r : mem) fail_req(r, st);
+        continue;
+      }
+      G.busy = true;
+      s->group_launches += c;
+      s->group_steps += c * (int64_t)mem.size();
+      for (auto& r : mem) r->launched += c;
+      progress = true;
+    }
+    for (auto& r : alone) {
       if (r->launched > 0 && cudaEventQuery(r->ev) != cudaSuccess) continue;
       const int64_t c = std::min<int64_t>(s->chunk, r->desc.M - r->launched);
-      tau_status st = tau_step(r->p, c);
+      tau_status st = TAU_OK;
+      if (r->launched > 0 && cudaStreamWaitEvent(r->st, r->ev, 0) != cudaSuccess) st = TAU_ECUDA;
+      if (st == TAU_OK) st = tau_step(r->p, c);
       if (st == TAU_OK && cudaEventRecord(r->ev, r->st) != cudaSuccess) st = TAU_ECUDA;
       if (st != TAU_OK) {
-        std::lock_guard<std::mutex> lk(s->mu);
-        finish(s, r, st, tau_last_error());
-        s->used -= r->bytes_est;
-        s->failed++;
-        s->active.erase(std::find(s->active.begin(), s->active.end(), r));
-        s->cv.notify_all();
+        fail_req(r, st);
         continue;
       }
       r->launched += c;
@@ -235,6 +339,13 @@ void worker_loop(tau_server* s) {
       idle = s->queue.empty() && s->active.empty();
       if (s->stop && idle) break;
     }
+    if (idle)
+      for (auto& kv : s->groups) {   // nothing runs: free the groups' graphs
+        tau::group_exec_destroy(kv.second.ge);
+        kv.second.ge = nullptr;
+        kv.second.ids.clear();
+        kv.second.busy = false;
+      }
     if (!progress) {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv.wait_for(lk, std::chrono::microseconds(idle ? 2000 : 50));
@@ -260,6 +371,8 @@ tau_status tau_server_create(int64_t device_bytes_budget, int max_active, int st
   s->max_active = max_active;
   s->chunk = steps_per_launch;
   s->t0 = Clock::now();
+  const char* ge = std::getenv("TAU_BATCH_GROUPS");
+  s->grouping = !(ge && ge[0] == '0');
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     delete s;
     return sfail("tau_server_create: no CUDA device");
@@ -404,6 +517,9 @@ tau_status tau_server_summary(tau_server* s, tau_server_stats* out) {
     out->latency_mean_s = sum / (double)l.size();
   }
   out->unknowns_steps = s->unk_steps;
+  out->group_launches = s->group_launches;
+  out->group_rebuilds = s->group_rebuilds;
+  out->group_request_steps = s->group_steps;
   out->span_s = s->t_first >= 0 ? s->t_last - s->t_first : 0.0;
   out->throughput = out->span_s > 0 ? s->unk_steps / out->span_s : 0.0;
   return TAU_OK;
@@ -424,6 +540,13 @@ tau_status tau_server_destroy(tau_server* s) {
     s->cv.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
+  for (auto& kv : s->groups) {
+    tau::group_exec_destroy(kv.second.ge);
+    if (kv.second.st) cudaStreamSynchronize(kv.second.st);
+    if (kv.second.tables) cudaFree(kv.second.tables);
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    if (kv.second.st) cudaStreamDestroy(kv.second.st);
+  }
   delete s;
   return TAU_OK;
 }

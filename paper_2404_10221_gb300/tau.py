@@ -37,6 +37,10 @@ TAU_SPGM = 2
 TAU_TC_AUTO = 0
 TAU_TC_OFF = 1
 TAU_TC_ON = 2
+TAU_TUNE_AUTO = 0
+TAU_TUNE_ON = 1
+TAU_TUNE_OFF = 2
+TAU_TUNE_RECORDED = 3
 TAU_ROUTE_AUTO = 0
 TAU_ROUTE_FFT = 1
 TAU_ROUTE_DENSE = 2
@@ -67,6 +71,7 @@ class tau_problem_desc(C.Structure):
         ("inner_tol", C.c_double),
         ("method", C.c_int),
         ("tc", C.c_int),
+        ("autotune", C.c_int),
     ]
 
 
@@ -159,6 +164,9 @@ class tau_server_stats(C.Structure):
         ("unknowns_steps", C.c_double),
         ("span_s", C.c_double),
         ("throughput", C.c_double),
+        ("group_launches", C.c_int64),
+        ("group_rebuilds", C.c_int64),
+        ("group_request_steps", C.c_int64),
     ]
 
 
@@ -258,7 +266,7 @@ def _stream(stream=None) -> int:
 def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
               e_bounds: Optional[tuple] = None, refine_tol: float = 0.0, inner_max_iter: int = 0,
               max_sweeps: int = 0, inner_tol: float = 0.0, method: int = TAU_OPGM,
-              tc: int = 0) -> tau_problem_desc:
+              tc: int = 0, autotune: int = TAU_TUNE_AUTO) -> tau_problem_desc:
     """tau_problem_desc from a workloads.Problem."""
     d = tau_problem_desc()
     d.d = prob.d
@@ -277,6 +285,7 @@ def make_desc(prob, precision: int = TAU_FP64, route: Sequence[int] = (0, 0, 0),
     d.precision = precision
     d.method = int(method)
     d.tc = int(tc)
+    d.autotune = int(autotune)
     if e_bounds is None:
         d.e_min = d.e_max = math.nan
     else:

@@ -49,7 +49,7 @@ def test_struct_layout_matches_c_compiler(tmp_path):
     checks = {
         "tau_problem_desc": ["d", "n", "L", "R", "alpha", "kappa", "T", "M", "tol", "max_iter", "x0_mode",
                              "precision", "route", "e_min", "e_max", "refine_tol", "inner_max_iter",
-                             "max_sweeps", "inner_tol", "method", "tc"],
+                             "max_sweeps", "inner_tol", "method", "tc", "autotune"],
         "tau_field": ["rank", "n_times", "time_coef", "space"],
         "tau_stats": ["steps_done", "total_iters", "last_iters", "max_iters_step", "last_relres", "ebar",
                       "e_hat", "e_check", "route", "graph", "device_bytes", "kernels_prologue",
@@ -59,7 +59,8 @@ def test_struct_layout_matches_c_compiler(tmp_path):
         "tau_request_info": ["id", "state", "status", "t_submit", "t_admit", "t_finish", "unknowns", "steps",
                              "gmres_iters", "device_bytes"],
         "tau_server_stats": ["completed", "failed", "queued", "active", "device_bytes_in_use", "latency_p50_s",
-                               "latency_p99_s", "latency_mean_s", "unknowns_steps", "span_s", "throughput"],
+                               "latency_p99_s", "latency_mean_s", "unknowns_steps", "span_s", "throughput",
+                               "group_launches", "group_rebuilds", "group_request_steps"],
     }
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "tau_rsfde.h"', "int main(void){"]
     for st, fields in checks.items():
@@ -113,6 +114,7 @@ def test_invalid_desc_rejected_before_any_device_call(lib):
         yield "precision", lambda d: setattr(d, "precision", 7)
         yield "method", lambda d: setattr(d, "method", 9)
         yield "tc", lambda d: setattr(d, "tc", 5)
+        yield "autotune", lambda d: setattr(d, "autotune", 4)
     for what, edit in edits():
         d = tau.make_desc(wl.prob)
         edit(d)

@@ -297,7 +297,9 @@ def test_served_long_request_same_as_alone():
     got = [tau.tau_server_result(s, i, wl.prob.n_tot) for i, wl in zip(ids, wls)]
     tau.tau_server_destroy(s)
     for wl, pr, um in zip(wls, precs, got):
-        p = tau.Problem(wl, precision=pr)
+        # alone as the server runs it: mixed requests on the line passes, recorded tuning choices
+        p = tau.Problem(wl, precision=pr, tc=tau.TAU_TC_OFF if pr == tau.TAU_MIXED else 0,
+                        autotune=tau.TAU_TUNE_RECORDED)
         p.solve()
         ua = p.solution().cpu().numpy()
         p.close()

@@ -317,3 +317,77 @@ def test_notconv_reported():
     assert st == tau.TAU_ENOTCONV
     assert np.all(p.iters() == 2)
     p.close()
+
+
+# Dense-route tiles that hold more than one round of 8 x 128 outputs (lines per CTA x n > 1024):
+# lines of 65..127 points across a strided axis (16 or 8 lines per CTA), and single lines longer
+# than 1024 points.  Every dense output reads the whole line, so the outputs must not overwrite
+# it before all of them are computed.
+DENSE_TILES = [
+    ((251, 129, 76), (0, 0, 0)),          # chirp, chirp, dense (the rules' routes)
+    ((251, 129, 76), (2, 2, 2)),          # dense on every axis
+    ((90, 70), (2, 2)),                   # dense, 16 lines of 70 per CTA on the strided axis
+    ((1500, 37), (2, 2)),                 # one dense line of 1500 per CTA
+    ((2000,), (2,)),                      # 1-D, one line of 2000
+]
+
+
+@pytest.mark.parametrize("n,route", DENSE_TILES)
+def test_dense_route_tiles_beyond_one_round(n, route):
+    tau = _tau()
+    d = len(n)
+    wl = _wl(d, n, max_iter=4)
+    pr = wl.prob
+    p = tau.Problem(wl, route=tuple(route) + (0,) * (3 - d), autotune=tau.TAU_TUNE_OFF)
+    st = p.stats()
+    if route[0] == 2:
+        assert all(r == tau.TAU_ROUTE_DENSE for r in st.route[:d])
+    t = wl.field_tables()
+    ebar = O.ebar_from_tables(pr, t["e_tc"], t["e_sp"])[0]
+    x = W.random_vector(pr.n_tot, 31)
+    xd = _cuda(x)
+    y = torch.empty_like(xd)
+    from oracle import tau_oracle as OT
+    for dim in range(d):
+        tau.tau_toeplitz_mode(p.handle, dim, xd, y)
+        torch.cuda.synchronize()
+        T = O.toeplitz_S(pr.alpha[dim], pr.n[dim])
+        _cmp(y, O.mode_product(x.reshape(OT._shape(pr)), T, OT._axis(pr, dim)).reshape(-1))
+    tau.tau_dst(p.handle, xd, y)
+    torch.cuda.synchronize()
+    X = x.reshape(OT._shape(pr))
+    for i in range(d):
+        X = O.mode_product(X, O.sine_matrix(pr.n[i]), OT._axis(pr, i))
+    _cmp(y, X.reshape(-1))
+    e0 = O.eval_field_interior(pr, t["e_tc"][0], t["e_sp"])
+    tau.tau_apply_A(p.handle, 0, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_A(pr, e0, x))
+    tau.tau_apply_Minv(p.handle, xd, y)
+    torch.cuda.synchronize()
+    _cmp(y, O.apply_Minv(pr, ebar, x), minv_rtol(pr, ebar))
+    p.close()
+
+
+def test_3d_chirp_and_dense_step_against_oracle():
+    """One Crank-Nicolson step of a 3-D grid whose axes take the chirp (251, 129) and dense (76)
+    routes, plain FP64 (1e-10, iterations +-1) and mixed (1e-8), against the oracle."""
+    tau = _tau()
+    wl = _wl(3, (251, 129, 76), M=115)
+    wl.prob.alpha = [1.82, 1.84, 1.68]
+    wl.prob.kappa = [0.35, 0.3, 0.96]
+    wl = W.manufactured("3d_chirp_dense", wl.prob, wl.e.terms, 2, 2, 1.0)
+    p = tau.Problem(wl)
+    p.step(1)
+    u = p.solution().cpu().numpy()
+    its = p.iters()[:1]
+    p.close()
+    q = tau.Problem(wl, precision=tau.TAU_MIXED, tc=tau.TAU_TC_OFF)
+    q.step(1)
+    umx = q.solution().cpu().numpy()
+    q.close()
+    ref = O.OracleSolver(wl.prob, wl.field_tables())
+    ref.run(steps=1)
+    assert np.linalg.norm(u - ref.u) <= SOLVE_RTOL * np.linalg.norm(ref.u)
+    assert abs(int(its[0]) - ref.iters[0]) <= 1, (its, ref.iters)
+    assert np.linalg.norm(umx - ref.u) <= 1e-8 * np.linalg.norm(ref.u)

@@ -31,8 +31,10 @@ def _mix(seed=20240416):
 
 
 def _alone(wl, precision):
+    """The request solved alone, as the server runs it (mixed: inner solve on the line passes)."""
     tau = _tau()
-    p = tau.Problem(wl, precision=precision)
+    p = tau.Problem(wl, precision=precision, tc=tau.TAU_TC_OFF if precision == tau.TAU_MIXED else 0,
+                    autotune=tau.TAU_TUNE_RECORDED)
     p.solve()
     u = p.solution().cpu().numpy()
     p.close()
@@ -80,3 +82,33 @@ def test_oversized_request_fails_fast():
     info = tau.tau_server_wait(s, rid, 10.0)
     tau.tau_server_destroy(s)
     assert info.state == tau.TAU_REQ_FAILED and info.status == tau.TAU_ENOMEM
+
+
+def test_requests_share_launches_and_late_arrivals_join():
+    """Mixed 2-D requests of different sizes and step counts batch their iterations together (shared
+    launches of one group graph, rebuilt as requests finish or arrive); requests submitted while the
+    first ones run are admitted and join; every result equals the request solved alone."""
+    import time
+    tau = _tau()
+    rng = W.SplitMix64(777)
+    early = [W.random_2d(rng, sizes=(31, 63, 127), M=6 + 2 * k) for k in range(4)]
+    late = [W.random_2d(rng, sizes=(31, 63), M=4 + k) for k in range(3)]
+    s = tau.tau_server_create(8 << 30, 16, 2)
+    desc = lambda wl: tau.make_desc(wl.prob, precision=tau.TAU_MIXED)
+    ids_e = [tau.tau_server_submit(s, desc(wl), wl.field_tables()) for wl in early]
+    t_end = time.time() + 60
+    while tau.tau_server_poll(s, ids_e[0]).state == tau.TAU_REQ_QUEUED and time.time() < t_end:
+        time.sleep(0.001)
+    ids_l = [tau.tau_server_submit(s, desc(wl), wl.field_tables()) for wl in late]
+    ids = ids_e + ids_l
+    infos = [tau.tau_server_wait(s, i, 300.0) for i in ids]
+    res = [tau.tau_server_result(s, i, wl.prob.n_tot) for i, wl in zip(ids, early + late)]
+    summ = tau.tau_server_summary(s)
+    tau.tau_server_destroy(s)
+    assert all(inf.state == tau.TAU_REQ_DONE and inf.status == tau.TAU_OK for inf in infos)
+    assert summ.group_launches > 0 and summ.group_rebuilds >= 2, (summ.group_launches, summ.group_rebuilds)
+    assert summ.group_request_steps > summ.group_launches
+    # at least one late request was admitted before the last early one finished
+    assert min(infos[len(early) + k].t_admit for k in range(len(late))) < max(inf.t_finish for inf in infos[:len(early)])
+    for wl, u in zip(early + late, res):
+        assert np.array_equal(_alone(wl, tau.TAU_MIXED), u)

@@ -37,6 +37,7 @@ def _wl(d, n, M=3, x0_mode=0):
     (2, (15, 15), 3, 0),
     (2, (12, 31), 3, 1),       # mixed τ routes
     (3, (7, 5, 7), 2, 0),
+    (2, (70, 90), 2, 0),       # Hartley tiles of more than 8 x 128 values (16 lines of 70 or 90)
 ])
 def test_spgm_solve_matches_oracle(case):
     tau = _tau()
