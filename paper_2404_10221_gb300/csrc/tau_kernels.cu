@@ -1066,6 +1066,9 @@ __device__ __forceinline__ double fields_hstencil(const FieldDev& F, const doubl
   return acc2;
 }
 
+// largest number of field terms (e's plus f's) whose per-line coefficients k_fields stages
+constexpr int FIELD_RMAX = 32;
+
 struct FieldsArgs {
   FieldDev F;
   const GmresDev* g;
@@ -1093,6 +1096,41 @@ __device__ __forceinline__ void fields_run(const FieldsArgs& A, VB vb) {
   }
   const double* etc = F.e_tc + m * F.re;
   const double* ftc = F.f_tc + m * F.rf;
+  const int n0 = F.n[0];
+  const int64_t nlines = F.n_tot / n0;
+  if (F.d > 1 && F.re + F.rf <= FIELD_RMAX && nlines >= 1024 && blockDim.x == 256) {
+    // one warp per line along x_1: the line's coefficients c_r prod_{i>=1} phi_{r,i}(x_i) once per
+    // line (per lane: a few products), then one FMA per term and element (the FP64 pipe is slow)
+    __shared__ double lc[8][FIELD_RMAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t L = (int64_t)vb.bid * 8 + warp; L < nlines; L += (int64_t)vb.nb * 8) {
+      const unsigned q = (unsigned)L;
+      const unsigned j1 = F.d > 1 ? q % (unsigned)F.n[1] : 0u, j2 = F.d > 2 ? q / (unsigned)F.n[1] : 0u;
+      __syncwarp();
+      for (int r = lane; r < F.re + F.rf; r += 32) {
+        double p;
+        if (r < F.re) {
+          p = etc[r] * F.e_sp[1][r * (F.n[1] + 2) + j1 + 1];
+          if (F.d > 2) p *= F.e_sp[2][r * (F.n[2] + 2) + j2 + 1];
+        } else {
+          const int rr = r - F.re;
+          p = ftc[rr] * F.f_hsp[1][rr * F.n[1] + j1];
+          if (F.d > 2) p *= F.f_hsp[2][rr * F.n[2] + j2];
+        }
+        lc[warp][r] = p;
+      }
+      __syncwarp();
+      for (int j0 = lane; j0 < n0; j0 += 32) {
+        double ev = 0.0, fv = 0.0;
+        for (int r = 0; r < F.re; ++r) ev = fma(lc[warp][r], F.e_sp[0][r * (n0 + 2) + j0 + 1], ev);
+        for (int r = 0; r < F.rf; ++r) fv = fma(lc[warp][F.re + r], F.f_hsp[0][r * n0 + j0], fv);
+        const int64_t idx = L * n0 + j0;
+        if (e_out) e_out[idx] = ev;
+        if (fdt_out) fdt_out[idx] = F.dt * fv;
+      }
+    }
+    return;
+  }
   for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < F.n_tot;
        idx += (int64_t)vb.nb * blockDim.x) {
     int j[3] = {0, 0, 0};
@@ -2097,6 +2135,13 @@ struct ScaleF32Args {
   const IRDev* ir;
 };
 
+// v = r / rho rounded to FP32 (a double-float r scaled on the FP32 pipes: hi/rho + lo/rho with
+// 1/rho as a double-float pair is exact to far below FP32's rounding)
+__device__ __forceinline__ float scale_f32(double r, double inv, df64) { return (float)(r * inv); }
+__device__ __forceinline__ float scale_f32(df64 r, double, df64 inv) {
+  return fmaf(r.hi, inv.hi, fmaf(r.hi, inv.lo, r.lo * inv.hi));
+}
+
 template <typename S>
 __device__ __forceinline__ void scale_to_f32_run(const ScaleF32Args<S>& A, VB vb) {
   if (A.ir->done) return;
@@ -2104,8 +2149,9 @@ __device__ __forceinline__ void scale_to_f32_run(const ScaleF32Args<S>& A, VB vb
   if (threadIdx.x == 0) sinv = 1.0 / A.ir->rho;
   __syncthreads();
   const double inv = sinv;
+  const df64 inv_df = from_d<df64>(inv);
   for (int64_t i = vb.bid * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)vb.nb * blockDim.x)
-    A.v[i] = (float)(to_d(A.r[i]) * inv);
+    A.v[i] = scale_f32(A.r[i], inv, inv_df);
 }
 
 template <typename S>
@@ -2128,13 +2174,23 @@ cudaError_t launch_scale_to_f32(const S* r, float* v, int64_t n, const IRDev* ir
 template cudaError_t launch_scale_to_f32<double>(const double*, float*, int64_t, const IRDev*, cudaStream_t);
 template cudaError_t launch_scale_to_f32<df64>(const df64*, float*, int64_t, const IRDev*, cudaStream_t);
 
-// x += rho * sum_{i<k} y_i Z_i over the FP32 preconditioned directions Z_i.  The sum runs in FP64:
-// the Z_i are exact FP32 vectors, and rounding the correction itself to FP32 would add an error of
-// eps_32 |d| whose image under A (not smooth, so A does not cancel on it) is a sizeable part of
-// the next residual.  x is FP64 or double-float (X = df64; the addition then on the FP32 pipes).
-template <typename X> __device__ __forceinline__ void add_to(X& x, double d);
-template <> __device__ __forceinline__ void add_to<double>(double& x, double d) { x += d; }
-template <> __device__ __forceinline__ void add_to<df64>(df64& x, double d) { x = x + from_d<df64>(d); }
+// x += rho * sum_{i<k} y_i Z_i over the FP32 preconditioned directions Z_i.  The sum runs in
+// double-float (about 48 bits, on the FP32 pipes; FP64 conversions and FMAs would run on the slow
+// FP64 pipe): the Z_i are exact FP32 vectors, and rounding the correction itself to FP32 would add
+// an error of eps_32 |d| whose image under A (not smooth, so A does not cancel on it) is a sizeable
+// part of the next residual.  x is FP64 or double-float.
+template <typename X> __device__ __forceinline__ void add_to(X& x, df64 d);
+template <> __device__ __forceinline__ void add_to<double>(double& x, df64 d) { x += to_d(d); }
+template <> __device__ __forceinline__ void add_to<df64>(df64& x, df64 d) { x = x + d; }
+
+// a + b * z with b double-float and z an FP32 value (FMA-exact products of both parts)
+__device__ __forceinline__ df64 df_fma_f(df64 b, float z, df64 a) {
+  const float p = b.hi * z;
+  float e = fmaf(b.hi, z, -p);
+  e = fmaf(b.lo, z, e);
+  const float h = p + e;
+  return a + df64{h, e - (h - p)};
+}
 
 template <typename X>
 struct UpdXArgs {
@@ -2148,18 +2204,18 @@ struct UpdXArgs {
 
 template <typename X>
 __device__ __forceinline__ void update_x_run(const UpdXArgs<X>& A, VB vb) {
-  __shared__ double ys[MAX_ITER_CAP];
+  __shared__ df64 ys[MAX_ITER_CAP];
   IRDev* ir = A.ir;
   if (ir->done) return;
   const int k = A.gin->k;
   const double rho = ir->rho;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = rho * A.y[i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) ys[i] = from_d<df64>(rho * A.y[i]);
   if (vb.bid == 0 && threadIdx.x == 0) ir->inner_total += k;
   __syncthreads();
   const int64_t n = A.n;
   for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-    double d = 0.0;
-    for (int i = 0; i < k; ++i) d = fma(ys[i], (double)A.Z[(int64_t)i * n + idx], d);
+    df64 d{0.0f, 0.0f};
+    for (int i = 0; i < k; ++i) d = df_fma_f(ys[i], A.Z[(int64_t)i * n + idx], d);
     add_to(A.x[idx], d);
   }
 }
