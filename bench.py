@@ -59,6 +59,8 @@ def parse():
                          "routes, 9 launches on the long-line route), then exit")
     ap.add_argument("--matvec-n", type=int, default=1023,
                     help="grid size per axis of --matvec-only (1023: FFT route; other n: chirp route in 2-D)")
+    ap.add_argument("--matvec-route", default="auto", choices=["auto", "fft", "dense", "chirp"],
+                    help="profiling driver: the route of every dimension for --matvec-only")
     ap.add_argument("--matvec-d", type=int, default=2, choices=[1, 2],
                     help="dimension of --matvec-only (1: the 1-D workload, long-line route from n = 128)")
     ap.add_argument("--tc", default="auto", choices=["auto", "on", "off"],
@@ -774,7 +776,8 @@ def run_matvec_only(args):
     # (--matvec-d 1; long-line route from n = 128)
     wl = W.c2_2d(n=args.matvec_n) if args.matvec_d == 2 else W.c1_1d(n=args.matvec_n)
     wl.prob.max_iter = 2
-    p = tau.Problem(wl)
+    r = {"auto": 0, "fft": tau.TAU_ROUTE_FFT, "dense": tau.TAU_ROUTE_DENSE, "chirp": tau.TAU_ROUTE_CHIRP}[args.matvec_route]
+    p = tau.Problem(wl, route=(r, r, 0))
     x = torch.randn(wl.prob.n_tot, dtype=torch.float64, device="cuda")
     z = torch.empty_like(x)
     torch.cuda.synchronize()
