@@ -198,13 +198,19 @@ class ClockSampler:
 # valid only for the kernel sources that capture measured (sha256 below), else the bench reports
 # null.
 TRAFFIC_CAPTURE = {
-    "bytes_per_matvec": 16916480 + 512 + 16963840 + 1280 + 16904192 + 0 + 8493312 + 0,
+    # DRAM read + write bytes of the four launches of one preconditioned matvec on 1023^2, from the
+    # cold-cache ncu capture summarised in profiles/k_pass_routes_2d1023.md
+    "bytes_per_matvec": 16906752 + 256 + 16954112 + 256 + 16903424 + 0 + 8491776 + 0,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "a94d0eb3d679a7db564bc1a87b6c868419eb242bd9d756b449ab16f61bd08daa",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "6873be8fcee38a12bcdaac1c1b138fc94673da13d44fafec12a8bb6b4c86acad",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "9f587cb0d8f5a72904ad82f11e418d8eee32746b1d477d82b85c0acf7ca7fdca",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "dc346f9bc1c44ac872843f58d2939d2ca4c149e84b8318e3644cb81872338e0c",
         "paper_2404_10221_gb300/csrc/tau_fft.cuh": "ccccc8cd138b0e0753a8603a34e7f4230828c94aa4bd560053e4eddc1469012a",
     },
 }
+
+
+# the same four launches with warm caches, inside the repeated chain (profiles/k_pass_routes_2d1023.md)
+WARM_TRAFFIC_BYTES = (182528 + 33280 + 344064 + 5376) + (1664512 + 2486528 + 357888 + 1097728)
 
 
 def captured_traffic():
@@ -704,7 +710,14 @@ def run_native(args):
             "traffic_unit": "DRAM bytes read + written by the 4 launches of one preconditioned matvec "
                             "(ncu capture of this kernel source; null if the source changed since)",
             "peak_kind": "measured FP64 FMA throughput (in-process probe, best of two runs); nominal 1.25 TFLOP/s",
-            "matvec_ms": t_chain * 1e3, "algorithmic_flops_per_matvec": flops}
+            "matvec_ms": t_chain * 1e3, "algorithmic_flops_per_matvec": flops,
+            "algorithmic_bytes_per_matvec": 40 * n_tot,
+            "algorithmic_bytes_model": "streaming minimum per unknown of one preconditioned matvec: x, e read "
+                                       "and the result written for the matvec (24 B), the tau solve's input read "
+                                       "and output written (16 B)",
+            "traffic_warm_cache": WARM_TRAFFIC_BYTES if captured_traffic() is not None else None,
+            "traffic_warm_cache_note": "DRAM bytes of the same 4 launches inside the timed chain (ncu "
+                                       "--cache-control none): the chain's working set stays in L2"}
 
     # ---- end to end through the C ABI with host buffers: per step, u^{(m)} in from pinned
     # host memory, one step, u^{(m+1)} back to pinned host memory
