@@ -137,7 +137,9 @@ struct tau_problem {
   bool tune_measure = false, tune_records = false;
   int route_src[3] = {0, 0, 0};                 // 0 rule or forced, 1 measured, 2 recorded measurement
   double route_ms[3] = {0, 0, 0}, route_alt_ms[3] = {0, 0, 0};
-  int lpb_tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // lines per CTA chosen by the autotuner
+  // the autotuner's tile per element type and dimension: lines per CTA, plus 1 << 16 when the CTA
+  // has 256 threads (the wide line-pass variant); 0: the shared-memory heuristic, 128 threads
+  int lpb_tuned[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
                                                           // (FP64, FP32, double-float)
   // double-float precision (TAU_DF64): solver vectors live in the FP64 buffers above as df64 pairs
   bool dfm = false;
@@ -308,7 +310,10 @@ PassT<T> base_pass_t(const tau_problem* p, int ax) {
   if (lpb > 16) lpb = 16;
   const int64_t cap = ax == 0 ? P.nlines : inner;
   const int tuned = p->lpb_tuned[prec_index<T>()][ax];
-  if (tuned > 0) lpb = tuned;
+  if (tuned > 0) {
+    lpb = tuned & 0xFFFF;
+    P.tpb = (tuned >> 16) ? 256 : 128;
+  }
   if (lpb > cap) lpb = cap;
   set_lpb(P, (int)lpb);
   P.vstride = p->n_tot;
@@ -1036,7 +1041,11 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  auto time_lpb = [&](int lpb, float* ms) -> tau_status {
+  // candidates: lines per CTA (powers of two within 200 KB of shared memory) x threads per CTA
+  // (128, or 256 for the wide variant); encoded lpb | (wide << 16)
+  auto time_lpb = [&](int code, float* ms) -> tau_status {
+    const int lpb = code & 0xFFFF;
+    P.tpb = Q.tpb = (code >> 16) ? 256 : 128;
     set_lpb(P, lpb);
     set_lpb(Q, lpb);
     CK(launch_pass(P, p->st));
@@ -1054,17 +1063,19 @@ tau_status tune_dim(tau_problem* p, int ax, T* chA, T* chC) {
   float best = 0.0f;
   TRY(time_lpb(heur, &best));
   int best_lpb = heur;
-  for (int lpb = 1; lpb <= 32 && lpb <= cap; lpb *= 2) {
-    if (lpb == heur) continue;
-    set_lpb(P, lpb);
-    if (pass_smem_bytes(P) > 200 * 1024) break;
-    float ms = 0.0f;
-    TRY(time_lpb(lpb, &ms));
-    if (ms < best * 0.97f) {
-      best = ms;
-      best_lpb = lpb;
+  for (int wide = 0; wide < 2; ++wide)
+    for (int lpb = 1; lpb <= 32 && lpb <= cap; lpb *= 2) {
+      if (lpb == heur && !wide) continue;
+      set_lpb(P, lpb);
+      if (pass_smem_bytes(P) > 200 * 1024) break;
+      float ms = 0.0f;
+      const int code = lpb | (wide << 16);
+      TRY(time_lpb(code, &ms));
+      if (ms < best * 0.97f) {
+        best = ms;
+        best_lpb = code;
+      }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->lpb_tuned[prec_index<T>()][ax] = best_lpb;
@@ -2391,23 +2402,39 @@ tau_status record_merge(Arena& ar, const std::vector<tau_problem*>& ps,
   const size_t L = R[0].size();
   for (size_t i = 1; i < ps.size(); ++i)
     if (R[i].size() != L) return fail(TAU_EUNSUPPORTED, "grouped launches: problems enqueue different kernel sequences");
+  // Problems may run a different kernel at the same position (the tile autotuner picks the
+  // 128- or 256-thread line pass per problem): each distinct (kernel, block) at a position becomes
+  // a grouped launch of its own over the problems that run it; they are independent of each other.
   const int n = (int)ps.size();
   for (size_t k = 0; k < L; ++k) {
-    const LaunchRec& r0 = R[0][k];
-    const size_t asz = r0.args.size();
-    const size_t oa = ar.take(asz * n), os = ar.take(sizeof(int) * (n + 1));
-    int* start = reinterpret_cast<int*>(ar.host.data() + os);
-    start[0] = 0;
-    size_t smem = 0;
-    for (int i = 0; i < n; ++i) {
-      const LaunchRec& r = R[i][k];
-      if (r.fn != r0.fn || r.block != r0.block || r.args.size() != asz)
-        return fail(TAU_EUNSUPPORTED, "grouped launches: launch %zu differs between problems", k);
-      memcpy(ar.host.data() + oa + asz * i, r.args.data(), asz);
-      start[i + 1] = start[i] + (int)r.grid;
-      smem = std::max(smem, r.smem);
+    std::vector<int> done(n, 0);
+    for (int first = 0; first < n; ++first) {
+      if (done[first]) continue;
+      const LaunchRec& r0 = R[first][k];
+      const size_t asz = r0.args.size();
+      std::vector<int> mem;
+      for (int i = first; i < n; ++i) {
+        const LaunchRec& r = R[i][k];
+        if (done[i] || r.fn != r0.fn || r.block != r0.block) continue;
+        if (r.args.size() != asz) return fail(TAU_EUNSUPPORTED, "grouped launches: argument sizes differ");
+        mem.push_back(i);
+        done[i] = 1;
+      }
+      const int m = (int)mem.size();
+      const size_t oa = ar.take(asz * m), os = ar.take(sizeof(int) * (m + 1));
+      int* start = reinterpret_cast<int*>(ar.host.data() + os);
+      start[0] = 0;
+      size_t smem = 0;
+      for (int q = 0; q < m; ++q) {
+        const LaunchRec& r = R[mem[q]][k];
+        memcpy(ar.host.data() + oa + asz * q, r.args.data(), asz);
+        start = reinterpret_cast<int*>(ar.host.data() + os);   // host may have grown: re-take
+        start[q + 1] = start[q] + (int)r.grid;
+        smem = std::max(smem, r.smem);
+      }
+      start = reinterpret_cast<int*>(ar.host.data() + os);
+      out.push_back(Merged{r0.fn, (unsigned)start[m], r0.block, smem, ar.at(oa), static_cast<int*>(ar.at(os)), m});
     }
-    out.push_back(Merged{r0.fn, (unsigned)start[n], r0.block, smem, ar.at(oa), static_cast<int*>(ar.at(os)), n});
   }
   return TAU_OK;
 }

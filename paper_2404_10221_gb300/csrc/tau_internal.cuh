@@ -223,6 +223,7 @@ struct PassT {
   int64_t inner;     // prod_{i<ax} n_i (element stride along the line)
   int64_t nlines;    // n_tot / len
   int lpb;           // lines per CTA
+  int tpb;           // threads per CTA: 128 (0 means 128) or 256 (the wide variant)
   int64_t ntiles;
   DimDataT<T> dim;
   // matvec channels

@@ -28,7 +28,8 @@ namespace tau {
 
 thread_local std::vector<LaunchRec>* tl_rec = nullptr;
 
-constexpr int PASS_THREADS = 128;
+constexpr int PASS_THREADS = 128;       // threads of a line-pass CTA (the wide variant: 256)
+constexpr int PASS_MAX_THREADS = 256;
 
 
 // FP64 route of the spectral step: one pass over the pairs (k, K-k) in the digit-reversed layout
@@ -383,8 +384,8 @@ __device__ void hartley_lines(const PassT<T>& P, T* xs, int xst) {
 template <typename T>
 __device__ void prefix_segments(T* xs, int xst, int lpb, int K2) {
   const int TH = blockDim.x, tid = threadIdx.x;
-  __shared__ T scan_incl[PASS_THREADS];
-  __shared__ T warp_tot[PASS_THREADS / 32];
+  __shared__ T scan_incl[PASS_MAX_THREADS];
+  __shared__ T warp_tot[PASS_MAX_THREADS / 32];
   int spl = TH / lpb;
   if (spl < 1) spl = 1;
   spl = 1 << (31 - __clz(spl));
@@ -459,7 +460,7 @@ __device__ void prefix_warps(T* xs, int xst, int lpb, int K2) {
     __syncthreads();
     return;
   }
-  __shared__ T part_tot[PASS_THREADS / 32];
+  __shared__ T part_tot[PASS_MAX_THREADS / 32];
   const int l = wid / wpl, pw = wid - l * wpl;
   const int part = K2 / wpl, k0 = pw * part;
   T* row = xs + l * xst;
@@ -855,9 +856,25 @@ struct PassBody {
   static constexpr int kCtas = PassOcc<T>::ctas;
   static __device__ __forceinline__ void run(const PassT<T>& P, VB vb) { pass_run<T>(P, vb); }
 };
+// The wide variant: 256 threads per CTA with the same registers per thread (half the CTAs per SM).
+// Lines of a few thousand points per CTA then get twice the threads per transform stage, which
+// lifts the warps in flight where the grid has few lines (the FP32 passes at 1023^2 run one or two
+// lines per CTA); the autotuner picks it per dimension and element type.
+template <typename T>
+struct PassBodyW {
+  using Args = PassT<T>;
+  static constexpr int kThreads = 2 * PASS_THREADS;
+  static constexpr int kCtas = PassOcc<T>::ctas / 2;
+  static __device__ __forceinline__ void run(const PassT<T>& P, VB vb) { pass_run<T>(P, vb); }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(PASS_THREADS, PassOcc<T>::ctas) k_pass(const PassT<T> P) {
+  pass_run<T>(P, VB{(int)blockIdx.x, (int)gridDim.x});
+}
+
+template <typename T>
+__global__ void __launch_bounds__(2 * PASS_THREADS, PassOcc<T>::ctas / 2) k_pass_w(const PassT<T> P) {
   pass_run<T>(P, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
@@ -921,6 +938,18 @@ cudaError_t init_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_ht_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_w<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_pass_w<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBodyW<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBodyW<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_grouped<PassBodyW<df64>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_grouped<PassBody<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_grouped<PassBody<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -935,9 +964,12 @@ cudaError_t init_kernel_attributes() {
 template <typename T>
 cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
   const size_t smem = pass_smem_bytes(p);
+  const bool wide = p.tpb == 2 * PASS_THREADS;
   if (tl_rec) {
     if (p.post == POST_HT || p.post == POST_HT_D_HT) return cudaErrorNotSupported;   // not grouped
-    return record_launch<PassBody<T>>(p, p.ntiles > 0 ? (unsigned)p.ntiles : 0u, PASS_THREADS, smem);
+    const unsigned g = p.ntiles > 0 ? (unsigned)p.ntiles : 0u;
+    return wide ? record_launch<PassBodyW<T>>(p, g, 2 * PASS_THREADS, smem)
+                : record_launch<PassBody<T>>(p, g, PASS_THREADS, smem);
   }
   if (p.ntiles <= 0) return cudaSuccess;
   if (p.post == POST_HT || p.post == POST_HT_D_HT) {
@@ -947,7 +979,8 @@ cudaError_t launch_pass(const PassT<T>& p, cudaStream_t st) {
     }
     return cudaErrorNotSupported;   // the Strang circulant method runs in FP64 only
   }
-  k_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
+  if (wide) k_pass_w<T><<<(unsigned)p.ntiles, 2 * PASS_THREADS, smem, st>>>(p);
+  else k_pass<T><<<(unsigned)p.ntiles, PASS_THREADS, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -1410,6 +1443,7 @@ cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cud
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 4;
+constexpr int UPD_KEEP = 16;   // basis vectors kept in registers by the fused FP32 update-and-dots pass
 
 // Block sum in FP64 (sh: at least blockDim.x doubles).  Every thread's value goes to shared memory
 // and warp 0 adds them, so the FP64 additions (a slow pipe on this part) number ~12 per lane of
@@ -1606,6 +1640,38 @@ __device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
   S* w = V + (int64_t)(jj + 1) * n;
   for (int i = threadIdx.x; i <= jj; i += blockDim.x) hs[i] = from_d<S>(h[i]);
   __syncthreads();
+  if constexpr (std::is_same<S, float>::value) {
+    if (!norm_only && jj < UPD_KEEP) {
+      // FP32 basis of at most UPD_KEEP vectors: each element's basis values stay in registers
+      // between the update and the second pass's dots, so the basis is read once here instead of
+      // twice (same operations in the same order as the two-pass form below)
+      float acc[UPD_KEEP];
+#pragma unroll
+      for (int i = 0; i < UPD_KEEP; ++i) acc[i] = 0.0f;
+      for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
+        float vv[UPD_KEEP];
+        float wv = w[idx];
+#pragma unroll
+        for (int i = 0; i < UPD_KEEP; ++i)
+          if (i <= jj) {
+            vv[i] = V[(int64_t)i * n + idx];
+            wv = fmaf(-hs[i], vv[i], wv);
+          }
+        w[idx] = wv;
+#pragma unroll
+        for (int i = 0; i < UPD_KEEP; ++i)
+          if (i <= jj) acc[i] = fmaf(wv, vv[i], acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < UPD_KEEP; ++i)
+        if (i <= jj) {
+          const double s = block_sum((double)acc[i], sh);
+          if (threadIdx.x == 0) partial[(int64_t)i * ld + vb.bid] = s;
+        }
+      if (last_block(&g->tickets, vb)) reduce_partials(partial, ld, jj, A.h_out, vb);
+      return;
+    }
+  }
   S nacc = from_f<S>(0.0f);
   for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
     S wv = w[idx];

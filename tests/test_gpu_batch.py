@@ -223,3 +223,20 @@ def test_grouping_off_gives_the_same_results(monkeypatch):
     assert info_g.groups >= 1 and info_b.groups == 0 and info_b.branches == len(wls)
     for (ug, ig, _), (ub, ib, _) in zip(got_g, got_b):
         assert np.array_equal(ug, ub) and np.array_equal(ig, ib)
+
+
+def test_grouped_batch_with_tuned_tiles_equals_alone(monkeypatch):
+    """With the tile autotuner on, problems of different shapes may run different line-pass
+    kernels (128 or 256 threads per CTA, different lines per CTA) at the same position of the step;
+    the group then splits that position into one grouped launch per kernel.  Results stay
+    bit-identical to each problem alone (the tuner's choices are recorded per shape, so the alone
+    runs take the same tiles)."""
+    monkeypatch.setenv("TAU_AUTOTUNE", "1")
+    shapes = [(255, 63), (127, 255), (63, 63), (255, 255), (31, 127)]
+    wls = _mixed_instances(shapes, 3, 515)
+    info, got = _run_batch(wls)
+    assert info.groups >= 1
+    for wl, (ub, ib, sb) in zip(wls, got):
+        ua, ia, sa = _alone_mixed(wl)
+        assert np.array_equal(ua, ub)
+        assert np.array_equal(ia, ib) and sa == sb
