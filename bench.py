@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the precision/batched/served form measurements")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--serve-requests", type=int, default=32)
-    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.5],
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.2, 0.5, 0.8, 1.2],
                     help="Poisson arrival rates of the served form, as fractions of its saturation throughput")
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
