@@ -112,3 +112,27 @@ def test_requests_share_launches_and_late_arrivals_join():
     assert min(infos[len(early) + k].t_admit for k in range(len(late))) < max(inf.t_finish for inf in infos[:len(early)])
     for wl, u in zip(early + late, res):
         assert np.array_equal(_alone(wl, tau.TAU_MIXED), u)
+
+
+def test_served_results_match_the_oracle():
+    """Requests of each kind the server handles (shared launches for small mixed requests, a
+    double-float request, a plain FP64 one, a 1-D one on its own stream) against the oracle: the
+    form's bar for the mixed and double-float requests, the plain bar for FP64."""
+    import oracle as O
+    tau = _tau()
+    rng = W.SplitMix64(4040)
+    wls = [W.random_2d(rng, sizes=(31, 63), M=3) for _ in range(3)]
+    wls += [W.c3_3d(n=15, M=3), W.c1_1d(n=127, M=3), W.c2_2d(n=31, M=3)]
+    precs = [tau.TAU_MIXED, tau.TAU_MIXED, tau.TAU_MIXED, tau.TAU_MIXED, tau.TAU_DF64, tau.TAU_FP64]
+    s = tau.tau_server_create(8 << 30, 8, 2)
+    ids = [tau.tau_server_submit(s, tau.make_desc(wl.prob, precision=pr), wl.field_tables())
+           for wl, pr in zip(wls, precs)]
+    infos = [tau.tau_server_wait(s, i, 300.0) for i in ids]
+    got = [tau.tau_server_result(s, i, wl.prob.n_tot) for i, wl in zip(ids, wls)]
+    tau.tau_server_destroy(s)
+    assert all(inf.state == tau.TAU_REQ_DONE and inf.status == tau.TAU_OK for inf in infos)
+    for wl, pr, u in zip(wls, precs, got):
+        ref = O.OracleSolver(wl.prob, wl.field_tables())
+        ref.run()
+        bar = 1e-10 if pr == tau.TAU_FP64 else 1e-8
+        assert np.linalg.norm(u - ref.u) <= bar * np.linalg.norm(ref.u), (wl.prob.n, pr)
