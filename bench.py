@@ -65,6 +65,8 @@ def parse():
                     help="dimension of --matvec-only (1: the 1-D workload, long-line route from n = 128)")
     ap.add_argument("--tc", default="auto", choices=["auto", "on", "off"],
                     help="tensor-core DST of the FP32 τ solve in --matvec-f32-3d (TAU_TC_AUTO/ON/OFF)")
+    ap.add_argument("--time-ops", type=int, default=0,
+                    help="with --matvec-f32-3d: time the FP32 A and M^{-1} alone, median of this many launches")
     ap.add_argument("--matvec-f32-3d", type=int, default=0,
                     help="profiling driver: the 3-D 255^3 workload in mixed precision (2 inner slots); run "
                          "this many FP32 A x (3 line passes) + M^{-1} r (5 line passes), then exit")
@@ -836,6 +838,7 @@ def run_profile_step(args):
 
 
 def run_matvec_f32_3d(args):
+    import numpy as np
     import torch
 
     from paper_2404_10221_gb300 import tau
@@ -853,9 +856,27 @@ def run_matvec_f32_3d(args):
         tau.tau_apply_Minv_f32(p.handle, y, x)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    tc_dims = int(p.stats().tc_dims)
+    out = {"matvec_f32_3d": args.matvec_f32_3d, "tc_dims": int(p.stats().tc_dims)}
+    if args.time_ops:
+        # each operator alone, CUDA events on the current stream (the operators run on it), median of
+        # args.time_ops launches after 3 warm-up ones; x and y together (133 MB) exceed L2
+        stream = torch.cuda.current_stream()
+        for name, op in (("A_ms", lambda: tau.tau_apply_A_f32(p.handle, 0, x, y)),
+                         ("Minv_ms", lambda: tau.tau_apply_Minv_f32(p.handle, x, y))):
+            for _ in range(3):
+                op()
+            ts = []
+            for _ in range(args.time_ops):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                op()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            out[name] = float(np.median(ts))
+    out["x_norm"] = float(torch.linalg.norm(x))
     p.close()
-    print(json.dumps({"matvec_f32_3d": args.matvec_f32_3d, "tc_dims": tc_dims, "x_norm": float(torch.linalg.norm(x))}))
+    print(json.dumps(out))
     return 0
 
 

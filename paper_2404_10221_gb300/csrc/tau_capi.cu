@@ -1245,10 +1245,11 @@ tau_status long_tables_as(tau_problem* p, int i, LongTab<T>& D, int cw, Conv con
   return TAU_OK;
 }
 
-// Tensor-core DST tables of the mixed form (TAU_TC_AUTO): for every dimension with n <= 256 the
-// orthonormal DST-I matrix S[k][j] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1)) (j k reduced mod 2(n+1)),
-// rounded to TF32 (nearest, ties away: the rounding the kernel applies to its inputs), zero padded to
-// N = n rounded up to 16 rows and Kp = n rounded up to 32 columns.
+// Tensor-core DST tables of the mixed form (TAU_TC_AUTO): for every dimension with n <= 256 the first
+// h = ceil(n/2) rows of the orthonormal DST-I matrix S[k][j] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1))
+// (j k reduced mod 2(n+1)); the other rows follow from S[n-1-k][j] = (-1)^j S[k][j].  Rounded to TF32
+// (nearest, ties away: the rounding the kernel applies to its inputs), zero padded to Nh rows (h
+// rounded up to 16; 128 on dimension 0) and Kp16 = n rounded up to 16 columns.
 tau_status setup_tc(tau_problem* p) {
   if (p->desc.tc == TAU_TC_OFF) return TAU_OK;
   for (int i = 0; i < p->d; ++i) {
@@ -1260,18 +1261,26 @@ tau_status setup_tc(tau_problem* p) {
     }
     TcTab& t = p->tc[i];
     t.n = n;
-    // dimension 0 takes S as the A operand in tiles of 128 rows (accumulators 128 columns per tile);
-    // the others take it as the B operand (N a multiple of 16)
+    // matvec: dimension 0 takes T as the A operand in tiles of 128 rows (accumulators 128 columns per
+    // tile); the others take it as the B operand (N a multiple of 16)
     t.N = i == 0 ? (n + 127) & ~127 : (n + 15) & ~15;
-    t.Kp = (n + 31) & ~31;
+    t.Kp16 = (n + 15) & ~15;
     t.nalloc = 32;
     while (t.nalloc < t.N) t.nalloc <<= 1;
-    // stored per K-chunk of 32 columns in the kernel's shared-memory layout (core matrices of 8
-    // rows x 4 values: byte offset (k/8)*1024 + (j/4)*128 + (k%8)*16 + (j%4)*4 within the chunk)
-    std::vector<float> S((size_t)t.N * t.Kp, 0.0f);
+    // DST: half of S, the A operand (128 rows) on dimension 0, else the B operand (Nh rows); two
+    // accumulators (even and odd j) of 128 (dimension 0: lines) or Nh columns each
+    const int h = (n + 1) / 2;
+    t.Nh = i == 0 ? 128 : (h + 15) & ~15;
+    const int acc_cols = i == 0 ? 128 : t.Nh;
+    t.nalloc_h = 32;
+    while (t.nalloc_h < 2 * acc_cols) t.nalloc_h <<= 1;
+    // stored per K-chunk of 16 columns in the kernel's shared-memory layout (core matrices of 8
+    // rows x 4 values: byte offset (k/8)*512 + (q/4)*128 + (k%8)*16 + (q%4)*4 within the chunk),
+    // slot q of chunk c holding column j = 16c + 2q (q < 8: even j) or 16c + 2(q-8) + 1 (odd j)
+    std::vector<float> S((size_t)t.Nh * t.Kp16, 0.0f);
     const double sc = std::sqrt(2.0 / (double)(n + 1));
     const int64_t L2 = 2 * ((int64_t)n + 1);
-    for (int k = 0; k < n; ++k)
+    for (int k = 0; k < h; ++k)
       for (int j = 0; j < n; ++j) {
         const int64_t r = ((int64_t)(j + 1) * (k + 1)) % L2;
         float v = (float)(sc * std::sin(M_PI * (double)r / (double)(n + 1)));
@@ -1279,8 +1288,8 @@ tau_status setup_tc(tau_problem* p) {
         std::memcpy(&b, &v, 4);
         b = (b + 0x1000u) & ~0x1FFFu;   // keep 10 mantissa bits, round to nearest (ties away)
         std::memcpy(&v, &b, 4);
-        const int c = j >> 5, jj = j & 31;
-        const size_t off = (size_t)c * t.N * 32 + ((size_t)(k >> 3) * 1024 + (jj >> 2) * 128 + (k & 7) * 16 + (jj & 3) * 4) / 4;
+        const int c = j >> 4, jj = j & 15, q = (jj & 1) * 8 + (jj >> 1);
+        const size_t off = (size_t)c * t.Nh * 16 + ((size_t)(k >> 3) * 512 + (q >> 2) * 128 + (k & 7) * 16 + (q & 3) * 4) / 4;
         S[off] = v;
       }
     float* dS = nullptr;
@@ -1292,7 +1301,6 @@ tau_status setup_tc(tau_problem* p) {
     // FP64 weights), per K-chunk of 16 in the matvec kernel's layout
     std::vector<double> sw(n);
     CK(cudaMemcpy(sw.data(), p->s[i], n * sizeof(double), cudaMemcpyDeviceToHost));
-    t.Kp16 = (n + 15) & ~15;
     std::vector<float> Th((size_t)t.N * t.Kp16, 0.0f), Tl((size_t)t.N * t.Kp16, 0.0f);
     auto rna = [](float v) {
       uint32_t b;

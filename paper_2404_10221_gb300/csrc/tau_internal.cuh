@@ -285,15 +285,17 @@ cudaError_t launch_twp(int S, double2* twp, cudaStream_t st);
 // tensor-core DST-I mode product of the FP32 τ solve (tau_tc.cu), one dimension with n <= 256
 struct TcTab {
   int n;          // line length
-  int N;          // rows of S: n rounded up to 128 on dimension 0, to 16 elsewhere
-  int Kp;         // n rounded up to 32 (shared-memory K chunks)
-  int nalloc;     // TMEM columns allocated (power of two >= max(32, N))
-  const float* S; // orthonormal DST-I matrix, TF32-rounded, zero padded to N x Kp, stored per K-chunk
-                  // of 32 columns in the kernel's shared-memory core-matrix layout
+  int N;          // rows of T: n rounded up to 128 on dimension 0, to 16 elsewhere
+  int Kp16;       // n rounded up to 16 (shared-memory K chunks of both kernels)
+  int nalloc;     // TMEM columns of the matvec (power of two >= max(32, N))
+  int Nh;         // rows of the half DST matrix: 128 on dimension 0, else ceil(n/2) rounded up to 16
+  int nalloc_h;   // TMEM columns of the DST (two accumulators: even and odd j)
+  const float* S; // rows 0..ceil(n/2)-1 of the orthonormal DST-I matrix, TF32-rounded, zero padded to
+                  // Nh x Kp16, per K-chunk of 16 columns in the core-matrix layout (512-byte row
+                  // groups), the chunk's even columns in slots 0-7 and its odd ones in slots 8-15
   int* err;       // device flag: an mbarrier wait gave up
-  // split-TF32 Toeplitz matvec: T_ax (FCD weights) = T_hi + T_lo, zero padded to N x Kp16 (n rounded
-  // up to 16), stored per K-chunk of 16 columns in the core-matrix layout (512-byte row groups)
-  int Kp16;
+  // split-TF32 Toeplitz matvec: T_ax (FCD weights) = T_hi + T_lo, zero padded to N x Kp16, stored
+  // per K-chunk of 16 columns in the same layout
   const float* Thi;
   const float* Tlo;
 };
