@@ -202,17 +202,18 @@ class ClockSampler:
 TRAFFIC_CAPTURE = {
     # DRAM read + write bytes of the four launches of one preconditioned matvec on 1023^2, from the
     # cold-cache ncu capture summarised in profiles/k_pass_routes_2d1023.md
-    "bytes_per_matvec": 16906752 + 256 + 16954112 + 256 + 16903424 + 0 + 8491776 + 0,
+    "bytes_per_matvec": 16912896 + 2304 + 16985856 + 256 + 16909056 + 0 + 8509184 + 0,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "9f587cb0d8f5a72904ad82f11e418d8eee32746b1d477d82b85c0acf7ca7fdca",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "dc346f9bc1c44ac872843f58d2939d2ca4c149e84b8318e3644cb81872338e0c",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "d15bb436a6922c9cd3ca8cfa14a6dbe458c8e31611556325a262867a927e1683",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "bc84bbf46afce103dec238b8aa5fac444396c216b7f8030ec497124cec6c7d36",
         "paper_2404_10221_gb300/csrc/tau_fft.cuh": "ccccc8cd138b0e0753a8603a34e7f4230828c94aa4bd560053e4eddc1469012a",
     },
 }
 
 
+
 # the same four launches with warm caches, inside the repeated chain (profiles/k_pass_routes_2d1023.md)
-WARM_TRAFFIC_BYTES = (182528 + 33280 + 344064 + 5376) + (1664512 + 2486528 + 357888 + 1097728)
+WARM_TRAFFIC_BYTES = (254464 + 2816 + 183296 + 13312) + (1816064 + 2466560 + 375296 + 1244416)
 
 
 def captured_traffic():
