@@ -202,18 +202,18 @@ class ClockSampler:
 TRAFFIC_CAPTURE = {
     # DRAM read + write bytes of the four launches of one preconditioned matvec on 1023^2, from the
     # cold-cache ncu capture summarised in profiles/k_pass_routes_2d1023.md
-    "bytes_per_matvec": 16912896 + 2304 + 16985856 + 256 + 16909056 + 0 + 8509184 + 0,
+    "bytes_per_matvec": 16912384 + 1024 + 16975360 + 256 + 16930816 + 0 + 8492800 + 0,
     "sha256": {
         "paper_2404_10221_gb300/csrc/tau_kernels.cu": "d15bb436a6922c9cd3ca8cfa14a6dbe458c8e31611556325a262867a927e1683",
         "paper_2404_10221_gb300/csrc/tau_internal.cuh": "bc84bbf46afce103dec238b8aa5fac444396c216b7f8030ec497124cec6c7d36",
-        "paper_2404_10221_gb300/csrc/tau_fft.cuh": "ccccc8cd138b0e0753a8603a34e7f4230828c94aa4bd560053e4eddc1469012a",
+        "paper_2404_10221_gb300/csrc/tau_fft.cuh": "95f9d401d31c501c4d0fff956398fe91ea5944634747fe33fec939ca030b69f8",
     },
 }
 
 
 
 # the same four launches with warm caches, inside the repeated chain (profiles/k_pass_routes_2d1023.md)
-WARM_TRAFFIC_BYTES = (254464 + 2816 + 183296 + 13312) + (1816064 + 2466560 + 375296 + 1244416)
+WARM_TRAFFIC_BYTES = (181504 + 2816 + 232960 + 1536) + (2158080 + 3411968 + 288000 + 1306880)
 
 
 def captured_traffic():

@@ -12,7 +12,17 @@ namespace tau {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double tfma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float tfma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ df64 tfma(df64 a, df64 b, df64 c) { return a * b + c; }
+// double-float product left as an unnormalised pair: the FMA-exact product of the high parts and
+// the sum of its error with the two cross terms (|lo| within a few units in the last place of hi);
+// a following double-float addition's two-sum absorbs it, so a multiply-add renormalises once
+__device__ __forceinline__ df64 mul_pair(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df64{p, e};
+}
+__device__ __forceinline__ df64 tfma(df64 a, df64 b, df64 c) { return mul_pair(a, b) + c; }
 __device__ __forceinline__ double shfl_up(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ float shfl_up(float v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ df64 shfl_up(df64 v, int o) {
@@ -35,6 +45,13 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
 // a * conj(b)
 template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
   return mk<V>(tfma(a.x, b.x, a.y * b.y), tfma(a.y, b.x, -a.x * b.y));
+}
+// double-float complex products: each part the sum of two unnormalised products, one renormalisation
+template <> __device__ __forceinline__ df64x2 cmul<df64x2>(df64x2 a, df64x2 b) {
+  return df64x2{mul_pair(a.x, b.x) + (-mul_pair(a.y, b.y)), mul_pair(a.x, b.y) + mul_pair(a.y, b.x)};
+}
+template <> __device__ __forceinline__ df64x2 cmulc<df64x2>(df64x2 a, df64x2 b) {
+  return df64x2{mul_pair(a.x, b.x) + mul_pair(a.y, b.y), mul_pair(a.y, b.x) + (-mul_pair(a.x, b.y))};
 }
 template <typename V> __device__ __forceinline__ V mul_mi(V a) { return mk<V>(a.y, -a.x); }  // -i a
 template <typename V> __device__ __forceinline__ V mul_pi(V a) { return mk<V>(-a.y, a.x); }  // +i a
