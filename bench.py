@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--tc", default="auto", choices=["auto", "on", "off"],
                     help="tensor-core DST of the FP32 τ solve in --matvec-f32-3d (TAU_TC_AUTO/ON/OFF)")
     ap.add_argument("--time-ops", type=int, default=0,
-                    help="with --matvec-f32-3d: time the FP32 A and M^{-1} alone, median of this many launches")
+                    help="with --matvec-f32-3d: time the FP32 A and M^{-1} alone, median of this many launches; "
+                         "with --profile-step: time this many further steps, median")
     ap.add_argument("--matvec-f32-3d", type=int, default=0,
                     help="profiling driver: the 3-D 255^3 workload in mixed precision (2 inner slots); run "
                          "this many FP32 A x (3 line passes) + M^{-1} r (5 line passes), then exit")
@@ -833,8 +834,23 @@ def run_profile_step(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     st = tau.tau_get_stats(p.handle)
+    out = {"profile_step": args.profile_step, "iters": int(st.last_iters), "graph": bool(st.graph)}
+    if args.time_ops:
+        # the next args.time_ops steps one by one, CUDA events on the problem's stream (torch's current
+        # stream at creation); median
+        import numpy as np
+        stream = torch.cuda.current_stream()
+        ts = []
+        for _ in range(args.time_ops):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.step(1)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out["step_ms"] = float(np.median(ts))
     p.close()
-    print(json.dumps({"profile_step": args.profile_step, "iters": int(st.last_iters), "graph": bool(st.graph)}))
+    print(json.dumps(out))
     return 0
 
 
