@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.2, 0.5, 0.8, 1.2],
                     help="Poisson arrival rates of the served form, as fractions of its saturation throughput")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run the served form alone (with --serve-requests/--serve-rates) and print its JSON")
     ap.add_argument("--plain-sample", type=int, default=8)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--profile-step", default="", choices=["", "2d_1023_fp64", "3d_255_mixed", "2d_1023_mixed"],
@@ -907,6 +909,11 @@ def main():
         return run_matvec_f32_3d(args)
     if args.profile_step:
         return run_profile_step(args)
+    if args.serve_only:
+        import torch
+        stream = torch.cuda.current_stream()
+        print(json.dumps({"served": run_serving(args, stream, torch.device("cuda", 0))}))
+        return 0
     return run_native(args)
 
 
