@@ -4,6 +4,8 @@
 #include "tau_rsfde.h"
 #include "tau_internal.cuh"
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -1245,6 +1247,35 @@ tau_status long_tables_as(tau_problem* p, int i, LongTab<T>& D, int cw, Conv con
   return TAU_OK;
 }
 
+// Tensor map of a table of `chunks` contiguous blocks of `chunk` FP32 values each (chunk a multiple of
+// 256, base 16-byte aligned), seen as a 2-D tensor of rows of 256 values: a box of chunk / 256 rows is
+// one block, which a tiled bulk copy (TMA) writes to shared memory unchanged.  The encoder is the
+// driver's, reached through the runtime's entry-point query (no link to libcuda).
+tau_status encode_chunk_map(CUtensorMap* map, const float* base, int chunk, int chunks) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!enc) return fail(TAU_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (chunk % 256 != 0 || chunk / 256 > 256 || chunks < 1 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    return fail(TAU_EINVAL, "tensor map of %d blocks of %d values: blocks of 256..65536 values in multiples of 256, "
+                "16-byte base", chunks, chunk);
+  const cuuint64_t dim[2] = {256, (cuuint64_t)chunks * (chunk / 256)};
+  const cuuint64_t stride[1] = {256 * 4};
+  const cuuint32_t box[2] = {256, (cuuint32_t)(chunk / 256)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dim, stride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TAU_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TAU_OK;
+}
+
 // Tensor-core DST tables of the mixed form (TAU_TC_AUTO): for every dimension with n <= 256 the first
 // h = ceil(n/2) rows of the orthonormal DST-I matrix S[k][j] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1))
 // (j k reduced mod 2(n+1)); the other rows follow from S[n-1-k][j] = (-1)^j S[k][j].  Rounded to TF32
@@ -1295,6 +1326,7 @@ tau_status setup_tc(tau_problem* p) {
     float* dS = nullptr;
     TRY(upload(p, &dS, S.data(), S.size()));
     t.S = dS;
+    TRY(encode_chunk_map(&t.tmS, dS, t.Nh * 16, t.Kp16 / 16));
     t.err = p->tc_err;
     p->tc_on[i] = true;
     // the Toeplitz factor T[k][j] = s_|k-j| split as T_hi + T_lo (each rounded to TF32 from the
@@ -1324,6 +1356,8 @@ tau_status setup_tc(tau_problem* p) {
     TRY(upload(p, &dl, Tl.data(), Tl.size()));
     t.Thi = dh;
     t.Tlo = dl;
+    TRY(encode_chunk_map(&t.tmThi, dh, t.N * 16, t.Kp16 / 16));
+    TRY(encode_chunk_map(&t.tmTlo, dl, t.N * 16, t.Kp16 / 16));
   }
   bool all = true;
   for (int i = 0; i < p->d; ++i) all = all && p->tc_on[i];

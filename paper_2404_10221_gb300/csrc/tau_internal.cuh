@@ -2,6 +2,7 @@
 // descriptors, host launchers).  Not part of the public C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -293,11 +294,14 @@ struct TcTab {
   const float* S; // rows 0..ceil(n/2)-1 of the orthonormal DST-I matrix, TF32-rounded, zero padded to
                   // Nh x Kp16, per K-chunk of 16 columns in the core-matrix layout (512-byte row
                   // groups), the chunk's even columns in slots 0-7 and its odd ones in slots 8-15
+  CUtensorMap tmS; // S as a 2-D tensor of 256-value rows, a box (Nh / 16 rows) per K-chunk: the tiled
+                   // bulk copy (TMA) of a chunk
   int* err;       // device flag: an mbarrier wait gave up
   // split-TF32 Toeplitz matvec: T_ax (FCD weights) = T_hi + T_lo, zero padded to N x Kp16, stored
-  // per K-chunk of 16 columns in the same layout
+  // per K-chunk of 16 columns in the same layout; tmThi, tmTlo: their tensor maps (box = one chunk)
   const float* Thi;
   const float* Tlo;
+  CUtensorMap tmThi, tmTlo;
 };
 cudaError_t init_tc_attributes();
 // one CTA waits (bounded, `polls` polls) on an mbarrier nothing arrives at; *gave_up = 1 when the

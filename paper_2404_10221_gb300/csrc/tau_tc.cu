@@ -9,12 +9,14 @@
 // per K-chunk of 16 one tcgen05.mma.kind::tf32 over its 8 even j and one over its 8 odd j (M = 128,
 // fp32 accumulators in tensor memory), the operands staged in shared memory in the 8-row x 16-byte
 // core-matrix layout (K-major, no swizzle: LBO = 128 B between core matrices along K, SBO = 512 B
-// between 8-row groups), a chunk's even j in slots 0-7 and its odd j in slots 8-15.
+// between 8-row groups), a chunk's even j in slots 0-7 and its odd j in slots 8-15.  S_h is stored at
+// setup in that layout chunk by chunk, and a chunk arrives by one tiled bulk copy (TMA, through a
+// tensor map of the table seen as rows of 256 values).
 //
 // Pipeline: six shared-memory stages of one K-chunk each, nine warps.  Chunk c's line values are
 // copied by the 256 threads of warps 0-7 with 4-byte asynchronous copies (cp.async, zero fill past
 // the line's end) straight into their slots, and its block of S_h (stored at setup in that layout)
-// by one bulk asynchronous copy (TMA engine) issued by warp 8 on the stage's mbarrier; both are
+// by one tiled bulk copy (TMA, tensor map) issued by warp 8 on the stage's mbarrier; both are
 // issued four chunks before the MMAs that read them.  A thread that sees its own copies of a chunk
 // land rounds those values to TF32 in place (10-bit mantissa, nearest, ties away) and arrives on the
 // stage's line barrier; warp 8 waits for both barriers of the chunk, issues its MMAs and commits
@@ -43,10 +45,11 @@ constexpr int TC_LA = 4;         // chunks copied ahead of the one whose MMAs ar
 constexpr int TC_WAIT = 4000000; // polls of an mbarrier before the kernel gives up
 
 struct TcArgs {
+  CUtensorMap tmS;       // S_h as a tensor of K-chunks (see TcTab::tmS)
   int n, ax, inner, N, Kp, nalloc;
   int64_t nlines;
   const float* S;        // per K-chunk c: the N x 16 block of S_h in the shared-memory core-matrix
-                         // layout (N*16 floats at c*N*16), TF32-rounded, zero padded
+                         // layout (N*16 floats at c*N*16), TF32-rounded, zero padded (read through tmS)
   const float* in;
   float* in_base;
   int in_sel;
@@ -121,13 +124,15 @@ __device__ __forceinline__ bool bar_wait_ab(uint32_t bar, uint32_t parity, const
   return false;
 }
 
-// Bulk asynchronous copy (TMA engine, untiled) of `bytes` from global to shared memory, completing
-// on the mbarrier `bar`; both addresses 16-byte aligned, bytes a multiple of 16.  The caller has
-// announced the bytes on the barrier with expect_tx.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+// Tiled bulk copy (TMA, tensor map in kernel-parameter space) of the box at coordinates (x, y) of a
+// 2-D tensor into shared memory, completing on the mbarrier `bar` (which the caller armed with the
+// box's byte count); x is 0 here, so the start is 16-byte aligned.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
@@ -159,7 +164,7 @@ template <int P> __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <bool MUL>
-__global__ void __launch_bounds__(TD_THREADS, 2) k_tc_mode(const TcArgs a) {
+__global__ void __launch_bounds__(TD_THREADS, 2) k_tc_mode(const __grid_constant__ TcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   if ((a.g && a.g->done) || (a.skip && *a.skip)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(TD_THREADS, 2) k_tc_mode(const TcArgs a) {
         const int s = c % TC_NST;
         const uint32_t sb = smem_u32(&sfull[s]);
         bar_expect_tx(sb, (uint32_t)sbytes);
-        bulk_g2s(sm0 + (uint32_t)(s * stage + xt), a.S + (int64_t)c * N * TC_KC, (uint32_t)sbytes, sb);
+        tma_load_2d(sm0 + (uint32_t)(s * stage + xt), &a.tmS, 0, c * (N >> 4), sb);
         s_pend |= 1u << s;
         s_par = (s_par & ~(1u << s)) | ((uint32_t)((c / TC_NST) & 1) << s);
       };
@@ -481,11 +486,12 @@ __global__ void __launch_bounds__(TD_THREADS, 2) k_tc_mode(const TcArgs a) {
 // operands: c = c_hi + c_lo, T = T_hi + T_lo (each part TF32), T c ~ T_hi c_hi + T_hi c_lo + T_lo c_hi
 // (the dropped T_lo c_lo is ~2^-22 relative).  K-chunks of 16 (two MMA K-steps, three products
 // each), core-matrix layout with 512-byte row groups; the chunk's T_hi and T_lo blocks arrive by
-// two bulk asynchronous copies on the stage's mbarrier.  The stencil reads a and c (neighbours
+// two tiled bulk copies (TMA, tensor maps of the pre-arranged tables) on the stage's mbarrier.  The stencil reads a and c (neighbours
 // included) from global memory in the epilogue, so the pass writes new channel buffers.
 constexpr int TM_KC = 16;
 
 struct TcMvArgs {
+  CUtensorMap tmThi, tmTlo;   // T_hi, T_lo as tensors of K-chunks (see TcTab)
   int n, ax, inner, N, Kp, nalloc;
   int64_t nlines;
   const float* Thi;      // per K-chunk of 16: N x 16 block of T_hi in the core-matrix layout
@@ -519,7 +525,7 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t da, uint64_t db, u
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
+__global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const __grid_constant__ TcMvArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   if ((a.g && a.g->done) || (a.skip && *a.skip)) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -598,8 +604,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_mv(const TcMvArgs a) {
     if (tid == 0) {
       const uint32_t bytes = (uint32_t)tt;
       bar_expect_tx(smem_u32(&bars[2 + s]), 2 * bytes);
-      bulk_g2s(smem_u32(sth), a.Thi + (int64_t)c * N * TM_KC, bytes, smem_u32(&bars[2 + s]));
-      bulk_g2s(smem_u32(stl), a.Tlo + (int64_t)c * N * TM_KC, bytes, smem_u32(&bars[2 + s]));
+      tma_load_2d(smem_u32(sth), &a.tmThi, 0, c * (N >> 4), smem_u32(&bars[2 + s]));
+      tma_load_2d(smem_u32(stl), &a.tmTlo, 0, c * (N >> 4), smem_u32(&bars[2 + s]));
     }
     pend = c;
     if (flip) {
@@ -764,6 +770,8 @@ cudaError_t launch_tc_mv(const PassT<float>& p, const TcTab& t, const float* c_i
                          const float* a_in, float* out_a, float* out_base, int out_sel, float* out_c, bool first,
                          bool last, cudaStream_t st) {
   TcMvArgs a{};
+  a.tmThi = t.tmThi;
+  a.tmTlo = t.tmTlo;
   a.n = t.n;
   a.ax = p.ax;
   a.inner = (int)p.inner;
@@ -828,6 +836,7 @@ cudaError_t init_tc_attributes() {
 
 cudaError_t launch_tc_dst(const PassT<float>& p, const TcTab& t, const float* mul, bool from_out, cudaStream_t st) {
   TcArgs a{};
+  a.tmS = t.tmS;
   a.n = t.n;
   a.ax = p.ax;
   a.inner = (int)p.inner;
