@@ -205,10 +205,10 @@ class ClockSampler:
 TRAFFIC_CAPTURE = {
     # DRAM read + write bytes of the four launches of one preconditioned matvec on 1023^2, from the
     # cold-cache ncu capture summarised in profiles/k_pass_routes_2d1023.md
-    "bytes_per_matvec": 16912384 + 1024 + 16975360 + 256 + 16930816 + 0 + 8492800 + 0,
+    "bytes_per_matvec": 16912640 + 1280 + 16962048 + 256 + 16904960 + 0 + 8494336 + 0,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "d15bb436a6922c9cd3ca8cfa14a6dbe458c8e31611556325a262867a927e1683",
-        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "bc84bbf46afce103dec238b8aa5fac444396c216b7f8030ec497124cec6c7d36",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "b1dc1d9881acd2d2a0c0ff2fd3193d42cbd3bd404a6f5318a59abbe054954f1b",
+        "paper_2404_10221_gb300/csrc/tau_internal.cuh": "26073af11002d04b5afbdd21189fa486c5d33150a69c08f86b2fa2fbd59e4750",
         "paper_2404_10221_gb300/csrc/tau_fft.cuh": "95f9d401d31c501c4d0fff956398fe91ea5944634747fe33fec939ca030b69f8",
     },
 }
@@ -216,7 +216,7 @@ TRAFFIC_CAPTURE = {
 
 
 # the same four launches with warm caches, inside the repeated chain (profiles/k_pass_routes_2d1023.md)
-WARM_TRAFFIC_BYTES = (181504 + 2816 + 232960 + 1536) + (2158080 + 3411968 + 288000 + 1306880)
+WARM_TRAFFIC_BYTES = (160000 + 2304 + 263680 + 1536) + (2132480 + 3172864 + 299776 + 1204992)
 
 
 def captured_traffic():

@@ -1444,6 +1444,37 @@ cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cud
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 4;
 constexpr int UPD_KEEP = 16;   // basis vectors kept in registers by the fused FP32 update-and-dots pass
+// elements per thread whose loads are issued together in the CGS loops (by element size: the
+// 8-byte types take two, which keeps the kernels within RED_CTAS CTAs' registers per SM)
+template <typename S> struct CgsUnroll { static constexpr int value = sizeof(S) == 4 ? 4 : 2; };
+constexpr int RED_CTAS = 4;    // CTAs per SM the CGS kernels are compiled for (RED_BLOCKS = 4 x 152: one wave)
+
+// acc[r] += sum of w[e] V_{i0+r}[e] (r < ni) over this thread's elements e = start, start + stride,
+// ... < n.  The loads of CgsUnroll elements are issued before their products, which are added in the
+// elements' order (the same sums as one element at a time, with that many times the loads in flight).
+template <typename S>
+__device__ __forceinline__ void dots_chunk(const S* __restrict__ w, const S* __restrict__ V, int64_t n, int i0,
+                                           int ni, int64_t start, int64_t stride, S (&acc)[DOT_CHUNK]) {
+  constexpr int CGS_U = CgsUnroll<S>::value;
+  for (int64_t idx = start; idx < n; idx += CGS_U * stride) {
+    S wv[CGS_U], vv[CGS_U][DOT_CHUNK];
+#pragma unroll
+    for (int u = 0; u < CGS_U; ++u) {
+      const int64_t e = idx + u * stride;
+      const bool ok = e < n;
+      wv[u] = ok ? w[e] : from_f<S>(0.0f);
+#pragma unroll
+      for (int r = 0; r < DOT_CHUNK; ++r) vv[u][r] = (ok && r < ni) ? V[(int64_t)(i0 + r) * n + e] : from_f<S>(0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < CGS_U; ++u)
+      if (idx + u * stride < n) {
+#pragma unroll
+        for (int r = 0; r < DOT_CHUNK; ++r)
+          if (r < ni) acc[r] = tfma(wv[u], vv[u][r], acc[r]);
+      }
+  }
+}
 
 // Block sum in FP64 (sh: at least blockDim.x doubles).  Every thread's value goes to shared memory
 // and warp 0 adds them, so the FP64 additions (a slow pipe on this part) number ~12 per lane of
@@ -1519,12 +1550,7 @@ __device__ __forceinline__ void dots_run(const DotsArgs<S>& A, VB vb) {
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
-    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-      const S wv = w[idx];
-#pragma unroll
-      for (int r = 0; r < DOT_CHUNK; ++r)
-        if (r < ni) acc[r] = tfma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
-    }
+    dots_chunk<S>(w, V, n, i0, ni, vb.bid * (int64_t)blockDim.x + threadIdx.x, (int64_t)vb.nb * blockDim.x, acc);
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
@@ -1539,12 +1565,12 @@ __device__ __forceinline__ void dots_run(const DotsArgs<S>& A, VB vb) {
 template <typename S>
 struct DotsBody {
   using Args = DotsArgs<S>;
-  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static constexpr int kThreads = RED_THREADS, kCtas = RED_CTAS;
   static __device__ __forceinline__ void run(const Args& a, VB vb) { dots_run<S>(a, vb); }
 };
 
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_dots(const DotsArgs<S> A) {
+__global__ void __launch_bounds__(RED_THREADS, RED_CTAS) k_dots(const DotsArgs<S> A) {
   dots_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
@@ -1673,11 +1699,30 @@ __device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
     }
   }
   S nacc = from_f<S>(0.0f);
-  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-    S wv = w[idx];
-    for (int i = 0; i <= jj; ++i) wv = tfma(-hs[i], V[(int64_t)i * n + idx], wv);
-    w[idx] = wv;
-    nacc = tfma(wv, wv, nacc);
+  {
+    // CgsUnroll elements at a time: their loads of each V_i issued together, each element's FMA chain and
+    // the norm's sum in the one-element order
+    constexpr int CGS_U = CgsUnroll<S>::value;
+    const int64_t stride = (int64_t)vb.nb * blockDim.x;
+    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += CGS_U * stride) {
+      S wv[CGS_U];
+#pragma unroll
+      for (int u = 0; u < CGS_U; ++u) wv[u] = idx + u * stride < n ? w[idx + u * stride] : from_f<S>(0.0f);
+      for (int i = 0; i <= jj; ++i) {
+        const S* __restrict__ vi = V + (int64_t)i * n;
+        S v[CGS_U];
+#pragma unroll
+        for (int u = 0; u < CGS_U; ++u) v[u] = idx + u * stride < n ? vi[idx + u * stride] : from_f<S>(0.0f);
+#pragma unroll
+        for (int u = 0; u < CGS_U; ++u) wv[u] = tfma(-hs[i], v[u], wv[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < CGS_U; ++u)
+        if (idx + u * stride < n) {
+          w[idx + u * stride] = wv[u];
+          nacc = tfma(wv[u], wv[u], nacc);
+        }
+    }
   }
   if (norm_only) {
     const double s = block_sum(to_d(nacc), sh);
@@ -1697,12 +1742,7 @@ __device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) acc[r] = from_f<S>(0.0f);
     const int ni = min(DOT_CHUNK, jj + 1 - i0);
-    for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-      const S wv = w[idx];
-#pragma unroll
-      for (int r = 0; r < DOT_CHUNK; ++r)
-        if (r < ni) acc[r] = tfma(wv, V[(int64_t)(i0 + r) * n + idx], acc[r]);
-    }
+    dots_chunk<S>(w, V, n, i0, ni, vb.bid * (int64_t)blockDim.x + threadIdx.x, (int64_t)vb.nb * blockDim.x, acc);
 #pragma unroll
     for (int r = 0; r < DOT_CHUNK; ++r) {
       if (r < ni) {
@@ -1717,12 +1757,12 @@ __device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
 template <typename S>
 struct UpdBody {
   using Args = UpdArgs<S>;
-  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static constexpr int kThreads = RED_THREADS, kCtas = RED_CTAS;
   static __device__ __forceinline__ void run(const Args& a, VB vb) { update_dots_run<S>(a, vb); }
 };
 
 template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) k_update_dots(const UpdArgs<S> A) {
+__global__ void __launch_bounds__(RED_THREADS, RED_CTAS) k_update_dots(const UpdArgs<S> A) {
   update_dots_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x});
 }
 
@@ -1771,19 +1811,27 @@ __device__ __forceinline__ void scale_next_run(const ScaleNextArgs<S>& A, VB vb)
   __syncthreads();
   const S inv = from_d<S>(sinv);
   S* v = A.V + (int64_t)j * A.n;
-  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < A.n; idx += (int64_t)vb.nb * blockDim.x)
-    v[idx] *= inv;
+  constexpr int CGS_U = CgsUnroll<S>::value;
+  const int64_t stride = (int64_t)vb.nb * blockDim.x, n = A.n;
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += CGS_U * stride) {
+    S t[CGS_U];
+#pragma unroll
+    for (int u = 0; u < CGS_U; ++u) t[u] = idx + u * stride < n ? v[idx + u * stride] : from_f<S>(0.0f);
+#pragma unroll
+    for (int u = 0; u < CGS_U; ++u)
+      if (idx + u * stride < n) v[idx + u * stride] = t[u] * inv;
+  }
 }
 
 template <typename S>
 struct ScaleNextBody {
   using Args = ScaleNextArgs<S>;
-  static constexpr int kThreads = RED_THREADS, kCtas = 1;
+  static constexpr int kThreads = RED_THREADS, kCtas = RED_CTAS;
   static __device__ __forceinline__ void run(const Args& a, VB vb) { scale_next_run<S>(a, vb); }
 };
 
 template <typename S>
-__global__ void k_scale_next(const ScaleNextArgs<S> A) { scale_next_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
+__global__ void __launch_bounds__(RED_THREADS, RED_CTAS) k_scale_next(const ScaleNextArgs<S> A) { scale_next_run<S>(A, VB{(int)blockIdx.x, (int)gridDim.x}); }
 
 template <typename S>
 cudaError_t launch_scale_next(S* V, int64_t n, const GmresDev* g, cudaStream_t st) {
@@ -2279,10 +2327,24 @@ __device__ __forceinline__ void update_x_run(const UpdXArgs<X>& A, VB vb) {
   if (vb.bid == 0 && threadIdx.x == 0) ir->inner_total += k;
   __syncthreads();
   const int64_t n = A.n;
-  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-    df64 d{0.0f, 0.0f};
-    for (int i = 0; i < k; ++i) d = df_fma_f(ys[i], A.Z[(int64_t)i * n + idx], d);
-    add_to(A.x[idx], d);
+  // four elements at a time: their loads of each Z_i issued together, each element's sum in order
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)vb.nb * blockDim.x;
+  for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += U * stride) {
+    df64 d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) d[u] = df64{0.0f, 0.0f};
+    for (int i = 0; i < k; ++i) {
+      const float* __restrict__ zi = A.Z + (int64_t)i * n;
+      float z[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) z[u] = idx + u * stride < n ? zi[idx + u * stride] : 0.0f;
+#pragma unroll
+      for (int u = 0; u < U; ++u) d[u] = df_fma_f(ys[i], z[u], d[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (idx + u * stride < n) add_to(A.x[idx + u * stride], d[u]);
   }
 }
 
