@@ -1443,7 +1443,11 @@ cudaError_t launch_add_into(double* u, const double* t, int64_t n, int keep, cud
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 constexpr int DOT_CHUNK = 4;
-constexpr int UPD_KEEP = 16;   // basis vectors kept in registers by the fused FP32 update-and-dots pass
+// the fused FP32 update-and-dots pass: basis vectors whose values it keeps in registers (more take
+// the two-pass form), and elements per thread it handles at a time (measured: 8 x 2 beats 16 x 1,
+// which held one element's loads in flight, and 8 x 4, which spills at four CTAs per SM)
+constexpr int UPD_KEEP = 8;
+constexpr int UPD_U = 2;
 // elements per thread whose loads are issued together in the CGS loops (by element size: the
 // 8-byte types take two, which keeps the kernels within RED_CTAS CTAs' registers per SM)
 template <typename S> struct CgsUnroll { static constexpr int value = sizeof(S) == 4 ? 4 : 2; };
@@ -1670,23 +1674,35 @@ __device__ __forceinline__ void update_dots_run(const UpdArgs<S>& A, VB vb) {
     if (!norm_only && jj < UPD_KEEP) {
       // FP32 basis of at most UPD_KEEP vectors: each element's basis values stay in registers
       // between the update and the second pass's dots, so the basis is read once here instead of
-      // twice (same operations in the same order as the two-pass form below)
+      // twice (same operations in the same order as the two-pass form below); UPD_U elements at a
+      // time, their loads issued together
+      const int64_t stride = (int64_t)vb.nb * blockDim.x;
       float acc[UPD_KEEP];
 #pragma unroll
       for (int i = 0; i < UPD_KEEP; ++i) acc[i] = 0.0f;
-      for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)vb.nb * blockDim.x) {
-        float vv[UPD_KEEP];
-        float wv = w[idx];
+      for (int64_t idx = vb.bid * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += UPD_U * stride) {
+        float vv[UPD_U][UPD_KEEP], wv[UPD_U];
 #pragma unroll
-        for (int i = 0; i < UPD_KEEP; ++i)
-          if (i <= jj) {
-            vv[i] = V[(int64_t)i * n + idx];
-            wv = fmaf(-hs[i], vv[i], wv);
+        for (int u = 0; u < UPD_U; ++u) {
+          const int64_t e = idx + u * stride;
+          const bool ok = e < n;
+          wv[u] = ok ? w[e] : 0.0f;
+#pragma unroll
+          for (int i = 0; i < UPD_KEEP; ++i) vv[u][i] = (ok && i <= jj) ? V[(int64_t)i * n + e] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u)
+#pragma unroll
+          for (int i = 0; i < UPD_KEEP; ++i)
+            if (i <= jj) wv[u] = fmaf(-hs[i], vv[u][i], wv[u]);
+#pragma unroll
+        for (int u = 0; u < UPD_U; ++u)
+          if (idx + u * stride < n) {
+            w[idx + u * stride] = wv[u];
+#pragma unroll
+            for (int i = 0; i < UPD_KEEP; ++i)
+              if (i <= jj) acc[i] = fmaf(wv[u], vv[u][i], acc[i]);
           }
-        w[idx] = wv;
-#pragma unroll
-        for (int i = 0; i < UPD_KEEP; ++i)
-          if (i <= jj) acc[i] = fmaf(wv, vv[i], acc[i]);
       }
 #pragma unroll
       for (int i = 0; i < UPD_KEEP; ++i)
