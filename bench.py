@@ -205,9 +205,9 @@ class ClockSampler:
 TRAFFIC_CAPTURE = {
     # DRAM read + write bytes of the four launches of one preconditioned matvec on 1023^2, from the
     # cold-cache ncu capture summarised in profiles/k_pass_routes_2d1023.md
-    "bytes_per_matvec": 16912640 + 1280 + 16962048 + 256 + 16904960 + 0 + 8494336 + 0,
+    "bytes_per_matvec": 16913152 + 1536 + 16959744 + 256 + 16904448 + 0 + 8497408 + 0,
     "sha256": {
-        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "b1dc1d9881acd2d2a0c0ff2fd3193d42cbd3bd404a6f5318a59abbe054954f1b",
+        "paper_2404_10221_gb300/csrc/tau_kernels.cu": "bd19b26707cc2202c43ca8613b1af0e2399d45a86b14f17e768ef2aa841edd61",
         "paper_2404_10221_gb300/csrc/tau_internal.cuh": "26073af11002d04b5afbdd21189fa486c5d33150a69c08f86b2fa2fbd59e4750",
         "paper_2404_10221_gb300/csrc/tau_fft.cuh": "95f9d401d31c501c4d0fff956398fe91ea5944634747fe33fec939ca030b69f8",
     },
@@ -216,7 +216,7 @@ TRAFFIC_CAPTURE = {
 
 
 # the same four launches with warm caches, inside the repeated chain (profiles/k_pass_routes_2d1023.md)
-WARM_TRAFFIC_BYTES = (160000 + 2304 + 263680 + 1536) + (2132480 + 3172864 + 299776 + 1204992)
+WARM_TRAFFIC_BYTES = (174592 + 1536 + 241664 + 2304) + (2141696 + 3325184 + 289536 + 1191168)
 
 
 def captured_traffic():
