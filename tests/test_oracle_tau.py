@@ -111,3 +111,27 @@ def test_row_helpers_closed_forms_at_large_n():
     t[0], t[1] = 2.0, -1.0
     ks = np.array([1, 17, 40000, n])
     assert np.allclose(O.tau_eigs_q_at(t, ks), 2.0 - 2.0 * np.cos(np.pi * ks / (n + 1)), atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 100, 127, 255, 256])
+def test_sine_matrix_row_mirror(n):
+    """The rows of the DST-I matrix satisfy S[n-1-k][j] = (-1)^j S[k][j] (0-based j, k), so the
+    product splits into even-j and odd-j sums E, O over the first ceil(n/2) rows:
+    y[k] = E_k + O_k and y[n-1-k] = E_k - O_k (the middle row of an odd n is its own mirror, where
+    O vanishes).  The tensor-core DST multiplies only those rows; this pins the identity on the
+    oracle's sine matrix and the reconstruction on a random vector."""
+    S = O.sine_matrix(n)
+    sign = (-1.0) ** np.arange(n)
+    assert np.allclose(S[::-1, :], S * sign[None, :], atol=1e-15, rtol=0)
+    h = (n + 1) // 2
+    x = np.random.default_rng(n).standard_normal(n)
+    E = S[:h, 0::2] @ x[0::2]
+    Od = S[:h, 1::2] @ x[1::2]
+    y = np.empty(n)
+    y[:h] = E + Od
+    km = n - 1 - np.arange(h)
+    mirror = km > np.arange(h)
+    y[km[mirror]] = (E - Od)[mirror]
+    if n % 2:
+        assert abs(Od[h - 1]) <= 1e-14 * np.abs(x).sum()
+    assert np.allclose(y, S @ x, atol=1e-13, rtol=0)
